@@ -1,0 +1,203 @@
+/*
+ * nuasm.h -- C ABI of the GB300 non-uniform sampled diffraction library.
+ *
+ * Computes the non-uniform sampled angular spectrum method (NU-ASM) and its
+ * Fresnel counterpart (NU-FRE) of Shimobaba et al., arXiv:1308.6644:
+ *
+ *   type 1 (NU-ASM_1, Eq. 6): non-uniform source samples -> uniform N x N plane
+ *       u2(m) = (1/N'^2) sum_k F(k) H(k) exp(2 pi i k.m / N'),
+ *       F(k)  = sum_j w_j c_j exp(-2 pi i f_k . x_j)           (NUFFT type 1, Eq. 7)
+ *   type 2 (NU-ASM_2, Eq. 9): uniform N x N source -> non-uniform points
+ *       v_j   = (1/N'^2) sum_k G(k) H(k) exp(2 pi i f_k . x_j)  (NUFFT type 2, Eq. 8)
+ *       G(k)  = sum_m u1(m) exp(-2 pi i k.m / N')
+ *
+ * with N' = 2N (zero padding, Eq. 3 discussion), f_k = k / (N' pitch),
+ * k in [-N'/2, N'/2)^2, m in [-N/2, N/2)^2, and H either the band-limited,
+ * off-axis shifted ASM transfer function of Eq. 4 or the Fresnel transfer
+ * function of Eq. 5 (the DFT of the sampled impulse response
+ * exp(ikz)/(i lambda z) exp(i pi |m pitch + o|^2/(lambda z)), area element
+ * pitch^2).
+ *
+ * Conventions shared by every call:
+ *  - Coordinates are metres relative to the centre of the uniform plane; a
+ *    point is valid iff x/pitch (IEEE division) lies in [-N/2, N/2) on both
+ *    axes (the half-open window the paper states for x1 and x2).
+ *  - Complex values are interleaved (re, im): float pairs under
+ *    NUASM_PREC_F32_F64PHASE, double pairs under NUASM_PREC_F64.
+ *  - Uniform planes are row-major [y][x], element (i_y, i_x) holding the
+ *    sample at m = (i_x - N/2, i_y - N/2).
+ *  - Array arguments of the execute calls may be device memory or host memory
+ *    (pinned or pageable); host arrays are staged through plan-owned device
+ *    buffers with cudaMemcpyAsync on the given stream.  Pageable host memory
+ *    makes the call block the host until its copies are done.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Execute calls
+ *    are asynchronous on it, never allocate device memory and never
+ *    synchronise the device; asynchronous CUDA faults surface as NUASM_ECUDA
+ *    from a later call.
+ *  - Errors are returned, never thrown or printed.  On any non-OK status no
+ *    output has been written unless stated otherwise.
+ *  - A plan may be used by one stream at a time.
+ */
+#ifndef NUASM_H
+#define NUASM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nuasm_plan_s* nuasm_plan_t;   /* opaque; owned by the library */
+
+typedef enum {
+    NUASM_OK = 0,
+    NUASM_EINVAL = 1,        /* invalid argument / parameter combination        */
+    NUASM_ERANGE = 2,        /* a point lies outside [-N pitch/2, N pitch/2)    */
+    NUASM_ENOMEM = 3,        /* device or host allocation failed                */
+    NUASM_ECUDA = 4,         /* a CUDA call or an earlier asynchronous launch failed */
+    NUASM_ETIMEOUT = 5,      /* a bounded device wait gave up                   */
+    NUASM_EUNSUPPORTED = 6   /* valid but outside what this build implements    */
+} nuasm_status;
+
+typedef enum { NUASM_KIND_ASM = 0, NUASM_KIND_FRESNEL = 1 } nuasm_kind;
+
+typedef enum {
+    NUASM_PREC_F32_F64PHASE = 0,  /* complex64 data; phases from FP64 tables and
+                                     compensated (double-float) FP32 arithmetic */
+    NUASM_PREC_F64 = 1            /* complex128 data and FP64 arithmetic throughout */
+} nuasm_prec;
+
+/* Problem definition (Eq. 4 / Eq. 5 parameters).  Plain old data. */
+typedef struct {
+    int32_t n;          /* N: side of the uniform plane; power of two, 16..4096 (F32) / 16..2048 (F64) */
+    int32_t n_pad;      /* N': 0 selects 2N (the paper's padding); else a power of two >= 2N */
+    double  pitch;      /* pitch of the uniform plane in metres (Delta_2 for type 1, Delta_1 for type 2) */
+    double  lambda;     /* wavelength, metres, > 0 */
+    double  z;          /* propagation distance, metres; != 0 for Fresnel */
+    double  ox, oy;     /* off-axis offset o of Eq. 4/5, metres: the destination
+                           window is centred at o relative to the source window */
+    int32_t band_auto;  /* ASM only.  1: Rect band derived from Nyquist sampling of
+                           the transfer-function phase (keep f with
+                           |o - z f / sqrt(1/lambda^2 - f^2)| <= N pitch per axis);
+                           0: use c_m, c_n, w_m, w_n below */
+    double  c_m, c_n;   /* Rect centre in mode-index units (x, y) when band_auto = 0 */
+    double  w_m, w_n;   /* Rect full width in mode-index units: keep |k - c| <= w/2 */
+    int32_t kind;       /* nuasm_kind */
+    int32_t prec;       /* nuasm_prec */
+    double  tol;        /* requested NUFFT relative tolerance; 0 selects 1e-6 (F32) or 1e-12 (F64) */
+} nuasm_params_t;
+
+/* Geometry of a plan (read-only report). */
+typedef struct {
+    int32_t n, n_pad;          /* N, N' */
+    int32_t grid;              /* oversampled NUFFT grid side G = 2 N' */
+    int32_t window;            /* side W of the non-zero fine-grid window (2N + 2h) */
+    int32_t window_origin;     /* first fine-grid index of the window */
+    int32_t kernel_width;      /* spreading kernel width w (taps per axis) */
+    double  kernel_beta;       /* exponential-of-semicircle shape parameter */
+    int32_t tile;              /* tile side used for spreading / interpolation */
+    int32_t tiles;             /* number of tiles */
+    int32_t band_lo_x, band_hi_x, band_lo_y, band_hi_y;  /* kept modes, inclusive (ASM) */
+    int64_t points;            /* M */
+    int64_t records;           /* binned records (points plus tile-halo duplicates) */
+    int64_t device_bytes;      /* device memory owned by the plan */
+} nuasm_plan_info_t;
+
+/*
+ * nuasm_plan -- build a plan for one plane geometry and one set of non-uniform
+ * points (Eq. 4-9; coordinate normalisation as in the paper's Fig. 1
+ * discussion).  Validates the parameters, derives the Rect band (Eq. 4), the
+ * Fresnel transfer-function tables (Eq. 5), the NUFFT kernel and its
+ * deconvolution, and sorts the points into fine-grid tiles on the device.
+ *
+ *  out      receives the plan (set to NULL on failure).
+ *  p        parameters (host memory, copied).
+ *  m        number of non-uniform points, >= 0.
+ *  x, y     m coordinates in metres (device or host memory; read during the
+ *           call only).  May be NULL when m == 0.
+ *  w        optional per-point weights multiplying the type-1 source values
+ *           (quadrature weights; NULL = 1 for every point, the paper's
+ *           unweighted Eq. 7).  Device or host memory.
+ *  stream   stream for the plan's device work; the call synchronises it
+ *           before returning.
+ *
+ * Returns NUASM_EINVAL for bad parameters (N not a power of two or out of
+ * range, pitch/lambda <= 0, Fresnel with z == 0, m < 0, NULL coordinates with
+ * m > 0, tol outside (0, 0.1]), NUASM_ERANGE if any point is outside the
+ * window, NUASM_ENOMEM, NUASM_ECUDA.  The plan allocates all the device memory
+ * its execute calls will need.
+ */
+nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m,
+                        const double* x, const double* y, const double* w, void* stream);
+
+/*
+ * nuasm1_execute -- NU-ASM_1 (Eq. 6): non-uniform source -> uniform plane.
+ *  c   m complex source values in the order the plan's points were given.
+ *  u2  N*N complex output plane.
+ * Plan kind must be NUASM_KIND_ASM (else NUASM_EINVAL).
+ */
+nuasm_status nuasm1_execute(nuasm_plan_t plan, const void* c, void* u2, void* stream);
+
+/*
+ * nuasm2_execute -- NU-ASM_2 (Eq. 9): uniform plane -> non-uniform points.
+ *  u1  N*N complex source plane.
+ *  v   m complex outputs, in the order of the plan's points.
+ * Plan kind must be NUASM_KIND_ASM (else NUASM_EINVAL).
+ */
+nuasm_status nuasm2_execute(nuasm_plan_t plan, const void* u1, void* v, void* stream);
+
+/*
+ * nufresnel_execute -- NU-FRE_1 / NU-FRE_2: Eq. 6 / Eq. 9 with the Fresnel
+ * transfer function of Eq. 5.  type = 1: `in` holds m source values and
+ * `out` the N*N plane; type = 2: `in` holds the N*N plane and `out` the m
+ * point values.  Plan kind must be NUASM_KIND_FRESNEL and type 1 or 2.
+ */
+nuasm_status nufresnel_execute(nuasm_plan_t plan, int32_t type, const void* in, void* out,
+                               void* stream);
+
+/* Release every resource of the plan (synchronises the plan's device work). NULL is a no-op. */
+nuasm_status nuasm_destroy(nuasm_plan_t plan);
+
+/* Static English description of a status code. */
+const char* nuasm_strerror(nuasm_status s);
+
+/* Copy the plan's geometry into *info (host only, no device work). */
+nuasm_status nuasm_plan_info(nuasm_plan_t plan, nuasm_plan_info_t* info);
+
+/*
+ * nuasm_band -- host-only evaluation of the Rect band of Eq. 4 for the given
+ * parameters, as inclusive mode-index ranges [lo, hi] per axis (out[0..3] =
+ * lo_x, hi_x, lo_y, hi_y, clamped to [-N'/2, N'/2 - 1]; an empty band has
+ * lo > hi).  Fresnel parameters give the full range.  No device work.
+ */
+nuasm_status nuasm_band(const nuasm_params_t* p, int32_t out[4]);
+
+/*
+ * nuasm_kernel_shape -- host-only: the spreading kernel width w and shape
+ * parameter beta the library uses for a requested tolerance (0 = the
+ * precision's default) and precision.  No device work.
+ */
+nuasm_status nuasm_kernel_shape(double tol, int32_t prec, int32_t* width, double* beta);
+
+/*
+ * Per-stage timing (instrumentation for benchmarks).  When enabled, execute
+ * calls record CUDA events around each stage on their stream; nuasm_profile_read
+ * synchronises on the last recorded event and returns the summed elapsed
+ * milliseconds and launch counts per stage since the last reset (arrays of
+ * NUASM_STAGE_COUNT entries), then resets.  Stage names come from
+ * nuasm_stage_name.  Disabled by default; enabling adds event records only.
+ */
+enum {
+    NUASM_STAGE_H2D = 0, NUASM_STAGE_SPREAD, NUASM_STAGE_COL_FWD_FOLD, NUASM_STAGE_ROW_T1,
+    NUASM_STAGE_COL_INV, NUASM_STAGE_COL_FWD, NUASM_STAGE_ROW_T2, NUASM_STAGE_COL_INV_FOLD,
+    NUASM_STAGE_INTERP, NUASM_STAGE_D2H, NUASM_STAGE_COUNT
+};
+nuasm_status nuasm_profile_enable(nuasm_plan_t plan, int32_t enable);
+nuasm_status nuasm_profile_read(nuasm_plan_t plan, double* ms, int64_t* launches);
+const char* nuasm_stage_name(int32_t stage);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUASM_H */

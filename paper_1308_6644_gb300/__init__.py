@@ -1,0 +1,12 @@
+"""GB300-native non-uniform sampled scalar diffraction (NU-ASM / NU-FRE).
+
+The computation lives in the CUDA library ``libnuasm.so`` (C ABI in
+``include/nuasm.h``); this package holds its Python binding and the seeded
+synthetic workload generators.
+"""
+from .nuasm import (  # noqa: F401
+    NuasmError, Params, Plan, make_params, nuasm_plan, nuasm1_execute, nuasm2_execute,
+    nufresnel_execute, nuasm_destroy, nuasm_strerror, nuasm_plan_info, nuasm_band,
+    nuasm_kernel_shape, nuasm_profile_enable, nuasm_profile_read, lib, LIB_PATH, STAGES,
+    KIND_ASM, KIND_FRESNEL, PREC_F32_F64PHASE, PREC_F64,
+)

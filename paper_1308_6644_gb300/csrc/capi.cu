@@ -1,0 +1,436 @@
+// C ABI of the NU-ASM / NU-FRE library (declared in include/nuasm.h).
+//
+// Plan: validate -> host FP64 tables (band of Eq. 4, Fresnel tables of Eq. 5,
+// deconvolution, twiddles) -> device allocations (tables, workspace, staging)
+// -> point binning on the device.  Execute: stream-ordered launches only.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nuasm_internal.h"
+
+using namespace nuasm;
+
+namespace {
+
+nuasm_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return NUASM_OK;
+    return e == cudaErrorMemoryAllocation ? NUASM_ENOMEM : NUASM_ECUDA;
+}
+
+#define NUASM_TRY(expr)                                    \
+    do {                                                   \
+        cudaError_t e__ = (expr);                          \
+        if (e__ != cudaSuccess) return cuda_status(e__);   \
+    } while (0)
+
+bool device_accessible(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the non-sticky error of a foreign pointer
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t elt_bytes(const nuasm_plan_s* P) { return P->f64 ? 16 : 8; }
+
+// ---------------------------------------------------------------- profiling ring
+struct ProfRing {
+    static constexpr int kCap = 64;
+    cudaEvent_t start[kCap], stop[kCap];
+    int head = 0, count = 0;
+    bool created = false;
+};
+
+struct PlanExtra {
+    ProfRing ring[NUASM_STAGE_COUNT];
+};
+
+}  // namespace
+
+static PlanExtra* extra_of(nuasm_plan_s* P) { return static_cast<PlanExtra*>(P->prof_state); }
+
+namespace {
+
+void ring_consume_oldest(nuasm_plan_s* P, int stage) {
+    ProfRing& r = extra_of(P)->ring[stage];
+    const int idx = (r.head - r.count + ProfRing::kCap) % ProfRing::kCap;
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.stop[idx]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, r.start[idx], r.stop[idx]) == cudaSuccess) {
+        P->prof_ms[stage] += ms;
+        P->prof_n[stage] += 1;
+    }
+    r.count -= 1;
+}
+
+struct StageScope {
+    nuasm_plan_s* P;
+    int stage;
+    cudaStream_t st;
+    int slot = -1;
+    StageScope(nuasm_plan_s* p, int s, cudaStream_t stream) : P(p), stage(s), st(stream) {
+        if (!P->prof) return;
+        ProfRing& r = extra_of(P)->ring[stage];
+        if (!r.created) {
+            for (int i = 0; i < ProfRing::kCap; ++i) {
+                cudaEventCreate(&r.start[i]);
+                cudaEventCreate(&r.stop[i]);
+            }
+            r.created = true;
+        }
+        if (r.count == ProfRing::kCap) ring_consume_oldest(P, stage);
+        slot = r.head;
+        cudaEventRecord(r.start[slot], st);
+    }
+    ~StageScope() {
+        if (slot < 0) return;
+        ProfRing& r = extra_of(P)->ring[stage];
+        cudaEventRecord(r.stop[slot], st);
+        r.head = (r.head + 1) % ProfRing::kCap;
+        r.count += 1;
+    }
+};
+
+void release(nuasm_plan_s* P) {
+    if (!P) return;
+    PlanExtra* X = extra_of(P);
+    if (X) {
+        for (auto& r : X->ring)
+            if (r.created)
+                for (int i = 0; i < ProfRing::kCap; ++i) {
+                    cudaEventDestroy(r.start[i]);
+                    cudaEventDestroy(r.stop[i]);
+                }
+        delete X;
+    }
+    void* ptrs[] = {P->d.tables, P->d.rec, P->d.wrec_f, P->d.wrec_d, P->d.tile_off, P->d.tile_home,
+                    P->d.win, P->d.bufA, P->d.bufB, P->d.stage_in, P->d.stage_out, P->d.err};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete P;
+}
+
+template <typename T> cudaError_t dalloc(nuasm_plan_s* P, T** out, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e == cudaSuccess) {
+        *out = static_cast<T*>(q);
+        P->device_bytes += int64_t(bytes);
+    }
+    return e;
+}
+
+// Upload the host tables in the plan's precision.
+cudaError_t upload_tables(nuasm_plan_s* P, const HostTables& t, cudaStream_t st) {
+    const int np = P->g.np, G = P->g.G;
+    const size_t eb = elt_bytes(P);
+    const size_t sb = P->f64 ? sizeof(double) : sizeof(float2);
+    const size_t bytes = 4 * np * eb + np * sb + size_t(G) * eb;
+    char* base = nullptr;
+    cudaError_t e = dalloc(P, &base, bytes);
+    if (e != cudaSuccess) return e;
+    P->d.tables = base;
+    P->d.t1x = base;
+    P->d.t1y = base + np * eb;
+    P->d.t2x = base + 2 * np * eb;
+    P->d.t2y = base + 3 * np * eb;
+    P->d.s = base + 4 * np * eb;
+    P->d.tw = base + 4 * np * eb + np * sb;
+    std::vector<char> host(bytes);
+    auto put_c = [&](size_t off, const double* src, int count) {
+        if (P->f64) std::memcpy(host.data() + off, src, sizeof(double) * 2 * count);
+        else {
+            float* d = reinterpret_cast<float*>(host.data() + off);
+            for (int i = 0; i < 2 * count; ++i) d[i] = float(src[i]);
+        }
+    };
+    put_c(0, t.t1x, np);
+    put_c(np * eb, t.t1y, np);
+    put_c(2 * np * eb, t.t2x, np);
+    put_c(3 * np * eb, t.t2y, np);
+    if (P->f64) std::memcpy(host.data() + 4 * np * eb, t.s, sizeof(double) * np);
+    else {
+        float* d = reinterpret_cast<float*>(host.data() + 4 * np * eb);
+        for (int i = 0; i < np; ++i) {
+            float hi = float(t.s[i]);
+            d[2 * i] = hi;
+            d[2 * i + 1] = float(t.s[i] - double(hi));
+        }
+    }
+    put_c(4 * np * eb + np * sb, t.tw, G);
+    e = cudaMemcpyAsync(base, host.data(), bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);   // host buffer goes out of scope
+}
+
+// Copy a host coordinate array to a temporary device buffer when needed.
+cudaError_t device_copy(const double* src, int64_t m, double** dev_out, bool* owned, cudaStream_t st) {
+    *owned = false;
+    *dev_out = const_cast<double*>(src);
+    if (!src || m == 0 || device_accessible(src)) return cudaSuccess;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(double) * size_t(m));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(q, src, sizeof(double) * size_t(m), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { cudaFree(q); return e; }
+    *dev_out = static_cast<double*>(q);
+    *owned = true;
+    return cudaSuccess;
+}
+
+nuasm_status check_plan_usable(nuasm_plan_s* P) {
+    if (!P) return NUASM_EINVAL;
+    // surface sticky asynchronous faults of earlier launches
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return NUASM_ECUDA;
+    }
+    return NUASM_OK;
+}
+
+// ---------------------------------------------------------------- execute chains
+nuasm_status exec_type1(nuasm_plan_s* P, const void* c, void* u2, cudaStream_t st) {
+    nuasm_status s0 = check_plan_usable(P);
+    if (s0 != NUASM_OK) return s0;
+    if (!u2 || (P->m > 0 && !c)) return NUASM_EINVAL;
+    const size_t eb = elt_bytes(P);
+    const void* cin = c;
+    if (P->m > 0 && !device_accessible(c)) {
+        StageScope sc(P, NUASM_STAGE_H2D, st);
+        NUASM_TRY(cudaMemcpyAsync(P->d.stage_in, c, eb * size_t(P->m), cudaMemcpyHostToDevice, st));
+        cin = P->d.stage_in;
+    }
+    const bool out_dev = device_accessible(u2);
+    void* uo = out_dev ? u2 : P->d.stage_out;
+    { StageScope sc(P, NUASM_STAGE_SPREAD, st); NUASM_TRY(launch_spread(P, cin, st)); }
+    { StageScope sc(P, NUASM_STAGE_COL_FWD_FOLD, st); NUASM_TRY(launch_col_fwd_fold(P, st)); }
+    { StageScope sc(P, NUASM_STAGE_ROW_T1, st); NUASM_TRY(launch_row_t1(P, st)); }
+    { StageScope sc(P, NUASM_STAGE_COL_INV, st); NUASM_TRY(launch_col_inv(P, uo, st)); }
+    if (!out_dev) {
+        StageScope sc(P, NUASM_STAGE_D2H, st);
+        NUASM_TRY(cudaMemcpyAsync(u2, P->d.stage_out, eb * size_t(P->g.n) * P->g.n, cudaMemcpyDeviceToHost, st));
+    }
+    return NUASM_OK;
+}
+
+nuasm_status exec_type2(nuasm_plan_s* P, const void* u1, void* v, cudaStream_t st) {
+    nuasm_status s0 = check_plan_usable(P);
+    if (s0 != NUASM_OK) return s0;
+    if (!u1 || (P->m > 0 && !v)) return NUASM_EINVAL;
+    const size_t eb = elt_bytes(P);
+    const void* uin = u1;
+    if (!device_accessible(u1)) {
+        StageScope sc(P, NUASM_STAGE_H2D, st);
+        NUASM_TRY(cudaMemcpyAsync(P->d.stage_in, u1, eb * size_t(P->g.n) * P->g.n, cudaMemcpyHostToDevice, st));
+        uin = P->d.stage_in;
+    }
+    const bool out_dev = P->m == 0 || device_accessible(v);
+    void* vo = out_dev ? v : P->d.stage_out;
+    { StageScope sc(P, NUASM_STAGE_COL_FWD, st); NUASM_TRY(launch_col_fwd(P, uin, st)); }
+    { StageScope sc(P, NUASM_STAGE_ROW_T2, st); NUASM_TRY(launch_row_t2(P, st)); }
+    { StageScope sc(P, NUASM_STAGE_COL_INV_FOLD, st); NUASM_TRY(launch_col_inv_fold(P, st)); }
+    if (P->m > 0) {
+        StageScope sc(P, NUASM_STAGE_INTERP, st);
+        NUASM_TRY(launch_interp(P, vo, st));
+    }
+    if (!out_dev) {
+        StageScope sc(P, NUASM_STAGE_D2H, st);
+        NUASM_TRY(cudaMemcpyAsync(v, P->d.stage_out, eb * size_t(P->m), cudaMemcpyDeviceToHost, st));
+    }
+    return NUASM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m, const double* x,
+                        const double* y, const double* w, void* stream) {
+    if (!out) return NUASM_EINVAL;
+    *out = nullptr;
+    if (!p) return NUASM_EINVAL;
+    nuasm_params_t rp;
+    nuasm_status s = validate(*p, m, &rp);
+    if (s != NUASM_OK) return s;
+    if (m > 0 && (!x || !y)) return NUASM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    nuasm_plan_s* P = new (std::nothrow) nuasm_plan_s();
+    if (!P) return NUASM_ENOMEM;
+    PlanExtra* X = new (std::nothrow) PlanExtra();
+    if (!X) { delete P; return NUASM_ENOMEM; }
+    P->prof_state = X;
+    P->p = rp;
+    P->g = make_geometry(rp);
+    P->m = m;
+    P->f64 = rp.prec == NUASM_PREC_F64;
+    P->has_w = w != nullptr;
+
+    auto bail = [&](nuasm_status code) { release(P); return code; };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return bail(NUASM_ECUDA); }
+
+    HostTables ht{};
+    build_tables(rp, P->g, &ht);
+    P->rc = ht.rc;
+    cudaError_t e = upload_tables(P, ht, st);
+    free_tables(&ht);
+    if (e != cudaSuccess) return bail(cuda_status(e));
+
+    const Geometry& g = P->g;
+    const size_t eb = elt_bytes(P);
+    const size_t stage = std::max<size_t>(size_t(m), size_t(g.n) * g.n) * eb;
+    if ((e = dalloc(P, &P->d.win, size_t(g.W) * g.Wp * eb)) != cudaSuccess) return bail(cuda_status(e));
+    if ((e = dalloc(P, &P->d.bufA, size_t(g.np) * g.Wp * eb)) != cudaSuccess) return bail(cuda_status(e));
+    if ((e = dalloc(P, &P->d.bufB, size_t(g.np) * g.n * eb)) != cudaSuccess) return bail(cuda_status(e));
+    if ((e = dalloc(P, &P->d.stage_in, stage)) != cudaSuccess) return bail(cuda_status(e));
+    if ((e = dalloc(P, &P->d.stage_out, stage)) != cudaSuccess) return bail(cuda_status(e));
+    if ((e = dalloc(P, &P->d.tile_off, sizeof(int) * (g.ntiles + 1))) != cudaSuccess) return bail(cuda_status(e));
+    if ((e = dalloc(P, &P->d.tile_home, sizeof(int) * g.ntiles)) != cudaSuccess) return bail(cuda_status(e));
+    if ((e = dalloc(P, &P->d.err, sizeof(int))) != cudaSuccess) return bail(cuda_status(e));
+
+    double *dx = nullptr, *dy = nullptr, *dw = nullptr;
+    bool ox = false, oy = false, ow = false;
+    auto free_coords = [&]() {
+        if (ox) cudaFree(dx);
+        if (oy) cudaFree(dy);
+        if (ow) cudaFree(dw);
+    };
+    if ((e = device_copy(x, m, &dx, &ox, st)) != cudaSuccess ||
+        (e = device_copy(y, m, &dy, &oy, st)) != cudaSuccess ||
+        (e = device_copy(w, m, &dw, &ow, st)) != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        free_coords();
+        return bail(cuda_status(e));
+    }
+    s = run_binning(P, dx, dy, dw, st);
+    cudaStreamSynchronize(st);
+    free_coords();
+    if (s != NUASM_OK) return bail(s);
+    *out = P;
+    return NUASM_OK;
+}
+
+nuasm_status nuasm1_execute(nuasm_plan_t plan, const void* c, void* u2, void* stream) {
+    if (!plan) return NUASM_EINVAL;
+    if (plan->p.kind != NUASM_KIND_ASM) return NUASM_EINVAL;
+    return exec_type1(plan, c, u2, static_cast<cudaStream_t>(stream));
+}
+
+nuasm_status nuasm2_execute(nuasm_plan_t plan, const void* u1, void* v, void* stream) {
+    if (!plan) return NUASM_EINVAL;
+    if (plan->p.kind != NUASM_KIND_ASM) return NUASM_EINVAL;
+    return exec_type2(plan, u1, v, static_cast<cudaStream_t>(stream));
+}
+
+nuasm_status nufresnel_execute(nuasm_plan_t plan, int32_t type, const void* in, void* out, void* stream) {
+    if (!plan) return NUASM_EINVAL;
+    if (plan->p.kind != NUASM_KIND_FRESNEL) return NUASM_EINVAL;
+    if (type == 1) return exec_type1(plan, in, out, static_cast<cudaStream_t>(stream));
+    if (type == 2) return exec_type2(plan, in, out, static_cast<cudaStream_t>(stream));
+    return NUASM_EINVAL;
+}
+
+nuasm_status nuasm_destroy(nuasm_plan_t plan) {
+    if (!plan) return NUASM_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    release(plan);
+    return cuda_status(e);
+}
+
+const char* nuasm_strerror(nuasm_status s) {
+    switch (s) {
+        case NUASM_OK: return "success";
+        case NUASM_EINVAL: return "invalid argument";
+        case NUASM_ERANGE: return "point outside the window [-N pitch/2, N pitch/2)";
+        case NUASM_ENOMEM: return "out of memory";
+        case NUASM_ECUDA: return "CUDA error";
+        case NUASM_ETIMEOUT: return "bounded device wait timed out";
+        case NUASM_EUNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+nuasm_status nuasm_plan_info(nuasm_plan_t plan, nuasm_plan_info_t* info) {
+    if (!plan || !info) return NUASM_EINVAL;
+    const Geometry& g = plan->g;
+    std::memset(info, 0, sizeof(*info));
+    info->n = g.n;
+    info->n_pad = g.np;
+    info->grid = g.G;
+    info->window = g.W;
+    info->window_origin = g.Lo;
+    info->kernel_width = g.w;
+    info->kernel_beta = g.beta;
+    info->tile = g.T;
+    info->tiles = g.ntiles;
+    info->band_lo_x = g.band[0];
+    info->band_hi_x = g.band[1];
+    info->band_lo_y = g.band[2];
+    info->band_hi_y = g.band[3];
+    info->points = plan->m;
+    info->records = plan->nrec;
+    info->device_bytes = plan->device_bytes;
+    return NUASM_OK;
+}
+
+nuasm_status nuasm_band(const nuasm_params_t* p, int32_t out[4]) {
+    if (!p || !out) return NUASM_EINVAL;
+    nuasm_params_t rp;
+    nuasm_status s = validate(*p, 0, &rp);
+    if (s != NUASM_OK && s != NUASM_EUNSUPPORTED) return s;
+    if (s == NUASM_EUNSUPPORTED) {
+        rp = *p;
+        if (rp.n_pad == 0) rp.n_pad = 2 * rp.n;
+    }
+    int b[4];
+    band_range(rp, b);
+    for (int i = 0; i < 4; ++i) out[i] = b[i];
+    return NUASM_OK;
+}
+
+nuasm_status nuasm_kernel_shape(double tol, int32_t prec, int32_t* width, double* beta) {
+    if (!width || !beta) return NUASM_EINVAL;
+    if (prec != NUASM_PREC_F32_F64PHASE && prec != NUASM_PREC_F64) return NUASM_EINVAL;
+    if (std::isnan(tol) || tol < 0 || tol > 0.1 || (tol > 0 && tol < 1e-15)) return NUASM_EINVAL;
+    int w = 0;
+    kernel_shape(tol, prec, &w, beta);
+    *width = w;
+    return NUASM_OK;
+}
+
+nuasm_status nuasm_profile_enable(nuasm_plan_t plan, int32_t enable) {
+    if (!plan) return NUASM_EINVAL;
+    plan->prof = enable != 0;
+    return NUASM_OK;
+}
+
+nuasm_status nuasm_profile_read(nuasm_plan_t plan, double* ms, int64_t* launches) {
+    if (!plan || !ms || !launches) return NUASM_EINVAL;
+    PlanExtra* X = extra_of(plan);
+    for (int s = 0; s < NUASM_STAGE_COUNT; ++s)
+        while (X->ring[s].count > 0) ring_consume_oldest(plan, s);
+    for (int s = 0; s < NUASM_STAGE_COUNT; ++s) {
+        ms[s] = plan->prof_ms[s];
+        launches[s] = plan->prof_n[s];
+        plan->prof_ms[s] = 0.0;
+        plan->prof_n[s] = 0;
+    }
+    return NUASM_OK;
+}
+
+const char* nuasm_stage_name(int32_t stage) {
+    static const char* names[NUASM_STAGE_COUNT] = {"h2d", "spread", "col_fwd_fold", "row_t1", "col_inv",
+                                                   "col_fwd", "row_t2", "col_inv_fold", "interp", "d2h"};
+    if (stage < 0 || stage >= NUASM_STAGE_COUNT) return "unknown";
+    return names[stage];
+}
+
+}  // extern "C"

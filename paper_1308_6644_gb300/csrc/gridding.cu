@@ -1,0 +1,401 @@
+// NUFFT gridding: point binning (plan time), type-1 spreading and type-2
+// interpolation on the oversampled fine grid (Eq. 7 / Eq. 8, the gridding
+// step of Greengard and Lee's NUFFT that the paper uses).
+//
+// Coordinate normalisation (the paper's x' = 2 pi (o' + x)/N, read as a map of
+// the window onto the central half of the padded period): a point x (metres)
+// becomes xi = x / pitch in [-N/2, N/2), then g = 2 (xi + N'/2) on the fine
+// grid of G = 2N' cells per period.  Relative to the window origin Lo =
+// N' - N - h (h = ceil(w/2)) this is g_w = 2 xi + N + h, and the w taps of the
+// kernel sit at l0 + i, i in [0, w), l0 = ceil(g_w - w/2), with offsets
+// t_i = i + f - w/2, f = l0 - (g_w - w/2) in [0, 1).  The split into the
+// integer cell and the fraction f is done in FP64 once per plan.
+//
+// The kernel is the exponential of semicircle
+//   phi(t) = exp(beta (sqrt(1 - (2t/w)^2) - 1)),  |t| <= w/2.
+//
+// Tiles: the W x W window is cut into T x T tiles.  Each point is binned to the
+// tile that holds its first tap l0 (its home tile) and duplicated into the +x,
+// +y and +x+y neighbours its taps reach.  Spreading is output-stationary: one
+// CTA owns one tile, accumulates every record of its bin into shared memory
+// (shared-memory atomics, no global atomics) clipping taps to the tile, and
+// writes the tile once.  Interpolation loads the tile plus a (w-1) halo into
+// shared memory and evaluates its home records only.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "nuasm_internal.h"
+
+namespace nuasm {
+
+// Binned point records.  cell = l0y << 16 | l0x (window coordinates of the first tap).
+struct RecF { uint32_t cell; float fx, fy; int32_t j; };
+struct RecD { uint32_t cell; int32_t j; double fx, fy; };
+
+template <typename S> struct RecOf;
+template <> struct RecOf<float> { using type = RecF; };
+template <> struct RecOf<double> { using type = RecD; };
+
+namespace {
+
+struct BinArgs {
+    int n, W, T, ntx, w, h;
+    double pitch;
+    int64_t m;
+};
+
+struct PointSplit { int l0x, l0y; double fx, fy; bool ok; };
+
+__device__ __forceinline__ PointSplit split_point(double x, double y, const BinArgs& a) {
+    PointSplit s;
+    const double xi = x / a.pitch, yi = y / a.pitch;
+    const double half = 0.5 * a.n;
+    s.ok = xi >= -half && xi < half && yi >= -half && yi < half;
+    const double gx = 2.0 * xi + double(a.n + a.h) - 0.5 * a.w;
+    const double gy = 2.0 * yi + double(a.n + a.h) - 0.5 * a.w;
+    const double cx = ceil(gx), cy = ceil(gy);
+    s.l0x = int(cx);
+    s.l0y = int(cy);
+    s.fx = cx - gx;
+    s.fy = cy - gy;
+    if (!s.ok) { s.l0x = 0; s.l0y = 0; s.fx = 0; s.fy = 0; }
+    return s;
+}
+
+// up to four tiles per point: home, +x, +y, +x+y
+__device__ __forceinline__ int point_tiles(const PointSplit& s, const BinArgs& a, int tiles[4]) {
+    const int tx = s.l0x / a.T, ty = s.l0y / a.T;
+    const bool dx = (s.l0x - tx * a.T) + a.w - 1 >= a.T;
+    const bool dy = (s.l0y - ty * a.T) + a.w - 1 >= a.T;
+    int k = 0;
+    tiles[k++] = ty * a.ntx + tx;
+    if (dx) tiles[k++] = ty * a.ntx + tx + 1;
+    if (dy) tiles[k++] = (ty + 1) * a.ntx + tx;
+    if (dx && dy) tiles[k++] = (ty + 1) * a.ntx + tx + 1;
+    return k;
+}
+
+__global__ void bin_count_kernel(const double* __restrict__ x, const double* __restrict__ y, BinArgs a,
+                                 int* __restrict__ home_cnt, int* __restrict__ dup_cnt, int* __restrict__ err) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < a.m; i += int64_t(gridDim.x) * blockDim.x) {
+        PointSplit s = split_point(x[i], y[i], a);
+        if (!s.ok) { atomicOr(err, 1); continue; }
+        int t[4];
+        const int k = point_tiles(s, a, t);
+        atomicAdd(&home_cnt[t[0]], 1);
+        for (int q = 1; q < k; ++q) atomicAdd(&dup_cnt[t[q]], 1);
+    }
+}
+
+// exclusive scan of home_cnt + dup_cnt into off[0..ntiles], single CTA of 1024 threads
+__global__ void bin_scan_kernel(const int* __restrict__ home_cnt, const int* __restrict__ dup_cnt,
+                                int ntiles, int* __restrict__ off, int* __restrict__ home) {
+    __shared__ long long part[1024];
+    const int t = threadIdx.x, P = blockDim.x;
+    const int chunk = (ntiles + P - 1) / P;
+    const int b = t * chunk, e = min(ntiles, b + chunk);
+    long long acc = 0;
+    for (int i = b; i < e; ++i) acc += home_cnt[i] + dup_cnt[i];
+    part[t] = acc;
+    __syncthreads();
+    for (int d = 1; d < P; d <<= 1) {
+        long long v = t >= d ? part[t - d] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    long long run = part[t] - acc;
+    for (int i = b; i < e; ++i) {
+        off[i] = int(run);
+        home[i] = home_cnt[i];
+        run += home_cnt[i] + dup_cnt[i];
+    }
+    if (t == P - 1) off[ntiles] = int(part[P - 1]);
+}
+
+template <typename Rec, typename S>
+__global__ void bin_scatter_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                   const double* __restrict__ w, BinArgs a, const int* __restrict__ off,
+                                   const int* __restrict__ home_cnt, int* __restrict__ cur_home,
+                                   int* __restrict__ cur_dup, Rec* __restrict__ rec, S* __restrict__ wrec) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < a.m; i += int64_t(gridDim.x) * blockDim.x) {
+        PointSplit s = split_point(x[i], y[i], a);
+        if (!s.ok) continue;
+        int t[4];
+        const int k = point_tiles(s, a, t);
+        Rec r;
+        r.cell = (uint32_t(s.l0y) << 16) | uint32_t(s.l0x);
+        r.fx = S(s.fx);
+        r.fy = S(s.fy);
+        r.j = int32_t(i);
+        for (int q = 0; q < k; ++q) {
+            int pos;
+            if (q == 0) pos = off[t[0]] + atomicAdd(&cur_home[t[0]], 1);
+            else pos = off[t[q]] + home_cnt[t[q]] + atomicAdd(&cur_dup[t[q]], 1);
+            rec[pos] = r;
+            if (wrec) wrec[pos] = S(w[i]);
+        }
+    }
+}
+
+// --------------------------------------------------------------- kernel values
+template <typename S> __device__ __forceinline__ S es_eval(S t, S inv_half_w, S beta);
+template <> __device__ __forceinline__ float es_eval<float>(float t, float ihw, float beta) {
+    const float s = t * ihw;
+    const float u = fmaxf((1.f - s) * (1.f + s), 0.f);
+    return expf(beta * (sqrtf(u) - 1.f));
+}
+template <> __device__ __forceinline__ double es_eval<double>(double t, double ihw, double beta) {
+    const double s = t * ihw;
+    const double u = fmax((1.0 - s) * (1.0 + s), 0.0);
+    return exp(beta * (sqrt(u) - 1.0));
+}
+
+template <typename S> struct VecOf;
+template <> struct VecOf<float> { using type = float2; };
+template <> struct VecOf<double> { using type = double2; };
+
+struct GridArgs {
+    int W, Wp, T, ntx, w;
+    double beta;
+};
+
+// --------------------------------------------------------------- spreading (type 1)
+template <typename S, int WMAX>
+__global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::type* __restrict__ rec,
+                                                     const int* __restrict__ off, const S* __restrict__ wrec,
+                                                     const typename VecOf<S>::type* __restrict__ c,
+                                                     typename VecOf<S>::type* __restrict__ win, GridArgs a) {
+    using V = typename VecOf<S>::type;
+    extern __shared__ unsigned char smem_raw[];
+    const int T = a.T, w = a.w;
+    S* sre = reinterpret_cast<S*>(smem_raw);
+    S* sim = sre + T * T;
+    const int tile = blockIdx.x;
+    const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
+    const int x0 = tx * T, y0 = ty * T;
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) { sre[i] = S(0); sim[i] = S(0); }
+    __syncthreads();
+    const S beta = S(a.beta), ihw = S(2) / S(w), hw = S(w) / S(2);
+    const int b = off[tile], e = off[tile + 1];
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const auto r = rec[i];
+        const int lx = int(r.cell & 0xffffu) - x0, ly = int(r.cell >> 16) - y0;
+        V val = c[r.j];
+        if (wrec) { const S wt = wrec[i]; val.x *= wt; val.y *= wt; }
+        S wx[WMAX], wy[WMAX];
+#pragma unroll
+        for (int q = 0; q < WMAX; ++q) {
+            if (q < w) {
+                wx[q] = es_eval<S>(S(q) + S(r.fx) - hw, ihw, beta);
+                wy[q] = es_eval<S>(S(q) + S(r.fy) - hw, ihw, beta);
+            }
+        }
+        const int ya = max(0, -ly), yb = min(w, T - ly);
+        const int xa = max(0, -lx), xb = min(w, T - lx);
+#pragma unroll
+        for (int qy = 0; qy < WMAX; ++qy) {
+            if (qy < ya || qy >= yb) continue;
+            const S vr = val.x * wy[qy], vi = val.y * wy[qy];
+            S* rowr = sre + (ly + qy) * T + lx;
+            S* rowi = sim + (ly + qy) * T + lx;
+#pragma unroll
+            for (int qx = 0; qx < WMAX; ++qx) {
+                if (qx < xa || qx >= xb) continue;
+                atomicAdd(rowr + qx, vr * wx[qx]);
+                atomicAdd(rowi + qx, vi * wx[qx]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        const int yy = i / T, xx = i - yy * T;
+        const int gy = y0 + yy, gx = x0 + xx;
+        if (gy < a.W && gx < a.W) {
+            V v;
+            v.x = sre[i];
+            v.y = sim[i];
+            win[size_t(gy) * a.Wp + gx] = v;
+        }
+    }
+}
+
+// --------------------------------------------------------------- interpolation (type 2)
+template <typename S, int WMAX>
+__global__ void __launch_bounds__(256) interp_kernel(const typename RecOf<S>::type* __restrict__ rec,
+                                                     const int* __restrict__ off, const int* __restrict__ home,
+                                                     const typename VecOf<S>::type* __restrict__ win,
+                                                     typename VecOf<S>::type* __restrict__ v, GridArgs a) {
+    using V = typename VecOf<S>::type;
+    extern __shared__ unsigned char smem_raw[];
+    V* tl = reinterpret_cast<V*>(smem_raw);
+    const int T = a.T, w = a.w, TH = T + w - 1;
+    const int tile = blockIdx.x;
+    const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
+    const int x0 = tx * T, y0 = ty * T;
+    for (int i = threadIdx.x; i < TH * TH; i += blockDim.x) {
+        const int yy = i / TH, xx = i - yy * TH;
+        const int gy = y0 + yy, gx = x0 + xx;
+        V val;
+        val.x = S(0);
+        val.y = S(0);
+        if (gy < a.W && gx < a.W) val = win[size_t(gy) * a.Wp + gx];
+        tl[i] = val;
+    }
+    __syncthreads();
+    const S beta = S(a.beta), ihw = S(2) / S(w), hw = S(w) / S(2);
+    const int b = off[tile], e = b + home[tile];
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const auto r = rec[i];
+        const int lx = int(r.cell & 0xffffu) - x0, ly = int(r.cell >> 16) - y0;
+        S wx[WMAX], wy[WMAX];
+#pragma unroll
+        for (int q = 0; q < WMAX; ++q) {
+            if (q < w) {
+                wx[q] = es_eval<S>(S(q) + S(r.fx) - hw, ihw, beta);
+                wy[q] = es_eval<S>(S(q) + S(r.fy) - hw, ihw, beta);
+            }
+        }
+        S ar = S(0), ai = S(0);
+#pragma unroll
+        for (int qy = 0; qy < WMAX; ++qy) {
+            if (qy >= w) continue;
+            const V* row = tl + (ly + qy) * TH + lx;
+            S rr = S(0), ri = S(0);
+#pragma unroll
+            for (int qx = 0; qx < WMAX; ++qx) {
+                if (qx >= w) continue;
+                const V g = row[qx];
+                rr = fma(g.x, wx[qx], rr);
+                ri = fma(g.y, wx[qx], ri);
+            }
+            ar = fma(rr, wy[qy], ar);
+            ai = fma(ri, wy[qy], ai);
+        }
+        V out;
+        out.x = ar;
+        out.y = ai;
+        v[r.j] = out;
+    }
+}
+
+GridArgs grid_args(const nuasm_plan_s* P) {
+    GridArgs a;
+    a.W = P->g.W;
+    a.Wp = P->g.Wp;
+    a.T = P->g.T;
+    a.ntx = P->g.ntx;
+    a.w = P->g.w;
+    a.beta = P->g.beta;
+    return a;
+}
+
+template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
+template <typename S, int WMAX>
+cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
+    using V = typename VecOf<S>::type;
+    GridArgs a = grid_args(P);
+    const size_t sm = size_t(2) * a.T * a.T * sizeof(S);
+    cudaError_t e = set_smem(spread_kernel<S, WMAX>, sm);
+    if (e != cudaSuccess) return e;
+    const S* wr = sizeof(S) == 4 ? reinterpret_cast<const S*>(P->d.wrec_f) : reinterpret_cast<const S*>(P->d.wrec_d);
+    spread_kernel<S, WMAX><<<P->g.ntiles, 256, sm, st>>>(
+        static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, wr,
+        static_cast<const V*>(c), static_cast<V*>(P->d.win), a);
+    return cudaGetLastError();
+}
+
+template <typename S, int WMAX>
+cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
+    using V = typename VecOf<S>::type;
+    GridArgs a = grid_args(P);
+    const int TH = a.T + a.w - 1;
+    const size_t sm = size_t(TH) * TH * sizeof(V);
+    cudaError_t e = set_smem(interp_kernel<S, WMAX>, sm);
+    if (e != cudaSuccess) return e;
+    interp_kernel<S, WMAX><<<P->g.ntiles, 256, sm, st>>>(
+        static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.tile_home,
+        static_cast<const V*>(P->d.win), static_cast<V*>(v), a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+static nuasm_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return NUASM_OK;
+    return e == cudaErrorMemoryAllocation ? NUASM_ENOMEM : NUASM_ECUDA;
+}
+
+nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, const double* w, cudaStream_t st) {
+    const Geometry& g = P->g;
+    BinArgs a{g.n, g.W, g.T, g.ntx, g.w, g.h, P->p.pitch, P->m};
+    const int nt = g.ntiles;
+    int* cnt = nullptr;   // home_cnt, dup_cnt, cur_home, cur_dup
+    cudaError_t e = cudaMallocAsync(&cnt, sizeof(int) * 4 * size_t(nt), st);
+    if (e != cudaSuccess) return cuda_status(e);
+    int* home_cnt = cnt;
+    int* dup_cnt = cnt + nt;
+    int* cur_home = cnt + 2 * nt;
+    int* cur_dup = cnt + 3 * nt;
+    auto fail = [&](cudaError_t err) {
+        cudaFreeAsync(cnt, st);
+        cudaStreamSynchronize(st);
+        return cuda_status(err);
+    };
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * 4 * size_t(nt), st)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(P->d.err, 0, sizeof(int), st)) != cudaSuccess) return fail(e);
+    const int blocks = int(std::min<int64_t>((P->m + 255) / 256, 152 * 16));
+    if (P->m > 0) {
+        bin_count_kernel<<<blocks, 256, 0, st>>>(x, y, a, home_cnt, dup_cnt, P->d.err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    }
+    bin_scan_kernel<<<1, 1024, 0, st>>>(home_cnt, dup_cnt, nt, P->d.tile_off, P->d.tile_home);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    int total = 0, errw = 0;
+    if ((e = cudaMemcpyAsync(&total, P->d.tile_off + nt, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(&errw, P->d.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    if (errw) {
+        fail(cudaSuccess);
+        return NUASM_ERANGE;
+    }
+    P->nrec = total;
+    const size_t rsz = P->f64 ? sizeof(RecD) : sizeof(RecF);
+    if ((e = cudaMalloc(&P->d.rec, rsz * size_t(total > 0 ? total : 1))) != cudaSuccess) return fail(e);
+    P->device_bytes += int64_t(rsz) * (total > 0 ? total : 1);
+    if (w) {
+        if (P->f64) e = cudaMalloc(&P->d.wrec_d, sizeof(double) * size_t(total > 0 ? total : 1));
+        else e = cudaMalloc(&P->d.wrec_f, sizeof(float) * size_t(total > 0 ? total : 1));
+        if (e != cudaSuccess) return fail(e);
+        P->device_bytes += int64_t(P->f64 ? 8 : 4) * (total > 0 ? total : 1);
+    }
+    if (P->m > 0) {
+        if (P->f64)
+            bin_scatter_kernel<RecD, double><<<blocks, 256, 0, st>>>(x, y, w, a, P->d.tile_off, home_cnt, cur_home,
+                                                                     cur_dup, static_cast<RecD*>(P->d.rec), P->d.wrec_d);
+        else
+            bin_scatter_kernel<RecF, float><<<blocks, 256, 0, st>>>(x, y, w, a, P->d.tile_off, home_cnt, cur_home,
+                                                                    cur_dup, static_cast<RecF*>(P->d.rec), P->d.wrec_f);
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    }
+    e = cudaFreeAsync(cnt, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+cudaError_t launch_spread(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
+    if (P->f64) return P->g.w <= 8 ? spread_impl<double, 8>(P, c, st) : spread_impl<double, 16>(P, c, st);
+    return P->g.w <= 8 ? spread_impl<float, 8>(P, c, st) : spread_impl<float, 16>(P, c, st);
+}
+
+cudaError_t launch_interp(const nuasm_plan_s* P, void* v, cudaStream_t st) {
+    if (P->f64) return P->g.w <= 8 ? interp_impl<double, 8>(P, v, st) : interp_impl<double, 16>(P, v, st);
+    return P->g.w <= 8 ? interp_impl<float, 8>(P, v, st) : interp_impl<float, 16>(P, v, st);
+}
+
+}  // namespace nuasm

@@ -1,0 +1,293 @@
+// Plan-time host mathematics for the NU-ASM / NU-FRE library: parameter
+// validation, the Rect band of Eq. 4, the NUFFT kernel and its deconvolution,
+// the per-axis transfer-function tables (Eq. 4 separable part, Eq. 5) and the
+// FFT twiddles.  Everything here runs once per plan in FP64 (double-double
+// where a phase can exceed 1e5 cycles).
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "nuasm_internal.h"
+
+namespace nuasm {
+
+namespace {
+
+using cd = std::complex<double>;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int64_t v) { int l = 0; while ((int64_t(1) << l) < v) ++l; return l; }
+
+// exp(2 pi i c) for a phase c in cycles with |c| <= 1/2 (callers reduce first)
+cd cis(double c) { double a = kTwoPi * c; return cd(std::cos(a), std::sin(a)); }
+
+// exp(2 pi i num/den) for integers, reduced exactly
+cd cis_ratio(int64_t num, int64_t den) {
+    int64_t r = num % den;
+    if (r < 0) r += den;
+    if (2 * r > den) r -= den;
+    return cis(double(r) / double(den));
+}
+
+double frac(double c) { return c - std::nearbyint(c); }
+
+// z / lambda reduced mod 1 with a double-double quotient: the phase of
+// exp(ikz) reaches 1e6 cycles, beyond what one rounded FP64 division resolves
+// at the 1e-10 level.
+double z_over_lambda_frac(double z, double lam) {
+    double q = z / lam;
+    double r = std::fma(-q, lam, z);          // exact remainder z - q lambda
+    double ql = r / lam;
+    return frac(q) + ql;
+}
+
+// Exponential-of-semicircle kernel phi(t) = exp(beta (sqrt(1 - (2t/w)^2) - 1)),
+// supported on |t| <= w/2 (Barnett, Magland, af Klinteberg 2019).
+double es_kernel(double t, int w, double beta) {
+    double s = 2.0 * t / w;
+    if (std::fabs(s) > 1.0) return 0.0;
+    return std::exp(beta * (std::sqrt(1.0 - s * s) - 1.0));
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] (Newton on the three-term recurrence).
+void gauss_legendre(int n, std::vector<double>* x, std::vector<double>* wt) {
+    x->assign(n, 0.0);
+    wt->assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        (*x)[i] = z;
+        (*wt)[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// In-place radix-2 FFT (forward, exp(-2 pi i k n / L)), FP64, twiddles computed
+// directly from the index so that no rounding accumulates.
+void fft_host(std::vector<cd>* a) {
+    const int64_t L = int64_t(a->size());
+    std::vector<cd>& v = *a;
+    for (int64_t i = 1, j = 0; i < L; ++i) {
+        int64_t bit = L >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(v[i], v[j]);
+    }
+    std::vector<cd> roots(L / 2);
+    for (int64_t t = 0; t < L / 2; ++t) roots[t] = cis_ratio(-t, L);
+    for (int64_t len = 2; len <= L; len <<= 1) {
+        int64_t step = L / len;
+        for (int64_t i = 0; i < L; i += len)
+            for (int64_t k = 0; k < len / 2; ++k) {
+                cd u = v[i + k], t = v[i + k + len / 2] * roots[k * step];
+                v[i + k] = u + t;
+                v[i + k + len / 2] = u - t;
+            }
+    }
+}
+
+// Band of Eq. 4 along one axis as a frequency interval (see nuasm.h).
+void band_limits(int n, double pitch, double lam, double z, double o, double* lo, double* hi) {
+    const double s = n * pitch;
+    if (z == 0.0) {
+        if (std::fabs(o) <= s) { *lo = -INFINITY; *hi = INFINITY; }
+        else { *lo = INFINITY; *hi = -INFINITY; }
+        return;
+    }
+    const double sg = z > 0 ? 1.0 : -1.0;
+    auto ginv = [&](double t) { return sg * t / (lam * std::sqrt(z * z + t * t)); };
+    double a = ginv(o - s), b = ginv(o + s);
+    *lo = a < b ? a : b;
+    *hi = a < b ? b : a;
+}
+
+bool in_band(const nuasm_params_t& p, int np, int k, int axis) {
+    if (p.kind != NUASM_KIND_ASM) return true;
+    if (!p.band_auto) {
+        double c = axis == 0 ? p.c_m : p.c_n;
+        double w = axis == 0 ? p.w_m : p.w_n;
+        return std::fabs(double(k) - c) <= w / 2.0;
+    }
+    double lo, hi;
+    band_limits(p.n, p.pitch, p.lambda, p.z, axis == 0 ? p.ox : p.oy, &lo, &hi);
+    double f = double(k) / (double(np) * p.pitch);
+    return f >= lo && f <= hi;
+}
+
+}  // namespace
+
+void kernel_shape(double tol, int prec, int* w, double* beta) {
+    if (!(tol > 0)) tol = prec == NUASM_PREC_F64 ? 1e-12 : 1e-6;
+    int ww = int(std::ceil(-std::log10(tol) - 1e-9)) + 1;
+    if (ww < 2) ww = 2;
+    if (ww > 16) ww = 16;
+    *w = ww;
+    *beta = 2.30 * ww;   // shape parameter for upsampling factor 2
+}
+
+nuasm_status validate(const nuasm_params_t& p0, int64_t m, nuasm_params_t* out) {
+    nuasm_params_t p = p0;
+    if (p.kind != NUASM_KIND_ASM && p.kind != NUASM_KIND_FRESNEL) return NUASM_EINVAL;
+    if (p.prec != NUASM_PREC_F32_F64PHASE && p.prec != NUASM_PREC_F64) return NUASM_EINVAL;
+    if (m < 0 || m > (int64_t(1) << 29)) return m < 0 ? NUASM_EINVAL : NUASM_EUNSUPPORTED;
+    if (p.n < 2 || (p.n & 1)) return NUASM_EINVAL;
+    if (!std::isfinite(p.pitch) || !(p.pitch > 0)) return NUASM_EINVAL;
+    if (!std::isfinite(p.lambda) || !(p.lambda > 0)) return NUASM_EINVAL;
+    if (!std::isfinite(p.z) || !std::isfinite(p.ox) || !std::isfinite(p.oy)) return NUASM_EINVAL;
+    if (p.kind == NUASM_KIND_FRESNEL && p.z == 0.0) return NUASM_EINVAL;
+    if (p.band_auto != 0 && p.band_auto != 1) return NUASM_EINVAL;
+    if (!p.band_auto && p.kind == NUASM_KIND_ASM) {
+        if (!std::isfinite(p.c_m) || !std::isfinite(p.c_n) || !std::isfinite(p.w_m) ||
+            !std::isfinite(p.w_n) || p.w_m < 0 || p.w_n < 0)
+            return NUASM_EINVAL;
+    }
+    if (std::isnan(p.tol) || p.tol < 0 || p.tol > 0.1) return NUASM_EINVAL;
+    if (p.tol == 0) p.tol = p.prec == NUASM_PREC_F64 ? 1e-12 : 1e-6;
+    if (p.tol < 1e-15) return NUASM_EINVAL;
+    if (p.n_pad == 0) p.n_pad = 2 * p.n;
+    if (p.n_pad < 2 * p.n || !is_pow2(p.n_pad)) return NUASM_EINVAL;
+    // what this build implements: power-of-two planes, N' <= 8192 (F32) / 4096 (F64)
+    if (!is_pow2(p.n) || p.n < 16) return NUASM_EUNSUPPORTED;
+    const int np_max = p.prec == NUASM_PREC_F64 ? 4096 : 8192;
+    if (p.n_pad > np_max) return NUASM_EUNSUPPORTED;
+    *out = p;
+    return NUASM_OK;
+}
+
+void band_range(const nuasm_params_t& p, int out[4]) {
+    const int np = p.n_pad ? p.n_pad : 2 * p.n;
+    for (int axis = 0; axis < 2; ++axis) {
+        int lo = np / 2, hi = -np / 2 - 1;   // empty
+        for (int k = -np / 2; k < np / 2; ++k)
+            if (in_band(p, np, k, axis)) {
+                if (k < lo) lo = k;
+                if (k > hi) hi = k;
+            }
+        out[2 * axis] = lo;
+        out[2 * axis + 1] = hi;
+    }
+}
+
+Geometry make_geometry(const nuasm_params_t& p) {
+    Geometry g{};
+    g.n = p.n;
+    g.np = p.n_pad;
+    g.G = 2 * p.n_pad;
+    g.logn = ilog2(p.n);
+    g.lognp = ilog2(p.n_pad);
+    kernel_shape(p.tol, p.prec, &g.w, &g.beta);
+    g.h = (g.w + 1) / 2;
+    g.W = 2 * p.n + 2 * g.h;
+    g.Wp = (g.W + 31) & ~31;
+    g.Lo = p.n_pad - p.n - g.h;
+    g.T = (p.prec == NUASM_PREC_F64 || g.W <= 512) ? 32 : 64;
+    g.ntx = (g.W + g.T - 1) / g.T;
+    g.ntiles = g.ntx * g.ntx;
+    band_range(p, g.band);
+    return g;
+}
+
+void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t) {
+    const int np = g.np, G = g.G, n = g.n;
+    t->t1x = new double[2 * np];
+    t->t1y = new double[2 * np];
+    t->t2x = new double[2 * np];
+    t->t2y = new double[2 * np];
+    t->s = new double[np];
+    t->tw = new double[2 * G];
+
+    // deconvolution 1/phihat(k/G) by Gauss-Legendre quadrature of the truncated kernel
+    std::vector<double> gx, gw;
+    const int nq = 2 * g.w + 48;
+    gauss_legendre(nq, &gx, &gw);
+    std::vector<double> tq(nq), fq(nq);
+    for (int i = 0; i < nq; ++i) {
+        tq[i] = (gx[i] + 1.0) * g.w / 4.0;              // [0, w/2]
+        fq[i] = gw[i] * g.w / 4.0 * es_kernel(tq[i], g.w, g.beta);
+    }
+    std::vector<double> phihat(np);
+    for (int q = 0; q < np; ++q) {
+        int k = q < np / 2 ? q : q - np;
+        double nu = double(k) / G, acc = 0.0;
+        for (int i = 0; i < nq; ++i) acc += fq[i] * std::cos(kTwoPi * nu * tq[i]);
+        phihat[q] = 2.0 * acc;
+    }
+
+    // separable transfer-function factor per axis (Eq. 4 or Eq. 5)
+    auto axis_factor = [&](int axis, std::vector<cd>* hs) {
+        hs->assign(np, cd(0, 0));
+        const double o = axis == 0 ? p.ox : p.oy;
+        if (p.kind == NUASM_KIND_ASM) {
+            for (int q = 0; q < np; ++q) {
+                int k = q < np / 2 ? q : q - np;
+                if (!in_band(p, np, k, axis)) continue;
+                double f = double(k) / (double(np) * p.pitch);
+                double ph = o * f - 0.5 * p.z * p.lambda * f * f;   // cycles
+                (*hs)[q] = cis(frac(ph));
+            }
+        } else {
+            // Hx(k) = pitch * sum_{m in [-N'/2, N'/2)} exp(i pi (m pitch + o)^2/(lambda z)) exp(-2 pi i k m / N')
+            std::vector<cd> chirp(np);
+            for (int i = 0; i < np; ++i) {
+                double xm = double(i - np / 2) * p.pitch + o;
+                chirp[i] = cis(frac(xm * xm / (2.0 * p.lambda * p.z)));
+            }
+            fft_host(&chirp);
+            for (int q = 0; q < np; ++q) {
+                int k = q < np / 2 ? q : q - np;
+                (*hs)[q] = p.pitch * ((k & 1) ? -1.0 : 1.0) * chirp[q];
+            }
+        }
+    };
+    std::vector<cd> hx, hy;
+    axis_factor(0, &hx);
+    axis_factor(1, &hy);
+    cd cst = cis(frac(z_over_lambda_frac(p.z, p.lambda)));
+    if (p.kind == NUASM_KIND_FRESNEL) cst /= cd(0.0, p.lambda * p.z);
+
+    for (int q = 0; q < np; ++q) {
+        const int k = q < np / 2 ? q : q - np;
+        const double sgn = (k & 1) ? -1.0 : 1.0;
+        const double dec = sgn / phihat[q] / np;
+        cd win1 = cis_ratio(-int64_t(k) * g.Lo, G);         // window origin on the G grid
+        cd ctr1 = cis_ratio(-int64_t(k) * (n / 2), np);      // centred output indices
+        cd a1x = win1 * ctr1 * dec * hx[q];
+        cd a1y = win1 * ctr1 * dec * hy[q] * cst;
+        cd a2x = std::conj(win1) * std::conj(ctr1) * dec * hx[q];
+        cd a2y = std::conj(win1) * std::conj(ctr1) * dec * hy[q] * cst;
+        t->t1x[2 * q] = a1x.real(); t->t1x[2 * q + 1] = a1x.imag();
+        t->t1y[2 * q] = a1y.real(); t->t1y[2 * q + 1] = a1y.imag();
+        t->t2x[2 * q] = a2x.real(); t->t2x[2 * q + 1] = a2x.imag();
+        t->t2y[2 * q] = a2y.real(); t->t2y[2 * q + 1] = a2y.imag();
+        double f = double(k) / (double(np) * p.pitch);
+        t->s[q] = p.lambda * p.lambda * f * f;
+    }
+    t->rc = p.z / (2.0 * p.lambda);
+    for (int i = 0; i < G; ++i) {
+        cd v = cis_ratio(-i, G);
+        t->tw[2 * i] = v.real();
+        t->tw[2 * i + 1] = v.imag();
+    }
+}
+
+void free_tables(HostTables* t) {
+    delete[] t->t1x; delete[] t->t1y; delete[] t->t2x; delete[] t->t2y;
+    delete[] t->s; delete[] t->tw;
+    std::memset(t, 0, sizeof(*t));
+}
+
+}  // namespace nuasm

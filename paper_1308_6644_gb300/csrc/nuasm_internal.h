@@ -1,0 +1,92 @@
+// Internal plan representation and launcher prototypes (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nuasm.h"
+
+namespace nuasm {
+
+// Host-side geometry and tables derived from nuasm_params_t.
+struct Geometry {
+    int n, np, G;          // N, N', G = 2N'
+    int logn, lognp;       // log2 N, log2 N'
+    int w;                 // kernel width
+    double beta;           // ES shape parameter
+    int h;                 // window margin ceil(w/2)
+    int W, Wp;             // window side, row pitch (elements)
+    int Lo;                // window origin on the G grid
+    int T, ntx, ntiles;    // tile side, tiles per axis, tile count
+    int band[4];           // inclusive kept-mode ranges lo_x, hi_x, lo_y, hi_y
+};
+
+// Host tables in FP64 (complex as re/im pairs), natural N'-bin order.
+struct HostTables {
+    // per-axis separable factors for type 1 and type 2, length N' each
+    double* t1x; double* t1y; double* t2x; double* t2y;   // 2*N' doubles each
+    double* s;        // lambda^2 f_k^2 per bin (ASM), length N'
+    double rc;        // z / (2 lambda)  (ASM non-separable phase scale)
+    double* tw;       // exp(-2 pi i t / G), t in [0, G): 2*G doubles
+};
+
+struct PlanDevice {
+    void* tables = nullptr;     // one block holding every table below
+    void* t1x = nullptr; void* t1y = nullptr; void* t2x = nullptr; void* t2y = nullptr;
+    void* s = nullptr;          // float2 (hi, lo) per bin (F32) or double (F64)
+    void* tw = nullptr;         // twiddles, G complex
+    void* rec = nullptr;        // binned point records
+    float* wrec_f = nullptr;    // optional weights in record order (F32)
+    double* wrec_d = nullptr;   // optional weights in record order (F64)
+    int* tile_off = nullptr;    // ntiles + 1 offsets into rec
+    int* tile_home = nullptr;   // home-record count per tile
+    void* win = nullptr;        // W x Wp fine-grid window
+    void* bufA = nullptr;       // N' x Wp
+    void* bufB = nullptr;       // N' x N
+    void* stage_in = nullptr;   // host-pointer staging (max of M, N^2 complex)
+    void* stage_out = nullptr;
+    int* err = nullptr;         // device error word
+};
+
+}  // namespace nuasm
+
+struct nuasm_plan_s {
+    nuasm_params_t p;
+    nuasm::Geometry g;
+    int64_t m = 0;
+    int64_t nrec = 0;
+    bool has_w = false;
+    bool f64 = false;
+    double rc = 0.0;            // z / (2 lambda)
+    int64_t device_bytes = 0;
+    nuasm::PlanDevice d;
+    // profiling
+    bool prof = false;
+    void* prof_state = nullptr;   // per-stage CUDA event rings (capi.cu)
+    double prof_ms[NUASM_STAGE_COUNT] = {};
+    int64_t prof_n[NUASM_STAGE_COUNT] = {};
+};
+
+namespace nuasm {
+
+// host math (hostmath.cpp)
+nuasm_status validate(const nuasm_params_t& p, int64_t m, nuasm_params_t* resolved);
+void kernel_shape(double tol, int prec, int* w, double* beta);
+void band_range(const nuasm_params_t& p, int out[4]);
+Geometry make_geometry(const nuasm_params_t& p);
+void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t);
+void free_tables(HostTables* t);
+
+// launchers (gridding.cu / passes.cu); all asynchronous on `s`
+nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, const double* w,
+                         cudaStream_t s);
+cudaError_t launch_spread(const nuasm_plan_s* P, const void* c, cudaStream_t s);
+cudaError_t launch_interp(const nuasm_plan_s* P, void* v, cudaStream_t s);
+cudaError_t launch_col_fwd_fold(const nuasm_plan_s* P, cudaStream_t s);
+cudaError_t launch_row_t1(const nuasm_plan_s* P, cudaStream_t s);
+cudaError_t launch_col_inv(const nuasm_plan_s* P, void* u2, cudaStream_t s);
+cudaError_t launch_col_fwd(const nuasm_plan_s* P, const void* u1, cudaStream_t s);
+cudaError_t launch_row_t2(const nuasm_plan_s* P, cudaStream_t s);
+cudaError_t launch_col_inv_fold(const nuasm_plan_s* P, cudaStream_t s);
+
+}  // namespace nuasm

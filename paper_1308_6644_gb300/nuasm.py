@@ -1,0 +1,284 @@
+"""Python binding of the C ABI in ``include/nuasm.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does
+nothing but check argument shapes/dtypes, pass pointers and translate status
+codes into exceptions: all computation runs in ``libnuasm.so``.  Arrays may be
+torch tensors (CUDA or CPU) or numpy arrays; host arrays are staged by the
+library itself.  Importing this module does not need a GPU; loading the
+library does need the shared object, and a missing library is an error (there
+is no fallback implementation).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libnuasm.so")
+
+KIND_ASM, KIND_FRESNEL = 0, 1
+PREC_F32_F64PHASE, PREC_F64 = 0, 1
+
+STATUS = {0: "NUASM_OK", 1: "NUASM_EINVAL", 2: "NUASM_ERANGE", 3: "NUASM_ENOMEM",
+          4: "NUASM_ECUDA", 5: "NUASM_ETIMEOUT", 6: "NUASM_EUNSUPPORTED"}
+STAGES = ["h2d", "spread", "col_fwd_fold", "row_t1", "col_inv", "col_fwd", "row_t2",
+          "col_inv_fold", "interp", "d2h"]
+
+
+class NuasmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({_strerror(code)})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_pad", ctypes.c_int32), ("pitch", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("z", ctypes.c_double), ("ox", ctypes.c_double),
+                ("oy", ctypes.c_double), ("band_auto", ctypes.c_int32), ("c_m", ctypes.c_double),
+                ("c_n", ctypes.c_double), ("w_m", ctypes.c_double), ("w_n", ctypes.c_double),
+                ("kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("tol", ctypes.c_double)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_pad", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("window", ctypes.c_int32), ("window_origin", ctypes.c_int32),
+                ("kernel_width", ctypes.c_int32), ("kernel_beta", ctypes.c_double),
+                ("tile", ctypes.c_int32), ("tiles", ctypes.c_int32),
+                ("band_lo_x", ctypes.c_int32), ("band_hi_x", ctypes.c_int32),
+                ("band_lo_y", ctypes.c_int32), ("band_hi_y", ctypes.c_int32),
+                ("points", ctypes.c_int64), ("records", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "nuasm_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Params), ctypes.c_int64,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "nuasm1_execute": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "nuasm2_execute": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "nufresnel_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "nuasm_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "nuasm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "nuasm_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
+    "nuasm_band": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int32)]),
+    "nuasm_kernel_shape": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "nuasm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "nuasm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64)]),
+    "nuasm_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnuasm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _strerror(code: int) -> str:
+    try:
+        return lib().nuasm_strerror(int(code)).decode()
+    except Exception:  # pragma: no cover
+        return "?"
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise NuasmError(code, where)
+
+
+# ---------------------------------------------------------------- marshalling
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _numel(a) -> int:
+    return int(a.numel()) if _is_torch(a) else int(a.size)
+
+
+def _dtype_name(a) -> str:
+    return str(a.dtype).replace("torch.", "")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:  # pragma: no cover
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_params(n, pitch, lam, z, ox=0.0, oy=0.0, kind="asm", prec="f32", tol=0.0, n_pad=0,
+                band=None) -> Params:
+    """nuasm_params_t from keyword values; band = (c_m, c_n, w_m, w_n) or None (auto rule)."""
+    p = Params()
+    p.n, p.n_pad, p.pitch, p.lambda_, p.z, p.ox, p.oy = int(n), int(n_pad), pitch, lam, z, ox, oy
+    if band is None:
+        p.band_auto = 1
+    else:
+        p.band_auto = 0
+        p.c_m, p.c_n, p.w_m, p.w_n = (float(v) for v in band)
+    p.kind = KIND_ASM if kind in ("asm", KIND_ASM) else KIND_FRESNEL
+    p.prec = PREC_F64 if prec in ("f64", PREC_F64) else PREC_F32_F64PHASE
+    p.tol = float(tol)
+    return p
+
+
+class Plan:
+    """Owner of a nuasm_plan_t handle."""
+
+    def __init__(self, handle: ctypes.c_void_p, params: Params, m: int):
+        self.handle = handle
+        self.params = params
+        self.m = m
+        self.n = params.n
+        self.complex_dtype = "complex128" if params.prec == PREC_F64 else "complex64"
+
+    @property
+    def _h(self):
+        if not self.handle:
+            raise RuntimeError("plan has been destroyed")
+        return self.handle
+
+    def info(self) -> dict:
+        return nuasm_plan_info(self)
+
+    def destroy(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            _check(lib().nuasm_destroy(h), "nuasm_destroy")
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _expect(a, count: int, dtype: str, what: str):
+    if a is None:
+        if count == 0:
+            return
+        raise ValueError(f"{what} is required")
+    if _numel(a) != count:
+        raise ValueError(f"{what} must have {count} elements, got {_numel(a)}")
+    if _dtype_name(a) != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {_dtype_name(a)}")
+
+
+def nuasm_plan(params: Params, x, y, w=None, stream=None) -> Plan:
+    """Build a plan (see nuasm_plan in include/nuasm.h).  x, y, w: float64 arrays of M entries."""
+    m = 0 if x is None else _numel(x)
+    for a, name in ((x, "x"), (y, "y"), (w, "w")):
+        if a is not None:
+            _expect(a, m, "float64", name)
+    h = ctypes.c_void_p()
+    _check(lib().nuasm_plan(ctypes.byref(h), ctypes.byref(params), m, _ptr(x), _ptr(y), _ptr(w),
+                            _stream(stream)), "nuasm_plan")
+    return Plan(h, params, m)
+
+
+def nuasm1_execute(plan: Plan, c, u2, stream=None):
+    """NU-ASM_1: c (M complex) -> u2 (N*N complex)."""
+    _expect(c, plan.m, plan.complex_dtype, "c")
+    _expect(u2, plan.n * plan.n, plan.complex_dtype, "u2")
+    _check(lib().nuasm1_execute(plan._h, _ptr(c), _ptr(u2), _stream(stream)), "nuasm1_execute")
+    return u2
+
+
+def nuasm2_execute(plan: Plan, u1, v, stream=None):
+    """NU-ASM_2: u1 (N*N complex) -> v (M complex)."""
+    _expect(u1, plan.n * plan.n, plan.complex_dtype, "u1")
+    _expect(v, plan.m, plan.complex_dtype, "v")
+    _check(lib().nuasm2_execute(plan._h, _ptr(u1), _ptr(v), _stream(stream)), "nuasm2_execute")
+    return v
+
+
+def nufresnel_execute(plan: Plan, type_: int, inp, out, stream=None):
+    """NU-FRE_1 (type 1: M -> N*N) or NU-FRE_2 (type 2: N*N -> M)."""
+    if type_ == 1:
+        _expect(inp, plan.m, plan.complex_dtype, "in")
+        _expect(out, plan.n * plan.n, plan.complex_dtype, "out")
+    elif type_ == 2:
+        _expect(inp, plan.n * plan.n, plan.complex_dtype, "in")
+        _expect(out, plan.m, plan.complex_dtype, "out")
+    _check(lib().nufresnel_execute(plan._h, int(type_), _ptr(inp), _ptr(out), _stream(stream)),
+           "nufresnel_execute")
+    return out
+
+
+def nuasm_destroy(plan: Plan):
+    plan.destroy()
+
+
+def nuasm_strerror(code: int) -> str:
+    return _strerror(code)
+
+
+def nuasm_plan_info(plan: Plan) -> dict:
+    info = PlanInfo()
+    _check(lib().nuasm_plan_info(plan._h, ctypes.byref(info)), "nuasm_plan_info")
+    return {name: getattr(info, name) for name, _ in PlanInfo._fields_}
+
+
+def nuasm_band(params: Params) -> tuple:
+    out = (ctypes.c_int32 * 4)()
+    _check(lib().nuasm_band(ctypes.byref(params), out), "nuasm_band")
+    return tuple(int(v) for v in out)
+
+
+def nuasm_kernel_shape(tol: float, prec: int) -> tuple:
+    w = ctypes.c_int32()
+    b = ctypes.c_double()
+    _check(lib().nuasm_kernel_shape(float(tol), int(prec), ctypes.byref(w), ctypes.byref(b)),
+           "nuasm_kernel_shape")
+    return int(w.value), float(b.value)
+
+
+def nuasm_profile_enable(plan: Plan, enable: bool = True):
+    _check(lib().nuasm_profile_enable(plan._h, 1 if enable else 0), "nuasm_profile_enable")
+
+
+def nuasm_profile_read(plan: Plan) -> dict:
+    """{stage name: (total ms, launches)} since the last read."""
+    n = len(STAGES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    _check(lib().nuasm_profile_read(plan._h, ms, cnt), "nuasm_profile_read")
+    return {lib().nuasm_stage_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(n)}

@@ -1,0 +1,216 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Tolerances (relative L2 over all outputs or the stated sample):
+* F32 plans (complex64 data, FP64-derived phase): 1e-5;
+* F64 plans (complex128, default NUFFT tolerance 1e-12): 1e-10.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1308_6644_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-5, "f64": 1e-10}
+CDT = {"f32": np.complex64, "f64": np.complex128}
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1308_6644_gb300 as pkg
+    return pkg
+
+
+def _t(a, dev="cuda"):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def run_gpu(P, kind, type_, prec, n, pitch, lam, z, x, y, values, ox=0.0, oy=0.0, w=None, n_pad=0,
+            band=None, tol=0.0, host=False):
+    """One plan + one execute; returns the output as a numpy array."""
+    import torch
+    params = P.make_params(n, pitch, lam, z, ox=ox, oy=oy, kind=kind, prec=prec, tol=tol,
+                           n_pad=n_pad, band=band)
+    cdt = CDT[prec]
+    tdt = torch.complex64 if prec == "f32" else torch.complex128
+    if host:
+        xs, ys = np.ascontiguousarray(x, np.float64), np.ascontiguousarray(y, np.float64)
+        ws = None if w is None else np.ascontiguousarray(w, np.float64)
+    else:
+        xs, ys = _t(np.asarray(x, np.float64)), _t(np.asarray(y, np.float64))
+        ws = None if w is None else _t(np.asarray(w, np.float64))
+    plan = P.nuasm_plan(params, xs, ys, ws)
+    try:
+        inp = np.ascontiguousarray(np.asarray(values).astype(cdt).reshape(-1))
+        if type_ == 1:
+            out = np.zeros(n * n, cdt) if host else torch.zeros(n * n, dtype=tdt, device="cuda")
+        else:
+            out = np.zeros(len(x), cdt) if host else torch.zeros(len(x), dtype=tdt, device="cuda")
+        src = inp if host else _t(inp)
+        if kind == "asm":
+            (P.nuasm1_execute if type_ == 1 else P.nuasm2_execute)(plan, src, out)
+        else:
+            P.nufresnel_execute(plan, type_, src, out)
+        torch.cuda.synchronize()
+        res = out if host else out.cpu().numpy()
+    finally:
+        plan.destroy()
+    return res.reshape(n, n) if type_ == 1 else res
+
+
+def run_oracle(kind, type_, n, pitch, lam, z, x, y, values, ox=0.0, oy=0.0, w=None, n_pad=0, band=None,
+               prec="f32"):
+    p = dict(n=n, n_pad=n_pad or 2 * n, pitch=pitch, lam=lam, z=z, ox=ox, oy=oy, kind=kind, band=band)
+    vals = np.asarray(values).astype(CDT[prec]).astype(np.complex128)   # the inputs the GPU saw
+    if type_ == 1:
+        return O.diffraction_type1(x, y, vals.reshape(-1), p, weights=w)
+    return O.diffraction_type2(vals.reshape(n, n), x, y, p)
+
+
+def random_case(seed, n, m, pitch=10e-6, type_=1):
+    rng = np.random.default_rng(seed)
+    half = 0.5 * n * pitch
+    x = WL.clamp_window(rng.uniform(-half, half, m), n, pitch)
+    y = WL.clamp_window(rng.uniform(-half, half, m), n, pitch)
+    if type_ == 1:
+        vals = rng.normal(size=m) + 1j * rng.normal(size=m)
+    else:
+        vals = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    return x, y, vals
+
+
+# ---------------------------------------------------------------- small end-to-end parity
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("kind", ["asm", "fresnel"])
+@pytest.mark.parametrize("type_", [1, 2])
+@pytest.mark.parametrize("n", [16, 64])
+def test_random_points_parity(P, prec, kind, type_, n):
+    m = 700 if n == 64 else 150
+    x, y, vals = random_case(11 + n + type_, n, m, type_=type_)
+    kw = dict(pitch=10e-6, lam=633e-9, z=0.03, ox=25e-6, oy=-12e-6)
+    got = run_gpu(P, kind, type_, prec, n, x=x, y=y, values=vals, **kw)
+    ref = run_oracle(kind, type_, n, x=x, y=y, values=vals, prec=prec, **kw)
+    assert O.rel_l2(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_nuasm1_dense_core_config(P, prec):
+    """NU-ASM_1, 64 x 64 jittered source with a 2x denser core (M = 4864),
+    10 um pitch, 633 nm, z = 5 cm, N' = 128, auto band."""
+    w = WL.nuasm1_small()
+    got = run_gpu(P, "asm", 1, prec, w.n, w.pitch, w.lam, w.z, w.x, w.y, w.values)
+    ref = run_oracle("asm", 1, w.n, w.pitch, w.lam, w.z, w.x, w.y, w.values, prec=prec)
+    assert O.rel_l2(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_nuasm2_graded_small(P, prec):
+    """NU-ASM_2 with the graded destination (4 -> 16 um) and off-axis offset at N = 128."""
+    w = WL.nuasm2_graded(n=128)
+    got = run_gpu(P, "asm", 2, prec, w.n, w.pitch, w.lam, w.z, w.x, w.y, w.values, ox=w.ox, oy=w.oy)
+    ref = run_oracle("asm", 2, w.n, w.pitch, w.lam, w.z, w.x, w.y, w.values, ox=w.ox, oy=w.oy, prec=prec)
+    assert O.rel_l2(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("type_", [1, 2])
+def test_fresnel_clustered_small(P, type_):
+    """NU-FRE with clustered points and a Gaussian-beam input at N = 128."""
+    w = WL.fresnel_clustered(type_=type_, n=128, m=6000)
+    got = run_gpu(P, "fresnel", type_, "f32", w.n, w.pitch, w.lam, w.z, w.x, w.y, w.values)
+    ref = run_oracle("fresnel", type_, w.n, w.pitch, w.lam, w.z, w.x, w.y, w.values)
+    assert O.rel_l2(got, ref) < TOL["f32"]
+
+
+# ---------------------------------------------------------------- options and edge cases
+def test_weights_type1(P):
+    x, y, vals = random_case(21, 32, 400)
+    wts = np.random.default_rng(3).uniform(0.5, 2.0, len(x))
+    kw = dict(pitch=10e-6, lam=633e-9, z=0.02)
+    got = run_gpu(P, "asm", 1, "f64", 32, x=x, y=y, values=vals, w=wts, **kw)
+    ref = run_oracle("asm", 1, 32, x=x, y=y, values=vals, w=wts, prec="f64", **kw)
+    assert O.rel_l2(got, ref) < TOL["f64"]
+
+
+@pytest.mark.parametrize("type_", [1, 2])
+def test_explicit_band_and_larger_padding(P, type_):
+    x, y, vals = random_case(22 + type_, 32, 300, type_=type_)
+    kw = dict(pitch=10e-6, lam=633e-9, z=0.04, ox=30e-6, n_pad=128, band=(3.0, -2.0, 40.0, 30.0))
+    got = run_gpu(P, "asm", type_, "f64", 32, x=x, y=y, values=vals, **kw)
+    ref = run_oracle("asm", type_, 32, x=x, y=y, values=vals, prec="f64", **kw)
+    assert O.rel_l2(got, ref) < TOL["f64"]
+
+
+def test_window_edges_and_single_tile(P):
+    """Points exactly on the lower window edge, just inside the upper edge and
+    all crowded into one tile."""
+    n, pitch = 64, 10e-6
+    half = 0.5 * n * pitch
+    edge = np.array([-half, half * (1 - 1e-12), -half, 0.0, half * (1 - 1e-12)])
+    rng = np.random.default_rng(5)
+    cx = rng.uniform(-3e-6, 3e-6, 200)
+    x = np.concatenate([edge, cx])
+    y = np.concatenate([np.roll(edge, 2), rng.uniform(-3e-6, 3e-6, 200)])
+    vals = rng.normal(size=len(x)) + 1j * rng.normal(size=len(x))
+    kw = dict(pitch=pitch, lam=633e-9, z=0.01)
+    for t in (1, 2):
+        v = vals if t == 1 else rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+        got = run_gpu(P, "asm", t, "f64", n, x=x, y=y, values=v, **kw)
+        ref = run_oracle("asm", t, n, x=x, y=y, values=v, prec="f64", **kw)
+        assert O.rel_l2(got, ref) < TOL["f64"]
+
+
+def test_zero_points(P):
+    import torch
+    params = P.make_params(32, 10e-6, 633e-9, 0.02)
+    plan = P.nuasm_plan(params, None, None)
+    try:
+        u2 = torch.full((32 * 32,), 1 + 1j, dtype=torch.complex64, device="cuda")
+        P.nuasm1_execute(plan, None, u2)
+        u1 = torch.ones(32 * 32, dtype=torch.complex64, device="cuda")
+        P.nuasm2_execute(plan, u1, None)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(u2).item() == 0
+    finally:
+        plan.destroy()
+
+
+def test_out_of_window_point_is_rejected(P):
+    n, pitch = 32, 10e-6
+    x = np.array([0.0, 0.5 * n * pitch])      # x / pitch == N/2 is outside [-N/2, N/2)
+    y = np.zeros(2)
+    with pytest.raises(P.NuasmError) as ei:
+        P.nuasm_plan(P.make_params(n, pitch, 633e-9, 0.01), _t(x), _t(y))
+    assert ei.value.code == 2
+
+
+def test_kind_mismatch_is_rejected(P):
+    import torch
+    x, y, _ = random_case(1, 32, 10)
+    plan = P.nuasm_plan(P.make_params(32, 10e-6, 633e-9, 0.01, kind="fresnel"), _t(x), _t(y))
+    try:
+        with pytest.raises(P.NuasmError):
+            P.nuasm1_execute(plan, torch.zeros(10, dtype=torch.complex64, device="cuda"),
+                             torch.zeros(1024, dtype=torch.complex64, device="cuda"))
+    finally:
+        plan.destroy()
+
+
+@pytest.mark.parametrize("type_", [1, 2])
+def test_host_buffers_match_device_buffers(P, type_):
+    x, y, vals = random_case(31, 64, 500, type_=type_)
+    kw = dict(pitch=10e-6, lam=633e-9, z=0.02)
+    a = run_gpu(P, "asm", type_, "f32", 64, x=x, y=y, values=vals, host=True, **kw)
+    b = run_gpu(P, "asm", type_, "f32", 64, x=x, y=y, values=vals, host=False, **kw)
+    assert O.rel_l2(a, b) < 1e-6
+
+
+def test_type2_is_deterministic(P):
+    x, y, vals = random_case(41, 64, 2000, type_=2)
+    kw = dict(pitch=10e-6, lam=633e-9, z=0.02)
+    a = run_gpu(P, "asm", 2, "f32", 64, x=x, y=y, values=vals, **kw)
+    b = run_gpu(P, "asm", 2, "f32", 64, x=x, y=y, values=vals, **kw)
+    assert np.array_equal(a, b)
