@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Benchmark: non-uniform points/s of one NU-ASM_2 solve on GB300.
+
+Workload (synthetic, seeded): uniform 1024 x 1024 source at 8 um holding a
+binary-amplitude random-phase pattern, zero-padded to 2048^2; 1,048,576
+destination points whose local pitch grades from 4 um at the centre to 16 um
+at the edge (radial warp, +-0.3 local-pitch jitter); lambda = 532 nm,
+z = 20 cm, off-axis offset (1 mm, 0); complex64 data with FP64-derived phase.
+
+A step is one full solve (column FFT, fused row pass with deconvolution and
+transfer function, folded column inverse FFT, tile interpolation) on inputs
+already resident in HBM.  L2 (129 MB) is flushed by writing a 256 MB buffer
+before every step; each step is timed with CUDA events on the solve's stream
+and `value` = points x steps / summed step time (max over ranks).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (weak scaling,
+no data-path collective).  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "non-uniform points/s per NUASM solve at rel-L2≤1e-5 vs FP64; served p50/p99"
+UNIT = "points/s"
+WORKLOAD = "nuasm2_graded_n1024_m1048576_lambda532nm_z20cm_o1mm"
+CPU_SAMPLE_POINTS = 16384
+FLUSH_BYTES = 256 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload():
+    from paper_1308_6644_gb300 import workloads as WL
+    return WL.nuasm2_graded(seed=1002, n=1024, pitch=8e-6)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [s.strip() for s in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.remove(self.path)
+        note = None
+        if not sm:
+            # timed region shorter than the sampling interval: one query right at its end
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=10).stdout
+                f = [s.strip() for s in out.split(",")]
+                sm, smax = [float(f[1])], [float(f[2])]
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+                note = "one sample at the end of the timed region (shorter than the 100 ms interval)"
+            except Exception:
+                return None
+        rec = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+               "samples": len(sm)}
+        if note:
+            rec["note"] = note
+        return rec
+
+
+# ---------------------------------------------------------------- roofline bookkeeping
+def stage_bytes(info: dict, m: int) -> dict:
+    """Algorithmic HBM bytes per launch of each type-2 stage (complex64 = 8 B):
+    each input read once, each output written once, records 16 B per point."""
+    n, np_, W = info["n"], info["n_pad"], info["window"]
+    return {
+        "col_fwd": 8 * (n * n + np_ * n),
+        "row_t2": 8 * (np_ * n + np_ * W),
+        "col_inv_fold": 8 * (np_ * W + W * W),
+        "interp": 8 * W * W + 16 * m + 8 * m,
+    }
+
+
+KERNEL_OF_STAGE = {"col_fwd": "col_kernel<float2, 2>", "row_t2": "row_t2_kernel<float2>",
+                   "col_inv_fold": "col_kernel<float2, 3>", "interp": "interp_kernel<float, 8>"}
+STAGE_SOURCES = {"col_fwd": ["passes.cu", "fft_engine.cuh"], "row_t2": ["passes.cu", "fft_engine.cuh"],
+                 "col_inv_fold": ["passes.cu", "fft_engine.cuh"], "interp": ["gridding.cu"]}
+
+
+def source_hash(stage: str) -> str:
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES[stage] + ["common.cuh"]:
+        with open(os.path.join(ROOT, "paper_1308_6644_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(stage: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    rec = t.get(stage)
+    if not rec or rec.get("source_hash") != source_hash(stage):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def oracle_sample(wl, n_sample: int, rng_seed: int = 5):
+    """Time the FP64 oracle on a bounded sample: the full spectrum G(k) H(k)
+    (separable DFT matrix products) plus the direct NUFFT_2 sum at n_sample
+    points; returns timings and the sampled outputs."""
+    import oracle as O
+    rng = np.random.default_rng(rng_seed)
+    idx = np.sort(rng.choice(wl.m, n_sample, replace=False))
+    n, n_pad = wl.n, 2 * wl.n
+    u1 = wl.values.astype(np.complex64).astype(np.complex128)
+    t0 = time.perf_counter()
+    g = O.uniform_dft(u1, n_pad)
+    h = O.asm_transfer(n, n_pad, wl.pitch, wl.lam, wl.z, wl.ox, wl.oy)
+    a = g * h / float(n_pad) ** 2
+    t1 = time.perf_counter()
+    v = O.nudft_type2(a, wl.x[idx] / wl.pitch, wl.y[idx] / wl.pitch, n_pad)
+    t2 = time.perf_counter()
+    return idx, v, t1 - t0, t2 - t1
+
+
+def cpu_baseline(wl, n_sample: int = CPU_SAMPLE_POINTS):
+    idx, v, t_spec, t_pts = oracle_sample(wl, n_sample)
+    full = t_spec + t_pts * wl.m / n_sample
+    rec = {"value": wl.m / full, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": (f"FP64 direct NUDFT oracle: full spectrum ({t_spec:.2f} s) + {n_sample} of "
+                      f"{wl.m} destination points ({t_pts:.2f} s), extrapolated to all points")}
+    return rec, idx, v
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if ws > 1 and rank != 0:
+        return 0
+    wl = _workload()
+    n_sample = 4096
+    for _ in range(args.warmup):
+        oracle_sample(wl, n_sample)
+    times = []
+    for _ in range(args.steps):
+        _, _, t_spec, t_pts = oracle_sample(wl, n_sample)
+        times.append(t_spec + t_pts * wl.m / n_sample)
+    tot = float(sum(times))
+    value = wl.m * args.steps / tot
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": wl.n, "n_pad": 2 * wl.n, "points": wl.m},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step: full spectrum + {n_sample} destination points, "
+                                       f"extrapolated to {wl.m} points"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1308_6644_gb300 import _build
+    _build.build()
+    import paper_1308_6644_gb300 as P
+
+    wl = _workload()
+    params = P.make_params(wl.n, wl.pitch, wl.lam, wl.z, ox=wl.ox, oy=wl.oy, kind="asm", prec="f32")
+    stream = torch.cuda.current_stream(dev)
+    x = torch.from_numpy(wl.x).to(dev)
+    y = torch.from_numpy(wl.y).to(dev)
+    t_plan0 = time.perf_counter()
+    plan = P.nuasm_plan(params, x, y, stream=stream)
+    plan_s = time.perf_counter() - t_plan0
+    info = plan.info()
+    u1 = torch.from_numpy(wl.values.astype(np.complex64).reshape(-1)).to(dev)
+    v = torch.empty(wl.m, dtype=torch.complex64, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def solve():
+        P.nuasm2_execute(plan, u1, v, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        solve()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        solve()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    total_ms = float(step_ms.sum())
+    points = float(wl.m * args.steps)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        pts = torch.tensor([points], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(pts)
+        points = float(pts.item())
+    value = points / (total_ms * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    hu1 = torch.from_numpy(wl.values.astype(np.complex64).reshape(-1)).pin_memory()
+    hv = torch.empty(wl.m, dtype=torch.complex64).pin_memory()
+    for _ in range(2):
+        P.nuasm2_execute(plan, hu1, hv, stream=stream)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    aux_steps = min(args.steps, 200)
+    for k in range(aux_steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        P.nuasm2_execute(plan, hu1, hv, stream=stream)
+        e.record(stream)
+        e.synchronize()
+        e2e_ms.append(s.elapsed_time(e))
+    e2e_value = wl.m / (np.mean(e2e_ms) * 1e-3)
+
+    # per-stage times for the roofline (separate pass, events on the solve stream)
+    P.nuasm_profile_enable(plan, True)
+    P.nuasm_profile_read(plan)
+    for _ in range(aux_steps):
+        flush.zero_()
+        solve()
+    torch.cuda.synchronize()
+    prof = P.nuasm_profile_read(plan)
+    P.nuasm_profile_enable(plan, False)
+    sbytes = stage_bytes(info, wl.m)
+    stages = {}
+    for name, b in sbytes.items():
+        ms, cnt = prof[name]
+        if cnt:
+            avg = ms / cnt
+            stages[name] = {"ms": avg, "gbs": b / (avg * 1e-3) / 1e9, "alg_bytes": b}
+    dom = max(stages, key=lambda s: stages[s]["ms"])
+    peak, peak_kind = hbm_peak()
+    ach = stages[dom]["gbs"]
+    roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": measured_traffic(dom), "kernel": KERNEL_OF_STAGE[dom],
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "stages": {k: {"ms": round(s["ms"], 5), "GB/s": round(s["gbs"], 1),
+                               "frac": round(s["gbs"] / peak, 3)} for k, s in stages.items()}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": wl.n, "n_pad": info["n_pad"], "points": wl.m,
+                       "kernel_width": info["kernel_width"], "precision": "complex64 + FP64-derived phase",
+                       "l2": "flushed (256 MB write) before every step", "plan_s": round(plan_s, 3),
+                       "parallelism": f"replicas x{ws}"},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hu1.numel() * 8),
+                    "d2h_bytes_per_step": int(hv.numel() * 8)},
+            "gpu_launches": 4 * args.steps,
+            "roofline": roofline,
+            "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rec, idx, ref = cpu_baseline(wl)
+        got = v.cpu().numpy()[idx]
+        line["cpu_baseline"] = rec
+        line["rel_l2_vs_fp64_sample"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    plan.destroy()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -109,7 +109,7 @@ void release(nuasm_plan_s* P) {
                 }
         delete X;
     }
-    void* ptrs[] = {P->d.tables, P->d.rec, P->d.wrec_f, P->d.wrec_d, P->d.tile_off, P->d.tile_home,
+    void* ptrs[] = {P->d.tables, P->d.rec, P->d.wpt, P->d.tile_off, P->d.tile_home,
                     P->d.win, P->d.bufA, P->d.bufB, P->d.stage_in, P->d.stage_out, P->d.err};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -280,6 +280,10 @@ nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m, c
     HostTables ht{};
     build_tables(rp, P->g, &ht);
     P->rc = ht.rc;
+    P->poly = ht.poly;
+    if (rp.kind != NUASM_KIND_ASM || rp.z == 0.0) P->nonsep_mode = 0;
+    else if (P->f64 || ht.rmax <= 0.5) P->nonsep_mode = 1;
+    else P->nonsep_mode = 2;
     cudaError_t e = upload_tables(P, ht, st);
     free_tables(&ht);
     if (e != cudaSuccess) return bail(cuda_status(e));

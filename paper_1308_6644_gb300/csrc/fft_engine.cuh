@@ -1,26 +1,25 @@
-// Block-level Stockham FFT engine.
+// Block-level Stockham FFT engine with a compile-time radix schedule.
 //
-// One CTA transforms C independent sequences of power-of-two length L with
-// E elements per thread held in registers.  Each pass applies radix-R
-// butterflies (R = 16, 8, 4 or 2) in the self-sorting Stockham form
+// One CTA transforms 2^LOGC independent sequences of length L = 2^LOGL with E
+// elements per thread held in registers (blockDim.x == L * 2^LOGC / E).  Each
+// pass applies radix-R butterflies in the self-sorting Stockham form
 // (decimation in time, natural order in and out): butterfly j reads elements
 // j + r L/R, multiplies input r by exp(DIR 2 pi i (j mod Ns) r / (Ns R)),
 // applies the length-R DFT and writes (j div Ns) Ns R + (j mod Ns) + r Ns,
-// with Ns the product of the radices of the earlier passes.
+// Ns being the product of the earlier radices.  The schedule is LOGL / log2(E)
+// passes of radix E followed by one smaller-radix pass for the remainder.
 //
-// The first pass reads its inputs through a load functor (global memory,
-// another shared buffer, or values computed on the fly: zero padding, folds,
-// pre-twiddles) and the last pass writes through a store functor (pruned,
-// scattered or fused epilogues), so neither the padded input nor the full
-// output ever touches shared memory.  Intermediate passes exchange through
-// one padded shared buffer: every thread loads all its inputs, the block
-// synchronises, then every thread writes, so the buffer is used in place.
+// The first pass reads through a load functor (global memory, another shared
+// buffer, or values computed on the fly: zero padding, folds, pre-twiddles)
+// and the last pass writes through a store functor (pruned, scattered or fused
+// epilogues), so neither the padded input nor the full output touches shared
+// memory.  Intermediate passes exchange through one padded shared buffer used
+// in place: all threads load, the block synchronises, then all threads store.
 //
-// Layout of the shared buffer: ROWMAJOR = true stores sequence c contiguously
-// (index c L + p; consecutive threads take consecutive j, which makes row
-// loads from global memory coalesced); ROWMAJOR = false interleaves the
-// sequences (index p C + c; consecutive threads take consecutive c, which
-// makes loads of C adjacent columns of a row-major array coalesced).
+// Layouts: ROWMAJOR = true stores sequence c contiguously (index c L + p;
+// consecutive threads take consecutive j).  ROWMAJOR = false interleaves the
+// sequences (index p C + c; consecutive threads take consecutive c), which
+// makes C adjacent columns of a row-major array coalesced.
 #pragma once
 
 #include "common.cuh"
@@ -29,6 +28,10 @@ namespace nuasm {
 
 // ---------------------------------------------------------------- DFTs in registers
 template <int R, int DIR, typename V> struct Dft;
+
+template <int DIR, typename V> struct Dft<1, DIR, V> {
+    __device__ __forceinline__ static void run(V*) {}
+};
 
 template <int DIR, typename V> struct Dft<2, DIR, V> {
     __device__ __forceinline__ static void run(V* v) {
@@ -56,9 +59,7 @@ template <int DIR, typename V> __device__ __forceinline__ V w8_1(V a) {
     return DIR < 0 ? CTraits<V>::make((a.x + a.y) * r, (a.y - a.x) * r)
                    : CTraits<V>::make((a.x - a.y) * r, (a.x + a.y) * r);
 }
-template <int DIR, typename V> __device__ __forceinline__ V w8_3(V a) {
-    return mul_i<DIR>(w8_1<DIR>(a));
-}
+template <int DIR, typename V> __device__ __forceinline__ V w8_3(V a) { return mul_i<DIR>(w8_1<DIR>(a)); }
 
 template <int DIR, typename V> struct Dft<8, DIR, V> {
     __device__ __forceinline__ static void run(V* v) {
@@ -77,35 +78,35 @@ template <int DIR, typename V> struct Dft<8, DIR, V> {
     }
 };
 
-// multiply by exp(DIR 2 pi i e / 16), e in [0, 9]
-template <int DIR, typename V> __device__ __forceinline__ V w16(V a, int e) {
+// multiply by exp(DIR 2 pi i e / 16) for the exponents a 4 x 4 split needs
+template <int DIR, int EXP, typename V> __device__ __forceinline__ V w16(V a) {
     using S = typename CTraits<V>::real;
     const S c1 = S(0.92387953251128675613), s1 = S(0.38268343236508977173);
-    V w;
-    switch (e) {
-        case 0: return a;
-        case 1: w = CTraits<V>::make(c1, DIR * s1); break;
-        case 2: return w8_1<DIR>(a);
-        case 3: w = CTraits<V>::make(s1, DIR * c1); break;
-        case 4: return mul_i<DIR>(a);
-        case 6: return w8_3<DIR>(a);
-        case 9: w = CTraits<V>::make(-c1, -DIR * s1); break;
-        default: w = CTraits<V>::make(S(1), S(0)); break;
-    }
-    return cmul(a, w);
+    if (EXP == 0) return a;
+    if (EXP == 2) return w8_1<DIR>(a);
+    if (EXP == 4) return mul_i<DIR>(a);
+    if (EXP == 6) return w8_3<DIR>(a);
+    if (EXP == 1) return cmul(a, CTraits<V>::make(c1, DIR * s1));
+    if (EXP == 3) return cmul(a, CTraits<V>::make(s1, DIR * c1));
+    return cmul(a, CTraits<V>::make(-c1, -DIR * s1));   // EXP == 9
 }
 
 template <int DIR, typename V> struct Dft<16, DIR, V> {
+    template <int N1> __device__ __forceinline__ static void col(const V* v, V* a) {
+        V t[4] = {v[N1], v[N1 + 4], v[N1 + 8], v[N1 + 12]};
+        Dft<4, DIR, V>::run(t);
+        a[N1] = t[0];
+        a[4 + N1] = w16<DIR, N1>(t[1]);
+        a[8 + N1] = w16<DIR, 2 * N1>(t[2]);
+        a[12 + N1] = w16<DIR, 3 * N1>(t[3]);
+    }
     __device__ __forceinline__ static void run(V* v) {
         // 16 = 4 x 4: DFT4 over n2 for each n1, twiddle w16^(n1 k2), DFT4 over n1
         V a[16];
-#pragma unroll
-        for (int n1 = 0; n1 < 4; ++n1) {
-            V t[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
-            Dft<4, DIR, V>::run(t);
-#pragma unroll
-            for (int k2 = 0; k2 < 4; ++k2) a[4 * k2 + n1] = w16<DIR>(t[k2], n1 * k2);
-        }
+        col<0>(v, a);
+        col<1>(v, a);
+        col<2>(v, a);
+        col<3>(v, a);
 #pragma unroll
         for (int k2 = 0; k2 < 4; ++k2) {
             V t[4] = {a[4 * k2], a[4 * k2 + 1], a[4 * k2 + 2], a[4 * k2 + 3]};
@@ -116,50 +117,49 @@ template <int DIR, typename V> struct Dft<16, DIR, V> {
     }
 };
 
-template <int R> struct Log2;
-template <> struct Log2<2> { static constexpr int v = 1; };
-template <> struct Log2<4> { static constexpr int v = 2; };
-template <> struct Log2<8> { static constexpr int v = 3; };
-template <> struct Log2<16> { static constexpr int v = 4; };
+template <int R> struct Log2 { static constexpr int v = R <= 1 ? 0 : 1 + Log2<R / 2>::v; };
+template <> struct Log2<1> { static constexpr int v = 0; };
 
 // ---------------------------------------------------------------- one pass
-template <typename V, int DIR, int E, int R, bool ROWMAJOR, class LoadF, class StoreF>
-__device__ __forceinline__ void stockham_pass(V* __restrict__ sm, int logL, int logC, int logNs,
-                                              bool first, bool last, const V* __restrict__ tw,
-                                              int logLt, LoadF& load, StoreF& store) {
+// Twiddle table: tw[t] = exp(-2 pi i t / 2L), t in [0, 2L).
+template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, int LR, int LOGNS, bool FIRST,
+          bool LAST, class LoadF, class StoreF>
+__device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __restrict__ tw, LoadF& load,
+                                              StoreF& store) {
+    constexpr int R = 1 << LR;
     constexpr int NB = E / R;
-    constexpr int LR = Log2<R>::v;
-    const int P = blockDim.x;
+    constexpr int L = 1 << LOGL;
+    constexpr int LDR = L >> LR;
+    constexpr int NS = 1 << LOGNS;
+    constexpr int C = 1 << LOGC;
+    constexpr int P = (L * C) / E;
+    constexpr int SH = LOGL + 1 - LOGNS - LR;
     const int tid = threadIdx.x;
-    const int L = 1 << logL;
-    const int LdR = L >> LR;
-    const int Ns = 1 << logNs;
     V v[E];
     int jj[NB], cc[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int beta = tid + b * P;
         int c, j;
-        if (ROWMAJOR) { j = beta & (LdR - 1); c = beta >> (logL - LR); }
-        else { c = beta & ((1 << logC) - 1); j = beta >> logC; }
+        if (ROWMAJOR) { j = beta & (LDR - 1); c = beta >> (LOGL - LR); }
+        else { c = beta & (C - 1); j = beta >> LOGC; }
         jj[b] = j;
         cc[b] = c;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int p = j + r * LdR;
-            if (first) v[b * R + r] = load(p, c);
-            else v[b * R + r] = sm[spad<V>(ROWMAJOR ? (c << logL) + p : (p << logC) + c)];
+            const int p = j + r * LDR;
+            if (FIRST) v[b * R + r] = load(p, c);
+            else v[b * R + r] = sm[spad<V>(ROWMAJOR ? (c << LOGL) + p : (p << LOGC) + c)];
         }
     }
-    if (!first) __syncthreads();
+    if (!FIRST) __syncthreads();
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        if (logNs > 0) {
-            const int k = jj[b] & (Ns - 1);
-            const int sh = logLt - logNs - LR;
+        if (LOGNS > 0) {
+            const int k = jj[b] & (NS - 1);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                V w = __ldg(&tw[(k * r) << sh]);
+                V w = __ldg(&tw[(k * r) << SH]);
                 if (DIR > 0) w = cconj(w);
                 v[b * R + r] = cmul(v[b * R + r], w);
             }
@@ -169,52 +169,39 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, int logL, int 
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int j = jj[b], c = cc[b];
-        const int k = j & (Ns - 1);
+        const int k = j & (NS - 1);
         const int base = ((j - k) << LR) + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int p = base + r * Ns;
-            if (last) store(p, c, v[b * R + r]);
-            else sm[spad<V>(ROWMAJOR ? (c << logL) + p : (p << logC) + c)] = v[b * R + r];
+            const int p = base + r * NS;
+            if (LAST) store(p, c, v[b * R + r]);
+            else sm[spad<V>(ROWMAJOR ? (c << LOGL) + p : (p << LOGC) + c)] = v[b * R + r];
         }
     }
-    if (!last) __syncthreads();
+    if (!LAST) __syncthreads();
 }
 
-// ---------------------------------------------------------------- full transform
-// Requires blockDim.x == (L * C) / E.  The caller must synchronise before the
-// call if `sm` still holds data other threads read.  DIR = -1: forward
-// (exp(-2 pi i ...)), +1: inverse, unnormalised.  `tw` holds exp(-2 pi i t / Lt)
-// for t in [0, Lt), Lt = 2^logLt >= L.
-template <typename V, int DIR, int E, bool ROWMAJOR, class LoadF, class StoreF>
-__device__ void block_fft(V* __restrict__ sm, int logL, int logC, const V* __restrict__ tw,
-                          int logLt, LoadF load, StoreF store) {
+// passes of radix E, then the remainder (LOGL mod log2 E) as one smaller-radix pass
+template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, int I, class LoadF, class StoreF>
+__device__ __forceinline__ void run_passes(V* __restrict__ sm, const V* __restrict__ tw, LoadF& load,
+                                           StoreF& store) {
     constexpr int LE = Log2<E>::v;
-    int rem = logL, logNs = 0;
-    while (rem > 0) {
-        const int lr = rem >= LE ? LE : rem;
-        const bool first = logNs == 0, last = rem == lr;
-        switch (lr) {
-            case 4:
-                stockham_pass<V, DIR, E, (E >= 16 ? 16 : 2), ROWMAJOR>(sm, logL, logC, logNs, first,
-                                                                       last, tw, logLt, load, store);
-                break;
-            case 3:
-                stockham_pass<V, DIR, E, (E >= 8 ? 8 : 2), ROWMAJOR>(sm, logL, logC, logNs, first, last,
-                                                                     tw, logLt, load, store);
-                break;
-            case 2:
-                stockham_pass<V, DIR, E, 4, ROWMAJOR>(sm, logL, logC, logNs, first, last, tw, logLt,
-                                                      load, store);
-                break;
-            default:
-                stockham_pass<V, DIR, E, 2, ROWMAJOR>(sm, logL, logC, logNs, first, last, tw, logLt,
-                                                      load, store);
-                break;
-        }
-        logNs += lr;
-        rem -= lr;
+    constexpr int NFULL = LOGL / LE;
+    constexpr int REM = LOGL % LE;
+    constexpr int NPASS = NFULL + (REM ? 1 : 0);
+    if constexpr (I < NPASS) {
+        constexpr int LR = I < NFULL ? LE : REM;
+        stockham_pass<V, DIR, E, LOGL, LOGC, ROWMAJOR, LR, I * LE, I == 0, I == NPASS - 1>(sm, tw, load, store);
+        run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, I + 1>(sm, tw, load, store);
     }
+}
+
+// Full transform.  DIR = -1: forward (exp(-2 pi i ...)), +1: inverse, unnormalised.
+// The caller synchronises before the call if `sm` still holds data that other
+// threads read.
+template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, class LoadF, class StoreF>
+__device__ __forceinline__ void block_fft(V* __restrict__ sm, const V* __restrict__ tw, LoadF load, StoreF store) {
+    run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, 0>(sm, tw, load, store);
 }
 
 }  // namespace nuasm

@@ -116,10 +116,9 @@ __global__ void bin_scan_kernel(const int* __restrict__ home_cnt, const int* __r
 }
 
 template <typename Rec, typename S>
-__global__ void bin_scatter_kernel(const double* __restrict__ x, const double* __restrict__ y,
-                                   const double* __restrict__ w, BinArgs a, const int* __restrict__ off,
-                                   const int* __restrict__ home_cnt, int* __restrict__ cur_home,
-                                   int* __restrict__ cur_dup, Rec* __restrict__ rec, S* __restrict__ wrec) {
+__global__ void bin_scatter_kernel(const double* __restrict__ x, const double* __restrict__ y, BinArgs a,
+                                   const int* __restrict__ off, const int* __restrict__ home_cnt,
+                                   int* __restrict__ cur_home, int* __restrict__ cur_dup, Rec* __restrict__ rec) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < a.m; i += int64_t(gridDim.x) * blockDim.x) {
         PointSplit s = split_point(x[i], y[i], a);
         if (!s.ok) continue;
@@ -135,9 +134,41 @@ __global__ void bin_scatter_kernel(const double* __restrict__ x, const double* _
             if (q == 0) pos = off[t[0]] + atomicAdd(&cur_home[t[0]], 1);
             else pos = off[t[q]] + home_cnt[t[q]] + atomicAdd(&cur_dup[t[q]], 1);
             rec[pos] = r;
-            if (wrec) wrec[pos] = S(w[i]);
         }
     }
+}
+
+// Counting sort of each tile's home records by first-tap cell (row-major in
+// the tile), so that a warp's interpolation gathers touch neighbouring cells
+// (distinct shared-memory banks) and its output writes cluster.  One CTA per
+// tile; reads the unsorted copy `src`, writes `dst`.  Halo duplicates are
+// copied unchanged.
+template <typename Rec>
+__global__ void sort_tile_kernel(const Rec* __restrict__ src, Rec* __restrict__ dst, const int* __restrict__ off,
+                                 const int* __restrict__ home, int T, int ntx) {
+    extern __shared__ int bins[];   // T*T counters
+    const int tile = blockIdx.x;
+    const int ty = tile / ntx, tx = tile - ty * ntx;
+    const int x0 = tx * T, y0 = ty * T, nb = T * T;
+    const int b = off[tile], e = off[tile + 1], eh = b + home[tile];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) bins[i] = 0;
+    __syncthreads();
+    for (int i = b + threadIdx.x; i < eh; i += blockDim.x) {
+        const uint32_t cell = src[i].cell;
+        atomicAdd(&bins[(int(cell >> 16) - y0) * T + int(cell & 0xffffu) - x0], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // exclusive scan (T*T <= 4096 entries, once per plan)
+        int run = 0;
+        for (int i = 0; i < nb; ++i) { const int c = bins[i]; bins[i] = run; run += c; }
+    }
+    __syncthreads();
+    for (int i = b + threadIdx.x; i < eh; i += blockDim.x) {
+        const Rec r = src[i];
+        const int key = (int(r.cell >> 16) - y0) * T + int(r.cell & 0xffffu) - x0;
+        dst[b + atomicAdd(&bins[key], 1)] = r;
+    }
+    for (int i = eh + threadIdx.x; i < e; i += blockDim.x) dst[i] = src[i];
 }
 
 // --------------------------------------------------------------- kernel values
@@ -153,6 +184,30 @@ template <> __device__ __forceinline__ double es_eval<double>(double t, double i
     return exp(beta * (sqrt(u) - 1.0));
 }
 
+// Tap weights of one axis: polynomial form for FP32 (Horner in x = 2f - 1,
+// coefficients zero-padded to DMAX so the loop is fully unrolled), the
+// exponential itself for FP64.
+template <int WMAX> __device__ __forceinline__ void tap_weights(float f, int w, float beta, const KernelPoly& kp,
+                                                                 float* out) {
+    constexpr int DMAX = WMAX + 3 < kPolyMaxD ? WMAX + 3 : kPolyMaxD;
+    (void)w;
+    (void)beta;
+    const float x = fmaf(2.f, f, -1.f);
+#pragma unroll
+    for (int i = 0; i < WMAX; ++i) {
+        float acc = kp.c[i][DMAX - 1];
+#pragma unroll
+        for (int k = DMAX - 2; k >= 0; --k) acc = fmaf(acc, x, kp.c[i][k]);
+        out[i] = acc;
+    }
+}
+template <int WMAX> __device__ __forceinline__ void tap_weights(double f, int w, double beta, const KernelPoly&,
+                                                                 double* out) {
+    const double ihw = 2.0 / w, hw = 0.5 * w;
+#pragma unroll
+    for (int i = 0; i < WMAX; ++i) out[i] = i < w ? es_eval<double>(double(i) + f - hw, ihw, beta) : 0.0;
+}
+
 template <typename S> struct VecOf;
 template <> struct VecOf<float> { using type = float2; };
 template <> struct VecOf<double> { using type = double2; };
@@ -165,9 +220,10 @@ struct GridArgs {
 // --------------------------------------------------------------- spreading (type 1)
 template <typename S, int WMAX>
 __global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::type* __restrict__ rec,
-                                                     const int* __restrict__ off, const S* __restrict__ wrec,
+                                                     const int* __restrict__ off, const double* __restrict__ wpt,
                                                      const typename VecOf<S>::type* __restrict__ c,
-                                                     typename VecOf<S>::type* __restrict__ win, GridArgs a) {
+                                                     typename VecOf<S>::type* __restrict__ win, GridArgs a,
+                                                     const KernelPoly kp) {
     using V = typename VecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
     const int T = a.T, w = a.w;
@@ -178,21 +234,16 @@ __global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::ty
     const int x0 = tx * T, y0 = ty * T;
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) { sre[i] = S(0); sim[i] = S(0); }
     __syncthreads();
-    const S beta = S(a.beta), ihw = S(2) / S(w), hw = S(w) / S(2);
+    const S beta = S(a.beta);
     const int b = off[tile], e = off[tile + 1];
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
         const auto r = rec[i];
         const int lx = int(r.cell & 0xffffu) - x0, ly = int(r.cell >> 16) - y0;
         V val = c[r.j];
-        if (wrec) { const S wt = wrec[i]; val.x *= wt; val.y *= wt; }
+        if (wpt) { const S wt = S(wpt[r.j]); val.x *= wt; val.y *= wt; }
         S wx[WMAX], wy[WMAX];
-#pragma unroll
-        for (int q = 0; q < WMAX; ++q) {
-            if (q < w) {
-                wx[q] = es_eval<S>(S(q) + S(r.fx) - hw, ihw, beta);
-                wy[q] = es_eval<S>(S(q) + S(r.fy) - hw, ihw, beta);
-            }
-        }
+        tap_weights<WMAX>(S(r.fx), w, beta, kp, wx);
+        tap_weights<WMAX>(S(r.fy), w, beta, kp, wy);
         const int ya = max(0, -ly), yb = min(w, T - ly);
         const int xa = max(0, -lx), xb = min(w, T - lx);
 #pragma unroll
@@ -227,7 +278,8 @@ template <typename S, int WMAX>
 __global__ void __launch_bounds__(256) interp_kernel(const typename RecOf<S>::type* __restrict__ rec,
                                                      const int* __restrict__ off, const int* __restrict__ home,
                                                      const typename VecOf<S>::type* __restrict__ win,
-                                                     typename VecOf<S>::type* __restrict__ v, GridArgs a) {
+                                                     typename VecOf<S>::type* __restrict__ v, GridArgs a,
+                                                     const KernelPoly kp) {
     using V = typename VecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
     V* tl = reinterpret_cast<V*>(smem_raw);
@@ -245,19 +297,14 @@ __global__ void __launch_bounds__(256) interp_kernel(const typename RecOf<S>::ty
         tl[i] = val;
     }
     __syncthreads();
-    const S beta = S(a.beta), ihw = S(2) / S(w), hw = S(w) / S(2);
+    const S beta = S(a.beta);
     const int b = off[tile], e = b + home[tile];
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
         const auto r = rec[i];
         const int lx = int(r.cell & 0xffffu) - x0, ly = int(r.cell >> 16) - y0;
         S wx[WMAX], wy[WMAX];
-#pragma unroll
-        for (int q = 0; q < WMAX; ++q) {
-            if (q < w) {
-                wx[q] = es_eval<S>(S(q) + S(r.fx) - hw, ihw, beta);
-                wy[q] = es_eval<S>(S(q) + S(r.fy) - hw, ihw, beta);
-            }
-        }
+        tap_weights<WMAX>(S(r.fx), w, beta, kp, wx);
+        tap_weights<WMAX>(S(r.fy), w, beta, kp, wy);
         S ar = S(0), ai = S(0);
 #pragma unroll
         for (int qy = 0; qy < WMAX; ++qy) {
@@ -303,10 +350,9 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     const size_t sm = size_t(2) * a.T * a.T * sizeof(S);
     cudaError_t e = set_smem(spread_kernel<S, WMAX>, sm);
     if (e != cudaSuccess) return e;
-    const S* wr = sizeof(S) == 4 ? reinterpret_cast<const S*>(P->d.wrec_f) : reinterpret_cast<const S*>(P->d.wrec_d);
     spread_kernel<S, WMAX><<<P->g.ntiles, 256, sm, st>>>(
-        static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, wr,
-        static_cast<const V*>(c), static_cast<V*>(P->d.win), a);
+        static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.wpt,
+        static_cast<const V*>(c), static_cast<V*>(P->d.win), a, P->poly);
     return cudaGetLastError();
 }
 
@@ -320,7 +366,7 @@ cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     interp_kernel<S, WMAX><<<P->g.ntiles, 256, sm, st>>>(
         static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.tile_home,
-        static_cast<const V*>(P->d.win), static_cast<V*>(v), a);
+        static_cast<const V*>(P->d.win), static_cast<V*>(v), a, P->poly);
     return cudaGetLastError();
 }
 
@@ -368,20 +414,37 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
     const size_t rsz = P->f64 ? sizeof(RecD) : sizeof(RecF);
     if ((e = cudaMalloc(&P->d.rec, rsz * size_t(total > 0 ? total : 1))) != cudaSuccess) return fail(e);
     P->device_bytes += int64_t(rsz) * (total > 0 ? total : 1);
-    if (w) {
-        if (P->f64) e = cudaMalloc(&P->d.wrec_d, sizeof(double) * size_t(total > 0 ? total : 1));
-        else e = cudaMalloc(&P->d.wrec_f, sizeof(float) * size_t(total > 0 ? total : 1));
+    if (w && P->m > 0) {
+        if ((e = cudaMalloc(&P->d.wpt, sizeof(double) * size_t(P->m))) != cudaSuccess) return fail(e);
+        P->device_bytes += int64_t(sizeof(double)) * P->m;
+        e = cudaMemcpyAsync(P->d.wpt, w, sizeof(double) * size_t(P->m), cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return fail(e);
-        P->device_bytes += int64_t(P->f64 ? 8 : 4) * (total > 0 ? total : 1);
     }
     if (P->m > 0) {
         if (P->f64)
-            bin_scatter_kernel<RecD, double><<<blocks, 256, 0, st>>>(x, y, w, a, P->d.tile_off, home_cnt, cur_home,
-                                                                     cur_dup, static_cast<RecD*>(P->d.rec), P->d.wrec_d);
+            bin_scatter_kernel<RecD, double><<<blocks, 256, 0, st>>>(x, y, a, P->d.tile_off, home_cnt, cur_home,
+                                                                     cur_dup, static_cast<RecD*>(P->d.rec));
         else
-            bin_scatter_kernel<RecF, float><<<blocks, 256, 0, st>>>(x, y, w, a, P->d.tile_off, home_cnt, cur_home,
-                                                                    cur_dup, static_cast<RecF*>(P->d.rec), P->d.wrec_f);
+            bin_scatter_kernel<RecF, float><<<blocks, 256, 0, st>>>(x, y, a, P->d.tile_off, home_cnt, cur_home,
+                                                                    cur_dup, static_cast<RecF*>(P->d.rec));
         if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    }
+    if (P->m > 0 && total > 0) {
+        void* tmp = nullptr;
+        if ((e = cudaMallocAsync(&tmp, rsz * size_t(total), st)) != cudaSuccess) return fail(e);
+        e = cudaMemcpyAsync(tmp, P->d.rec, rsz * size_t(total), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) {
+            const size_t smb = sizeof(int) * size_t(g.T) * g.T;
+            if (P->f64)
+                sort_tile_kernel<RecD><<<nt, 256, smb, st>>>(static_cast<const RecD*>(tmp), static_cast<RecD*>(P->d.rec),
+                                                             P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+            else
+                sort_tile_kernel<RecF><<<nt, 256, smb, st>>>(static_cast<const RecF*>(tmp), static_cast<RecF*>(P->d.rec),
+                                                             P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+            e = cudaGetLastError();
+        }
+        cudaFreeAsync(tmp, st);
+        if (e != cudaSuccess) return fail(e);
     }
     e = cudaFreeAsync(cnt, st);
     if (e != cudaSuccess) return cuda_status(e);

@@ -158,10 +158,10 @@ nuasm_status validate(const nuasm_params_t& p0, int64_t m, nuasm_params_t* out) 
     if (std::isnan(p.tol) || p.tol < 0 || p.tol > 0.1) return NUASM_EINVAL;
     if (p.tol == 0) p.tol = p.prec == NUASM_PREC_F64 ? 1e-12 : 1e-6;
     if (p.tol < 1e-15) return NUASM_EINVAL;
-    if (p.n_pad == 0) p.n_pad = 2 * p.n;
-    if (p.n_pad < 2 * p.n || !is_pow2(p.n_pad)) return NUASM_EINVAL;
+    if (p.n_pad != 0 && (p.n_pad < 2 * p.n || !is_pow2(p.n_pad))) return NUASM_EINVAL;
     // what this build implements: power-of-two planes, N' <= 8192 (F32) / 4096 (F64)
     if (!is_pow2(p.n) || p.n < 16) return NUASM_EUNSUPPORTED;
+    if (p.n_pad == 0) p.n_pad = 2 * p.n;
     const int np_max = p.prec == NUASM_PREC_F64 ? 4096 : 8192;
     if (p.n_pad > np_max) return NUASM_EUNSUPPORTED;
     *out = p;
@@ -200,6 +200,8 @@ Geometry make_geometry(const nuasm_params_t& p) {
     band_range(p, g.band);
     return g;
 }
+
+static void fit_kernel_poly(const Geometry& g, KernelPoly* kp);
 
 void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t) {
     const int np = g.np, G = g.G, n = g.n;
@@ -277,10 +279,59 @@ void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t) {
         t->s[q] = p.lambda * p.lambda * f * f;
     }
     t->rc = p.z / (2.0 * p.lambda);
+    t->rmax = 0.0;
+    if (p.kind == NUASM_KIND_ASM && p.z != 0.0) {
+        // largest kept s = lambda^2 |f|^2 sits at the band corner farthest from DC
+        double sx = 0.0, sy = 0.0;
+        for (int q = 0; q < np; ++q) {
+            const int k = q < np / 2 ? q : q - np;
+            if (in_band(p, np, k, 0) && t->s[q] > sx) sx = t->s[q];
+            if (in_band(p, np, k, 1) && t->s[q] > sy) sy = t->s[q];
+        }
+        const double sm = sx + sy;
+        const double qm = sm >= 1.0 ? 1.0 : sm / (1.0 + std::sqrt(1.0 - sm));
+        t->rmax = std::fabs(t->rc) * qm * qm;
+    }
+    fit_kernel_poly(g, &t->poly);
     for (int i = 0; i < G; ++i) {
         cd v = cis_ratio(-i, G);
         t->tw[2 * i] = v.real();
         t->tw[2 * i + 1] = v.imag();
+    }
+}
+
+// Chebyshev interpolation of each tap phi(i + f - w/2), f in [0, 1), at
+// Chebyshev nodes of x = 2f - 1, converted to monomial coefficients in x (the
+// coefficients stay O(1), so Horner's rule in FP32 is as accurate as direct
+// evaluation of the exponential).
+static void fit_kernel_poly(const Geometry& g, KernelPoly* kp) {
+    std::memset(kp, 0, sizeof(*kp));
+    int d = g.w + 2;
+    if (d > kPolyMaxD - 1) d = kPolyMaxD - 1;
+    kp->deg = d;
+    const int K = 2 * d + 2;
+    std::vector<double> xn(K), tj(d + 1);
+    for (int k = 0; k < K; ++k) xn[k] = std::cos(M_PI * (k + 0.5) / K);
+    // monomial coefficients of the Chebyshev polynomials T_0..T_d
+    std::vector<std::vector<double>> T(d + 1, std::vector<double>(d + 1, 0.0));
+    T[0][0] = 1.0;
+    if (d >= 1) T[1][1] = 1.0;
+    for (int j = 2; j <= d; ++j)
+        for (int m = 0; m <= d; ++m)
+            T[j][m] = (m > 0 ? 2.0 * T[j - 1][m - 1] : 0.0) - T[j - 2][m];
+    for (int i = 0; i < g.w && i < kPolyMaxW; ++i) {
+        std::vector<double> cheb(d + 1, 0.0);
+        for (int k = 0; k < K; ++k) {
+            const double f = 0.5 * (xn[k] + 1.0);
+            const double val = es_kernel(i + f - 0.5 * g.w, g.w, g.beta);
+            for (int j = 0; j <= d; ++j) cheb[j] += val * std::cos(j * M_PI * (k + 0.5) / K);
+        }
+        for (int j = 0; j <= d; ++j) cheb[j] *= (j == 0 ? 1.0 : 2.0) / K;
+        for (int m = 0; m <= d; ++m) {
+            double acc = 0.0;
+            for (int j = m; j <= d; ++j) acc += cheb[j] * T[j][m];
+            kp->c[i][m] = float(acc);
+        }
     }
 }
 

@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/nuasm.h"
+#include "nuasm.h"
 
 namespace nuasm {
 
@@ -21,13 +21,23 @@ struct Geometry {
     int band[4];           // inclusive kept-mode ranges lo_x, hi_x, lo_y, hi_y
 };
 
+// Piecewise-polynomial form of the spreading kernel: tap i of a point with
+// fractional offset f in [0, 1) has weight sum_k c[i][k] x^k, x = 2f - 1.
+constexpr int kPolyMaxW = 16, kPolyMaxD = 16;
+struct KernelPoly {
+    float c[kPolyMaxW][kPolyMaxD];
+    int deg;
+};
+
 // Host tables in FP64 (complex as re/im pairs), natural N'-bin order.
 struct HostTables {
     // per-axis separable factors for type 1 and type 2, length N' each
     double* t1x; double* t1y; double* t2x; double* t2y;   // 2*N' doubles each
     double* s;        // lambda^2 f_k^2 per bin (ASM), length N'
     double rc;        // z / (2 lambda)  (ASM non-separable phase scale)
+    double rmax;      // largest |r| = |rc| q^2 over kept modes (0 when there is no such term)
     double* tw;       // exp(-2 pi i t / G), t in [0, G): 2*G doubles
+    KernelPoly poly;  // FP32 Horner coefficients of the kernel taps
 };
 
 struct PlanDevice {
@@ -36,8 +46,7 @@ struct PlanDevice {
     void* s = nullptr;          // float2 (hi, lo) per bin (F32) or double (F64)
     void* tw = nullptr;         // twiddles, G complex
     void* rec = nullptr;        // binned point records
-    float* wrec_f = nullptr;    // optional weights in record order (F32)
-    double* wrec_d = nullptr;   // optional weights in record order (F64)
+    double* wpt = nullptr;      // optional per-point weights, in point order
     int* tile_off = nullptr;    // ntiles + 1 offsets into rec
     int* tile_home = nullptr;   // home-record count per tile
     void* win = nullptr;        // W x Wp fine-grid window
@@ -58,6 +67,8 @@ struct nuasm_plan_s {
     bool has_w = false;
     bool f64 = false;
     double rc = 0.0;            // z / (2 lambda)
+    int nonsep_mode = 0;        // ASM non-separable phase: 0 none, 1 plain, 2 double-float
+    nuasm::KernelPoly poly{};   // kernel taps as polynomials (F32 gridding)
     int64_t device_bytes = 0;
     nuasm::PlanDevice d;
     // profiling

@@ -1,0 +1,393 @@
+// FFT passes of the NU-ASM / NU-FRE pipeline (kernel templates; instantiated
+// per precision and per N' in passes_f32.cu / passes_f64.cu).
+//
+// Every transform here has length N' (the padded plane size).  The length-2N'
+// transforms of the oversampled NUFFT grid are split into their even and odd
+// halves, each an N'-point transform:
+//   forward (window -> modes, type 1):  B(2k')   = FFT_N'[x(n) + x(n+N')](k'),
+//                                       B(2k'+1) = FFT_N'[(x(n) - x(n+N')) e^{-2 pi i n/2N'}](k');
+//   inverse (modes -> window, type 2):  y(2u')   = IFFT_N'[Y(q)](u'),
+//                                       y(2u'+1) = IFFT_N'[Y(q) e^{2 pi i p(q)/2N'}](u'),
+// where p(q) is the 2N'-grid bin of natural N'-bin q.  Only the modes
+// k in [-N'/2, N'/2) and the window rows [0, W) are ever produced.
+//
+// Type 1 (Eq. 6):  window --col_fwd_fold--> A (N' x W) --row_t1--> B (N' x N)
+//                  --col_inv--> u2 (N x N).  row_t1 fuses the forward row
+//                  transform, the deconvolution, H (Eq. 4 / Eq. 5) and the
+//                  inverse row transform.
+// Type 2 (Eq. 9):  u1 --col_fwd--> B (N' x N) --row_t2--> A (N' x W)
+//                  --col_inv_fold--> window.
+//
+// The non-separable part of the ASM phase is evaluated per mode:
+//   z sqrt(1/lambda^2 - |f|^2) = z/lambda - (z lambda/2)|f|^2 - (z/(2 lambda)) q^2,
+//   q = s / (1 + sqrt(1 - s)),  s = lambda^2 |f|^2,
+// an exact rearrangement whose first two terms are separable (folded into the
+// per-axis tables in FP64 on the host) and whose last term r is small.  r is
+// computed in FP64 (F64 plans), in plain FP32 when the plan's largest |r| is
+// at most 1/2 cycle (absolute error below 1e-7 cycles), else in double-float
+// FP32; it is reduced mod 1 and passed to sincospi.  Evanescent modes
+// (s >= 1) are zeroed.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fft_engine.cuh"
+#include "nuasm_internal.h"
+
+namespace nuasm {
+namespace passes {
+
+// --------------------------------------------------------------- launch configuration
+template <typename V> struct Prec;
+template <> struct Prec<float2> {
+    static constexpr bool f64 = false;
+    static constexpr int col_e = 16, col_budget = 8192;   // elements per thread / per CTA
+    static constexpr int regs = 64;
+};
+template <> struct Prec<double2> {
+    static constexpr bool f64 = true;
+    static constexpr int col_e = 8, col_budget = 4096;
+    static constexpr int regs = 128;
+};
+
+template <typename V, int LOGNP> struct RowCfg {
+    static constexpr int NP = 1 << LOGNP;
+    static constexpr int LOGROWS = LOGNP >= 11 ? 0 : (11 - LOGNP > LOGNP ? LOGNP : 11 - LOGNP);
+    static constexpr int ROWS = 1 << LOGROWS;
+    // merged even/odd engines (two sequences per row in one pass sequence)
+    static constexpr bool MERGE = !Prec<V>::f64 && LOGNP <= 12;
+    static constexpr int EF = (!Prec<V>::f64 && LOGNP >= 13) ? 16 : 8;   // single-sequence engines
+    static constexpr int EM = 16;                                         // merged engines
+    static constexpr int P = (NP * ROWS) / EF;
+    static constexpr int MINB = (65536 / (P * Prec<V>::regs)) > 0 ? 65536 / (P * Prec<V>::regs) : 1;
+    static constexpr int SEQ = MERGE ? 2 * ROWS : ROWS;                  // sequences in the work buffer
+    static size_t smem() { return (size_t(spad_size<V>(NP * SEQ)) + size_t(NP) * ROWS) * sizeof(V); }
+};
+
+template <typename V, int LOGNP> struct ColCfg {
+    static constexpr int NP = 1 << LOGNP;
+    static constexpr int E = Prec<V>::col_e;
+    static constexpr int CRAW = Prec<V>::col_budget / NP;
+    static constexpr int C = CRAW > 16 ? 16 : (CRAW < 1 ? 1 : CRAW);
+    static constexpr int LOGC = Log2<C>::v;
+    static constexpr int P = (NP * C) / E;
+    static constexpr int MINB = (65536 / (P * Prec<V>::regs)) > 0 ? 65536 / (P * Prec<V>::regs) : 1;
+    static size_t smem() { return size_t(spad_size<V>(NP * C)) * sizeof(V); }
+};
+
+template <typename V> struct STable;
+template <> struct STable<float2> { using type = float2; };
+template <> struct STable<double2> { using type = double; };
+
+struct RowArgs {
+    int n, W, Wp;
+    int nonsep;            // 0: none (Fresnel, z = 0); 1: plain (FP32 or FP64); 2: double-float FP32
+    double rc;             // z / (2 lambda)
+    float rc_hi, rc_lo;
+};
+
+struct ColArgs {
+    int n, W, Wp;
+};
+
+// --------------------------------------------------------------- non-separable ASM factor
+__device__ __forceinline__ float2 nonsep_factor(const float2* __restrict__ s, int qx, int qy, const RowArgs& a) {
+    const float2 sa = __ldg(&s[qx]), sb = __ldg(&s[qy]);
+    float fr;
+    if (a.nonsep == 1) {
+        const float sv = sa.x + sb.x;
+        if (sv >= 1.f) return make_float2(0.f, 0.f);
+        const float q = sv / (1.f + sqrtf(1.f - sv));
+        const float r = a.rc_hi * q * q;
+        fr = r - rintf(r);
+    } else {
+        df sv = df_add({sa.x, sa.y}, {sb.x, sb.y});
+        if (sv.hi >= 1.f) return make_float2(0.f, 0.f);
+        df root = df_sqrt(df_add({1.f, 0.f}, {-sv.hi, -sv.lo}));
+        df q = df_div(sv, df_add({1.f, 0.f}, root));
+        df r = df_mul({a.rc_hi, a.rc_lo}, df_mul(q, q));
+        fr = (r.hi - rintf(r.hi)) + r.lo;
+    }
+    float sn, cs;
+    sincospif(-2.f * fr, &sn, &cs);
+    return make_float2(cs, sn);
+}
+
+__device__ __forceinline__ double2 nonsep_factor(const double* __restrict__ s, int qx, int qy, const RowArgs& a) {
+    const double sv = __ldg(&s[qx]) + __ldg(&s[qy]);
+    if (sv >= 1.0) return make_double2(0.0, 0.0);
+    const double q = sv / (1.0 + sqrt(1.0 - sv));
+    const double r = a.rc * q * q;
+    double sn, cs;
+    sincospi(-2.0 * (r - rint(r)), &sn, &cs);
+    return make_double2(cs, sn);
+}
+
+// M[c][q] *= Tx(q) Ty(r0 + c) E(q, r0 + c) for the CTA's rows
+template <typename V, int LOGNP, int ROWS, int P>
+__device__ __forceinline__ void apply_modes(V* __restrict__ M, int r0, const V* __restrict__ tx,
+                                            const V* __restrict__ ty,
+                                            const typename STable<V>::type* __restrict__ s, const RowArgs& a) {
+    constexpr int NP = 1 << LOGNP;
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < ROWS * NP; idx += P) {
+        const int c = idx >> LOGNP, q = idx & (NP - 1);
+        const int r = r0 + c;
+        V f = cmul(__ldg(&tx[q]), __ldg(&ty[r]));
+        if (a.nonsep && (f.x != 0 || f.y != 0)) f = cmul(f, nonsep_factor(s, q, r, a));
+        M[idx] = cmul(M[idx], f);
+    }
+}
+
+// --------------------------------------------------------------- type-1 row pass
+// One CTA = ROWS rows r of A (ky bin r): forward 2N' transform of the window
+// row restricted to the kept modes (two folded N'-point FFTs), multiply by
+// T1x(kx) T1y(ky) E(kx, ky), inverse N'-point FFT, keep the N outputs.
+template <typename V, int LOGNP>
+__global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
+    row_t1_kernel(const V* __restrict__ A, V* __restrict__ B, const V* __restrict__ tx, const V* __restrict__ ty,
+                  const typename STable<V>::type* __restrict__ s, const V* __restrict__ tw, RowArgs a) {
+    using Cf = RowCfg<V, LOGNP>;
+    constexpr int NP = Cf::NP, ROWS = Cf::ROWS, HALF = NP / 2;
+    extern __shared__ unsigned char smem_raw[];
+    V* S = reinterpret_cast<V*>(smem_raw);
+    V* M = S + spad_size<V>(NP * Cf::SEQ);
+    const int r0 = blockIdx.x * ROWS;
+    const int W = a.W, Wp = a.Wp;
+    const V zero = CTraits<V>::zero();
+
+    auto folded = [&](int row, int p, int sgn) -> V {
+        const V* x = A + (r0 + row) * Wp;
+        const V u = p < W ? x[p] : zero;
+        const V t = p + NP < W ? x[p + NP] : zero;
+        return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
+    };
+    auto put = [&](int row, int pk, int sgn, V v) {
+        const int pb = 2 * pk + sgn;
+        if (pb < HALF) M[row * NP + pb] = v;
+        else if (pb >= 3 * HALF) M[row * NP + pb - NP] = v;
+    };
+    if constexpr (Cf::MERGE) {
+        block_fft<V, -1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false>(
+            S, tw, [&](int p, int cs) { return folded(cs >> 1, p, cs & 1); },
+            [&](int pk, int cs, V v) { put(cs >> 1, pk, cs & 1, v); });
+    } else {
+#pragma unroll 1
+        for (int sgn = 0; sgn < 2; ++sgn)
+            block_fft<V, -1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
+                S, tw, [&](int p, int c) { return folded(c, p, sgn); },
+                [&](int pk, int c, V v) { put(c, pk, sgn, v); });
+    }
+    __syncthreads();
+    apply_modes<V, LOGNP, ROWS, Cf::P>(M, r0, tx, ty, s, a);
+    __syncthreads();
+    const int n = a.n;
+    block_fft<V, +1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
+        S, tw, [&](int p, int c) { return M[c * NP + p]; },
+        [&](int p, int c, V v) {
+            if (p < n) B[(r0 + c) * n + p] = v;
+        });
+}
+
+// --------------------------------------------------------------- type-2 row pass
+// One CTA = ROWS rows r of B (ky bin r, N values): forward N'-point FFT,
+// multiply by T2x T2y E, then the inverse 2N' transform onto the window row
+// (even and odd outputs as two N'-point FFTs), keeping the W window entries.
+template <typename V, int LOGNP>
+__global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
+    row_t2_kernel(const V* __restrict__ B, V* __restrict__ A, const V* __restrict__ tx, const V* __restrict__ ty,
+                  const typename STable<V>::type* __restrict__ s, const V* __restrict__ tw, RowArgs a) {
+    using Cf = RowCfg<V, LOGNP>;
+    constexpr int NP = Cf::NP, ROWS = Cf::ROWS, HALF = NP / 2;
+    extern __shared__ unsigned char smem_raw[];
+    V* S = reinterpret_cast<V*>(smem_raw);
+    V* M = S + spad_size<V>(NP * Cf::SEQ);
+    const int r0 = blockIdx.x * ROWS;
+    const int n = a.n, W = a.W, Wp = a.Wp;
+    const V zero = CTraits<V>::zero();
+    block_fft<V, -1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
+        S, tw, [&](int p, int c) { return p < n ? B[(r0 + c) * n + p] : zero; },
+        [&](int p, int c, V v) { M[c * NP + p] = v; });
+    __syncthreads();
+    apply_modes<V, LOGNP, ROWS, Cf::P>(M, r0, tx, ty, s, a);
+    __syncthreads();
+    auto get = [&](int row, int q, int sgn) -> V {
+        const V y = M[row * NP + q];
+        if (sgn == 0) return y;
+        const int pg = q < HALF ? q : q + NP;
+        return cmul(y, cconj(__ldg(&tw[pg])));
+    };
+    auto put = [&](int row, int k, int sgn, V v) {
+        const int u = 2 * k + sgn;
+        if (u < W) A[(r0 + row) * Wp + u] = v;
+    };
+    if constexpr (Cf::MERGE) {
+        block_fft<V, +1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false>(
+            S, tw, [&](int q, int cs) { return get(cs >> 1, q, cs & 1); },
+            [&](int k, int cs, V v) { put(cs >> 1, k, cs & 1, v); });
+    } else {
+#pragma unroll 1
+        for (int sgn = 0; sgn < 2; ++sgn)
+            block_fft<V, +1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
+                S, tw, [&](int q, int c) { return get(c, q, sgn); },
+                [&](int k, int c, V v) { put(c, k, sgn, v); });
+    }
+}
+
+// --------------------------------------------------------------- column passes
+enum ColMode { COL_FWD_FOLD = 0, COL_INV = 1, COL_FWD = 2, COL_INV_FOLD = 3 };
+
+// One CTA = C adjacent columns (blockIdx.x) and, for the folded modes, one
+// half (blockIdx.y: 0 even, 1 odd).
+template <typename V, int LOGNP, int MODE>
+__global__ void __launch_bounds__(ColCfg<V, LOGNP>::P, ColCfg<V, LOGNP>::MINB)
+    col_kernel(const V* __restrict__ src, V* __restrict__ dst, const V* __restrict__ tw, ColArgs a) {
+    using Cf = ColCfg<V, LOGNP>;
+    constexpr int NP = Cf::NP, HALF = NP / 2, C = Cf::C;
+    extern __shared__ unsigned char smem_raw[];
+    V* S = reinterpret_cast<V*>(smem_raw);
+    const int col0 = blockIdx.x * C;
+    const int sgn = blockIdx.y;
+    const int W = a.W, Wp = a.Wp, n = a.n;
+    const V zero = CTraits<V>::zero();
+    if constexpr (MODE == COL_FWD_FOLD) {
+        // src: window (W x Wp); dst: A (N' x Wp), kept modes in natural N'-bin rows
+        block_fft<V, -1, Cf::E, LOGNP, Cf::LOGC, false>(
+            S, tw,
+            [&](int p, int c) -> V {
+                const int col = col0 + c;
+                if (col >= W) return zero;
+                const V u = p < W ? src[p * Wp + col] : zero;
+                const V t = p + NP < W ? src[(p + NP) * Wp + col] : zero;
+                return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
+            },
+            [&](int pk, int c, V v) {
+                const int col = col0 + c;
+                const int pb = 2 * pk + sgn;
+                const int r = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
+                if (r >= 0 && col < W) dst[r * Wp + col] = v;
+            });
+    } else if constexpr (MODE == COL_INV) {
+        // src: B (N' x N); dst: u2 (N x N)
+        block_fft<V, +1, Cf::E, LOGNP, Cf::LOGC, false>(
+            S, tw, [&](int p, int c) { return src[p * n + col0 + c]; },
+            [&](int p, int c, V v) {
+                if (p < n) dst[p * n + col0 + c] = v;
+            });
+    } else if constexpr (MODE == COL_FWD) {
+        // src: u1 (N x N); dst: B (N' x N)
+        block_fft<V, -1, Cf::E, LOGNP, Cf::LOGC, false>(
+            S, tw, [&](int p, int c) { return p < n ? src[p * n + col0 + c] : zero; },
+            [&](int p, int c, V v) { dst[p * n + col0 + c] = v; });
+    } else {
+        // src: A (N' x Wp); dst: window (W x Wp)
+        block_fft<V, +1, Cf::E, LOGNP, Cf::LOGC, false>(
+            S, tw,
+            [&](int q, int c) -> V {
+                const int col = col0 + c;
+                if (col >= W) return zero;
+                const V y = src[q * Wp + col];
+                if (sgn == 0) return y;
+                const int pg = q < HALF ? q : q + NP;
+                return cmul(y, cconj(__ldg(&tw[pg])));
+            },
+            [&](int k, int c, V v) {
+                const int col = col0 + c;
+                const int u = 2 * k + sgn;
+                if (u < W && col < W) dst[u * Wp + col] = v;
+            });
+    }
+}
+
+// --------------------------------------------------------------- launchers
+template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
+inline RowArgs row_args(const nuasm_plan_s* P) {
+    RowArgs a{};
+    a.n = P->g.n;
+    a.W = P->g.W;
+    a.Wp = P->g.Wp;
+    a.nonsep = P->nonsep_mode;
+    a.rc = P->rc;
+    a.rc_hi = float(P->rc);
+    a.rc_lo = float(P->rc - double(a.rc_hi));
+    return a;
+}
+
+template <typename V, int LOGNP>
+cudaError_t launch_row(const nuasm_plan_s* P, int type, cudaStream_t st) {
+    using Cf = RowCfg<V, LOGNP>;
+    using ST = typename STable<V>::type;
+    const RowArgs a = row_args(P);
+    const size_t sm = Cf::smem();
+    const V* tw = static_cast<const V*>(P->d.tw);
+    const ST* s = static_cast<const ST*>(P->d.s);
+    const int blocks = Cf::NP / Cf::ROWS;
+    cudaError_t e;
+    if (type == 1) {
+        if ((e = set_smem(row_t1_kernel<V, LOGNP>, sm)) != cudaSuccess) return e;
+        row_t1_kernel<V, LOGNP><<<blocks, Cf::P, sm, st>>>(
+            static_cast<const V*>(P->d.bufA), static_cast<V*>(P->d.bufB), static_cast<const V*>(P->d.t1x),
+            static_cast<const V*>(P->d.t1y), s, tw, a);
+    } else {
+        if ((e = set_smem(row_t2_kernel<V, LOGNP>, sm)) != cudaSuccess) return e;
+        row_t2_kernel<V, LOGNP><<<blocks, Cf::P, sm, st>>>(
+            static_cast<const V*>(P->d.bufB), static_cast<V*>(P->d.bufA), static_cast<const V*>(P->d.t2x),
+            static_cast<const V*>(P->d.t2y), s, tw, a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename V, int LOGNP, int MODE>
+cudaError_t launch_col(const nuasm_plan_s* P, const void* src, void* dst, int ncols, int halves, cudaStream_t st) {
+    using Cf = ColCfg<V, LOGNP>;
+    const ColArgs a{P->g.n, P->g.W, P->g.Wp};
+    const size_t sm = Cf::smem();
+    cudaError_t e = set_smem(col_kernel<V, LOGNP, MODE>, sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((ncols + Cf::C - 1) / Cf::C, halves);
+    col_kernel<V, LOGNP, MODE><<<grid, Cf::P, sm, st>>>(static_cast<const V*>(src), static_cast<V*>(dst),
+                                                        static_cast<const V*>(P->d.tw), a);
+    return cudaGetLastError();
+}
+
+// all FFT stages of one precision and one N'
+template <typename V, int LOGNP> struct Stages {
+    static cudaError_t col_fwd_fold(const nuasm_plan_s* P, cudaStream_t s) {
+        return launch_col<V, LOGNP, COL_FWD_FOLD>(P, P->d.win, P->d.bufA, P->g.W, 2, s);
+    }
+    static cudaError_t col_inv(const nuasm_plan_s* P, void* u2, cudaStream_t s) {
+        return launch_col<V, LOGNP, COL_INV>(P, P->d.bufB, u2, P->g.n, 1, s);
+    }
+    static cudaError_t col_fwd(const nuasm_plan_s* P, const void* u1, cudaStream_t s) {
+        return launch_col<V, LOGNP, COL_FWD>(P, u1, P->d.bufB, P->g.n, 1, s);
+    }
+    static cudaError_t col_inv_fold(const nuasm_plan_s* P, cudaStream_t s) {
+        return launch_col<V, LOGNP, COL_INV_FOLD>(P, P->d.bufA, P->d.win, P->g.W, 2, s);
+    }
+    static cudaError_t row(const nuasm_plan_s* P, int type, cudaStream_t s) { return launch_row<V, LOGNP>(P, type, s); }
+};
+
+// dispatch on log2 N' (5 .. LOGMAX) at run time
+template <typename V, int LOGMAX, class F> cudaError_t dispatch(int lognp, F&& f) {
+    switch (lognp) {
+        case 5: return f(Stages<V, 5>{});
+        case 6: return f(Stages<V, 6>{});
+        case 7: return f(Stages<V, 7>{});
+        case 8: return f(Stages<V, 8>{});
+        case 9: return f(Stages<V, 9>{});
+        case 10: return f(Stages<V, 10>{});
+        case 11: return f(Stages<V, 11>{});
+        case 12: return f(Stages<V, 12>{});
+        case 13:
+            if constexpr (LOGMAX >= 13) return f(Stages<V, 13>{});
+            else return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace passes
+}  // namespace nuasm

@@ -1,0 +1,140 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every symbol include/nuasm.h declares, validates parameters
+before touching the device, and its host-only band and kernel queries agree
+with the oracle and the documented rules."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1308_6644_gb300 as pkg
+    return pkg
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "nuasm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b((?:nuasm|nufresnel)\w*)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("nuasm_plan", "nuasm1_execute", "nuasm2_execute", "nufresnel_execute",
+                     "nuasm_destroy", "nuasm_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(P):
+    lib = ctypes.CDLL(P.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(P):
+    from paper_1308_6644_gb300 import nuasm as B
+    assert set(_declared_functions()) <= set(B._SIGS)
+
+
+def test_strerror_names_every_status(P):
+    for code in range(7):
+        assert P.nuasm_strerror(code) not in ("unknown status", "")
+    assert P.nuasm_strerror(99) == "unknown status"
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(n=64, pitch=10e-6, lam=-1.0, z=0.1), 1),            # lambda <= 0
+    (dict(n=64, pitch=0.0, lam=633e-9, z=0.1), 1),            # pitch <= 0
+    (dict(n=63, pitch=10e-6, lam=633e-9, z=0.1), 1),          # odd N
+    (dict(n=64, pitch=10e-6, lam=633e-9, z=0.0, kind="fresnel"), 1),   # Fresnel z = 0
+    (dict(n=64, pitch=10e-6, lam=633e-9, z=0.1, n_pad=96), 1),  # N' not a power of two
+    (dict(n=64, pitch=10e-6, lam=633e-9, z=0.1, n_pad=64), 1),  # N' < 2N
+    (dict(n=64, pitch=10e-6, lam=633e-9, z=0.1, tol=0.5), 1),   # tolerance out of range
+    (dict(n=48, pitch=10e-6, lam=633e-9, z=0.1), 6),          # N not a power of two
+    (dict(n=8192, pitch=10e-6, lam=633e-9, z=0.1), 6),        # N' beyond 8192
+    (dict(n=4096, pitch=10e-6, lam=633e-9, z=0.1, prec="f64"), 6),
+])
+def test_plan_rejects_bad_parameters_before_device_work(P, kw, code):
+    x = np.zeros(4)
+    with pytest.raises(P.NuasmError) as ei:
+        P.nuasm_plan(P.make_params(**kw), x, x)
+    assert ei.value.code == code
+
+
+def test_plan_rejects_null_arguments(P):
+    from paper_1308_6644_gb300 import nuasm as B
+    lib = P.lib()
+    h = ctypes.c_void_p()
+    params = P.make_params(64, 10e-6, 633e-9, 0.1)
+    assert lib.nuasm_plan(None, ctypes.byref(params), 0, None, None, None, None) == 1
+    assert lib.nuasm_plan(ctypes.byref(h), None, 0, None, None, None, None) == 1
+    assert lib.nuasm_plan(ctypes.byref(h), ctypes.byref(params), 5, None, None, None, None) == 1
+    assert lib.nuasm_plan(ctypes.byref(h), ctypes.byref(params), -1, None, None, None, None) == 1
+    assert lib.nuasm1_execute(None, None, None, None) == 1
+    assert lib.nuasm_destroy(None) == 0
+    info = B.PlanInfo()
+    assert lib.nuasm_plan_info(None, ctypes.byref(info)) == 1
+
+
+@pytest.mark.parametrize("o", [0.0, 300e-6, -1.5e-3])
+@pytest.mark.parametrize("z", [0.05, -0.2, 0.0])
+def test_band_matches_oracle(P, o, z):
+    n, pitch, lam = 64, 10e-6, 633e-9
+    lo_x, hi_x, lo_y, hi_y = P.nuasm_band(P.make_params(n, pitch, lam, z, ox=o, oy=-o / 2))
+    k = O.modes(2 * n)
+    for lo, hi, oo in ((lo_x, hi_x, o), (lo_y, hi_y, -o / 2)):
+        mask = O.band_mask_1d(n, 2 * n, pitch, lam, z, oo)
+        if mask.any():
+            assert (lo, hi) == (k[mask].min(), k[mask].max())
+            assert mask[(k >= lo) & (k <= hi)].all()     # the kept set is an interval
+        else:
+            assert lo > hi
+
+
+def test_explicit_band_matches_oracle(P):
+    lo_x, hi_x, lo_y, hi_y = P.nuasm_band(P.make_params(32, 10e-6, 633e-9, 0.01, band=(2.0, -3.5, 10.0, 7.0)))
+    k = O.modes(64)
+    mx = O.band_mask_1d(32, 64, 10e-6, 633e-9, 0.01, 0.0, 2.0, 10.0)
+    my = O.band_mask_1d(32, 64, 10e-6, 633e-9, 0.01, 0.0, -3.5, 7.0)
+    assert (lo_x, hi_x) == (k[mx].min(), k[mx].max())
+    assert (lo_y, hi_y) == (k[my].min(), k[my].max())
+
+
+def test_fresnel_band_is_full(P):
+    assert P.nuasm_band(P.make_params(32, 10e-6, 633e-9, 1.0, kind="fresnel")) == (-32, 31, -32, 31)
+
+
+@pytest.mark.parametrize("tol,prec,w", [(0, 0, 7), (0, 1, 13), (1e-6, 0, 7), (1e-3, 0, 4), (1e-11, 1, 12),
+                                        (1e-9, 1, 10), (1e-15, 1, 16)])
+def test_kernel_width_rule(P, tol, prec, w):
+    width, beta = P.nuasm_kernel_shape(tol, prec)
+    assert width == w and abs(beta - 2.30 * w) < 1e-12
+
+
+def test_kernel_shape_rejects_bad_input(P):
+    with pytest.raises(P.NuasmError):
+        P.nuasm_kernel_shape(0.5, 0)
+    with pytest.raises(P.NuasmError):
+        P.nuasm_kernel_shape(1e-6, 7)
+
+
+def test_binding_checks_shapes_and_dtypes(P):
+    plan = P.Plan(ctypes.c_void_p(1), P.make_params(16, 10e-6, 633e-9, 0.01), 10)
+    plan.handle = None          # never reaches the library
+    from paper_1308_6644_gb300 import nuasm as B
+    with pytest.raises(ValueError):
+        B._expect(np.zeros(9, np.complex64), 10, "complex64", "c")
+    with pytest.raises(TypeError):
+        B._expect(np.zeros(10, np.complex128), 10, "complex64", "c")
+    with pytest.raises(RuntimeError):
+        plan.info()
