@@ -53,9 +53,7 @@ double es_kernel(double t, int w, double beta) {
 }
 
 // Gauss-Legendre nodes/weights on [-1, 1] (Newton on the three-term recurrence).
-void gauss_legendre(int n, std::vector<double>* x, std::vector<double>* wt) {
-    x->assign(n, 0.0);
-    wt->assign(n, 0.0);
+void gauss_legendre(int n, double* x, double* wt) {
     for (int i = 0; i < n; ++i) {
         double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
         double dp = 1.0;
@@ -71,8 +69,8 @@ void gauss_legendre(int n, std::vector<double>* x, std::vector<double>* wt) {
             z -= dz;
             if (std::fabs(dz) < 1e-16) break;
         }
-        (*x)[i] = z;
-        (*wt)[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        x[i] = z;
+        wt[i] = 2.0 / ((1.0 - z * z) * dp * dp);
     }
 }
 
@@ -129,6 +127,77 @@ bool in_band(const nuasm_params_t& p, int np, int k, int axis) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- shared per-mode helpers
+// (heap-free, so that the no-allocation solve can use them too)
+
+void make_quad(const Geometry& g, KernelQuad* qd) {
+    qd->n = 2 * g.w + 48;
+    double gx[KernelQuad::kMax], gw[KernelQuad::kMax];
+    gauss_legendre(qd->n, gx, gw);
+    for (int i = 0; i < qd->n; ++i) {
+        qd->t[i] = (gx[i] + 1.0) * g.w / 4.0;              // [0, w/2]
+        qd->f[i] = gw[i] * g.w / 4.0 * es_kernel(qd->t[i], g.w, g.beta);
+    }
+}
+
+double phihat_at(const KernelQuad& qd, double nu) {
+    double acc = 0.0;
+    for (int i = 0; i < qd.n; ++i) acc += qd.f[i] * std::cos(kTwoPi * nu * qd.t[i]);
+    return 2.0 * acc;
+}
+
+void asm_axis_factor(const nuasm_params_t& p, int np, int k, int axis, double* re, double* im) {
+    *re = 0.0;
+    *im = 0.0;
+    if (!in_band(p, np, k, axis)) return;
+    const double o = axis == 0 ? p.ox : p.oy;
+    const double f = double(k) / (double(np) * p.pitch);
+    const cd v = cis(frac(o * f - 0.5 * p.z * p.lambda * f * f));   // cycles
+    *re = v.real();
+    *im = v.imag();
+}
+
+void table_entry(const nuasm_params_t& p, const Geometry& g, int q, int type, double phihat, double hs_re,
+                 double hs_im, double* re, double* im) {
+    const int np = g.np;
+    const int k = q < np / 2 ? q : q - np;
+    const double dec = ((k & 1) ? -1.0 : 1.0) / phihat / np;
+    const cd win1 = cis_ratio(-int64_t(k) * g.Lo, g.G);      // window origin on the 2N' grid
+    const cd ctr1 = cis_ratio(-int64_t(k) * (g.n / 2), np);   // centred plane indices
+    const cd f = (type == 1 ? win1 * ctr1 : std::conj(win1) * std::conj(ctr1)) * dec * cd(hs_re, hs_im);
+    *re = f.real();
+    *im = f.imag();
+}
+
+void constant_factor(const nuasm_params_t& p, double* re, double* im) {
+    cd cst = cis(frac(z_over_lambda_frac(p.z, p.lambda)));
+    if (p.kind == NUASM_KIND_FRESNEL) cst /= cd(0.0, p.lambda * p.z);
+    *re = cst.real();
+    *im = cst.imag();
+}
+
+void twiddle(int i, int G, double* re, double* im) {
+    const cd v = cis_ratio(-i, G);
+    *re = v.real();
+    *im = v.imag();
+}
+
+double nonsep_rmax(const nuasm_params_t& p, const Geometry& g) {
+    if (p.kind != NUASM_KIND_ASM || p.z == 0.0) return 0.0;
+    const int np = g.np;
+    double sx = 0.0, sy = 0.0;   // largest kept lambda^2 f^2 per axis
+    for (int q = 0; q < np; ++q) {
+        const int k = q < np / 2 ? q : q - np;
+        const double f = double(k) / (double(np) * p.pitch);
+        const double sv = p.lambda * p.lambda * f * f;
+        if (in_band(p, np, k, 0) && sv > sx) sx = sv;
+        if (in_band(p, np, k, 1) && sv > sy) sy = sv;
+    }
+    const double sm = sx + sy;
+    const double qm = sm >= 1.0 ? 1.0 : sm / (1.0 + std::sqrt(1.0 - sm));
+    return std::fabs(p.z / (2.0 * p.lambda)) * qm * qm;
+}
 
 void kernel_shape(double tol, int prec, int* w, double* beta) {
     if (!(tol > 0)) tol = prec == NUASM_PREC_F64 ? 1e-12 : 1e-6;
@@ -201,10 +270,8 @@ Geometry make_geometry(const nuasm_params_t& p) {
     return g;
 }
 
-static void fit_kernel_poly(const Geometry& g, KernelPoly* kp);
-
 void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t) {
-    const int np = g.np, G = g.G, n = g.n;
+    const int np = g.np, G = g.G;
     t->t1x = new double[2 * np];
     t->t1y = new double[2 * np];
     t->t2x = new double[2 * np];
@@ -213,114 +280,75 @@ void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t) {
     t->tw = new double[2 * G];
 
     // deconvolution 1/phihat(k/G) by Gauss-Legendre quadrature of the truncated kernel
-    std::vector<double> gx, gw;
-    const int nq = 2 * g.w + 48;
-    gauss_legendre(nq, &gx, &gw);
-    std::vector<double> tq(nq), fq(nq);
-    for (int i = 0; i < nq; ++i) {
-        tq[i] = (gx[i] + 1.0) * g.w / 4.0;              // [0, w/2]
-        fq[i] = gw[i] * g.w / 4.0 * es_kernel(tq[i], g.w, g.beta);
-    }
-    std::vector<double> phihat(np);
-    for (int q = 0; q < np; ++q) {
-        int k = q < np / 2 ? q : q - np;
-        double nu = double(k) / G, acc = 0.0;
-        for (int i = 0; i < nq; ++i) acc += fq[i] * std::cos(kTwoPi * nu * tq[i]);
-        phihat[q] = 2.0 * acc;
-    }
-
+    KernelQuad qd;
+    make_quad(g, &qd);
     // separable transfer-function factor per axis (Eq. 4 or Eq. 5)
-    auto axis_factor = [&](int axis, std::vector<cd>* hs) {
-        hs->assign(np, cd(0, 0));
-        const double o = axis == 0 ? p.ox : p.oy;
+    std::vector<cd> hx(np), hy(np);
+    for (int axis = 0; axis < 2; ++axis) {
+        std::vector<cd>& hs = axis == 0 ? hx : hy;
         if (p.kind == NUASM_KIND_ASM) {
             for (int q = 0; q < np; ++q) {
-                int k = q < np / 2 ? q : q - np;
-                if (!in_band(p, np, k, axis)) continue;
-                double f = double(k) / (double(np) * p.pitch);
-                double ph = o * f - 0.5 * p.z * p.lambda * f * f;   // cycles
-                (*hs)[q] = cis(frac(ph));
+                const int k = q < np / 2 ? q : q - np;
+                double re, im;
+                asm_axis_factor(p, np, k, axis, &re, &im);
+                hs[q] = cd(re, im);
             }
         } else {
             // Hx(k) = pitch * sum_{m in [-N'/2, N'/2)} exp(i pi (m pitch + o)^2/(lambda z)) exp(-2 pi i k m / N')
+            const double o = axis == 0 ? p.ox : p.oy;
             std::vector<cd> chirp(np);
             for (int i = 0; i < np; ++i) {
-                double xm = double(i - np / 2) * p.pitch + o;
+                const double xm = double(i - np / 2) * p.pitch + o;
                 chirp[i] = cis(frac(xm * xm / (2.0 * p.lambda * p.z)));
             }
             fft_host(&chirp);
             for (int q = 0; q < np; ++q) {
-                int k = q < np / 2 ? q : q - np;
-                (*hs)[q] = p.pitch * ((k & 1) ? -1.0 : 1.0) * chirp[q];
+                const int k = q < np / 2 ? q : q - np;
+                hs[q] = p.pitch * ((k & 1) ? -1.0 : 1.0) * chirp[q];
             }
         }
-    };
-    std::vector<cd> hx, hy;
-    axis_factor(0, &hx);
-    axis_factor(1, &hy);
-    cd cst = cis(frac(z_over_lambda_frac(p.z, p.lambda)));
-    if (p.kind == NUASM_KIND_FRESNEL) cst /= cd(0.0, p.lambda * p.z);
-
+    }
+    double cre, cim;
+    constant_factor(p, &cre, &cim);
+    const cd cst(cre, cim);
     for (int q = 0; q < np; ++q) {
         const int k = q < np / 2 ? q : q - np;
-        const double sgn = (k & 1) ? -1.0 : 1.0;
-        const double dec = sgn / phihat[q] / np;
-        cd win1 = cis_ratio(-int64_t(k) * g.Lo, G);         // window origin on the G grid
-        cd ctr1 = cis_ratio(-int64_t(k) * (n / 2), np);      // centred output indices
-        cd a1x = win1 * ctr1 * dec * hx[q];
-        cd a1y = win1 * ctr1 * dec * hy[q] * cst;
-        cd a2x = std::conj(win1) * std::conj(ctr1) * dec * hx[q];
-        cd a2y = std::conj(win1) * std::conj(ctr1) * dec * hy[q] * cst;
-        t->t1x[2 * q] = a1x.real(); t->t1x[2 * q + 1] = a1x.imag();
-        t->t1y[2 * q] = a1y.real(); t->t1y[2 * q + 1] = a1y.imag();
-        t->t2x[2 * q] = a2x.real(); t->t2x[2 * q + 1] = a2x.imag();
-        t->t2y[2 * q] = a2y.real(); t->t2y[2 * q + 1] = a2y.imag();
-        double f = double(k) / (double(np) * p.pitch);
+        const double ph = phihat_at(qd, double(k) / G);
+        const cd hyc = hy[q] * cst;
+        table_entry(p, g, q, 1, ph, hx[q].real(), hx[q].imag(), &t->t1x[2 * q], &t->t1x[2 * q + 1]);
+        table_entry(p, g, q, 1, ph, hyc.real(), hyc.imag(), &t->t1y[2 * q], &t->t1y[2 * q + 1]);
+        table_entry(p, g, q, 2, ph, hx[q].real(), hx[q].imag(), &t->t2x[2 * q], &t->t2x[2 * q + 1]);
+        table_entry(p, g, q, 2, ph, hyc.real(), hyc.imag(), &t->t2y[2 * q], &t->t2y[2 * q + 1]);
+        const double f = double(k) / (double(np) * p.pitch);
         t->s[q] = p.lambda * p.lambda * f * f;
     }
     t->rc = p.z / (2.0 * p.lambda);
-    t->rmax = 0.0;
-    if (p.kind == NUASM_KIND_ASM && p.z != 0.0) {
-        // largest kept s = lambda^2 |f|^2 sits at the band corner farthest from DC
-        double sx = 0.0, sy = 0.0;
-        for (int q = 0; q < np; ++q) {
-            const int k = q < np / 2 ? q : q - np;
-            if (in_band(p, np, k, 0) && t->s[q] > sx) sx = t->s[q];
-            if (in_band(p, np, k, 1) && t->s[q] > sy) sy = t->s[q];
-        }
-        const double sm = sx + sy;
-        const double qm = sm >= 1.0 ? 1.0 : sm / (1.0 + std::sqrt(1.0 - sm));
-        t->rmax = std::fabs(t->rc) * qm * qm;
-    }
+    t->rmax = nonsep_rmax(p, g);
     fit_kernel_poly(g, &t->poly);
-    for (int i = 0; i < G; ++i) {
-        cd v = cis_ratio(-i, G);
-        t->tw[2 * i] = v.real();
-        t->tw[2 * i + 1] = v.imag();
-    }
+    for (int i = 0; i < G; ++i) twiddle(i, G, &t->tw[2 * i], &t->tw[2 * i + 1]);
 }
 
 // Chebyshev interpolation of each tap phi(i + f - w/2), f in [0, 1), at
 // Chebyshev nodes of x = 2f - 1, converted to monomial coefficients in x (the
 // coefficients stay O(1), so Horner's rule in FP32 is as accurate as direct
 // evaluation of the exponential).
-static void fit_kernel_poly(const Geometry& g, KernelPoly* kp) {
+void fit_kernel_poly(const Geometry& g, KernelPoly* kp) {
     std::memset(kp, 0, sizeof(*kp));
     int d = g.w + 2;
     if (d > kPolyMaxD - 1) d = kPolyMaxD - 1;
     kp->deg = d;
     const int K = 2 * d + 2;
-    std::vector<double> xn(K), tj(d + 1);
+    double xn[2 * kPolyMaxD + 2];
     for (int k = 0; k < K; ++k) xn[k] = std::cos(M_PI * (k + 0.5) / K);
     // monomial coefficients of the Chebyshev polynomials T_0..T_d
-    std::vector<std::vector<double>> T(d + 1, std::vector<double>(d + 1, 0.0));
+    double T[kPolyMaxD][kPolyMaxD] = {};
     T[0][0] = 1.0;
     if (d >= 1) T[1][1] = 1.0;
     for (int j = 2; j <= d; ++j)
         for (int m = 0; m <= d; ++m)
             T[j][m] = (m > 0 ? 2.0 * T[j - 1][m - 1] : 0.0) - T[j - 2][m];
     for (int i = 0; i < g.w && i < kPolyMaxW; ++i) {
-        std::vector<double> cheb(d + 1, 0.0);
+        double cheb[kPolyMaxD] = {};
         for (int k = 0; k < K; ++k) {
             const double f = 0.5 * (xn[k] + 1.0);
             const double val = es_kernel(i + f - 0.5 * g.w, g.w, g.beta);

@@ -80,7 +80,23 @@ struct nuasm_plan_s {
 
 namespace nuasm {
 
-// host math (hostmath.cpp)
+// Gauss-Legendre quadrature of the kernel on [0, w/2] for its Fourier transform.
+struct KernelQuad {
+    static constexpr int kMax = 2 * 16 + 48;
+    int n;
+    double t[kMax], f[kMax];   // nodes and weight x kernel value
+};
+
+// host math (hostmath.cpp); the per-mode helpers allocate nothing
+void make_quad(const Geometry& g, KernelQuad* qd);
+double phihat_at(const KernelQuad& qd, double nu);
+void asm_axis_factor(const nuasm_params_t& p, int np, int k, int axis, double* re, double* im);
+void table_entry(const nuasm_params_t& p, const Geometry& g, int q, int type, double phihat, double hs_re,
+                 double hs_im, double* re, double* im);
+void constant_factor(const nuasm_params_t& p, double* re, double* im);
+void twiddle(int i, int G, double* re, double* im);
+double nonsep_rmax(const nuasm_params_t& p, const Geometry& g);
+void fit_kernel_poly(const Geometry& g, KernelPoly* kp);
 nuasm_status validate(const nuasm_params_t& p, int64_t m, nuasm_params_t* resolved);
 void kernel_shape(double tol, int prec, int* w, double* beta);
 void band_range(const nuasm_params_t& p, int out[4]);
