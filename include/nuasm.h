@@ -196,6 +196,37 @@ nuasm_status nuasm_profile_enable(nuasm_plan_t plan, int32_t enable);
 nuasm_status nuasm_profile_read(nuasm_plan_t plan, double* ms, int64_t* launches);
 const char* nuasm_stage_name(int32_t stage);
 
+/*
+ * nuasm2_solve_noalloc -- NU-ASM_2 (the same result as nuasm_plan followed by
+ * nuasm2_execute) in one call that allocates nothing.  The paper has no
+ * counterpart: this exists for callers that must not call cudaMalloc or any
+ * allocating routine -- code running while a stream is captured into a CUDA
+ * graph, plug-ins whose host framework owns all device memory, real-time
+ * loops that cannot take an allocation's latency or failure.  Those callers
+ * cannot build a plan, so the plan work and the solve happen here, with every
+ * intermediate in one 16 MiB file-scope device array that every GPU loading
+ * the library holds until the process exits.
+ *
+ *  p         parameters; kind must be NUASM_KIND_ASM and prec
+ *            NUASM_PREC_F32_F64PHASE (else NUASM_EINVAL).
+ *  m         number of destination points, 0 <= m <= 65536.
+ *  x, y      m coordinates in metres, device memory.
+ *  u1        N*N complex64 source plane, device memory.
+ *  v         m complex64 outputs in point order, device memory.
+ *  stream    stream for the work; the call waits for it to finish before
+ *            returning (it reads back the out-of-window flag).
+ *
+ * Limits: N <= 256 and N' <= 512 and m <= 65536, else NUASM_EUNSUPPORTED;
+ * host pointers give NUASM_EINVAL.  The device address of the array is looked
+ * up on the first call made on each device; make that first call before any
+ * stream capture begins.  Every call reuses the same array (counters are
+ * cleared at the start of each call); calls whose device work overlaps --
+ * other streams, other host threads -- race on it and must be serialised by
+ * the caller.
+ */
+nuasm_status nuasm2_solve_noalloc(const nuasm_params_t* p, int64_t m, const double* x, const double* y,
+                                  const void* u1, void* v, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

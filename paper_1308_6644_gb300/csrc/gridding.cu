@@ -451,6 +451,48 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
     return cuda_status(cudaStreamSynchronize(st));
 }
 
+// Binning into caller-provided device storage, with no allocation and no host
+// read-back: `cnt` holds 4 * ntiles ints of scratch, `rec_tmp` and P->d.rec
+// hold at least 4 * m records each (a point lands in at most four tiles), and
+// P->d.tile_off, P->d.tile_home and P->d.err are set by the caller.  The
+// out-of-window flag is left in P->d.err for the caller to read.
+cudaError_t bin_points_into(const nuasm_plan_s* P, const double* x, const double* y, int* cnt, void* rec_tmp,
+                            cudaStream_t st) {
+    const Geometry& g = P->g;
+    const BinArgs a{g.n, g.W, g.T, g.ntx, g.w, g.h, P->p.pitch, P->m};
+    const int nt = g.ntiles;
+    int* home_cnt = cnt;
+    int* dup_cnt = cnt + nt;
+    int* cur_home = cnt + 2 * nt;
+    int* cur_dup = cnt + 3 * nt;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * 4 * size_t(nt), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(P->d.err, 0, sizeof(int), st)) != cudaSuccess) return e;
+    const int blocks = int(std::min<int64_t>((P->m + 255) / 256, 152 * 16));
+    if (P->m > 0) {
+        bin_count_kernel<<<blocks, 256, 0, st>>>(x, y, a, home_cnt, dup_cnt, P->d.err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    bin_scan_kernel<<<1, 1024, 0, st>>>(home_cnt, dup_cnt, nt, P->d.tile_off, P->d.tile_home);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (P->m == 0) return cudaSuccess;
+    const size_t smb = sizeof(int) * size_t(g.T) * g.T;
+    if (P->f64) {
+        bin_scatter_kernel<RecD, double><<<blocks, 256, 0, st>>>(x, y, a, P->d.tile_off, home_cnt, cur_home,
+                                                                 cur_dup, static_cast<RecD*>(rec_tmp));
+        sort_tile_kernel<RecD><<<nt, 256, smb, st>>>(static_cast<const RecD*>(rec_tmp), static_cast<RecD*>(P->d.rec),
+                                                     P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+    } else {
+        bin_scatter_kernel<RecF, float><<<blocks, 256, 0, st>>>(x, y, a, P->d.tile_off, home_cnt, cur_home,
+                                                                cur_dup, static_cast<RecF*>(rec_tmp));
+        sort_tile_kernel<RecF><<<nt, 256, smb, st>>>(static_cast<const RecF*>(rec_tmp), static_cast<RecF*>(P->d.rec),
+                                                     P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+    }
+    return cudaGetLastError();
+}
+
+size_t record_bytes(bool f64) { return f64 ? sizeof(RecD) : sizeof(RecF); }
+
 cudaError_t launch_spread(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     if (P->f64) return P->g.w <= 8 ? spread_impl<double, 8>(P, c, st) : spread_impl<double, 16>(P, c, st);
     return P->g.w <= 8 ? spread_impl<float, 8>(P, c, st) : spread_impl<float, 16>(P, c, st);

@@ -107,6 +107,9 @@ void free_tables(HostTables* t);
 // launchers (gridding.cu / passes.cu); all asynchronous on `s`
 nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, const double* w,
                          cudaStream_t s);
+cudaError_t bin_points_into(const nuasm_plan_s* P, const double* x, const double* y, int* cnt, void* rec_tmp,
+                            cudaStream_t s);
+size_t record_bytes(bool f64);
 cudaError_t launch_spread(const nuasm_plan_s* P, const void* c, cudaStream_t s);
 cudaError_t launch_interp(const nuasm_plan_s* P, void* v, cudaStream_t s);
 cudaError_t launch_col_fwd_fold(const nuasm_plan_s* P, cudaStream_t s);

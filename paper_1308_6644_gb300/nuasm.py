@@ -72,6 +72,8 @@ _SIGS = {
     "nuasm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]),
     "nuasm_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
+    "nuasm2_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int64, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -282,3 +284,17 @@ def nuasm_profile_read(plan: Plan) -> dict:
     cnt = (ctypes.c_int64 * n)()
     _check(lib().nuasm_profile_read(plan._h, ms, cnt), "nuasm_profile_read")
     return {lib().nuasm_stage_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(n)}
+
+
+def nuasm2_solve_noalloc(params: Params, x, y, u1, v, stream=None):
+    """One-shot NU-ASM_2 that allocates nothing (see include/nuasm.h): float64
+    device coordinates x, y (M), complex64 device u1 (N*N) -> complex64 v (M)."""
+    m = 0 if x is None else _numel(x)
+    for a, name in ((x, "x"), (y, "y")):
+        if a is not None:
+            _expect(a, m, "float64", name)
+    _expect(u1, params.n * params.n, "complex64", "u1")
+    _expect(v, m, "complex64", "v")
+    _check(lib().nuasm2_solve_noalloc(ctypes.byref(params), m, _ptr(x), _ptr(y), _ptr(u1), _ptr(v),
+                                      _stream(stream)), "nuasm2_solve_noalloc")
+    return v
