@@ -1,0 +1,139 @@
+"""Full-size parity: the benchmark workload and the large NU-FRE workloads in
+the launch configuration bench.py uses, checked on outputs the oracle can
+compute one by one (sampled points), on sparse inputs, and against closed
+forms that hold at any size.  F32 tolerance: rel-L2 1e-5."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1308_6644_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1308_6644_gb300 as pkg
+    return pkg
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _solve(P, w, type_, values, weights=None, kind=None):
+    import torch
+    kind = kind or w.kind
+    params = P.make_params(w.n, w.pitch, w.lam, w.z, ox=w.ox, oy=w.oy, kind=kind)
+    plan = P.nuasm_plan(params, _dev(w.x), _dev(w.y), None if weights is None else _dev(weights))
+    try:
+        src = _dev(np.asarray(values).astype(np.complex64).reshape(-1))
+        out = torch.zeros(w.n * w.n if type_ == 1 else w.m, dtype=torch.complex64, device="cuda")
+        if kind == "asm":
+            (P.nuasm1_execute if type_ == 1 else P.nuasm2_execute)(plan, src, out)
+        else:
+            P.nufresnel_execute(plan, type_, src, out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    finally:
+        plan.destroy()
+
+
+def _oracle_type2_sampled(w, idx, kind):
+    n, n_pad = w.n, 2 * w.n
+    u1 = w.values.astype(np.complex64).astype(np.complex128)
+    g = O.uniform_dft(u1, n_pad)
+    if kind == "asm":
+        h = O.asm_transfer(n, n_pad, w.pitch, w.lam, w.z, w.ox, w.oy)
+    else:
+        h = O.fresnel_transfer(n_pad, w.pitch, w.lam, w.z, w.ox, w.oy)
+    return O.nudft_type2(g * h / float(n_pad) ** 2, w.x[idx] / w.pitch, w.y[idx] / w.pitch, n_pad)
+
+
+def gaussian_fresnel(x, y, lam, z, w0):
+    """Fresnel propagation of exp(-|x|^2/w0^2) (completing the square)."""
+    a, b, zr = 1 / w0 ** 2, np.pi / (lam * z), np.pi * w0 ** 2 / lam
+    ph = np.longdouble(z) / np.longdouble(lam)
+    ph = float(ph - np.rint(ph))
+    return np.exp(2j * np.pi * ph) / (1 + 1j * z / zr) * np.exp(1j * a * b * (x * x + y * y) / (a - 1j * b))
+
+
+def test_nuasm2_benchmark_workload_sampled(P):
+    """NU-ASM_2, N = 1024, M = 1,048,576 graded points (the bench workload):
+    4096 sampled points against the direct NUDFT oracle."""
+    w = WL.nuasm2_graded(seed=1002, n=1024, pitch=8e-6)
+    got = _solve(P, w, 2, w.values)
+    idx = np.sort(np.random.default_rng(11).choice(w.m, 4096, replace=False))
+    ref = _oracle_type2_sampled(w, idx, "asm")
+    assert O.rel_l2(got[idx], ref) < TOL
+
+
+def test_nufresnel2_clustered_full_size(P):
+    """NU-FRE_2, N = 2048, M = 4,194,304 clustered points, Gaussian-beam
+    source: sampled points against the oracle, every point against the
+    closed form."""
+    w = WL.fresnel_clustered(type_=2, n=2048)
+    got = _solve(P, w, 2, w.values)
+    want = gaussian_fresnel(w.x + w.ox, w.y + w.oy, w.lam, w.z, w.extra["w0"])
+    assert O.rel_l2(got, want) < TOL
+    idx = np.sort(np.random.default_rng(12).choice(w.m, 2048, replace=False))
+    ref = _oracle_type2_sampled(w, idx, "fresnel")
+    assert O.rel_l2(got[idx], ref) < TOL
+
+
+def test_nufresnel1_full_size_warped_lattice_closed_form(P):
+    """NU-FRE_1 at N = 2048 with all 4,194,304 source points non-zero: a
+    smoothly warped lattice with Jacobian weights is a spectrally accurate
+    quadrature, so the output is the Gaussian-beam closed form."""
+    n, pitch, lam, z, w0 = 2048, 4e-6, 633e-9, 1.0, 0.5e-3
+    L = n * pitch
+    t = O.lattice(n) * pitch
+    phi = t + 0.3 * L / (2 * np.pi) * np.sin(2 * np.pi * t / L)
+    dphi = 1 + 0.3 * np.cos(2 * np.pi * t / L)
+    ty, tx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    x, y = phi[tx].ravel(), phi[ty].ravel()
+    wts = (dphi[tx] * dphi[ty]).ravel()
+    c = np.exp(-(x * x + y * y) / w0 ** 2)
+    wl = WL.Workload("warped", "fresnel", 1, n, pitch, lam, z, x=x, y=y, values=c)
+    got = _solve(P, wl, 1, c, weights=wts).reshape(n, n)
+    g = O.lattice(n) * pitch
+    gy, gx = np.meshgrid(g, g, indexing="ij")
+    assert O.rel_l2(got, gaussian_fresnel(gx, gy, lam, z, w0)) < TOL
+
+
+def test_nufresnel1_clustered_full_size_sparse_sources(P):
+    """NU-FRE_1 on the 4,194,304 clustered points with 256 non-zero sources:
+    every output pixel against the oracle (the full launch configuration with
+    an oracle cost of 256 points)."""
+    w = WL.fresnel_clustered(type_=1, n=2048)
+    rng = np.random.default_rng(13)
+    c = np.zeros(w.m, np.complex128)
+    nz = rng.choice(w.m, 256, replace=False)
+    c[nz] = rng.normal(size=256) + 1j * rng.normal(size=256)
+    got = _solve(P, w, 1, c).reshape(w.n, w.n)
+    p = dict(n=w.n, pitch=w.pitch, lam=w.lam, z=w.z, kind="fresnel")
+    ref = O.diffraction_type1(w.x[nz], w.y[nz], c[nz].astype(np.complex64), p)
+    assert O.rel_l2(got, ref) < TOL
+
+
+@pytest.mark.parametrize("plane", [0, 1, 2, 3])
+def test_mixed_planes(P, plane):
+    """Planes of the mixed batch (N up to 2048, 0.25-4 N^2 points): type 2 on
+    sampled points, type 1 with 128 non-zero sources, against the oracle."""
+    w = WL.mixed_plane(1004, plane)
+    rng = np.random.default_rng(100 + plane)
+    if w.type == 2:
+        got = _solve(P, w, 2, w.values)
+        idx = np.sort(rng.choice(w.m, min(w.m, 1024), replace=False))
+        assert O.rel_l2(got[idx], _oracle_type2_sampled(w, idx, "asm")) < TOL
+    else:
+        c = np.zeros(w.m, np.complex128)
+        nz = rng.choice(w.m, min(w.m, 128), replace=False)
+        c[nz] = w.values[nz]
+        got = _solve(P, w, 1, c).reshape(w.n, w.n)
+        p = dict(n=w.n, pitch=w.pitch, lam=w.lam, z=w.z)
+        assert O.rel_l2(got, O.nuasm1(w.x[nz], w.y[nz], c[nz].astype(np.complex64), p)) < TOL
