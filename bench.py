@@ -52,6 +52,20 @@ def _workload():
     return WL.nuasm2_graded(seed=1002, n=1024, pitch=8e-6)
 
 
+def reduce_over_ranks(total_ms: float, points: float, device) -> tuple[float, float]:
+    """Replicas only: the job time is the slowest rank's time (MAX) and the job
+    processed every rank's points (SUM).  Single process: unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_ms, points
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([points], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -281,14 +295,7 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
     total_ms = float(step_ms.sum())
-    points = float(wl.m * args.steps)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        pts = torch.tensor([points], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(pts)
-        points = float(pts.item())
+    total_ms, points = reduce_over_ranks(total_ms, float(wl.m * args.steps), dev)
     value = points / (total_ms * 1e-3)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
