@@ -120,6 +120,36 @@ template <int DIR, typename V> struct Dft<16, DIR, V> {
 template <int R> struct Log2 { static constexpr int v = R <= 1 ? 0 : 1 + Log2<R / 2>::v; };
 template <> struct Log2<1> { static constexpr int v = 0; };
 
+// ---------------------------------------------------------------- twiddle powers
+// w[r] = exp(-2 pi i k r / (Ns R)) = tw[(k r) << sh] for r in [1, R).  FP64
+// reads every power from the table; FP32 reads w^1 and w^4 (w^1 and w^2 for
+// R = 4) and forms the others by complex products (at most four roundings,
+// about 2.4e-7 relative), which trades table loads for FMA-pipe work.
+template <typename V, int R>
+__device__ __forceinline__ void twiddle_powers(const V* __restrict__ tw, int k, int sh, V* w) {
+    if constexpr (sizeof(V) == 16 || R == 2) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[r] = __ldg(&tw[(k * r) << sh]);
+    } else if constexpr (R == 4) {
+        w[1] = __ldg(&tw[k << sh]);
+        w[2] = __ldg(&tw[(2 * k) << sh]);
+        w[3] = cmul(w[2], w[1]);
+    } else {
+        w[1] = __ldg(&tw[k << sh]);
+        w[4] = __ldg(&tw[(4 * k) << sh]);
+        w[2] = cmul(w[1], w[1]);
+        w[3] = cmul(w[2], w[1]);
+        w[5] = cmul(w[4], w[1]);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+        if constexpr (R == 16) {
+            w[8] = cmul(w[4], w[4]);
+#pragma unroll
+            for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- one pass
 // Twiddle table: tw[t] = exp(-2 pi i t / 2L), t in [0, 2L).
 template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, int LR, int LOGNS, bool FIRST,
@@ -157,12 +187,10 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
     for (int b = 0; b < NB; ++b) {
         if (LOGNS > 0) {
             const int k = jj[b] & (NS - 1);
+            V w[R];
+            twiddle_powers<V, R>(tw, k, SH, w);
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                V w = __ldg(&tw[(k * r) << SH]);
-                if (DIR > 0) w = cconj(w);
-                v[b * R + r] = cmul(v[b * R + r], w);
-            }
+            for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], DIR > 0 ? cconj(w[r]) : w[r]);
         }
         Dft<R, DIR, V>::run(v + b * R);
     }

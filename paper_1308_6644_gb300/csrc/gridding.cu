@@ -138,37 +138,42 @@ __global__ void bin_scatter_kernel(const double* __restrict__ x, const double* _
     }
 }
 
-// Counting sort of each tile's home records by first-tap cell (row-major in
-// the tile), so that a warp's interpolation gathers touch neighbouring cells
-// (distinct shared-memory banks) and its output writes cluster.  One CTA per
-// tile; reads the unsorted copy `src`, writes `dst`.  Halo duplicates are
-// copied unchanged.
+// Order each tile's records so that consecutive records have distinct
+// first-tap columns modulo 32 (round-robin over the 32 classes lx mod 32, home
+// records and halo duplicates separately).  A warp then gathers (type 2) or
+// accumulates (type 1) its w x w taps at 32 distinct shared-memory banks for
+// every tap offset: the tile rows are a multiple of 32 banks apart.  One CTA
+// per tile, reading the unordered copy `src` and writing `dst`; the order
+// within a class is arbitrary (results do not depend on record order in
+// type 2; type 1 sums in shared memory whatever the order).
 template <typename Rec>
-__global__ void sort_tile_kernel(const Rec* __restrict__ src, Rec* __restrict__ dst, const int* __restrict__ off,
-                                 const int* __restrict__ home, int T, int ntx) {
-    extern __shared__ int bins[];   // T*T counters
+__global__ void order_tile_kernel(const Rec* __restrict__ src, Rec* __restrict__ dst, const int* __restrict__ off,
+                                  const int* __restrict__ home, int T, int ntx) {
+    __shared__ int cnt[2][32], cur[2][32];
     const int tile = blockIdx.x;
-    const int ty = tile / ntx, tx = tile - ty * ntx;
-    const int x0 = tx * T, y0 = ty * T, nb = T * T;
+    const int x0 = (tile - (tile / ntx) * ntx) * T;
     const int b = off[tile], e = off[tile + 1], eh = b + home[tile];
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) bins[i] = 0;
-    __syncthreads();
-    for (int i = b + threadIdx.x; i < eh; i += blockDim.x) {
-        const uint32_t cell = src[i].cell;
-        atomicAdd(&bins[(int(cell >> 16) - y0) * T + int(cell & 0xffffu) - x0], 1);
+    if (threadIdx.x < 64) {
+        (&cnt[0][0])[threadIdx.x] = 0;
+        (&cur[0][0])[threadIdx.x] = 0;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {   // exclusive scan (T*T <= 4096 entries, once per plan)
-        int run = 0;
-        for (int i = 0; i < nb; ++i) { const int c = bins[i]; bins[i] = run; run += c; }
-    }
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x)
+        atomicAdd(&cnt[i >= eh][(int(src[i].cell & 0xffffu) - x0) & 31], 1);
     __syncthreads();
-    for (int i = b + threadIdx.x; i < eh; i += blockDim.x) {
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
         const Rec r = src[i];
-        const int key = (int(r.cell >> 16) - y0) * T + int(r.cell & 0xffffu) - x0;
-        dst[b + atomicAdd(&bins[key], 1)] = r;
+        const int seg = i >= eh;
+        const int c = (int(r.cell & 0xffffu) - x0) & 31;
+        const int rank = atomicAdd(&cur[seg][c], 1);
+        int pos = 0;   // records of lower rank, then same rank and lower class
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const int n = cnt[seg][k];
+            pos += min(n, rank) + ((k < c && n > rank) ? 1 : 0);
+        }
+        dst[(seg ? eh : b) + pos] = r;
     }
-    for (int i = eh + threadIdx.x; i < e; i += blockDim.x) dst[i] = src[i];
 }
 
 // --------------------------------------------------------------- kernel values
@@ -218,7 +223,8 @@ struct GridArgs {
 };
 
 // --------------------------------------------------------------- spreading (type 1)
-template <typename S, int WMAX>
+// EXACT: the kernel width is WMAX itself (compile-time loops); else w <= WMAX at run time.
+template <typename S, int WMAX, bool EXACT>
 __global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::type* __restrict__ rec,
                                                      const int* __restrict__ off, const double* __restrict__ wpt,
                                                      const typename VecOf<S>::type* __restrict__ c,
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::ty
                                                      const KernelPoly kp) {
     using V = typename VecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
-    const int T = a.T, w = a.w;
+    const int T = a.T, w = EXACT ? WMAX : a.w;
     S* sre = reinterpret_cast<S*>(smem_raw);
     S* sim = sre + T * T;
     const int tile = blockIdx.x;
@@ -274,7 +280,9 @@ __global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::ty
 }
 
 // --------------------------------------------------------------- interpolation (type 2)
-template <typename S, int WMAX>
+// The tile plus its (w-1) halo is staged with a row stride rounded up to 16
+// elements, so bank classes depend on the column only (see order_tile_kernel).
+template <typename S, int WMAX, bool EXACT>
 __global__ void __launch_bounds__(256) interp_kernel(const typename RecOf<S>::type* __restrict__ rec,
                                                      const int* __restrict__ off, const int* __restrict__ home,
                                                      const typename VecOf<S>::type* __restrict__ win,
@@ -283,17 +291,17 @@ __global__ void __launch_bounds__(256) interp_kernel(const typename RecOf<S>::ty
     using V = typename VecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
     V* tl = reinterpret_cast<V*>(smem_raw);
-    const int T = a.T, w = a.w, TH = T + w - 1;
+    const int T = a.T, w = EXACT ? WMAX : a.w, TH = T + w - 1, THP = (TH + 15) & ~15;
     const int tile = blockIdx.x;
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
-    for (int i = threadIdx.x; i < TH * TH; i += blockDim.x) {
-        const int yy = i / TH, xx = i - yy * TH;
+    for (int i = threadIdx.x; i < TH * THP; i += blockDim.x) {
+        const int yy = i / THP, xx = i - yy * THP;
         const int gy = y0 + yy, gx = x0 + xx;
         V val;
         val.x = S(0);
         val.y = S(0);
-        if (gy < a.W && gx < a.W) val = win[size_t(gy) * a.Wp + gx];
+        if (xx < TH && gy < a.W && gx < a.W) val = win[gy * a.Wp + gx];
         tl[i] = val;
     }
     __syncthreads();
@@ -309,7 +317,7 @@ __global__ void __launch_bounds__(256) interp_kernel(const typename RecOf<S>::ty
 #pragma unroll
         for (int qy = 0; qy < WMAX; ++qy) {
             if (qy >= w) continue;
-            const V* row = tl + (ly + qy) * TH + lx;
+            const V* row = tl + (ly + qy) * THP + lx;
             S rr = S(0), ri = S(0);
 #pragma unroll
             for (int qx = 0; qx < WMAX; ++qx) {
@@ -343,31 +351,55 @@ template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
 }
 
-template <typename S, int WMAX>
+template <typename S, int WMAX, bool EXACT>
 cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     using V = typename VecOf<S>::type;
     GridArgs a = grid_args(P);
     const size_t sm = size_t(2) * a.T * a.T * sizeof(S);
-    cudaError_t e = set_smem(spread_kernel<S, WMAX>, sm);
+    cudaError_t e = set_smem(spread_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
-    spread_kernel<S, WMAX><<<P->g.ntiles, 256, sm, st>>>(
+    spread_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
         static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.wpt,
         static_cast<const V*>(c), static_cast<V*>(P->d.win), a, P->poly);
     return cudaGetLastError();
 }
 
-template <typename S, int WMAX>
+template <typename S, int WMAX, bool EXACT>
 cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
     using V = typename VecOf<S>::type;
     GridArgs a = grid_args(P);
-    const int TH = a.T + a.w - 1;
-    const size_t sm = size_t(TH) * TH * sizeof(V);
-    cudaError_t e = set_smem(interp_kernel<S, WMAX>, sm);
+    const int TH = a.T + a.w - 1, THP = (TH + 15) & ~15;
+    const size_t sm = size_t(TH) * THP * sizeof(V);
+    cudaError_t e = set_smem(interp_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
-    interp_kernel<S, WMAX><<<P->g.ntiles, 256, sm, st>>>(
+    interp_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
         static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.tile_home,
         static_cast<const V*>(P->d.win), static_cast<V*>(v), a, P->poly);
     return cudaGetLastError();
+}
+
+template <typename S_, int W_, bool X_> struct GTag {
+    using S = S_;
+    static constexpr int W = W_;
+    static constexpr bool X = X_;
+};
+
+// width dispatch: exact instantiations for the common FP32 widths
+template <bool SPREAD> cudaError_t gridding(const nuasm_plan_s* P, const void* in, void* out, cudaStream_t st) {
+    auto run = [&](auto tag) -> cudaError_t {
+        using Tg = decltype(tag);
+        if constexpr (SPREAD) return spread_impl<typename Tg::S, Tg::W, Tg::X>(P, in, st);
+        else return interp_impl<typename Tg::S, Tg::W, Tg::X>(P, out, st);
+    };
+    if (P->f64) return P->g.w <= 8 ? run(GTag<double, 8, false>{}) : run(GTag<double, 16, false>{});
+    switch (P->g.w) {
+        case 4: return run(GTag<float, 4, true>{});
+        case 5: return run(GTag<float, 5, true>{});
+        case 6: return run(GTag<float, 6, true>{});
+        case 7: return run(GTag<float, 7, true>{});
+        case 8: return run(GTag<float, 8, true>{});
+        default: return run(GTag<float, 16, false>{});
+    }
 }
 
 }  // namespace
@@ -434,13 +466,12 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
         if ((e = cudaMallocAsync(&tmp, rsz * size_t(total), st)) != cudaSuccess) return fail(e);
         e = cudaMemcpyAsync(tmp, P->d.rec, rsz * size_t(total), cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) {
-            const size_t smb = sizeof(int) * size_t(g.T) * g.T;
             if (P->f64)
-                sort_tile_kernel<RecD><<<nt, 256, smb, st>>>(static_cast<const RecD*>(tmp), static_cast<RecD*>(P->d.rec),
-                                                             P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+                order_tile_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(tmp), static_cast<RecD*>(P->d.rec),
+                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx);
             else
-                sort_tile_kernel<RecF><<<nt, 256, smb, st>>>(static_cast<const RecF*>(tmp), static_cast<RecF*>(P->d.rec),
-                                                             P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+                order_tile_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(tmp), static_cast<RecF*>(P->d.rec),
+                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx);
             e = cudaGetLastError();
         }
         cudaFreeAsync(tmp, st);
@@ -476,17 +507,16 @@ cudaError_t bin_points_into(const nuasm_plan_s* P, const double* x, const double
     bin_scan_kernel<<<1, 1024, 0, st>>>(home_cnt, dup_cnt, nt, P->d.tile_off, P->d.tile_home);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (P->m == 0) return cudaSuccess;
-    const size_t smb = sizeof(int) * size_t(g.T) * g.T;
     if (P->f64) {
         bin_scatter_kernel<RecD, double><<<blocks, 256, 0, st>>>(x, y, a, P->d.tile_off, home_cnt, cur_home,
                                                                  cur_dup, static_cast<RecD*>(rec_tmp));
-        sort_tile_kernel<RecD><<<nt, 256, smb, st>>>(static_cast<const RecD*>(rec_tmp), static_cast<RecD*>(P->d.rec),
-                                                     P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+        order_tile_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(rec_tmp), static_cast<RecD*>(P->d.rec),
+                                                    P->d.tile_off, P->d.tile_home, g.T, g.ntx);
     } else {
         bin_scatter_kernel<RecF, float><<<blocks, 256, 0, st>>>(x, y, a, P->d.tile_off, home_cnt, cur_home,
                                                                 cur_dup, static_cast<RecF*>(rec_tmp));
-        sort_tile_kernel<RecF><<<nt, 256, smb, st>>>(static_cast<const RecF*>(rec_tmp), static_cast<RecF*>(P->d.rec),
-                                                     P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+        order_tile_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(rec_tmp), static_cast<RecF*>(P->d.rec),
+                                                    P->d.tile_off, P->d.tile_home, g.T, g.ntx);
     }
     return cudaGetLastError();
 }
@@ -494,13 +524,11 @@ cudaError_t bin_points_into(const nuasm_plan_s* P, const double* x, const double
 size_t record_bytes(bool f64) { return f64 ? sizeof(RecD) : sizeof(RecF); }
 
 cudaError_t launch_spread(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
-    if (P->f64) return P->g.w <= 8 ? spread_impl<double, 8>(P, c, st) : spread_impl<double, 16>(P, c, st);
-    return P->g.w <= 8 ? spread_impl<float, 8>(P, c, st) : spread_impl<float, 16>(P, c, st);
+    return gridding<true>(P, c, nullptr, st);
 }
 
 cudaError_t launch_interp(const nuasm_plan_s* P, void* v, cudaStream_t st) {
-    if (P->f64) return P->g.w <= 8 ? interp_impl<double, 8>(P, v, st) : interp_impl<double, 16>(P, v, st);
-    return P->g.w <= 8 ? interp_impl<float, 8>(P, v, st) : interp_impl<float, 16>(P, v, st);
+    return gridding<false>(P, nullptr, v, st);
 }
 
 }  // namespace nuasm

@@ -1,5 +1,5 @@
 // FFT passes of the NU-ASM / NU-FRE pipeline (kernel templates; instantiated
-// per precision and per N' in passes_f32.cu / passes_f64.cu).
+// per precision and per N' in passes_{row,col}_{f32,f64}.cu).
 //
 // Every transform here has length N' (the padded plane size).  The length-2N'
 // transforms of the oversampled NUFFT grid are split into their even and odd
@@ -23,9 +23,9 @@
 //   q = s / (1 + sqrt(1 - s)),  s = lambda^2 |f|^2,
 // an exact rearrangement whose first two terms are separable (folded into the
 // per-axis tables in FP64 on the host) and whose last term r is small.  r is
-// computed in FP64 (F64 plans), in plain FP32 when the plan's largest |r| is
-// at most 1/2 cycle (absolute error below 1e-7 cycles), else in double-float
-// FP32; it is reduced mod 1 and passed to sincospi.  Evanescent modes
+// computed in FP64 (F64 plans), with FP32 fast-math intrinsics when the plan's
+// largest |r| is at most 1/2 cycle (phase error below 2e-6 rad), else in
+// double-float FP32 reduced mod 1 and passed to sincospi.  Evanescent modes
 // (s >= 1) are zeroed.
 #pragma once
 
@@ -96,11 +96,15 @@ __device__ __forceinline__ float2 nonsep_factor(const float2* __restrict__ s, in
     const float2 sa = __ldg(&s[qx]), sb = __ldg(&s[qy]);
     float fr;
     if (a.nonsep == 1) {
+        // |r| <= 1/2 cycle: fast-math evaluation, phase error below 2e-6 rad
         const float sv = sa.x + sb.x;
         if (sv >= 1.f) return make_float2(0.f, 0.f);
-        const float q = sv / (1.f + sqrtf(1.f - sv));
+        const float t = 1.f - sv;
+        const float q = __fdividef(sv, 1.f + t * rsqrtf(t));
         const float r = a.rc_hi * q * q;
-        fr = r - rintf(r);
+        float sn, cs;
+        __sincosf(-6.28318530717958647692f * (r - rintf(r)), &sn, &cs);
+        return make_float2(cs, sn);
     } else {
         df sv = df_add({sa.x, sa.y}, {sb.x, sb.y});
         if (sv.hi >= 1.f) return make_float2(0.f, 0.f);
@@ -124,20 +128,13 @@ __device__ __forceinline__ double2 nonsep_factor(const double* __restrict__ s, i
     return make_double2(cs, sn);
 }
 
-// M[c][q] *= Tx(q) Ty(r0 + c) E(q, r0 + c) for the CTA's rows
-template <typename V, int LOGNP, int ROWS, int P>
-__device__ __forceinline__ void apply_modes(V* __restrict__ M, int r0, const V* __restrict__ tx,
-                                            const V* __restrict__ ty,
-                                            const typename STable<V>::type* __restrict__ s, const RowArgs& a) {
-    constexpr int NP = 1 << LOGNP;
-#pragma unroll 4
-    for (int idx = threadIdx.x; idx < ROWS * NP; idx += P) {
-        const int c = idx >> LOGNP, q = idx & (NP - 1);
-        const int r = r0 + c;
-        V f = cmul(__ldg(&tx[q]), __ldg(&ty[r]));
-        if (a.nonsep && (f.x != 0 || f.y != 0)) f = cmul(f, nonsep_factor(s, q, r, a));
-        M[idx] = cmul(M[idx], f);
-    }
+// Tx(q) Ty(r) E(q, r): the per-mode factor applied between the row transforms
+template <typename V>
+__device__ __forceinline__ V mode_factor(int q, int r, const V* __restrict__ tx, const V* __restrict__ ty,
+                                         const typename STable<V>::type* __restrict__ s, const RowArgs& a) {
+    V f = cmul(__ldg(&tx[q]), __ldg(&ty[r]));
+    if (a.nonsep && (f.x != 0 || f.y != 0)) f = cmul(f, nonsep_factor(s, q, r, a));
+    return f;
 }
 
 // --------------------------------------------------------------- type-1 row pass
@@ -165,8 +162,8 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     };
     auto put = [&](int row, int pk, int sgn, V v) {
         const int pb = 2 * pk + sgn;
-        if (pb < HALF) M[row * NP + pb] = v;
-        else if (pb >= 3 * HALF) M[row * NP + pb - NP] = v;
+        const int q = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
+        if (q >= 0) M[row * NP + q] = cmul(v, mode_factor<V>(q, r0 + row, tx, ty, s, a));
     };
     if constexpr (Cf::MERGE) {
         block_fft<V, -1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false>(
@@ -179,8 +176,6 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
                 S, tw, [&](int p, int c) { return folded(c, p, sgn); },
                 [&](int pk, int c, V v) { put(c, pk, sgn, v); });
     }
-    __syncthreads();
-    apply_modes<V, LOGNP, ROWS, Cf::P>(M, r0, tx, ty, s, a);
     __syncthreads();
     const int n = a.n;
     block_fft<V, +1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
@@ -208,9 +203,7 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     const V zero = CTraits<V>::zero();
     block_fft<V, -1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
         S, tw, [&](int p, int c) { return p < n ? B[(r0 + c) * n + p] : zero; },
-        [&](int p, int c, V v) { M[c * NP + p] = v; });
-    __syncthreads();
-    apply_modes<V, LOGNP, ROWS, Cf::P>(M, r0, tx, ty, s, a);
+        [&](int p, int c, V v) { M[c * NP + p] = cmul(v, mode_factor<V>(p, r0 + c, tx, ty, s, a)); });
     __syncthreads();
     auto get = [&](int row, int q, int sgn) -> V {
         const V y = M[row * NP + q];
