@@ -210,9 +210,10 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
 }
 
 // passes of radix E, then the remainder (LOGL mod log2 E) as one smaller-radix pass
-template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, int I, class LoadF, class StoreF>
+template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, int I, class LoadF, class StoreF,
+          class HookF>
 __device__ __forceinline__ void run_passes(V* __restrict__ sm, const V* __restrict__ tw, LoadF& load,
-                                           StoreF& store) {
+                                           StoreF& store, HookF& after_first) {
     constexpr int LE = Log2<E>::v;
     constexpr int NFULL = LOGL / LE;
     constexpr int REM = LOGL % LE;
@@ -220,16 +221,27 @@ __device__ __forceinline__ void run_passes(V* __restrict__ sm, const V* __restri
     if constexpr (I < NPASS) {
         constexpr int LR = I < NFULL ? LE : REM;
         stockham_pass<V, DIR, E, LOGL, LOGC, ROWMAJOR, LR, I * LE, I == 0, I == NPASS - 1>(sm, tw, load, store);
-        run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, I + 1>(sm, tw, load, store);
+        if constexpr (I == 0) after_first();
+        run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, I + 1>(sm, tw, load, store, after_first);
     }
 }
 
 // Full transform.  DIR = -1: forward (exp(-2 pi i ...)), +1: inverse, unnormalised.
 // The caller synchronises before the call if `sm` still holds data that other
-// threads read.
+// threads read.  `after_first` runs on every thread once the first pass has
+// finished reading its inputs (after that pass's closing barrier when there
+// are further passes): the load functor's source may be reused from then on.
+template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, class LoadF, class StoreF,
+          class HookF>
+__device__ __forceinline__ void block_fft(V* __restrict__ sm, const V* __restrict__ tw, LoadF load, StoreF store,
+                                          HookF after_first) {
+    run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, 0>(sm, tw, load, store, after_first);
+}
+
 template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, class LoadF, class StoreF>
 __device__ __forceinline__ void block_fft(V* __restrict__ sm, const V* __restrict__ tw, LoadF load, StoreF store) {
-    run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, 0>(sm, tw, load, store);
+    auto none = [] {};
+    run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, 0>(sm, tw, load, store, none);
 }
 
 }  // namespace nuasm

@@ -105,6 +105,8 @@ void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t);
 void free_tables(HostTables* t);
 
 // launchers (gridding.cu / passes.cu); all asynchronous on `s`
+// (the device error word P->d.err: bit 1 = point outside the window at plan
+// time, bit 2 = a bounded device wait gave up)
 nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, const double* w,
                          cudaStream_t s);
 cudaError_t bin_points_into(const nuasm_plan_s* P, const double* x, const double* y, int* cnt, void* rec_tmp,

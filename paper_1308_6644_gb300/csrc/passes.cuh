@@ -34,6 +34,7 @@
 #include "common.cuh"
 #include "fft_engine.cuh"
 #include "nuasm_internal.h"
+#include "tma.cuh"
 
 namespace nuasm {
 namespace passes {
@@ -293,6 +294,129 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP>::P, ColCfg<V, LOGNP>::MINB)
     }
 }
 
+// --------------------------------------------------------------- TMA column passes (FP32)
+// Persistent variant of col_kernel: each CTA walks column strips s, s + G, ...
+// One elected thread loads a strip (C columns x all needed rows) into a raw
+// shared buffer with 2-D TMA boxes of C x BOXR elements completed on an
+// mbarrier; rows and columns outside the array arrive as zeros, which provides
+// the zero padding and the window clipping for free.  The FFT's first pass
+// reads the raw buffer; right after that pass the next strip's load is issued,
+// so it overlaps the remaining passes.  The folded modes compute both halves
+// from one load.  Waits are bounded: a wait that gives up sets bit 2 of the
+// plan's error word, waits once more for its own copy and the CTA returns.
+// Tuning knobs: columns per TMA strip (NUASM_TMA_C) and the column modes that
+// use the TMA pipeline (bit MODE of NUASM_TMA_MODES; by default the two folded
+// passes, whose strips are numerous enough to keep a persistent pipeline busy).
+#ifndef NUASM_TMA_C
+#define NUASM_TMA_C 4
+#endif
+#ifndef NUASM_TMA_MODES
+#define NUASM_TMA_MODES 0x9
+#endif
+
+template <int LOGNP, int MODE> struct TmaColCfg {
+    using Base = ColCfg<float2, LOGNP>;
+    static constexpr int NP = Base::NP;
+    static constexpr int C = Base::C < NUASM_TMA_C ? Base::C : NUASM_TMA_C;
+    static constexpr int LOGC = Log2<C>::v;
+    static constexpr int E = Base::E;
+    static constexpr int P = (NP * C) / E;
+    static constexpr int BOXR = NP < 256 ? NP : 256;
+    static constexpr int RAW_ROWS = MODE == COL_FWD_FOLD ? NP + BOXR : NP;
+    static constexpr size_t RAW_BYTES = size_t(RAW_ROWS) * C * sizeof(float2);
+    static constexpr size_t WORK_BYTES = ((size_t(spad_size<float2>(NP * C)) * sizeof(float2)) + 127) & ~size_t(127);
+    static size_t smem() { return 128 + RAW_BYTES + WORK_BYTES + 16; }
+};
+
+template <int LOGNP, int MODE>
+__global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, 65536 / (TmaColCfg<LOGNP, MODE>::P * 64))
+    col_tma_kernel(const __grid_constant__ CUtensorMap map, float2* __restrict__ dst, const float2* __restrict__ tw,
+                   ColArgs a, int nstrips, int nboxes, int* __restrict__ err) {
+    using Cf = TmaColCfg<LOGNP, MODE>;
+    constexpr int NP = Cf::NP, HALF = NP / 2, C = Cf::C, BOXR = Cf::BOXR;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float2* raw = reinterpret_cast<float2*>(base);
+    float2* S = reinterpret_cast<float2*>(base + Cf::RAW_BYTES);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + Cf::RAW_BYTES + Cf::WORK_BYTES);
+    const int tid = threadIdx.x;
+    const int W = a.W, Wp = a.Wp, n = a.n;
+    const float2 zero = make_float2(0.f, 0.f);
+    if (tid == 0) tma::mbar_init(bar, 1);
+    __syncthreads();
+    auto issue = [&](int strip) {
+        tma::mbar_expect_tx(bar, uint32_t(nboxes) * BOXR * C * uint32_t(sizeof(float2)));
+        for (int b = 0; b < nboxes; ++b) tma::load_2d(raw + b * BOXR * C, &map, strip * C, b * BOXR, bar);
+    };
+    if (tid == 0 && int(blockIdx.x) < nstrips) issue(blockIdx.x);
+    uint32_t parity = 0;
+    for (int s = blockIdx.x; s < nstrips; s += gridDim.x) {
+        const bool ok = tma::mbar_wait(bar, parity);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(err, 2);
+                tma::mbar_wait(bar, parity);
+            }
+            return;
+        }
+        parity ^= 1;
+        const int col0 = s * C, next = s + gridDim.x;
+        auto prefetch = [&] {
+            if (tid == 0 && next < nstrips) issue(next);
+        };
+        auto nothing = [] {};
+        if constexpr (MODE == COL_FWD_FOLD) {
+            // raw: window rows [0, NP + BOXR) of C columns (zero beyond the window)
+#pragma unroll 1
+            for (int sgn = 0; sgn < 2; ++sgn) {
+                auto load = [&](int p, int c) -> float2 {
+                    // rows p + N' < W lie within the first BOXR rows past N' (W - N' = 2h <= 16)
+                    const float2 u = raw[p * C + c], t = p < BOXR ? raw[(p + NP) * C + c] : zero;
+                    return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
+                };
+                auto store = [&](int pk, int c, float2 v) {
+                    const int col = col0 + c;
+                    const int pb = 2 * pk + sgn;
+                    const int r = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
+                    if (r >= 0 && col < W) dst[r * Wp + col] = v;
+                };
+                if (sgn == 0) block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, nothing);
+                else block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, prefetch);
+            }
+        } else if constexpr (MODE == COL_INV_FOLD) {
+            // raw: rows [0, N') of A, C columns (zero beyond the window's columns)
+#pragma unroll 1
+            for (int sgn = 0; sgn < 2; ++sgn) {
+                auto load = [&](int q, int c) -> float2 {
+                    const float2 y = raw[q * C + c];
+                    if (sgn == 0) return y;
+                    const int pg = q < HALF ? q : q + NP;
+                    return cmul(y, cconj(__ldg(&tw[pg])));
+                };
+                auto store = [&](int k, int c, float2 v) {
+                    const int col = col0 + c;
+                    const int u = 2 * k + sgn;
+                    if (u < W && col < W) dst[u * Wp + col] = v;
+                };
+                if (sgn == 0) block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, nothing);
+                else block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, prefetch);
+            }
+        } else if constexpr (MODE == COL_INV) {
+            block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGC, false>(
+                S, tw, [&](int p, int c) { return raw[p * C + c]; },
+                [&](int p, int c, float2 v) {
+                    if (p < n) dst[p * n + col0 + c] = v;
+                },
+                prefetch);
+        } else {
+            block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGC, false>(
+                S, tw, [&](int p, int c) { return p < n ? raw[p * C + c] : zero; },
+                [&](int p, int c, float2 v) { dst[p * n + col0 + c] = v; }, prefetch);
+        }
+    }
+}
+
 // --------------------------------------------------------------- launchers
 template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
@@ -347,19 +471,70 @@ cudaError_t launch_col(const nuasm_plan_s* P, const void* src, void* dst, int nc
     return cudaGetLastError();
 }
 
+// TMA variant (FP32, at least two columns per strip); returns cudaErrorNotSupported
+// when the source array breaks the TMA alignment rules, so the caller can fall back.
+template <int LOGNP, int MODE>
+cudaError_t launch_col_tma(const nuasm_plan_s* P, const void* src, void* dst, int ncols, int src_cols,
+                           int src_rows, int src_pitch, int load_rows, cudaStream_t st) {
+    using Cf = TmaColCfg<LOGNP, MODE>;
+    if constexpr (Cf::C < 2 || Cf::NP < 512 || !((NUASM_TMA_MODES >> MODE) & 1)) {
+        return cudaErrorNotSupported;
+    } else {
+        CUtensorMap map;
+        if (!encode_map_8b(&map, src, src_cols, src_rows, src_pitch, Cf::C, Cf::BOXR)) return cudaErrorNotSupported;
+        const size_t sm = Cf::smem();
+        cudaError_t e = set_smem(col_tma_kernel<LOGNP, MODE>, sm);
+        if (e != cudaSuccess) return e;
+        static int ctas = 0;   // persistent grid: resident CTAs on the whole GPU
+        if (ctas == 0) {
+            int dev = 0, nsm = 0, per = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, col_tma_kernel<LOGNP, MODE>, Cf::P, sm)) !=
+                cudaSuccess)
+                return e;
+            ctas = nsm * (per > 0 ? per : 1);
+        }
+        const int nstrips = (ncols + Cf::C - 1) / Cf::C;
+        const int nboxes = (load_rows + Cf::BOXR - 1) / Cf::BOXR;
+        const int grid = nstrips < ctas ? nstrips : ctas;
+        const ColArgs a{P->g.n, P->g.W, P->g.Wp};
+        col_tma_kernel<LOGNP, MODE><<<grid, Cf::P, sm, st>>>(map, static_cast<float2*>(dst),
+                                                             static_cast<const float2*>(P->d.tw), a, nstrips, nboxes,
+                                                             P->d.err);
+        return cudaGetLastError();
+    }
+}
+
 // all FFT stages of one precision and one N'
 template <typename V, int LOGNP> struct Stages {
+    static constexpr bool kTma = sizeof(V) == 8;
+    template <int MODE>
+    static cudaError_t col(const nuasm_plan_s* P, const void* src, void* dst, int ncols, int src_cols, int src_rows,
+                           int src_pitch, int load_rows, cudaStream_t s) {
+        if constexpr (kTma) {
+            const cudaError_t e = launch_col_tma<LOGNP, MODE>(P, src, dst, ncols, src_cols, src_rows, src_pitch,
+                                                              load_rows, s);
+            if (e != cudaErrorNotSupported) return e;
+        }
+        const int halves = (MODE == COL_FWD_FOLD || MODE == COL_INV_FOLD) ? 2 : 1;
+        return launch_col<V, LOGNP, MODE>(P, src, dst, ncols, halves, s);
+    }
     static cudaError_t col_fwd_fold(const nuasm_plan_s* P, cudaStream_t s) {
-        return launch_col<V, LOGNP, COL_FWD_FOLD>(P, P->d.win, P->d.bufA, P->g.W, 2, s);
+        const Geometry& g = P->g;
+        return col<COL_FWD_FOLD>(P, P->d.win, P->d.bufA, g.W, g.W, g.W, g.Wp, g.np + (g.np < 256 ? g.np : 256), s);
     }
     static cudaError_t col_inv(const nuasm_plan_s* P, void* u2, cudaStream_t s) {
-        return launch_col<V, LOGNP, COL_INV>(P, P->d.bufB, u2, P->g.n, 1, s);
+        const Geometry& g = P->g;
+        return col<COL_INV>(P, P->d.bufB, u2, g.n, g.n, g.np, g.n, g.np, s);
     }
     static cudaError_t col_fwd(const nuasm_plan_s* P, const void* u1, cudaStream_t s) {
-        return launch_col<V, LOGNP, COL_FWD>(P, u1, P->d.bufB, P->g.n, 1, s);
+        const Geometry& g = P->g;
+        return col<COL_FWD>(P, u1, P->d.bufB, g.n, g.n, g.n, g.n, g.n, s);
     }
     static cudaError_t col_inv_fold(const nuasm_plan_s* P, cudaStream_t s) {
-        return launch_col<V, LOGNP, COL_INV_FOLD>(P, P->d.bufA, P->d.win, P->g.W, 2, s);
+        const Geometry& g = P->g;
+        return col<COL_INV_FOLD>(P, P->d.bufA, P->d.win, g.W, g.W, g.np, g.Wp, g.np, s);
     }
     static cudaError_t row(const nuasm_plan_s* P, int type, cudaStream_t s) { return launch_row<V, LOGNP>(P, type, s); }
 };
