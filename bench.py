@@ -147,13 +147,15 @@ def stage_bytes(info: dict, m: int) -> dict:
     }
 
 
-KERNEL_OF_STAGE = {"col_fwd": "col_kernel<float2, 2>", "row_t2": "row_t2_kernel<float2>",
-                   "col_inv_fold": "col_kernel<float2, 3>", "interp": "interp_kernel<float, 8>"}
-STAGE_SOURCES = {"col_fwd": ["passes.cu", "fft_engine.cuh"], "row_t2": ["passes.cu", "fft_engine.cuh"],
-                 "col_inv_fold": ["passes.cu", "fft_engine.cuh"], "interp": ["gridding.cu"]}
+KERNEL_OF_STAGE = {"col_fwd": "col_kernel<float2, 11, 2>", "row_t2": "row_t2_kernel<float2, 11>",
+                   "col_inv_fold": "col_tma_kernel<11, 3>", "interp": "interp_kernel<float, 7, true>"}
+STAGE_SOURCES = {"col_fwd": ["passes.cuh", "fft_engine.cuh"], "row_t2": ["passes.cuh", "fft_engine.cuh"],
+                 "col_inv_fold": ["passes.cuh", "fft_engine.cuh", "tma.cuh"], "interp": ["gridding.cu"]}
 
 
 def source_hash(stage: str) -> str:
+    """Hash of the sources a stage's kernel is compiled from (traffic figures
+    taken with ncu are reported only while this matches)."""
     h = hashlib.sha256()
     for f in STAGE_SOURCES[stage] + ["common.cuh"]:
         with open(os.path.join(ROOT, "paper_1308_6644_gb300", "csrc", f), "rb") as fh:
