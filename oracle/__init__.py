@@ -7,7 +7,7 @@ package imports nothing from the library: the two share no code.
 Parity status of each function (see the pins in ``tests/test_oracle_pins.py``):
 
 * asm_transfer, fresnel_transfer, nudft_type1, nudft_type2, uniform_dft,
-  uniform_idft_crop, diffraction_type1/2 and their NU-ASM / NU-FRE wrappers:
+  uniform_idft_crop, diffraction_type1/2/3 and their NU-ASM / NU-FRE wrappers:
   pinned (brute-force pairwise sums, numpy.fft ASM on lattice points, the
   z = 0 Dirichlet closed form, Parseval in band, the adjoint identity, the
   Fresnel Gaussian-beam closed form, the exact complex-source-point solution
@@ -18,5 +18,6 @@ Parity status of each function (see the pins in ``tests/test_oracle_pins.py``):
 from .diffraction import (  # noqa: F401
     modes, lattice, band_limits, band_mask_1d, asm_transfer, fresnel_transfer,
     nudft_type1, nudft_type2, uniform_dft, uniform_idft_crop,
-    diffraction_type1, diffraction_type2, nuasm1, nuasm2, nufresnel, rel_l2,
+    diffraction_type1, diffraction_type2, diffraction_type3, nuasm1, nuasm2, nuasm3, nufresnel,
+    nufresnel3, rel_l2,
 )

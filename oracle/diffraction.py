@@ -283,6 +283,29 @@ def diffraction_type2(u1, x, y, p: dict, h=None) -> np.ndarray:
     return nudft_type2(g * hh / float(n_pad) ** 2, xi_x, xi_y, n_pad)
 
 
+def diffraction_type3(x1, y1, c, x2, y2, p: dict, weights=None, h=None) -> np.ndarray:
+    """NU-ASM_3 / NU-FRE_3: non-uniform source points -> non-uniform
+    destination points, the combination of Eq. 6 and Eq. 9 through the
+    spectrum:  v_j = (1/N'^2) sum_k F(k) H(k) exp(2 pi i f_k . x2_j),
+    F = NUFFT_1[w c] at the source points (Eq. 7), the outer sum NUFFT_2 at
+    the destination points (Eq. 8), both evaluated directly.
+    """
+    n = p["n"]
+    n_pad = p.get("n_pad") or 2 * n
+    xi1x = np.asarray(x1, np.float64) / p["pitch"]
+    xi1y = np.asarray(y1, np.float64) / p["pitch"]
+    xi2x = np.asarray(x2, np.float64) / p["pitch"]
+    xi2y = np.asarray(y2, np.float64) / p["pitch"]
+    for xi in (xi1x, xi1y, xi2x, xi2y):
+        _check_window(xi, n)
+    c = np.asarray(c, np.complex128)
+    if weights is not None:
+        c = c * np.asarray(weights, np.float64)
+    f = nudft_type1(xi1x, xi1y, c, n_pad)
+    hh = _transfer(p) if h is None else h
+    return nudft_type2(f * hh / float(n_pad) ** 2, xi2x, xi2y, n_pad)
+
+
 def nuasm1(x, y, c, p, weights=None):
     """NU-ASM_1 (Eq. 6)."""
     return diffraction_type1(x, y, c, dict(p, kind="asm"), weights)
@@ -291,6 +314,16 @@ def nuasm1(x, y, c, p, weights=None):
 def nuasm2(u1, x, y, p):
     """NU-ASM_2 (Eq. 9)."""
     return diffraction_type2(u1, x, y, dict(p, kind="asm"))
+
+
+def nuasm3(x1, y1, c, x2, y2, p, weights=None):
+    """NU-ASM_3: non-uniform source -> non-uniform destination (ASM, Eq. 4)."""
+    return diffraction_type3(x1, y1, c, x2, y2, dict(p, kind="asm"), weights)
+
+
+def nufresnel3(x1, y1, c, x2, y2, p, weights=None):
+    """NU-FRE_3: non-uniform source -> non-uniform destination (Fresnel, Eq. 5)."""
+    return diffraction_type3(x1, y1, c, x2, y2, dict(p, kind="fresnel"), weights)
 
 
 def nufresnel(type_: int, inp, x, y, p, weights=None):

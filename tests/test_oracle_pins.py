@@ -392,3 +392,54 @@ def test_paper_quadrant_geometry_fits_window():
         sel = (np.sign(x) == sx) & (np.sign(y) == sy)
         xs = np.unique(np.round(np.abs(x[sel]) / pitch, 9))
         assert np.allclose(np.diff(xs), s)
+
+
+# ----------------------------------------------------------------------------
+# Type 3 (NU-ASM_3 / NU-FRE_3): both planes non-uniform
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["asm", "fresnel"])
+def test_type3_matches_pairwise_sum(kind):
+    rng = _rng(20)
+    n, pitch = 4, 10e-6
+    p = _asm_params(n, pitch, z=0.004, ox=4e-6, oy=-3e-6, kind=kind)
+    x1, y1 = _points(rng, n, pitch, 5)
+    x2, y2 = _points(rng, n, pitch, 4)
+    c = rng.normal(size=5) + 1j * rng.normal(size=5)
+    h = O.diffraction._transfer(p)
+    got = O.diffraction_type3(x1, y1, c, x2, y2, p)
+    for j in range(len(x2)):
+        want = sum(c[i] * _h_tilde(h, 2 * n, (x2[j] - x1[i]) / pitch, (y2[j] - y1[i]) / pitch)
+                   for i in range(len(c)))
+        assert abs(got[j] - want) <= 1e-13 * max(1.0, abs(want))
+
+
+@pytest.mark.parametrize("kind", ["asm", "fresnel"])
+def test_type3_reduces_to_types_1_and_2_on_lattices(kind):
+    rng = _rng(21)
+    n, pitch = 16, 8e-6
+    p = _asm_params(n, pitch, lam=532e-9, z=0.03, ox=16e-6, oy=-8e-6, kind=kind)
+    m = O.lattice(n) * pitch
+    gy, gx = np.meshgrid(m, m, indexing="ij")
+    xs, ys = _points(rng, n, pitch, 40)
+    c = rng.normal(size=40) + 1j * rng.normal(size=40)
+    u1 = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    # lattice destination: type 3 == type 1
+    assert O.rel_l2(O.diffraction_type3(xs, ys, c, gx.ravel(), gy.ravel(), p),
+                    O.diffraction_type1(xs, ys, c, p).ravel()) < 1e-13
+    # lattice source: type 3 == type 2
+    assert O.rel_l2(O.diffraction_type3(gx.ravel(), gy.ravel(), u1.ravel(), xs, ys, p),
+                    O.diffraction_type2(u1, xs, ys, p)) < 1e-13
+
+
+def test_type3_z0_dirichlet_closed_form():
+    rng = _rng(22)
+    n, pitch = 8, 10e-6
+    p = _asm_params(n, pitch, z=0.0)
+    x1, y1 = _points(rng, n, pitch, 12)
+    x2, y2 = _points(rng, n, pitch, 9)
+    c = rng.normal(size=12) + 1j * rng.normal(size=12)
+    got = O.nuasm3(x1, y1, c, x2, y2, p)
+    want = np.array([np.sum(c * _dirichlet((x2[j] - x1) / pitch, 2 * n) * _dirichlet((y2[j] - y1) / pitch, 2 * n))
+                     for j in range(len(x2))])
+    assert O.rel_l2(got, want) < 1e-13
