@@ -155,6 +155,23 @@ nuasm_status nuasm2_execute(nuasm_plan_t plan, const void* u1, void* v, void* st
 nuasm_status nufresnel_execute(nuasm_plan_t plan, int32_t type, const void* in, void* out,
                                void* stream);
 
+/*
+ * nuasm3_execute -- NU-ASM_3: non-uniform source -> non-uniform destination,
+ * obtained by combining NU-ASM_1 and NU-ASM_2 through the spectrum (Eq. 6-9):
+ *     v_j = (1/N'^2) sum_k [sum_i w_i c_i exp(-2 pi i f_k . x_i)] H(k) exp(2 pi i f_k . y_j).
+ *  src  plan whose points x_i (and optional weights w_i) are the source samples;
+ *       its workspace is used.
+ *  dst  plan whose points y_j are the destination samples (read only).
+ *  c    src->m complex source values;  v  dst->m complex outputs.
+ * Both plans must have been built with identical parameters (else
+ * NUASM_EINVAL) and kind NUASM_KIND_ASM.
+ */
+nuasm_status nuasm3_execute(nuasm_plan_t src, nuasm_plan_t dst, const void* c, void* v, void* stream);
+
+/* nufresnel3_execute -- NU-FRE_3: as nuasm3_execute with the Fresnel transfer
+ * function of Eq. 5 (both plans of kind NUASM_KIND_FRESNEL). */
+nuasm_status nufresnel3_execute(nuasm_plan_t src, nuasm_plan_t dst, const void* c, void* v, void* stream);
+
 /* Release every resource of the plan (synchronises the plan's device work). NULL is a no-op. */
 nuasm_status nuasm_destroy(nuasm_plan_t plan);
 
@@ -190,7 +207,7 @@ nuasm_status nuasm_kernel_shape(double tol, int32_t prec, int32_t* width, double
 enum {
     NUASM_STAGE_H2D = 0, NUASM_STAGE_SPREAD, NUASM_STAGE_COL_FWD_FOLD, NUASM_STAGE_ROW_T1,
     NUASM_STAGE_COL_INV, NUASM_STAGE_COL_FWD, NUASM_STAGE_ROW_T2, NUASM_STAGE_COL_INV_FOLD,
-    NUASM_STAGE_INTERP, NUASM_STAGE_D2H, NUASM_STAGE_COUNT
+    NUASM_STAGE_INTERP, NUASM_STAGE_D2H, NUASM_STAGE_ROW_T3, NUASM_STAGE_COUNT
 };
 nuasm_status nuasm_profile_enable(nuasm_plan_t plan, int32_t enable);
 nuasm_status nuasm_profile_read(nuasm_plan_t plan, double* ms, int64_t* launches);

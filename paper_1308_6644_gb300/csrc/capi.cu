@@ -131,7 +131,7 @@ cudaError_t upload_tables(nuasm_plan_s* P, const HostTables& t, cudaStream_t st)
     const int np = P->g.np, G = P->g.G;
     const size_t eb = elt_bytes(P);
     const size_t sb = P->f64 ? sizeof(double) : sizeof(float2);
-    const size_t bytes = 4 * np * eb + np * sb + size_t(G) * eb;
+    const size_t bytes = 6 * np * eb + np * sb + size_t(G) * eb;
     char* base = nullptr;
     cudaError_t e = dalloc(P, &base, bytes);
     if (e != cudaSuccess) return e;
@@ -140,8 +140,10 @@ cudaError_t upload_tables(nuasm_plan_s* P, const HostTables& t, cudaStream_t st)
     P->d.t1y = base + np * eb;
     P->d.t2x = base + 2 * np * eb;
     P->d.t2y = base + 3 * np * eb;
-    P->d.s = base + 4 * np * eb;
-    P->d.tw = base + 4 * np * eb + np * sb;
+    P->d.t3x = base + 4 * np * eb;
+    P->d.t3y = base + 5 * np * eb;
+    P->d.s = base + 6 * np * eb;
+    P->d.tw = base + 6 * np * eb + np * sb;
     std::vector<char> host(bytes);
     auto put_c = [&](size_t off, const double* src, int count) {
         if (P->f64) std::memcpy(host.data() + off, src, sizeof(double) * 2 * count);
@@ -154,16 +156,18 @@ cudaError_t upload_tables(nuasm_plan_s* P, const HostTables& t, cudaStream_t st)
     put_c(np * eb, t.t1y, np);
     put_c(2 * np * eb, t.t2x, np);
     put_c(3 * np * eb, t.t2y, np);
-    if (P->f64) std::memcpy(host.data() + 4 * np * eb, t.s, sizeof(double) * np);
+    put_c(4 * np * eb, t.t3x, np);
+    put_c(5 * np * eb, t.t3y, np);
+    if (P->f64) std::memcpy(host.data() + 6 * np * eb, t.s, sizeof(double) * np);
     else {
-        float* d = reinterpret_cast<float*>(host.data() + 4 * np * eb);
+        float* d = reinterpret_cast<float*>(host.data() + 6 * np * eb);
         for (int i = 0; i < np; ++i) {
             float hi = float(t.s[i]);
             d[2 * i] = hi;
             d[2 * i + 1] = float(t.s[i] - double(hi));
         }
     }
-    put_c(4 * np * eb + np * sb, t.tw, G);
+    put_c(6 * np * eb + np * sb, t.tw, G);
     e = cudaMemcpyAsync(base, host.data(), bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(st);   // host buffer goes out of scope
@@ -243,6 +247,50 @@ nuasm_status exec_type2(nuasm_plan_s* P, const void* u1, void* v, cudaStream_t s
     if (!out_dev) {
         StageScope sc(P, NUASM_STAGE_D2H, st);
         NUASM_TRY(cudaMemcpyAsync(v, P->d.stage_out, eb * size_t(P->m), cudaMemcpyDeviceToHost, st));
+    }
+    return NUASM_OK;
+}
+
+bool same_problem(const nuasm_params_t& a, const nuasm_params_t& b) {
+    bool same = a.n == b.n && a.n_pad == b.n_pad && a.pitch == b.pitch && a.lambda == b.lambda && a.z == b.z &&
+                a.ox == b.ox && a.oy == b.oy && a.band_auto == b.band_auto && a.kind == b.kind &&
+                a.prec == b.prec && a.tol == b.tol;
+    if (same && !a.band_auto)
+        same = a.c_m == b.c_m && a.c_n == b.c_n && a.w_m == b.w_m && a.w_n == b.w_n;
+    return same;
+}
+
+// type 3: spread the source plan's points, fused forward/H/inverse row pass,
+// interpolate at the destination plan's points (same geometry, the source
+// plan's workspace)
+nuasm_status exec_type3(nuasm_plan_s* P, nuasm_plan_s* Q, const void* c, void* v, cudaStream_t st) {
+    nuasm_status s0 = check_plan_usable(P);
+    if (s0 != NUASM_OK) return s0;
+    if (!Q || !same_problem(P->p, Q->p)) return NUASM_EINVAL;
+    if ((P->m > 0 && !c) || (Q->m > 0 && !v)) return NUASM_EINVAL;
+    const size_t eb = elt_bytes(P);
+    const void* cin = c;
+    if (P->m > 0 && !device_accessible(c)) {
+        StageScope sc(P, NUASM_STAGE_H2D, st);
+        NUASM_TRY(cudaMemcpyAsync(P->d.stage_in, c, eb * size_t(P->m), cudaMemcpyHostToDevice, st));
+        cin = P->d.stage_in;
+    }
+    const bool out_dev = Q->m == 0 || device_accessible(v);
+    void* vo = out_dev ? v : Q->d.stage_out;
+    { StageScope sc(P, NUASM_STAGE_SPREAD, st); NUASM_TRY(launch_spread(P, cin, st)); }
+    { StageScope sc(P, NUASM_STAGE_COL_FWD_FOLD, st); NUASM_TRY(launch_col_fwd_fold(P, st)); }
+    { StageScope sc(P, NUASM_STAGE_ROW_T3, st); NUASM_TRY(launch_row_t3(P, st)); }
+    { StageScope sc(P, NUASM_STAGE_COL_INV_FOLD, st); NUASM_TRY(launch_col_inv_fold(P, st)); }
+    if (Q->m > 0) {
+        nuasm_plan_s view = *Q;          // destination records over the source plan's window
+        view.d.win = P->d.win;
+        view.prof = false;
+        StageScope sc(P, NUASM_STAGE_INTERP, st);
+        NUASM_TRY(launch_interp(&view, vo, st));
+    }
+    if (!out_dev) {
+        StageScope sc(P, NUASM_STAGE_D2H, st);
+        NUASM_TRY(cudaMemcpyAsync(v, Q->d.stage_out, eb * size_t(Q->m), cudaMemcpyDeviceToHost, st));
     }
     return NUASM_OK;
 }
@@ -342,6 +390,18 @@ nuasm_status nufresnel_execute(nuasm_plan_t plan, int32_t type, const void* in, 
     return NUASM_EINVAL;
 }
 
+nuasm_status nuasm3_execute(nuasm_plan_t src, nuasm_plan_t dst, const void* c, void* v, void* stream) {
+    if (!src || !dst) return NUASM_EINVAL;
+    if (src->p.kind != NUASM_KIND_ASM) return NUASM_EINVAL;
+    return exec_type3(src, dst, c, v, static_cast<cudaStream_t>(stream));
+}
+
+nuasm_status nufresnel3_execute(nuasm_plan_t src, nuasm_plan_t dst, const void* c, void* v, void* stream) {
+    if (!src || !dst) return NUASM_EINVAL;
+    if (src->p.kind != NUASM_KIND_FRESNEL) return NUASM_EINVAL;
+    return exec_type3(src, dst, c, v, static_cast<cudaStream_t>(stream));
+}
+
 nuasm_status nuasm_destroy(nuasm_plan_t plan) {
     if (!plan) return NUASM_OK;
     cudaError_t e = cudaDeviceSynchronize();
@@ -431,8 +491,9 @@ nuasm_status nuasm_profile_read(nuasm_plan_t plan, double* ms, int64_t* launches
 }
 
 const char* nuasm_stage_name(int32_t stage) {
-    static const char* names[NUASM_STAGE_COUNT] = {"h2d", "spread", "col_fwd_fold", "row_t1", "col_inv",
-                                                   "col_fwd", "row_t2", "col_inv_fold", "interp", "d2h"};
+    static const char* names[NUASM_STAGE_COUNT] = {"h2d",    "spread",       "col_fwd_fold", "row_t1",
+                                                   "col_inv", "col_fwd",      "row_t2",       "col_inv_fold",
+                                                   "interp", "d2h",          "row_t3"};
     if (stage < 0 || stage >= NUASM_STAGE_COUNT) return "unknown";
     return names[stage];
 }

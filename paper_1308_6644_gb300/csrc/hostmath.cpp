@@ -161,6 +161,13 @@ void asm_axis_factor(const nuasm_params_t& p, int np, int k, int axis, double* r
 void table_entry(const nuasm_params_t& p, const Geometry& g, int q, int type, double phihat, double hs_re,
                  double hs_im, double* re, double* im) {
     const int np = g.np;
+    if (type == 3) {
+        // type 1 forward then type 2 back: window phases and (-1)^k cancel
+        const double dec = 1.0 / (phihat * phihat * np);
+        *re = hs_re * dec;
+        *im = hs_im * dec;
+        return;
+    }
     const int k = q < np / 2 ? q : q - np;
     const double dec = ((k & 1) ? -1.0 : 1.0) / phihat / np;
     const cd win1 = cis_ratio(-int64_t(k) * g.Lo, g.G);      // window origin on the 2N' grid
@@ -276,6 +283,8 @@ void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t) {
     t->t1y = new double[2 * np];
     t->t2x = new double[2 * np];
     t->t2y = new double[2 * np];
+    t->t3x = new double[2 * np];
+    t->t3y = new double[2 * np];
     t->s = new double[np];
     t->tw = new double[2 * G];
 
@@ -319,6 +328,8 @@ void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t) {
         table_entry(p, g, q, 1, ph, hyc.real(), hyc.imag(), &t->t1y[2 * q], &t->t1y[2 * q + 1]);
         table_entry(p, g, q, 2, ph, hx[q].real(), hx[q].imag(), &t->t2x[2 * q], &t->t2x[2 * q + 1]);
         table_entry(p, g, q, 2, ph, hyc.real(), hyc.imag(), &t->t2y[2 * q], &t->t2y[2 * q + 1]);
+        table_entry(p, g, q, 3, ph, hx[q].real(), hx[q].imag(), &t->t3x[2 * q], &t->t3x[2 * q + 1]);
+        table_entry(p, g, q, 3, ph, hyc.real(), hyc.imag(), &t->t3y[2 * q], &t->t3y[2 * q + 1]);
         const double f = double(k) / (double(np) * p.pitch);
         t->s[q] = p.lambda * p.lambda * f * f;
     }
@@ -364,7 +375,7 @@ void fit_kernel_poly(const Geometry& g, KernelPoly* kp) {
 }
 
 void free_tables(HostTables* t) {
-    delete[] t->t1x; delete[] t->t1y; delete[] t->t2x; delete[] t->t2y;
+    delete[] t->t1x; delete[] t->t1y; delete[] t->t2x; delete[] t->t2y; delete[] t->t3x; delete[] t->t3y;
     delete[] t->s; delete[] t->tw;
     std::memset(t, 0, sizeof(*t));
 }

@@ -31,8 +31,8 @@ struct KernelPoly {
 
 // Host tables in FP64 (complex as re/im pairs), natural N'-bin order.
 struct HostTables {
-    // per-axis separable factors for type 1 and type 2, length N' each
-    double* t1x; double* t1y; double* t2x; double* t2y;   // 2*N' doubles each
+    // per-axis separable factors for types 1, 2 and 3, length N' each
+    double* t1x; double* t1y; double* t2x; double* t2y; double* t3x; double* t3y;   // 2*N' doubles each
     double* s;        // lambda^2 f_k^2 per bin (ASM), length N'
     double rc;        // z / (2 lambda)  (ASM non-separable phase scale)
     double rmax;      // largest |r| = |rc| q^2 over kept modes (0 when there is no such term)
@@ -43,6 +43,7 @@ struct HostTables {
 struct PlanDevice {
     void* tables = nullptr;     // one block holding every table below
     void* t1x = nullptr; void* t1y = nullptr; void* t2x = nullptr; void* t2y = nullptr;
+    void* t3x = nullptr; void* t3y = nullptr;
     void* s = nullptr;          // float2 (hi, lo) per bin (F32) or double (F64)
     void* tw = nullptr;         // twiddles, G complex
     void* rec = nullptr;        // binned point records
@@ -119,6 +120,7 @@ cudaError_t launch_row_t1(const nuasm_plan_s* P, cudaStream_t s);
 cudaError_t launch_col_inv(const nuasm_plan_s* P, void* u2, cudaStream_t s);
 cudaError_t launch_col_fwd(const nuasm_plan_s* P, const void* u1, cudaStream_t s);
 cudaError_t launch_row_t2(const nuasm_plan_s* P, cudaStream_t s);
+cudaError_t launch_row_t3(const nuasm_plan_s* P, cudaStream_t s);
 cudaError_t launch_col_inv_fold(const nuasm_plan_s* P, cudaStream_t s);
 
 }  // namespace nuasm

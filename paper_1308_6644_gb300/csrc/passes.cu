@@ -55,5 +55,8 @@ cudaError_t launch_row_t1(const nuasm_plan_s* P, cudaStream_t s) {
 cudaError_t launch_row_t2(const nuasm_plan_s* P, cudaStream_t s) {
     return P->f64 ? row_f64(P, 2, s) : row_f32(P, 2, s);
 }
+cudaError_t launch_row_t3(const nuasm_plan_s* P, cudaStream_t s) {
+    return P->f64 ? row_f64(P, 3, s) : row_f32(P, 3, s);
+}
 
 }  // namespace nuasm

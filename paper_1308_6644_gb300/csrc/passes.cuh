@@ -229,6 +229,68 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     }
 }
 
+// --------------------------------------------------------------- type-3 row pass
+// NU-ASM_3 / NU-FRE_3: one CTA = ROWS rows r of A (ky bin r, W window
+// entries): forward 2N' transform restricted to the kept modes (folded halves,
+// as in row_t1), multiply by T3x T3y E, inverse 2N' transform back onto the
+// window row (even/odd halves, as in row_t2), written over the input row (all
+// reads happen in the first forward pass, before any write).
+template <typename V, int LOGNP>
+__global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
+    row_t3_kernel(V* __restrict__ A, const V* __restrict__ tx, const V* __restrict__ ty,
+                  const typename STable<V>::type* __restrict__ s, const V* __restrict__ tw, RowArgs a) {
+    using Cf = RowCfg<V, LOGNP>;
+    constexpr int NP = Cf::NP, ROWS = Cf::ROWS, HALF = NP / 2;
+    extern __shared__ unsigned char smem_raw[];
+    V* S = reinterpret_cast<V*>(smem_raw);
+    V* M = S + spad_size<V>(NP * Cf::SEQ);
+    const int r0 = blockIdx.x * ROWS;
+    const int W = a.W, Wp = a.Wp;
+    const V zero = CTraits<V>::zero();
+    auto folded = [&](int row, int p, int sgn) -> V {
+        const V* x = A + (r0 + row) * Wp;
+        const V u = p < W ? x[p] : zero;
+        const V t = p + NP < W ? x[p + NP] : zero;
+        return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
+    };
+    auto put_mode = [&](int row, int pk, int sgn, V v) {
+        const int pb = 2 * pk + sgn;
+        const int q = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
+        if (q >= 0) M[row * NP + q] = cmul(v, mode_factor<V>(q, r0 + row, tx, ty, s, a));
+    };
+    auto get_mode = [&](int row, int q, int sgn) -> V {
+        const V y = M[row * NP + q];
+        if (sgn == 0) return y;
+        const int pg = q < HALF ? q : q + NP;
+        return cmul(y, cconj(__ldg(&tw[pg])));
+    };
+    auto put_row = [&](int row, int k, int sgn, V v) {
+        const int u = 2 * k + sgn;
+        if (u < W) A[(r0 + row) * Wp + u] = v;
+    };
+    if constexpr (Cf::MERGE) {
+        block_fft<V, -1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false>(
+            S, tw, [&](int p, int cs) { return folded(cs >> 1, p, cs & 1); },
+            [&](int pk, int cs, V v) { put_mode(cs >> 1, pk, cs & 1, v); });
+        __syncthreads();
+        block_fft<V, +1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false>(
+            S, tw, [&](int q, int cs) { return get_mode(cs >> 1, q, cs & 1); },
+            [&](int k, int cs, V v) { put_row(cs >> 1, k, cs & 1, v); });
+    } else {
+#pragma unroll 1
+        for (int sgn = 0; sgn < 2; ++sgn)
+            block_fft<V, -1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
+                S, tw, [&](int p, int c) { return folded(c, p, sgn); },
+                [&](int pk, int c, V v) { put_mode(c, pk, sgn, v); });
+        __syncthreads();
+#pragma unroll 1
+        for (int sgn = 0; sgn < 2; ++sgn)
+            block_fft<V, +1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
+                S, tw, [&](int q, int c) { return get_mode(c, q, sgn); },
+                [&](int k, int c, V v) { put_row(c, k, sgn, v); });
+    }
+}
+
 // --------------------------------------------------------------- column passes
 enum ColMode { COL_FWD_FOLD = 0, COL_INV = 1, COL_FWD = 2, COL_INV_FOLD = 3 };
 
@@ -449,6 +511,11 @@ cudaError_t launch_row(const nuasm_plan_s* P, int type, cudaStream_t st) {
         row_t1_kernel<V, LOGNP><<<blocks, Cf::P, sm, st>>>(
             static_cast<const V*>(P->d.bufA), static_cast<V*>(P->d.bufB), static_cast<const V*>(P->d.t1x),
             static_cast<const V*>(P->d.t1y), s, tw, a);
+    } else if (type == 3) {
+        if ((e = set_smem(row_t3_kernel<V, LOGNP>, sm)) != cudaSuccess) return e;
+        row_t3_kernel<V, LOGNP><<<blocks, Cf::P, sm, st>>>(static_cast<V*>(P->d.bufA),
+                                                          static_cast<const V*>(P->d.t3x),
+                                                          static_cast<const V*>(P->d.t3y), s, tw, a);
     } else {
         if ((e = set_smem(row_t2_kernel<V, LOGNP>, sm)) != cudaSuccess) return e;
         row_t2_kernel<V, LOGNP><<<blocks, Cf::P, sm, st>>>(

@@ -24,7 +24,7 @@ PREC_F32_F64PHASE, PREC_F64 = 0, 1
 STATUS = {0: "NUASM_OK", 1: "NUASM_EINVAL", 2: "NUASM_ERANGE", 3: "NUASM_ENOMEM",
           4: "NUASM_ECUDA", 5: "NUASM_ETIMEOUT", 6: "NUASM_EUNSUPPORTED"}
 STAGES = ["h2d", "spread", "col_fwd_fold", "row_t1", "col_inv", "col_fwd", "row_t2",
-          "col_inv_fold", "interp", "d2h"]
+          "col_inv_fold", "interp", "d2h", "row_t3"]
 
 
 class NuasmError(RuntimeError):
@@ -62,6 +62,8 @@ _SIGS = {
     "nuasm2_execute": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "nufresnel_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p]),
+    "nuasm3_execute": (ctypes.c_int, [ctypes.c_void_p] * 5),
+    "nufresnel3_execute": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "nuasm_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "nuasm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "nuasm_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
@@ -243,6 +245,22 @@ def nufresnel_execute(plan: Plan, type_: int, inp, out, stream=None):
     _check(lib().nufresnel_execute(plan._h, int(type_), _ptr(inp), _ptr(out), _stream(stream)),
            "nufresnel_execute")
     return out
+
+
+def nuasm3_execute(src: Plan, dst: Plan, c, v, stream=None):
+    """NU-ASM_3: c (src.m complex, at src's points) -> v (dst.m complex, at dst's points)."""
+    _expect(c, src.m, src.complex_dtype, "c")
+    _expect(v, dst.m, dst.complex_dtype, "v")
+    _check(lib().nuasm3_execute(src._h, dst._h, _ptr(c), _ptr(v), _stream(stream)), "nuasm3_execute")
+    return v
+
+
+def nufresnel3_execute(src: Plan, dst: Plan, c, v, stream=None):
+    """NU-FRE_3: as nuasm3_execute with the Fresnel transfer function."""
+    _expect(c, src.m, src.complex_dtype, "c")
+    _expect(v, dst.m, dst.complex_dtype, "v")
+    _check(lib().nufresnel3_execute(src._h, dst._h, _ptr(c), _ptr(v), _stream(stream)), "nufresnel3_execute")
+    return v
 
 
 def nuasm_destroy(plan: Plan):

@@ -1,0 +1,121 @@
+"""NU-ASM_3 / NU-FRE_3 (both planes non-uniform) on the GPU against the oracle
+and, at full size, against the Gaussian-beam closed form."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1308_6644_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+TOL = {"f32": 1e-5, "f64": 1e-10}
+CDT = {"f32": np.complex64, "f64": np.complex128}
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1308_6644_gb300 as pkg
+    return pkg
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run3(P, kind, prec, params, x1, y1, c, x2, y2, w=None):
+    import torch
+    src = P.nuasm_plan(params, _dev(x1), _dev(y1), None if w is None else _dev(w))
+    dst = P.nuasm_plan(params, _dev(x2), _dev(y2))
+    try:
+        tdt = torch.complex64 if prec == "f32" else torch.complex128
+        v = torch.zeros(len(x2), dtype=tdt, device="cuda")
+        cc = _dev(np.asarray(c).astype(CDT[prec]))
+        (P.nuasm3_execute if kind == "asm" else P.nufresnel3_execute)(src, dst, cc, v)
+        torch.cuda.synchronize()
+        return v.cpu().numpy()
+    finally:
+        src.destroy()
+        dst.destroy()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("kind", ["asm", "fresnel"])
+@pytest.mark.parametrize("n", [16, 64])
+def test_type3_random_points(P, prec, kind, n):
+    rng = np.random.default_rng(300 + n)
+    pitch = 10e-6
+    half = 0.5 * n * pitch
+    m1, m2 = (600, 500) if n == 64 else (120, 90)
+    x1 = WL.clamp_window(rng.uniform(-half, half, m1), n, pitch)
+    y1 = WL.clamp_window(rng.uniform(-half, half, m1), n, pitch)
+    x2 = WL.clamp_window(rng.uniform(-half, half, m2), n, pitch)
+    y2 = WL.clamp_window(rng.uniform(-half, half, m2), n, pitch)
+    c = rng.normal(size=m1) + 1j * rng.normal(size=m1)
+    kw = dict(lam=633e-9, z=0.03, ox=20e-6, oy=-10e-6)
+    params = P.make_params(n, pitch, kw["lam"], kw["z"], ox=kw["ox"], oy=kw["oy"], kind=kind, prec=prec)
+    got = run3(P, kind, prec, params, x1, y1, c, x2, y2)
+    p = dict(n=n, pitch=pitch, kind=kind, **kw)
+    ref = O.diffraction_type3(x1, y1, c.astype(CDT[prec]), x2, y2, p)
+    assert O.rel_l2(got, ref) < TOL[prec]
+
+
+def test_type3_weights_and_graded_destination(P):
+    n, pitch = 64, 8e-6
+    rng = np.random.default_rng(7)
+    wl = WL.nuasm2_graded(seed=31, n=n, pitch=pitch)
+    x1, y1 = WL.dense_centre_lattice(rng, n, pitch, 0.4, 16)
+    x1, y1 = WL.clamp_window(x1, n, pitch), WL.clamp_window(y1, n, pitch)
+    c = WL.random_phasor(rng, len(x1))
+    w = rng.uniform(0.5, 1.5, len(x1))
+    params = P.make_params(n, pitch, 532e-9, 0.05, ox=100e-6, prec="f64")
+    got = run3(P, "asm", "f64", params, x1, y1, c, wl.x, wl.y, w=w)
+    ref = O.nuasm3(x1, y1, c, wl.x, wl.y, dict(n=n, pitch=pitch, lam=532e-9, z=0.05, ox=100e-6), weights=w)
+    assert O.rel_l2(got, ref) < TOL["f64"]
+
+
+def test_type3_rejects_mismatched_plans(P):
+    import torch
+    x = _dev(np.zeros(4))
+    a = P.nuasm_plan(P.make_params(32, 10e-6, 633e-9, 0.01), x, x)
+    b = P.nuasm_plan(P.make_params(32, 10e-6, 633e-9, 0.02), x, x)
+    try:
+        with pytest.raises(P.NuasmError) as ei:
+            P.nuasm3_execute(a, b, torch.zeros(4, dtype=torch.complex64, device="cuda"),
+                             torch.zeros(4, dtype=torch.complex64, device="cuda"))
+        assert ei.value.code == 1
+        with pytest.raises(P.NuasmError):
+            P.nufresnel3_execute(a, a, torch.zeros(4, dtype=torch.complex64, device="cuda"),
+                                 torch.zeros(4, dtype=torch.complex64, device="cuda"))
+    finally:
+        a.destroy()
+        b.destroy()
+
+
+def _gaussian_fresnel(x, y, lam, z, w0):
+    a, b, zr = 1 / w0 ** 2, np.pi / (lam * z), np.pi * w0 ** 2 / lam
+    ph = np.longdouble(z) / np.longdouble(lam)
+    ph = float(ph - np.rint(ph))
+    return np.exp(2j * np.pi * ph) / (1 + 1j * z / zr) * np.exp(1j * a * b * (x * x + y * y) / (a - 1j * b))
+
+
+@pytest.mark.parametrize("kind", ["fresnel", "asm"])
+def test_type3_full_size_closed_form(P, kind):
+    """N = 2048: 4,194,304 warped-lattice sources (Jacobian weights, Gaussian
+    beam) to the 4,194,304 clustered destination points.  The beam is wide
+    (w0 = 0.5 mm), so the ASM agrees with the paraxial closed form far below
+    the tolerance."""
+    n, pitch, lam, z, w0 = 2048, 4e-6, 633e-9, 1.0, 0.5e-3
+    L = n * pitch
+    t = O.lattice(n) * pitch
+    phi = t + 0.3 * L / (2 * np.pi) * np.sin(2 * np.pi * t / L)
+    dphi = 1 + 0.3 * np.cos(2 * np.pi * t / L)
+    ty, tx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    x1, y1 = phi[tx].ravel(), phi[ty].ravel()
+    wts = (dphi[tx] * dphi[ty]).ravel()
+    c = np.exp(-(x1 * x1 + y1 * y1) / w0 ** 2)
+    dst = WL.fresnel_clustered(type_=2, n=n)
+    params = P.make_params(n, pitch, lam, z, kind=kind)
+    got = run3(P, kind, "f32", params, x1, y1, c, dst.x, dst.y, w=wts)
+    assert O.rel_l2(got, _gaussian_fresnel(dst.x, dst.y, lam, z, w0)) < TOL["f32"]
