@@ -61,6 +61,14 @@ typedef enum {
 
 typedef enum { NUASM_KIND_ASM = 0, NUASM_KIND_FRESNEL = 1 } nuasm_kind;
 
+/* Spreading kernel (any kernel reaching the tolerance gives the same result to
+ * within it; the exact result is the non-uniform DFT). */
+typedef enum {
+    NUASM_KERNEL_ES = 0,        /* exponential of semicircle, width ceil(log10(1/tol)) + 1 */
+    NUASM_KERNEL_GAUSSIAN = 1   /* Gaussian (the Greengard-Lee gridding the paper uses),
+                                   width ceil(ln(1/tol)/1.11) <= 16, so tol >= 2e-8 */
+} nuasm_kernel;
+
 typedef enum {
     NUASM_PREC_F32_F64PHASE = 0,  /* complex64 data; phases from FP64 tables and
                                      compensated (double-float) FP32 arithmetic */
@@ -85,6 +93,7 @@ typedef struct {
     int32_t kind;       /* nuasm_kind */
     int32_t prec;       /* nuasm_prec */
     double  tol;        /* requested NUFFT relative tolerance; 0 selects 1e-6 (F32) or 1e-12 (F64) */
+    int32_t kernel;     /* nuasm_kernel: spreading kernel of the NUFFT gridding */
 } nuasm_params_t;
 
 /* Geometry of a plan (read-only report). */
@@ -129,6 +138,21 @@ typedef struct {
  */
 nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m,
                         const double* x, const double* y, const double* w, void* stream);
+
+/*
+ * nuasm_plan_lattice -- a plan whose points form a uniform nx x ny lattice,
+ *     x = x0 + i * pitch2,  y = y0 + j * pitch2,  point index j * nx + i,
+ * generated on the device (no coordinate arrays).  With it, type 2 evaluates
+ * the destination plane at pitch2 and type 1 propagates a source plane
+ * sampled at pitch2 onto the uniform plane at p->pitch: the scaled ASM /
+ * scaled Fresnel the paper's introduction discusses (different but uniform
+ * pitches on the two planes), as the lattice special case of NU-ASM.
+ * nx, ny >= 0 (nx * ny <= 2^29), pitch2 > 0; every lattice point must lie
+ * in the window (else NUASM_ERANGE).  Other arguments and errors as
+ * nuasm_plan (no weights).
+ */
+nuasm_status nuasm_plan_lattice(nuasm_plan_t* out, const nuasm_params_t* p, int32_t nx, int32_t ny,
+                                double pitch2, double x0, double y0, void* stream);
 
 /*
  * nuasm1_execute -- NU-ASM_1 (Eq. 6): non-uniform source -> uniform plane.
@@ -192,9 +216,12 @@ nuasm_status nuasm_band(const nuasm_params_t* p, int32_t out[4]);
 /*
  * nuasm_kernel_shape -- host-only: the spreading kernel width w and shape
  * parameter beta the library uses for a requested tolerance (0 = the
- * precision's default) and precision.  No device work.
+ * precision's default), precision and kernel (nuasm_kernel): exp(beta
+ * (sqrt(1 - (2t/w)^2) - 1)) for the exponential of semicircle, exp(-beta t^2)
+ * for the Gaussian, t in fine-grid cells, |t| <= w/2.  NUASM_EUNSUPPORTED
+ * when the kernel needs more than 16 taps for the tolerance.  No device work.
  */
-nuasm_status nuasm_kernel_shape(double tol, int32_t prec, int32_t* width, double* beta);
+nuasm_status nuasm_kernel_shape(double tol, int32_t prec, int32_t kernel, int32_t* width, double* beta);
 
 /*
  * Per-stage timing (instrumentation for benchmarks).  When enabled, execute

@@ -251,6 +251,15 @@ nuasm_status exec_type2(nuasm_plan_s* P, const void* u1, void* v, cudaStream_t s
     return NUASM_OK;
 }
 
+__global__ void lattice_kernel(double* __restrict__ x, double* __restrict__ y, int nx, int64_t m, double pitch2,
+                               double x0, double y0) {
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < m; t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t j = t / nx, i = t - j * nx;
+        x[t] = x0 + double(i) * pitch2;
+        y[t] = y0 + double(j) * pitch2;
+    }
+}
+
 bool same_problem(const nuasm_params_t& a, const nuasm_params_t& b) {
     bool same = a.n == b.n && a.n_pad == b.n_pad && a.pitch == b.pitch && a.lambda == b.lambda && a.z == b.z &&
                 a.ox == b.ox && a.oy == b.oy && a.band_auto == b.band_auto && a.kind == b.kind &&
@@ -370,6 +379,32 @@ nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m, c
     return NUASM_OK;
 }
 
+nuasm_status nuasm_plan_lattice(nuasm_plan_t* out, const nuasm_params_t* p, int32_t nx, int32_t ny,
+                                double pitch2, double x0, double y0, void* stream) {
+    if (!out) return NUASM_EINVAL;
+    *out = nullptr;
+    if (!p || nx < 0 || ny < 0 || !std::isfinite(pitch2) || !(pitch2 > 0) || !std::isfinite(x0) ||
+        !std::isfinite(y0))
+        return NUASM_EINVAL;
+    const int64_t m = int64_t(nx) * ny;
+    if (m > (int64_t(1) << 29)) return NUASM_EUNSUPPORTED;
+    nuasm_params_t rp;
+    const nuasm_status s = validate(*p, m, &rp);
+    if (s != NUASM_OK) return s;
+    if (m == 0) return nuasm_plan(out, p, 0, nullptr, nullptr, nullptr, stream);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double* xy = nullptr;
+    cudaError_t e = cudaMalloc(&xy, sizeof(double) * 2 * size_t(m));
+    if (e != cudaSuccess) return cuda_status(e);
+    const int blocks = int(std::min<int64_t>((m + 255) / 256, 152 * 8));
+    lattice_kernel<<<blocks, 256, 0, st>>>(xy, xy + m, nx, m, pitch2, x0, y0);
+    e = cudaGetLastError();
+    nuasm_status r = e == cudaSuccess ? nuasm_plan(out, p, m, xy, xy + m, nullptr, stream) : cuda_status(e);
+    cudaStreamSynchronize(st);
+    cudaFree(xy);
+    return r;
+}
+
 nuasm_status nuasm1_execute(nuasm_plan_t plan, const void* c, void* u2, void* stream) {
     if (!plan) return NUASM_EINVAL;
     if (plan->p.kind != NUASM_KIND_ASM) return NUASM_EINVAL;
@@ -460,14 +495,15 @@ nuasm_status nuasm_band(const nuasm_params_t* p, int32_t out[4]) {
     return NUASM_OK;
 }
 
-nuasm_status nuasm_kernel_shape(double tol, int32_t prec, int32_t* width, double* beta) {
+nuasm_status nuasm_kernel_shape(double tol, int32_t prec, int32_t kernel, int32_t* width, double* beta) {
     if (!width || !beta) return NUASM_EINVAL;
     if (prec != NUASM_PREC_F32_F64PHASE && prec != NUASM_PREC_F64) return NUASM_EINVAL;
+    if (kernel != NUASM_KERNEL_ES && kernel != NUASM_KERNEL_GAUSSIAN) return NUASM_EINVAL;
     if (std::isnan(tol) || tol < 0 || tol > 0.1 || (tol > 0 && tol < 1e-15)) return NUASM_EINVAL;
     int w = 0;
-    kernel_shape(tol, prec, &w, beta);
+    const bool ok = kernel_shape(tol, prec, kernel, &w, beta);
     *width = w;
-    return NUASM_OK;
+    return ok ? NUASM_OK : NUASM_EUNSUPPORTED;
 }
 
 nuasm_status nuasm_profile_enable(nuasm_plan_t plan, int32_t enable) {

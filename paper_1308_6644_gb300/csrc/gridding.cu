@@ -206,9 +206,17 @@ template <int WMAX> __device__ __forceinline__ void tap_weights(float f, int w, 
         out[i] = acc;
     }
 }
-template <int WMAX> __device__ __forceinline__ void tap_weights(double f, int w, double beta, const KernelPoly&,
+template <int WMAX> __device__ __forceinline__ void tap_weights(double f, int w, double beta, const KernelPoly& kp,
                                                                  double* out) {
     const double ihw = 2.0 / w, hw = 0.5 * w;
+    if (kp.deg < 0) {   // Gaussian kernel exp(-beta t^2)
+#pragma unroll
+        for (int i = 0; i < WMAX; ++i) {
+            const double t = double(i) + f - hw;
+            out[i] = i < w ? exp(-beta * t * t) : 0.0;
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < WMAX; ++i) out[i] = i < w ? es_eval<double>(double(i) + f - hw, ihw, beta) : 0.0;
 }
@@ -351,6 +359,13 @@ template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
 }
 
+// FP64 taps evaluate the kernel itself; a negative degree marks the Gaussian
+KernelPoly taps_arg(const nuasm_plan_s* P) {
+    KernelPoly kp = P->poly;
+    if (P->f64 && P->g.kernel == NUASM_KERNEL_GAUSSIAN) kp.deg = -1;
+    return kp;
+}
+
 template <typename S, int WMAX, bool EXACT>
 cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     using V = typename VecOf<S>::type;
@@ -360,7 +375,7 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     spread_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
         static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.wpt,
-        static_cast<const V*>(c), static_cast<V*>(P->d.win), a, P->poly);
+        static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg(P));
     return cudaGetLastError();
 }
 
@@ -374,7 +389,7 @@ cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     interp_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
         static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.tile_home,
-        static_cast<const V*>(P->d.win), static_cast<V*>(v), a, P->poly);
+        static_cast<const V*>(P->d.win), static_cast<V*>(v), a, taps_arg(P));
     return cudaGetLastError();
 }
 

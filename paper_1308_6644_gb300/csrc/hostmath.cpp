@@ -131,13 +131,23 @@ bool in_band(const nuasm_params_t& p, int np, int k, int axis) {
 // ---------------------------------------------------------------- shared per-mode helpers
 // (heap-free, so that the no-allocation solve can use them too)
 
+// Gaussian kernel exp(-beta t^2), |t| <= w/2 (Greengard and Lee's gridding kernel)
+double gaussian_kernel(double t, int w, double beta) {
+    if (std::fabs(t) > 0.5 * w) return 0.0;
+    return std::exp(-beta * t * t);
+}
+
+double kernel_value(const Geometry& g, double t) {
+    return g.kernel == NUASM_KERNEL_GAUSSIAN ? gaussian_kernel(t, g.w, g.beta) : es_kernel(t, g.w, g.beta);
+}
+
 void make_quad(const Geometry& g, KernelQuad* qd) {
     qd->n = 2 * g.w + 48;
     double gx[KernelQuad::kMax], gw[KernelQuad::kMax];
     gauss_legendre(qd->n, gx, gw);
     for (int i = 0; i < qd->n; ++i) {
         qd->t[i] = (gx[i] + 1.0) * g.w / 4.0;              // [0, w/2]
-        qd->f[i] = gw[i] * g.w / 4.0 * es_kernel(qd->t[i], g.w, g.beta);
+        qd->f[i] = gw[i] * g.w / 4.0 * kernel_value(g, qd->t[i]);
     }
 }
 
@@ -206,19 +216,31 @@ double nonsep_rmax(const nuasm_params_t& p, const Geometry& g) {
     return std::fabs(p.z / (2.0 * p.lambda)) * qm * qm;
 }
 
-void kernel_shape(double tol, int prec, int* w, double* beta) {
+bool kernel_shape(double tol, int prec, int kernel, int* w, double* beta) {
     if (!(tol > 0)) tol = prec == NUASM_PREC_F64 ? 1e-12 : 1e-6;
-    int ww = int(std::ceil(-std::log10(tol) - 1e-9)) + 1;
+    int ww;
+    if (kernel == NUASM_KERNEL_GAUSSIAN) {
+        // aliasing exp(-pi^2 s^2) balanced against truncation exp(-w^2 / (8 s^2))
+        // at s^2 = w / (2 sqrt(2) pi): error about exp(-1.11 w)
+        ww = int(std::ceil(-std::log(tol) / 1.11 - 1e-9));
+        if (ww < 2) ww = 2;
+        *w = ww;
+        *beta = std::sqrt(2.0) * M_PI / ww;   // 1 / (2 s^2)
+        return ww <= 16;
+    }
+    ww = int(std::ceil(-std::log10(tol) - 1e-9)) + 1;
     if (ww < 2) ww = 2;
     if (ww > 16) ww = 16;
     *w = ww;
     *beta = 2.30 * ww;   // shape parameter for upsampling factor 2
+    return true;
 }
 
 nuasm_status validate(const nuasm_params_t& p0, int64_t m, nuasm_params_t* out) {
     nuasm_params_t p = p0;
     if (p.kind != NUASM_KIND_ASM && p.kind != NUASM_KIND_FRESNEL) return NUASM_EINVAL;
     if (p.prec != NUASM_PREC_F32_F64PHASE && p.prec != NUASM_PREC_F64) return NUASM_EINVAL;
+    if (p.kernel != NUASM_KERNEL_ES && p.kernel != NUASM_KERNEL_GAUSSIAN) return NUASM_EINVAL;
     if (m < 0 || m > (int64_t(1) << 29)) return m < 0 ? NUASM_EINVAL : NUASM_EUNSUPPORTED;
     if (p.n < 2 || (p.n & 1)) return NUASM_EINVAL;
     if (!std::isfinite(p.pitch) || !(p.pitch > 0)) return NUASM_EINVAL;
@@ -234,6 +256,11 @@ nuasm_status validate(const nuasm_params_t& p0, int64_t m, nuasm_params_t* out) 
     if (std::isnan(p.tol) || p.tol < 0 || p.tol > 0.1) return NUASM_EINVAL;
     if (p.tol == 0) p.tol = p.prec == NUASM_PREC_F64 ? 1e-12 : 1e-6;
     if (p.tol < 1e-15) return NUASM_EINVAL;
+    {
+        int w;
+        double beta;
+        if (!kernel_shape(p.tol, p.prec, p.kernel, &w, &beta)) return NUASM_EUNSUPPORTED;
+    }
     if (p.n_pad != 0 && (p.n_pad < 2 * p.n || !is_pow2(p.n_pad))) return NUASM_EINVAL;
     // what this build implements: power-of-two planes, N' <= 8192 (F32) / 4096 (F64)
     if (!is_pow2(p.n) || p.n < 16) return NUASM_EUNSUPPORTED;
@@ -265,7 +292,8 @@ Geometry make_geometry(const nuasm_params_t& p) {
     g.G = 2 * p.n_pad;
     g.logn = ilog2(p.n);
     g.lognp = ilog2(p.n_pad);
-    kernel_shape(p.tol, p.prec, &g.w, &g.beta);
+    g.kernel = p.kernel;
+    kernel_shape(p.tol, p.prec, p.kernel, &g.w, &g.beta);
     g.h = (g.w + 1) / 2;
     g.W = 2 * p.n + 2 * g.h;
     g.Wp = (g.W + 31) & ~31;
@@ -362,7 +390,7 @@ void fit_kernel_poly(const Geometry& g, KernelPoly* kp) {
         double cheb[kPolyMaxD] = {};
         for (int k = 0; k < K; ++k) {
             const double f = 0.5 * (xn[k] + 1.0);
-            const double val = es_kernel(i + f - 0.5 * g.w, g.w, g.beta);
+            const double val = kernel_value(g, i + f - 0.5 * g.w);
             for (int j = 0; j <= d; ++j) cheb[j] += val * std::cos(j * M_PI * (k + 0.5) / K);
         }
         for (int j = 0; j <= d; ++j) cheb[j] *= (j == 0 ? 1.0 : 2.0) / K;

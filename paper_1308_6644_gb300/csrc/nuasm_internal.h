@@ -13,7 +13,8 @@ struct Geometry {
     int n, np, G;          // N, N', G = 2N'
     int logn, lognp;       // log2 N, log2 N'
     int w;                 // kernel width
-    double beta;           // ES shape parameter
+    double beta;           // kernel shape parameter
+    int kernel;            // nuasm_kernel
     int h;                 // window margin ceil(w/2)
     int W, Wp;             // window side, row pitch (elements)
     int Lo;                // window origin on the G grid
@@ -99,7 +100,8 @@ void twiddle(int i, int G, double* re, double* im);
 double nonsep_rmax(const nuasm_params_t& p, const Geometry& g);
 void fit_kernel_poly(const Geometry& g, KernelPoly* kp);
 nuasm_status validate(const nuasm_params_t& p, int64_t m, nuasm_params_t* resolved);
-void kernel_shape(double tol, int prec, int* w, double* beta);
+bool kernel_shape(double tol, int prec, int kernel, int* w, double* beta);
+double kernel_value(const Geometry& g, double t);
 void band_range(const nuasm_params_t& p, int out[4]);
 Geometry make_geometry(const nuasm_params_t& p);
 void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t);

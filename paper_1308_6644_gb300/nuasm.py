@@ -38,7 +38,8 @@ class Params(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("z", ctypes.c_double), ("ox", ctypes.c_double),
                 ("oy", ctypes.c_double), ("band_auto", ctypes.c_int32), ("c_m", ctypes.c_double),
                 ("c_n", ctypes.c_double), ("w_m", ctypes.c_double), ("w_n", ctypes.c_double),
-                ("kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("tol", ctypes.c_double)]
+                ("kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("kernel", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -58,6 +59,9 @@ _lib = None
 _SIGS = {
     "nuasm_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Params), ctypes.c_int64,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "nuasm_plan_lattice": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Params), ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_void_p]),
     "nuasm1_execute": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "nuasm2_execute": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "nufresnel_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -68,8 +72,8 @@ _SIGS = {
     "nuasm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "nuasm_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
     "nuasm_band": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int32)]),
-    "nuasm_kernel_shape": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
-                                          ctypes.POINTER(ctypes.c_double)]),
+    "nuasm_kernel_shape": (ctypes.c_int, [ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     "nuasm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "nuasm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]),
@@ -148,9 +152,13 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+KERNEL_ES, KERNEL_GAUSSIAN = 0, 1
+
+
 def make_params(n, pitch, lam, z, ox=0.0, oy=0.0, kind="asm", prec="f32", tol=0.0, n_pad=0,
-                band=None) -> Params:
-    """nuasm_params_t from keyword values; band = (c_m, c_n, w_m, w_n) or None (auto rule)."""
+                band=None, kernel="es") -> Params:
+    """nuasm_params_t from keyword values; band = (c_m, c_n, w_m, w_n) or None
+    (auto rule); kernel = "es" (exponential of semicircle) or "gaussian"."""
     p = Params()
     p.n, p.n_pad, p.pitch, p.lambda_, p.z, p.ox, p.oy = int(n), int(n_pad), pitch, lam, z, ox, oy
     if band is None:
@@ -161,6 +169,7 @@ def make_params(n, pitch, lam, z, ox=0.0, oy=0.0, kind="asm", prec="f32", tol=0.
     p.kind = KIND_ASM if kind in ("asm", KIND_ASM) else KIND_FRESNEL
     p.prec = PREC_F64 if prec in ("f64", PREC_F64) else PREC_F32_F64PHASE
     p.tol = float(tol)
+    p.kernel = KERNEL_GAUSSIAN if kernel in ("gaussian", KERNEL_GAUSSIAN) else KERNEL_ES
     return p
 
 
@@ -216,6 +225,15 @@ def nuasm_plan(params: Params, x, y, w=None, stream=None) -> Plan:
     _check(lib().nuasm_plan(ctypes.byref(h), ctypes.byref(params), m, _ptr(x), _ptr(y), _ptr(w),
                             _stream(stream)), "nuasm_plan")
     return Plan(h, params, m)
+
+
+def nuasm_plan_lattice(params: Params, nx: int, ny: int, pitch2: float, x0: float, y0: float,
+                       stream=None) -> Plan:
+    """Plan over the lattice x0 + i pitch2, y0 + j pitch2 (point index j nx + i)."""
+    h = ctypes.c_void_p()
+    _check(lib().nuasm_plan_lattice(ctypes.byref(h), ctypes.byref(params), int(nx), int(ny), float(pitch2),
+                                    float(x0), float(y0), _stream(stream)), "nuasm_plan_lattice")
+    return Plan(h, params, int(nx) * int(ny))
 
 
 def nuasm1_execute(plan: Plan, c, u2, stream=None):
@@ -283,10 +301,10 @@ def nuasm_band(params: Params) -> tuple:
     return tuple(int(v) for v in out)
 
 
-def nuasm_kernel_shape(tol: float, prec: int) -> tuple:
+def nuasm_kernel_shape(tol: float, prec: int, kernel: int = KERNEL_ES) -> tuple:
     w = ctypes.c_int32()
     b = ctypes.c_double()
-    _check(lib().nuasm_kernel_shape(float(tol), int(prec), ctypes.byref(w), ctypes.byref(b)),
+    _check(lib().nuasm_kernel_shape(float(tol), int(prec), int(kernel), ctypes.byref(w), ctypes.byref(b)),
            "nuasm_kernel_shape")
     return int(w.value), float(b.value)
 

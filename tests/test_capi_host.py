@@ -138,3 +138,24 @@ def test_binding_checks_shapes_and_dtypes(P):
         B._expect(np.zeros(10, np.complex128), 10, "complex64", "c")
     with pytest.raises(RuntimeError):
         plan.info()
+
+
+@pytest.mark.parametrize("tol,w", [(1e-3, 7), (1e-5, 11), (1e-6, 13), (1e-7, 15)])
+def test_gaussian_kernel_width_rule(P, tol, w):
+    width, beta = P.nuasm_kernel_shape(tol, 0, P.KERNEL_GAUSSIAN)
+    assert width == w and abs(beta - np.sqrt(2) * np.pi / w) < 1e-12
+
+
+def test_gaussian_kernel_limits(P):
+    with pytest.raises(P.NuasmError) as ei:
+        P.nuasm_kernel_shape(1e-10, 1, P.KERNEL_GAUSSIAN)
+    assert ei.value.code == 6
+    x = np.zeros(2)
+    with pytest.raises(P.NuasmError) as ei:
+        P.nuasm_plan(P.make_params(32, 10e-6, 633e-9, 0.01, prec="f64", kernel="gaussian"), x, x)
+    assert ei.value.code == 6        # the F64 default tolerance needs more than 16 taps
+    bad = P.make_params(32, 10e-6, 633e-9, 0.01)
+    bad.kernel = 7
+    with pytest.raises(P.NuasmError) as ei:
+        P.nuasm_plan(bad, x, x)
+    assert ei.value.code == 1

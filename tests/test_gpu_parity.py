@@ -30,11 +30,11 @@ def _t(a, dev="cuda"):
 
 
 def run_gpu(P, kind, type_, prec, n, pitch, lam, z, x, y, values, ox=0.0, oy=0.0, w=None, n_pad=0,
-            band=None, tol=0.0, host=False):
+            band=None, tol=0.0, host=False, kernel="es"):
     """One plan + one execute; returns the output as a numpy array."""
     import torch
     params = P.make_params(n, pitch, lam, z, ox=ox, oy=oy, kind=kind, prec=prec, tol=tol,
-                           n_pad=n_pad, band=band)
+                           n_pad=n_pad, band=band, kernel=kernel)
     cdt = CDT[prec]
     tdt = torch.complex64 if prec == "f32" else torch.complex128
     if host:
@@ -214,3 +214,15 @@ def test_type2_is_deterministic(P):
     a = run_gpu(P, "asm", 2, "f32", 64, x=x, y=y, values=vals, **kw)
     b = run_gpu(P, "asm", 2, "f32", 64, x=x, y=y, values=vals, **kw)
     assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- Gaussian (Greengard-Lee) kernel option
+@pytest.mark.parametrize("kind", ["asm", "fresnel"])
+@pytest.mark.parametrize("type_", [1, 2])
+@pytest.mark.parametrize("prec,tol,bound", [("f32", 0.0, 1e-5), ("f64", 1e-7, 1e-6)])
+def test_gaussian_kernel_parity(P, kind, type_, prec, tol, bound):
+    x, y, vals = random_case(51 + type_, 64, 600, type_=type_)
+    kw = dict(pitch=10e-6, lam=633e-9, z=0.03, ox=25e-6, oy=-12e-6)
+    got = run_gpu(P, kind, type_, prec, 64, x=x, y=y, values=vals, tol=tol, kernel="gaussian", **kw)
+    ref = run_oracle(kind, type_, 64, x=x, y=y, values=vals, prec=prec, **kw)
+    assert O.rel_l2(got, ref) < bound

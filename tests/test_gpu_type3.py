@@ -119,3 +119,61 @@ def test_type3_full_size_closed_form(P, kind):
     params = P.make_params(n, pitch, lam, z, kind=kind)
     got = run3(P, kind, "f32", params, x1, y1, c, dst.x, dst.y, w=wts)
     assert O.rel_l2(got, _gaussian_fresnel(dst.x, dst.y, lam, z, w0)) < TOL["f32"]
+
+
+# ---------------------------------------------------------------- scaled diffraction (lattice plans)
+@pytest.mark.parametrize("kind", ["asm", "fresnel"])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_scaled_type2_destination_lattice(P, kind, prec):
+    """Uniform 64^2 source at 10 um -> 48^2 destination lattice at 12 um."""
+    import torch
+    n, pitch, p2, nd = 64, 10e-6, 12e-6, 48
+    rng = np.random.default_rng(41)
+    u1 = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    x0 = y0 = -(nd // 2) * p2
+    params = P.make_params(n, pitch, 633e-9, 0.02, ox=30e-6, kind=kind, prec=prec)
+    plan = P.nuasm_plan_lattice(params, nd, nd, p2, x0, y0)
+    try:
+        v = torch.zeros(nd * nd, dtype=torch.complex64 if prec == "f32" else torch.complex128, device="cuda")
+        src = _dev(u1.astype(CDT[prec]).ravel())
+        if kind == "asm":
+            P.nuasm2_execute(plan, src, v)
+        else:
+            P.nufresnel_execute(plan, 2, src, v)
+        torch.cuda.synchronize()
+        got = v.cpu().numpy()
+    finally:
+        plan.destroy()
+    g = x0 + np.arange(nd) * p2
+    gy, gx = np.meshgrid(g, g, indexing="ij")
+    p = dict(n=n, pitch=pitch, lam=633e-9, z=0.02, ox=30e-6, kind=kind)
+    ref = O.diffraction_type2(u1.astype(CDT[prec]), gx.ravel(), gy.ravel(), p)
+    assert O.rel_l2(got, ref) < TOL[prec]
+
+
+def test_scaled_type1_source_lattice(P):
+    """80^2 source lattice at 7 um -> uniform 64^2 plane at 10 um."""
+    import torch
+    n, pitch, p1, ns = 64, 10e-6, 7e-6, 80
+    rng = np.random.default_rng(42)
+    c = rng.normal(size=ns * ns) + 1j * rng.normal(size=ns * ns)
+    x0 = y0 = -(ns // 2) * p1
+    params = P.make_params(n, pitch, 532e-9, 0.03, prec="f64")
+    plan = P.nuasm_plan_lattice(params, ns, ns, p1, x0, y0)
+    try:
+        u2 = torch.zeros(n * n, dtype=torch.complex128, device="cuda")
+        P.nuasm1_execute(plan, _dev(c), u2)
+        torch.cuda.synchronize()
+        got = u2.cpu().numpy().reshape(n, n)
+    finally:
+        plan.destroy()
+    g = x0 + np.arange(ns) * p1
+    gy, gx = np.meshgrid(g, g, indexing="ij")
+    ref = O.nuasm1(gx.ravel(), gy.ravel(), c, dict(n=n, pitch=pitch, lam=532e-9, z=0.03))
+    assert O.rel_l2(got, ref) < TOL["f64"]
+
+
+def test_lattice_outside_window_is_rejected(P):
+    with pytest.raises(P.NuasmError) as ei:
+        P.nuasm_plan_lattice(P.make_params(32, 10e-6, 633e-9, 0.01), 40, 40, 10e-6, -200e-6, -200e-6)
+    assert ei.value.code == 2
