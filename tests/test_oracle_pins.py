@@ -443,3 +443,34 @@ def test_type3_z0_dirichlet_closed_form():
     want = np.array([np.sum(c * _dirichlet((x2[j] - x1) / pitch, 2 * n) * _dirichlet((y2[j] - y1) / pitch, 2 * n))
                      for j in range(len(x2))])
     assert O.rel_l2(got, want) < 1e-13
+
+
+# ----------------------------------------------------------------------------
+# Rayleigh-Sommerfeld direct sum (Eq. 10)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("z", [5e-6, 20e-6])
+def test_rs_direct_propagates_the_exact_solution(z):
+    """Rayleigh-Sommerfeld of the first kind is exact for fields without
+    sources in z > 0; its Riemann sum over well-sampled data reproduces the
+    complex-source-point beam."""
+    n, pitch, lam, w0 = 96, 0.2e-6, 0.5e-6, 2e-6
+    b = np.pi * w0 ** 2 / lam
+    gx, gy = _grid(n, pitch)
+    u1 = csp_field(gx, gy, 0.0, lam, b)
+    rng = _rng(30)
+    x2, y2 = _points(rng, n, pitch * 0.5, 150)
+    ox, oy = 0.8e-6, -0.4e-6
+    got = O.rs_direct(gx.ravel(), gy.ravel(), u1.ravel(), np.full(n * n, pitch * pitch), x2, y2, lam, z, ox, oy)
+    assert O.rel_l2(got, csp_field(x2 + ox, y2 + oy, z, lam, b)) < 1e-9
+
+
+def test_rs_direct_agrees_with_asm_for_a_smooth_field():
+    n, pitch, lam, w0, z = 64, 0.25e-6, 0.5e-6, 1.5e-6, 8e-6
+    gx, gy = _grid(n, pitch)
+    u1 = np.exp(-(gx ** 2 + gy ** 2) / w0 ** 2)
+    rng = _rng(31)
+    x2, y2 = _points(rng, n, pitch * 0.5, 100)
+    rs = O.rs_direct(gx.ravel(), gy.ravel(), u1.ravel(), np.full(n * n, pitch * pitch), x2, y2, lam, z)
+    asm = O.nuasm2(u1, x2, y2, dict(n=n, pitch=pitch, lam=lam, z=z))
+    assert O.rel_l2(rs, asm) < 1e-8
