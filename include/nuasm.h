@@ -196,6 +196,28 @@ nuasm_status nuasm3_execute(nuasm_plan_t src, nuasm_plan_t dst, const void* c, v
  * function of Eq. 5 (both plans of kind NUASM_KIND_FRESNEL). */
 nuasm_status nufresnel3_execute(nuasm_plan_t src, nuasm_plan_t dst, const void* c, void* v, void* stream);
 
+/*
+ * nuasm_rs_direct -- Rayleigh-Sommerfeld diffraction (Eq. 10) as a direct
+ * O(m1 m2) sum: the rigorous reference the paper measures NU-ASM and NU-FRE
+ * against (its experiments and Fig. 4).
+ *     u2(x2) = (1/2 pi) sum_j a_j c_j (z/r)(1 - i k r) exp(i k r) / r^2,
+ *     r = sqrt(|x2 + o - x1_j|^2 + z^2),  k = 2 pi / lambda.
+ *  p        uses lambda, z (> 0), ox, oy and prec only (no plan is built).
+ *  x1, y1   m1 source coordinates (metres), device memory.
+ *  c        m1 complex source values (complex64 for NUASM_PREC_F32_F64PHASE,
+ *           complex128 for NUASM_PREC_F64), device memory.
+ *  area     m1 area elements a_j (square metres), device memory.
+ *  x2, y2   m2 destination coordinates relative to the destination window
+ *           centre o, device memory.
+ *  out      m2 complex outputs, device memory.
+ * Asynchronous on `stream`; NUASM_EINVAL for bad parameters or host pointers.
+ * FP32 evaluates the phase as 2 pi (frac(z/lambda) + (r - z)/lambda) with
+ * r - z = rho^2/(r + z); FP64 evaluates every term in double precision.
+ */
+nuasm_status nuasm_rs_direct(const nuasm_params_t* p, int64_t m1, const double* x1, const double* y1,
+                             const void* c, const double* area, int64_t m2, const double* x2, const double* y2,
+                             void* out, void* stream);
+
 /* Release every resource of the plan (synchronises the plan's device work). NULL is a no-op. */
 nuasm_status nuasm_destroy(nuasm_plan_t plan);
 

@@ -6,7 +6,7 @@ synthetic workload generators.
 """
 from .nuasm import (  # noqa: F401
     NuasmError, Params, Plan, make_params, nuasm_plan, nuasm_plan_lattice, nuasm1_execute, nuasm2_execute,
-    nuasm3_execute, nufresnel3_execute,
+    nuasm3_execute, nufresnel3_execute, nuasm_rs_direct,
     nufresnel_execute, nuasm_destroy, nuasm_strerror, nuasm_plan_info, nuasm_band,
     nuasm_kernel_shape, nuasm_profile_enable, nuasm2_solve_noalloc, nuasm_profile_read, lib, LIB_PATH, STAGES,
     KIND_ASM, KIND_FRESNEL, PREC_F32_F64PHASE, PREC_F64, KERNEL_ES, KERNEL_GAUSSIAN,

@@ -68,6 +68,9 @@ _SIGS = {
                                          ctypes.c_void_p]),
     "nuasm3_execute": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "nufresnel3_execute": (ctypes.c_int, [ctypes.c_void_p] * 5),
+    "nuasm_rs_direct": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "nuasm_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "nuasm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "nuasm_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
@@ -279,6 +282,23 @@ def nufresnel3_execute(src: Plan, dst: Plan, c, v, stream=None):
     _expect(v, dst.m, dst.complex_dtype, "v")
     _check(lib().nufresnel3_execute(src._h, dst._h, _ptr(c), _ptr(v), _stream(stream)), "nufresnel3_execute")
     return v
+
+
+def nuasm_rs_direct(params: Params, x1, y1, c, area, x2, y2, out, stream=None):
+    """Rayleigh-Sommerfeld direct sum (Eq. 10): device arrays x1, y1, area
+    (float64, m1), c (complex, m1), x2, y2 (float64, m2) -> out (complex, m2)."""
+    m1 = 0 if x1 is None else _numel(x1)
+    m2 = _numel(x2)
+    cdt = "complex128" if params.prec == PREC_F64 else "complex64"
+    for a, nm in ((x1, "x1"), (y1, "y1"), (area, "area")):
+        if a is not None:
+            _expect(a, m1, "float64", nm)
+    _expect(c, m1, cdt, "c")
+    _expect(y2, m2, "float64", "y2")
+    _expect(out, m2, cdt, "out")
+    _check(lib().nuasm_rs_direct(ctypes.byref(params), m1, _ptr(x1), _ptr(y1), _ptr(c), _ptr(area), m2, _ptr(x2),
+                                 _ptr(y2), _ptr(out), _stream(stream)), "nuasm_rs_direct")
+    return out
 
 
 def nuasm_destroy(plan: Plan):
