@@ -370,6 +370,240 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------- batched planes
+def _timed_steps(fn, steps, stream, flush):
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        fn()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in zip(starts, ends)])
+
+
+def run_batch(args):
+    """64 mixed planes (N in {256..2048}, types 1/2 interleaved, z in [1, 50] cm,
+    lambda in {450, 532, 633} nm, M/N^2 log-uniform in [1/4, 4]) recorded into
+    one CUDA graph over `lanes` streams, against the same planes issued one
+    execute call per plane on one stream."""
+    import torch
+    from paper_1308_6644_gb300 import workloads as WL
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1308_6644_gb300 import _build
+    _build.build()
+    import paper_1308_6644_gb300 as P
+    stream = torch.cuda.current_stream(dev)
+    planes, items, total_m, in_bytes, out_bytes = [], [], 0, 0, 0
+    for i in range(args.planes):
+        wl = WL.mixed_plane(1004, i)
+        params = P.make_params(wl.n, wl.pitch, wl.lam, wl.z, kind="asm", prec="f32")
+        plan = P.nuasm_plan(params, torch.from_numpy(wl.x).to(dev), torch.from_numpy(wl.y).to(dev), stream=stream)
+        inp = torch.from_numpy(np.ascontiguousarray(wl.values.astype(np.complex64).reshape(-1))).to(dev)
+        out = torch.empty(wl.n * wl.n if wl.type == 1 else wl.m, dtype=torch.complex64, device=dev)
+        planes.append((plan, wl.type, inp, out))
+        items.append((plan, wl.type, inp, out))
+        total_m += wl.m
+        in_bytes += inp.numel() * 8
+        out_bytes += out.numel() * 8
+    batch = P.nuasm_batch_create(items, lanes=args.lanes)
+    lanes, kernels = batch.info()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def plain():
+        for plan, t, inp, out in planes:
+            (P.nuasm1_execute if t == 1 else P.nuasm2_execute)(plan, inp, out, stream=stream)
+
+    def batched():
+        batch.execute(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        plain()
+        batched()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    b_ms = _timed_steps(batched, args.steps, stream, flush)
+    clk = clocks.stop()
+    p_ms = _timed_steps(plain, max(3, min(args.steps, 20)), stream, flush)
+    total_ms, points = reduce_over_ranks(float(b_ms.sum()), float(total_m * args.steps), dev)
+    value = points / (total_ms * 1e-3)
+    plain_value = total_m / (float(p_ms.mean()) * 1e-3)
+
+    # end to end: pinned host inputs copied in, the graph, outputs copied back, every step
+    h_in = [inp.cpu().pin_memory() for _, _, inp, _ in planes]
+    h_out = [torch.empty(out.shape, dtype=out.dtype).pin_memory() for _, _, _, out in planes]
+
+    def e2e_step():
+        for h, (_, _, inp, _) in zip(h_in, planes):
+            inp.copy_(h, non_blocking=True)
+        batch.execute(stream)
+        for h, (_, _, _, out) in zip(h_out, planes):
+            h.copy_(out, non_blocking=True)
+
+    e_ms = _timed_steps(e2e_step, max(3, min(args.steps, 20)), stream, flush)
+    alg = 0
+    for plan, t, inp, out in planes:
+        info = plan.info()
+        n, np_, W = info["n"], info["n_pad"], info["window"]
+        alg += 8 * (n * n + 2 * np_ * n + 2 * np_ * W + W * W) + 24 * info["points"]
+    peak, peak_kind = hbm_peak()
+    ach = alg / (float(b_ms.mean()) * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"mixed{args.planes}_planes_n256-2048_types1+2", "planes": args.planes,
+                       "points_per_step": total_m, "lanes": lanes, "graph_kernels": kernels,
+                       "plain_points_per_s": plain_value, "batched_over_plain": value / plain_value,
+                       "plain": "one execute call per plane, back to back on one stream",
+                       "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{ws}"},
+            "latency_ms": {"p50": float(np.percentile(b_ms, 50)), "p99": float(np.percentile(b_ms, 99))},
+            "e2e": {"value": total_m / (float(e_ms.mean()) * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes},
+            "gpu_launches": kernels * args.steps,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": None, "kernel": "whole batch graph (every kernel of every plane)",
+                         "peak_source": f"{peak_kind} copy bandwidth"},
+            "clocks": clk}
+    batch.destroy()
+    for plan, *_ in planes:
+        plan.destroy()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- serving loop
+def run_serve(args):
+    """Poisson arrivals of requests over resident point sets (N in
+    {512..4096}, up to 16M points), each with its own wavelength, distance and
+    type, served with continuous batching; against the same requests run one
+    at a time through the plain path (plan, execute, destroy)."""
+    import torch
+    from paper_1308_6644_gb300 import workloads as WL
+    ws, rank, local = _dist()
+    if ws > 1 and rank != 0:
+        return 0          # one server per GPU; replicas add nothing to this line
+    torch.cuda.set_device(local)
+    from paper_1308_6644_gb300 import _build
+    _build.build()
+    import paper_1308_6644_gb300 as P
+    sets = [WL.serving_point_set(1005, k) for k in range(args.sets)]
+    trace = WL.serving_trace(1005, args.requests, len(sets))
+    rng = np.random.default_rng(1005)
+    host = []
+    for s in sets:
+        nn = s.n * s.n
+        host.append({"in1": torch.from_numpy(WL.random_phasor(rng, s.m).astype(np.complex64)).pin_memory(),
+                     "in2": torch.from_numpy(WL.random_phasor(rng, nn).astype(np.complex64)).pin_memory(),
+                     "out1": [torch.empty(nn, dtype=torch.complex64).pin_memory() for _ in range(2)],
+                     "out2": [torch.empty(s.m, dtype=torch.complex64).pin_memory() for _ in range(2)]})
+
+    def request(i, rec):
+        k, t, z, lam, _ = rec
+        s, h = sets[k], host[k]
+        params = P.make_params(s.n, s.pitch, lam, z, kind="asm", prec="f32")
+        inp = h["in1"] if t == 1 else h["in2"]
+        out = (h["out1"] if t == 1 else h["out2"])[i % 2]
+        return s, params, t, inp, out
+
+    srv = P.nuasm_server_create(slots=args.slots)
+    # every set binned once (resident from then on)
+    warm = []
+    for k, s in enumerate(sets):
+        params = P.make_params(s.n, s.pitch, 532e-9, 0.1, kind="asm", prec="f32")
+        warm.append(P.nuasm_server_submit(srv, params, 2, s.x, s.y, host[k]["in2"], host[k]["out2"][0],
+                                          points_id=k + 1))
+    for t in warm:
+        P.nuasm_server_wait(srv, t)
+    def closed_burst(recs):
+        t0 = time.perf_counter()
+        tk, pts = [], 0
+        for i, rec in enumerate(recs):
+            s, params, t, inp, out = request(i, rec)
+            tk.append(P.nuasm_server_submit(srv, params, t, s.x, s.y, inp, out, points_id=rec[0] + 1))
+            pts += s.m
+        for t in tk:
+            P.nuasm_server_wait(srv, t)
+        return time.perf_counter() - t0, pts
+
+    # warm the pools and staging buffers, then probe the capacity with a closed burst
+    closed_burst(trace[: min(len(trace), 4 * args.slots)])
+    burst = trace[: min(len(trace), 16 * args.slots)]
+    el, pts = closed_burst(burst)
+    rate = len(burst) / el                               # requests/s the GPU sustains
+    capacity = pts / el
+    P.nuasm_server_stats(srv, reset=True)
+    # Poisson arrivals at the measured capacity (saturating)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_start = time.perf_counter()
+    arrival = 0.0
+    tickets = []
+    for i, rec in enumerate(trace):
+        arrival += rec[4] / rate
+        delay = t_start + arrival - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        s, params, t, inp, out = request(i, rec)
+        tickets.append(P.nuasm_server_submit(srv, params, t, s.x, s.y, inp, out, points_id=rec[0] + 1))
+    res = [P.nuasm_server_wait(srv, t) for t in tickets]
+    clk = clocks.stop()
+    st = P.nuasm_server_stats(srv)
+    srv.destroy()
+    failed = sum(1 for r in res if r["status"] != 0)
+    served = st["points"] / st["wall_s"]
+    # plain path: the first requests of the same trace, one at a time
+    n_plain = min(len(trace), args.plain_requests)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pts = 0
+    for i, rec in enumerate(trace[:n_plain]):
+        s, params, t, inp, out = request(i, rec)
+        plan = P.nuasm_plan(params, s.x, s.y)
+        (P.nuasm1_execute if t == 1 else P.nuasm2_execute)(plan, inp, out)
+        plan.destroy()
+        pts += s.m
+    plain = pts / (time.perf_counter() - t0)
+    h2d = d2h = 0
+    for rec in trace:
+        s = sets[rec[0]]
+        h2d += 8 * (s.m if rec[1] == 1 else s.n * s.n)
+        d2h += 8 * (s.n * s.n if rec[1] == 1 else s.m)
+    line = {"metric": METRIC, "value": served, "unit": UNIT, "n_gpus": 1, "steps": len(trace),
+            "warmup": len(burst), "ms_per_step": 1e3 * st["wall_s"] / len(trace), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serve_poisson_{len(trace)}req_{len(sets)}sets_n512-4096",
+                       "slots": args.slots, "arrival_rate_per_s": rate, "closed_loop_points_per_s": capacity,
+                       "failed": failed,
+                       "points_served": st["points"], "bins_built_during_run": st["bins_built"],
+                       "resident_sets": st["resident_sets"], "resident_gb": st["resident_bytes"] / 1e9,
+                       "peak_budget_gb": st["peak_bytes"] / 1e9, "hbm_budget_gb": 150,
+                       "plain_points_per_s": plain, "plain_requests_timed": n_plain,
+                       "served_over_plain": served / plain,
+                       "plain": "per request: nuasm_plan from host coordinates, execute with host buffers, destroy",
+                       "inputs": "pinned host memory, copied in and out by every request"},
+            "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
+            "e2e": {"value": served, "unit": UNIT, "h2d_bytes_per_step": h2d // len(trace),
+                    "d2h_bytes_per_step": d2h // len(trace)},
+            "gpu_launches": 4 * len(trace),
+            "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,9 +611,22 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["nuasm2", "batch64", "serve"], default="nuasm2",
+                    help="nuasm2: the single-solve benchmark (default); batch64: 64 mixed planes in one "
+                         "graph; serve: Poisson-arrival serving loop")
+    ap.add_argument("--planes", type=int, default=64)
+    ap.add_argument("--lanes", type=int, default=8)
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--sets", type=int, default=12)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--plain-requests", type=int, default=60)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

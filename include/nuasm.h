@@ -293,6 +293,140 @@ const char* nuasm_stage_name(int32_t stage);
 nuasm_status nuasm2_solve_noalloc(const nuasm_params_t* p, int64_t m, const double* x, const double* y,
                                   const void* u1, void* v, void* stream);
 
+/*
+ * Batches -- many planes (depth layers, colour channels, mixed N and point
+ * counts) solved together.  The paper solves one plane per call; a batch is
+ * a fixed list of solves on existing plans that nuasm_batch_create records
+ * once into a CUDA graph, distributing the planes over `lanes` internal
+ * streams so that planes too small to fill the GPU run side by side, and
+ * that nuasm_batch_execute replays with a single graph launch.
+ *
+ * Items that name the same `plan` share its workspace: they are placed on
+ * one lane and run in list order.  Other planes are assigned to lanes
+ * longest-first by an estimate of their HBM bytes and kernel taps.
+ * The plans and every `in`/`out` array are caller-owned device memory that
+ * must stay valid, at the same addresses, for the life of the batch (their
+ * addresses are baked into the graph); the contents of `in` are read anew on
+ * every execute.
+ */
+typedef struct nuasm_batch_s* nuasm_batch_t;
+
+typedef struct {
+    nuasm_plan_t plan;   /* the plane's plan (type 3: the source plan) */
+    nuasm_plan_t dst;    /* type 3: destination plan built with identical parameters; else NULL */
+    int32_t type;        /* 1 (Eq. 6), 2 (Eq. 9) or 3 (both planes non-uniform); the
+                            transfer function (Eq. 4 or Eq. 5) is the plan's kind */
+    const void* in;      /* device: type 1/3 m source values, type 2 the N*N plane */
+    void* out;           /* device: type 1 the N*N plane, type 2 m values, type 3 dst->m values */
+} nuasm_batch_item_t;
+
+/*
+ * nuasm_batch_create -- validate `count` items (1..65536) and record them.
+ * lanes: 1..64 concurrent streams (0 = 8).  NUASM_EINVAL for a NULL plan, a
+ * type that is not 1-3, host pointers, or type-3 plans whose parameters
+ * differ; NUASM_ECUDA when capture or instantiation fails.  No device work
+ * is run by this call.
+ */
+nuasm_status nuasm_batch_create(nuasm_batch_t* out, const nuasm_batch_item_t* items, int32_t count, int32_t lanes);
+
+/* Run every item once: one graph launch on `stream`, asynchronous; the work
+ * is ordered after earlier work on `stream` and later work waits for all of it. */
+nuasm_status nuasm_batch_execute(nuasm_batch_t batch, void* stream);
+
+/* lanes actually used and kernel launches per execute (host only). */
+nuasm_status nuasm_batch_info(nuasm_batch_t batch, int32_t* lanes, int64_t* kernels);
+
+/* Release the graph and the batch's streams (synchronises the device). NULL is a no-op. */
+nuasm_status nuasm_batch_destroy(nuasm_batch_t batch);
+
+/*
+ * Serving -- a request loop with continuous batching.  The paper times
+ * single solves and has no counterpart.  A server runs `slots` worker
+ * threads, each with its own CUDA stream.  Submitted requests wait in one
+ * FIFO queue; the head is admitted as soon as a slot is free and its device
+ * memory fits in the budget, and then runs on that slot's stream while the
+ * other slots run theirs, so requests arriving while others are on the GPU
+ * overlap with them on the device (copies of one with kernels of another).
+ *
+ * Resident point sets: a request names its points by a non-zero `points_id`.
+ * The first request with a given (points_id, n, n_pad, pitch, prec, tol,
+ * kernel) bins its points (reading x, y); later requests with the same key
+ * reuse the resident bins and do not read x, y.  Wavelength, distance,
+ * offset, band and kind may differ between requests on one point set: the
+ * FP64 transfer-function tables (Eq. 4 / Eq. 5) are built per request, while
+ * the kernel's Fourier transform and the FFT twiddles stay with the bins.
+ * Resident sets not in use are evicted least recently used when the budget
+ * needs room; points_id = 0 bins the points for that request only.
+ *
+ * Memory: resident sets plus, per admitted request, its workspace (the
+ * fine-grid window and two pass buffers), tables and input/output copies,
+ * taken from a stream-ordered pool owned by the server and returned when the
+ * request completes.  The budget bounds their sum.
+ */
+typedef struct nuasm_server_s* nuasm_server_t;
+
+typedef struct {
+    int32_t slots;        /* requests on the device at once, 1..32 (0 = 4) */
+    int32_t device;       /* CUDA device ordinal */
+    int64_t hbm_budget;   /* bytes for resident sets + admitted requests (0 = 150e9) */
+} nuasm_server_config_t;
+
+typedef struct {
+    nuasm_params_t p;     /* as for nuasm_plan */
+    int32_t type;         /* 1 (Eq. 6) or 2 (Eq. 9); the transfer function is p.kind */
+    uint64_t points_id;   /* key of the point set; 0 = not kept */
+    int64_t m;            /* number of points */
+    const double* x;      /* m coordinates in metres (host or device), read only when the set is binned */
+    const double* y;
+    const void* in;       /* type 1: m values, type 2: the N*N plane (complex64, or complex128 for
+                             NUASM_PREC_F64); host or device memory */
+    void* out;            /* type 1: the N*N plane, type 2: m values; host or device memory */
+} nuasm_request_t;
+
+typedef struct {
+    int32_t status;          /* nuasm_status of the request */
+    int32_t reused_points;   /* 1 when resident bins were used */
+    double latency_ms;       /* submit -> result complete in `out` */
+    double queue_ms;         /* submit -> admitted to a slot */
+} nuasm_request_result_t;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t points;          /* sum of m over completed requests */
+    double p50_ms, p99_ms;   /* latency percentiles over completed requests */
+    double wall_s;           /* first submit -> last completion */
+    int64_t resident_sets, resident_bytes, bins_built, bins_reused, evictions;
+    int64_t peak_bytes;      /* largest budget use */
+} nuasm_server_stats_t;
+
+/* Start the workers on `device`.  NUASM_EINVAL for a bad configuration. */
+nuasm_status nuasm_server_create(nuasm_server_t* out, const nuasm_server_config_t* cfg);
+
+/*
+ * Queue a request; *ticket identifies it for nuasm_server_wait.  The
+ * descriptor is copied, the arrays are not: x, y, in and out must stay valid
+ * until the request's wait returns.  NUASM_EINVAL for invalid parameters,
+ * type or pointers; NUASM_ENOMEM when the request alone exceeds the budget.
+ * Errors found while it runs (NUASM_ERANGE for points outside the window,
+ * NUASM_ECUDA, ...) are returned in its result.
+ */
+nuasm_status nuasm_server_submit(nuasm_server_t server, const nuasm_request_t* req, int64_t* ticket);
+
+/*
+ * Wait up to timeout_s seconds (< 0: no limit) for a request; on completion
+ * fills *res and forgets the ticket (a second wait gives NUASM_EINVAL).
+ * NUASM_ETIMEOUT when it is still running (the ticket stays valid).
+ */
+nuasm_status nuasm_server_wait(nuasm_server_t server, int64_t ticket, double timeout_s,
+                               nuasm_request_result_t* res);
+
+/* Counters and latency percentiles since creation or the last reset (reset != 0 clears them
+ * after reading; resident-set figures are not reset). */
+nuasm_status nuasm_server_stats(nuasm_server_t server, nuasm_server_stats_t* st, int32_t reset);
+
+/* Finish every queued request, stop the workers and release all device memory. */
+nuasm_status nuasm_server_destroy(nuasm_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

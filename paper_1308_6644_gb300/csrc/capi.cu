@@ -15,6 +15,28 @@
 
 using namespace nuasm;
 
+namespace nuasm {
+
+bool device_accessible(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the non-sticky error of a foreign pointer
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool same_problem(const nuasm_params_t& a, const nuasm_params_t& b) {
+    bool same = a.n == b.n && a.n_pad == b.n_pad && a.pitch == b.pitch && a.lambda == b.lambda && a.z == b.z &&
+                a.ox == b.ox && a.oy == b.oy && a.band_auto == b.band_auto && a.kind == b.kind &&
+                a.prec == b.prec && a.tol == b.tol && a.kernel == b.kernel;
+    if (same && !a.band_auto)
+        same = a.c_m == b.c_m && a.c_n == b.c_n && a.w_m == b.w_m && a.w_n == b.w_n;
+    return same;
+}
+
+}  // namespace nuasm
+
 namespace {
 
 nuasm_status cuda_status(cudaError_t e) {
@@ -27,15 +49,6 @@ nuasm_status cuda_status(cudaError_t e) {
         cudaError_t e__ = (expr);                          \
         if (e__ != cudaSuccess) return cuda_status(e__);   \
     } while (0)
-
-bool device_accessible(const void* p) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();   // clear the non-sticky error of a foreign pointer
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
 
 size_t elt_bytes(const nuasm_plan_s* P) { return P->f64 ? 16 : 8; }
 
@@ -97,7 +110,9 @@ struct StageScope {
     }
 };
 
-void release(nuasm_plan_s* P) {
+}  // namespace
+
+void nuasm::plan_release(nuasm_plan_s* P) {
     if (!P) return;
     PlanExtra* X = extra_of(P);
     if (X) {
@@ -116,6 +131,8 @@ void release(nuasm_plan_s* P) {
     delete P;
 }
 
+namespace {
+
 template <typename T> cudaError_t dalloc(nuasm_plan_s* P, T** out, size_t bytes) {
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
@@ -128,10 +145,10 @@ template <typename T> cudaError_t dalloc(nuasm_plan_s* P, T** out, size_t bytes)
 
 // Upload the host tables in the plan's precision.
 cudaError_t upload_tables(nuasm_plan_s* P, const HostTables& t, cudaStream_t st) {
-    const int np = P->g.np, G = P->g.G;
+    const int np = P->g.np;
     const size_t eb = elt_bytes(P);
     const size_t sb = P->f64 ? sizeof(double) : sizeof(float2);
-    const size_t bytes = 6 * np * eb + np * sb + size_t(G) * eb;
+    const size_t bytes = table_bytes(P->g, P->f64, true);
     char* base = nullptr;
     cudaError_t e = dalloc(P, &base, bytes);
     if (e != cudaSuccess) return e;
@@ -145,29 +162,7 @@ cudaError_t upload_tables(nuasm_plan_s* P, const HostTables& t, cudaStream_t st)
     P->d.s = base + 6 * np * eb;
     P->d.tw = base + 6 * np * eb + np * sb;
     std::vector<char> host(bytes);
-    auto put_c = [&](size_t off, const double* src, int count) {
-        if (P->f64) std::memcpy(host.data() + off, src, sizeof(double) * 2 * count);
-        else {
-            float* d = reinterpret_cast<float*>(host.data() + off);
-            for (int i = 0; i < 2 * count; ++i) d[i] = float(src[i]);
-        }
-    };
-    put_c(0, t.t1x, np);
-    put_c(np * eb, t.t1y, np);
-    put_c(2 * np * eb, t.t2x, np);
-    put_c(3 * np * eb, t.t2y, np);
-    put_c(4 * np * eb, t.t3x, np);
-    put_c(5 * np * eb, t.t3y, np);
-    if (P->f64) std::memcpy(host.data() + 6 * np * eb, t.s, sizeof(double) * np);
-    else {
-        float* d = reinterpret_cast<float*>(host.data() + 6 * np * eb);
-        for (int i = 0; i < np; ++i) {
-            float hi = float(t.s[i]);
-            d[2 * i] = hi;
-            d[2 * i + 1] = float(t.s[i] - double(hi));
-        }
-    }
-    put_c(6 * np * eb + np * sb, t.tw, G);
+    pack_tables(t, P->g, P->f64, true, host.data());
     e = cudaMemcpyAsync(base, host.data(), bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(st);   // host buffer goes out of scope
@@ -199,6 +194,52 @@ nuasm_status check_plan_usable(nuasm_plan_s* P) {
     return NUASM_OK;
 }
 
+}  // namespace
+
+// ---------------------------------------------------------------- device-pointer chains
+// (per-stage event scopes are no-ops unless the plan's profiling is on)
+cudaError_t nuasm::chain_type1(nuasm_plan_s* P, const void* c, void* u2, cudaStream_t st) {
+    cudaError_t e;
+    { StageScope sc(P, NUASM_STAGE_SPREAD, st); if ((e = launch_spread(P, c, st)) != cudaSuccess) return e; }
+    { StageScope sc(P, NUASM_STAGE_COL_FWD_FOLD, st); if ((e = launch_col_fwd_fold(P, st)) != cudaSuccess) return e; }
+    { StageScope sc(P, NUASM_STAGE_ROW_T1, st); if ((e = launch_row_t1(P, st)) != cudaSuccess) return e; }
+    { StageScope sc(P, NUASM_STAGE_COL_INV, st); if ((e = launch_col_inv(P, u2, st)) != cudaSuccess) return e; }
+    return cudaSuccess;
+}
+
+cudaError_t nuasm::chain_type2(nuasm_plan_s* P, const void* u1, void* v, cudaStream_t st) {
+    cudaError_t e;
+    { StageScope sc(P, NUASM_STAGE_COL_FWD, st); if ((e = launch_col_fwd(P, u1, st)) != cudaSuccess) return e; }
+    { StageScope sc(P, NUASM_STAGE_ROW_T2, st); if ((e = launch_row_t2(P, st)) != cudaSuccess) return e; }
+    { StageScope sc(P, NUASM_STAGE_COL_INV_FOLD, st); if ((e = launch_col_inv_fold(P, st)) != cudaSuccess) return e; }
+    if (P->m > 0) {
+        StageScope sc(P, NUASM_STAGE_INTERP, st);
+        if ((e = launch_interp(P, v, st)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// type 3: spread the source plan's points, fused forward/H/inverse row pass,
+// interpolate at the destination plan's points (same geometry, the source
+// plan's workspace)
+cudaError_t nuasm::chain_type3(nuasm_plan_s* P, const nuasm_plan_s* Q, const void* c, void* v, cudaStream_t st) {
+    cudaError_t e;
+    { StageScope sc(P, NUASM_STAGE_SPREAD, st); if ((e = launch_spread(P, c, st)) != cudaSuccess) return e; }
+    { StageScope sc(P, NUASM_STAGE_COL_FWD_FOLD, st); if ((e = launch_col_fwd_fold(P, st)) != cudaSuccess) return e; }
+    { StageScope sc(P, NUASM_STAGE_ROW_T3, st); if ((e = launch_row_t3(P, st)) != cudaSuccess) return e; }
+    { StageScope sc(P, NUASM_STAGE_COL_INV_FOLD, st); if ((e = launch_col_inv_fold(P, st)) != cudaSuccess) return e; }
+    if (Q->m > 0) {
+        nuasm_plan_s view = *Q;          // destination records over the source plan's window
+        view.d.win = P->d.win;
+        view.prof = false;
+        StageScope sc(P, NUASM_STAGE_INTERP, st);
+        if ((e = launch_interp(&view, v, st)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+namespace {
+
 // ---------------------------------------------------------------- execute chains
 nuasm_status exec_type1(nuasm_plan_s* P, const void* c, void* u2, cudaStream_t st) {
     nuasm_status s0 = check_plan_usable(P);
@@ -213,10 +254,7 @@ nuasm_status exec_type1(nuasm_plan_s* P, const void* c, void* u2, cudaStream_t s
     }
     const bool out_dev = device_accessible(u2);
     void* uo = out_dev ? u2 : P->d.stage_out;
-    { StageScope sc(P, NUASM_STAGE_SPREAD, st); NUASM_TRY(launch_spread(P, cin, st)); }
-    { StageScope sc(P, NUASM_STAGE_COL_FWD_FOLD, st); NUASM_TRY(launch_col_fwd_fold(P, st)); }
-    { StageScope sc(P, NUASM_STAGE_ROW_T1, st); NUASM_TRY(launch_row_t1(P, st)); }
-    { StageScope sc(P, NUASM_STAGE_COL_INV, st); NUASM_TRY(launch_col_inv(P, uo, st)); }
+    NUASM_TRY(chain_type1(P, cin, uo, st));
     if (!out_dev) {
         StageScope sc(P, NUASM_STAGE_D2H, st);
         NUASM_TRY(cudaMemcpyAsync(u2, P->d.stage_out, eb * size_t(P->g.n) * P->g.n, cudaMemcpyDeviceToHost, st));
@@ -237,13 +275,7 @@ nuasm_status exec_type2(nuasm_plan_s* P, const void* u1, void* v, cudaStream_t s
     }
     const bool out_dev = P->m == 0 || device_accessible(v);
     void* vo = out_dev ? v : P->d.stage_out;
-    { StageScope sc(P, NUASM_STAGE_COL_FWD, st); NUASM_TRY(launch_col_fwd(P, uin, st)); }
-    { StageScope sc(P, NUASM_STAGE_ROW_T2, st); NUASM_TRY(launch_row_t2(P, st)); }
-    { StageScope sc(P, NUASM_STAGE_COL_INV_FOLD, st); NUASM_TRY(launch_col_inv_fold(P, st)); }
-    if (P->m > 0) {
-        StageScope sc(P, NUASM_STAGE_INTERP, st);
-        NUASM_TRY(launch_interp(P, vo, st));
-    }
+    NUASM_TRY(chain_type2(P, uin, vo, st));
     if (!out_dev) {
         StageScope sc(P, NUASM_STAGE_D2H, st);
         NUASM_TRY(cudaMemcpyAsync(v, P->d.stage_out, eb * size_t(P->m), cudaMemcpyDeviceToHost, st));
@@ -260,18 +292,6 @@ __global__ void lattice_kernel(double* __restrict__ x, double* __restrict__ y, i
     }
 }
 
-bool same_problem(const nuasm_params_t& a, const nuasm_params_t& b) {
-    bool same = a.n == b.n && a.n_pad == b.n_pad && a.pitch == b.pitch && a.lambda == b.lambda && a.z == b.z &&
-                a.ox == b.ox && a.oy == b.oy && a.band_auto == b.band_auto && a.kind == b.kind &&
-                a.prec == b.prec && a.tol == b.tol;
-    if (same && !a.band_auto)
-        same = a.c_m == b.c_m && a.c_n == b.c_n && a.w_m == b.w_m && a.w_n == b.w_n;
-    return same;
-}
-
-// type 3: spread the source plan's points, fused forward/H/inverse row pass,
-// interpolate at the destination plan's points (same geometry, the source
-// plan's workspace)
 nuasm_status exec_type3(nuasm_plan_s* P, nuasm_plan_s* Q, const void* c, void* v, cudaStream_t st) {
     nuasm_status s0 = check_plan_usable(P);
     if (s0 != NUASM_OK) return s0;
@@ -286,17 +306,7 @@ nuasm_status exec_type3(nuasm_plan_s* P, nuasm_plan_s* Q, const void* c, void* v
     }
     const bool out_dev = Q->m == 0 || device_accessible(v);
     void* vo = out_dev ? v : Q->d.stage_out;
-    { StageScope sc(P, NUASM_STAGE_SPREAD, st); NUASM_TRY(launch_spread(P, cin, st)); }
-    { StageScope sc(P, NUASM_STAGE_COL_FWD_FOLD, st); NUASM_TRY(launch_col_fwd_fold(P, st)); }
-    { StageScope sc(P, NUASM_STAGE_ROW_T3, st); NUASM_TRY(launch_row_t3(P, st)); }
-    { StageScope sc(P, NUASM_STAGE_COL_INV_FOLD, st); NUASM_TRY(launch_col_inv_fold(P, st)); }
-    if (Q->m > 0) {
-        nuasm_plan_s view = *Q;          // destination records over the source plan's window
-        view.d.win = P->d.win;
-        view.prof = false;
-        StageScope sc(P, NUASM_STAGE_INTERP, st);
-        NUASM_TRY(launch_interp(&view, vo, st));
-    }
+    NUASM_TRY(chain_type3(P, Q, cin, vo, st));
     if (!out_dev) {
         StageScope sc(P, NUASM_STAGE_D2H, st);
         NUASM_TRY(cudaMemcpyAsync(v, Q->d.stage_out, eb * size_t(Q->m), cudaMemcpyDeviceToHost, st));
@@ -312,12 +322,19 @@ nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m, c
                         const double* y, const double* w, void* stream) {
     if (!out) return NUASM_EINVAL;
     *out = nullptr;
+    return plan_create(out, p, m, x, y, w, static_cast<cudaStream_t>(stream), true);
+}
+
+}  // extern "C"
+
+nuasm_status nuasm::plan_create(nuasm_plan_s** out, const nuasm_params_t* p, int64_t m, const double* x,
+                                const double* y, const double* w, cudaStream_t st, bool workspace) {
+    *out = nullptr;
     if (!p) return NUASM_EINVAL;
     nuasm_params_t rp;
     nuasm_status s = validate(*p, m, &rp);
     if (s != NUASM_OK) return s;
     if (m > 0 && (!x || !y)) return NUASM_EINVAL;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     nuasm_plan_s* P = new (std::nothrow) nuasm_plan_s();
     if (!P) return NUASM_ENOMEM;
@@ -330,7 +347,7 @@ nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m, c
     P->f64 = rp.prec == NUASM_PREC_F64;
     P->has_w = w != nullptr;
 
-    auto bail = [&](nuasm_status code) { release(P); return code; };
+    auto bail = [&](nuasm_status code) { plan_release(P); return code; };
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return bail(NUASM_ECUDA); }
 
@@ -338,21 +355,21 @@ nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m, c
     build_tables(rp, P->g, &ht);
     P->rc = ht.rc;
     P->poly = ht.poly;
-    if (rp.kind != NUASM_KIND_ASM || rp.z == 0.0) P->nonsep_mode = 0;
-    else if (P->f64 || ht.rmax <= 0.5) P->nonsep_mode = 1;
-    else P->nonsep_mode = 2;
+    P->nonsep_mode = choose_nonsep_mode(rp, ht.rmax);
     cudaError_t e = upload_tables(P, ht, st);
     free_tables(&ht);
     if (e != cudaSuccess) return bail(cuda_status(e));
 
     const Geometry& g = P->g;
     const size_t eb = elt_bytes(P);
-    const size_t stage = std::max<size_t>(size_t(m), size_t(g.n) * g.n) * eb;
-    if ((e = dalloc(P, &P->d.win, size_t(g.W) * g.Wp * eb)) != cudaSuccess) return bail(cuda_status(e));
-    if ((e = dalloc(P, &P->d.bufA, size_t(g.np) * g.Wp * eb)) != cudaSuccess) return bail(cuda_status(e));
-    if ((e = dalloc(P, &P->d.bufB, size_t(g.np) * g.n * eb)) != cudaSuccess) return bail(cuda_status(e));
-    if ((e = dalloc(P, &P->d.stage_in, stage)) != cudaSuccess) return bail(cuda_status(e));
-    if ((e = dalloc(P, &P->d.stage_out, stage)) != cudaSuccess) return bail(cuda_status(e));
+    if (workspace) {
+        const size_t stage = std::max<size_t>(size_t(m), size_t(g.n) * g.n) * eb;
+        if ((e = dalloc(P, &P->d.win, ws_win_elems(g) * eb)) != cudaSuccess) return bail(cuda_status(e));
+        if ((e = dalloc(P, &P->d.bufA, ws_bufA_elems(g) * eb)) != cudaSuccess) return bail(cuda_status(e));
+        if ((e = dalloc(P, &P->d.bufB, ws_bufB_elems(g) * eb)) != cudaSuccess) return bail(cuda_status(e));
+        if ((e = dalloc(P, &P->d.stage_in, stage)) != cudaSuccess) return bail(cuda_status(e));
+        if ((e = dalloc(P, &P->d.stage_out, stage)) != cudaSuccess) return bail(cuda_status(e));
+    }
     if ((e = dalloc(P, &P->d.tile_off, sizeof(int) * (g.ntiles + 1))) != cudaSuccess) return bail(cuda_status(e));
     if ((e = dalloc(P, &P->d.tile_home, sizeof(int) * g.ntiles)) != cudaSuccess) return bail(cuda_status(e));
     if ((e = dalloc(P, &P->d.err, sizeof(int))) != cudaSuccess) return bail(cuda_status(e));
@@ -378,6 +395,8 @@ nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m, c
     *out = P;
     return NUASM_OK;
 }
+
+extern "C" {
 
 nuasm_status nuasm_plan_lattice(nuasm_plan_t* out, const nuasm_params_t* p, int32_t nx, int32_t ny,
                                 double pitch2, double x0, double y0, void* stream) {
@@ -440,7 +459,7 @@ nuasm_status nufresnel3_execute(nuasm_plan_t src, nuasm_plan_t dst, const void* 
 nuasm_status nuasm_destroy(nuasm_plan_t plan) {
     if (!plan) return NUASM_OK;
     cudaError_t e = cudaDeviceSynchronize();
-    release(plan);
+    plan_release(plan);
     return cuda_status(e);
 }
 

@@ -305,7 +305,18 @@ Geometry make_geometry(const nuasm_params_t& p) {
     return g;
 }
 
-void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t) {
+void phihat_table(const Geometry& g, double* out) {
+    KernelQuad qd;
+    make_quad(g, &qd);
+    const int np = g.np;
+    for (int q = 0; q < np; ++q) {
+        const int k = q < np / 2 ? q : q - np;
+        out[q] = phihat_at(qd, double(k) / g.G);
+    }
+}
+
+void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t, const double* phihat,
+                  bool with_twiddles) {
     const int np = g.np, G = g.G;
     t->t1x = new double[2 * np];
     t->t1y = new double[2 * np];
@@ -314,11 +325,16 @@ void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t) {
     t->t3x = new double[2 * np];
     t->t3y = new double[2 * np];
     t->s = new double[np];
-    t->tw = new double[2 * G];
+    t->tw = with_twiddles ? new double[2 * G] : nullptr;
 
     // deconvolution 1/phihat(k/G) by Gauss-Legendre quadrature of the truncated kernel
-    KernelQuad qd;
-    make_quad(g, &qd);
+    // (geometry only: callers that keep it pass it in)
+    std::vector<double> ph_own;
+    if (!phihat) {
+        ph_own.resize(np);
+        phihat_table(g, ph_own.data());
+        phihat = ph_own.data();
+    }
     // separable transfer-function factor per axis (Eq. 4 or Eq. 5)
     std::vector<cd> hx(np), hy(np);
     for (int axis = 0; axis < 2; ++axis) {
@@ -350,21 +366,71 @@ void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t) {
     const cd cst(cre, cim);
     for (int q = 0; q < np; ++q) {
         const int k = q < np / 2 ? q : q - np;
-        const double ph = phihat_at(qd, double(k) / G);
+        const double ph = phihat[q];
         const cd hyc = hy[q] * cst;
-        table_entry(p, g, q, 1, ph, hx[q].real(), hx[q].imag(), &t->t1x[2 * q], &t->t1x[2 * q + 1]);
-        table_entry(p, g, q, 1, ph, hyc.real(), hyc.imag(), &t->t1y[2 * q], &t->t1y[2 * q + 1]);
-        table_entry(p, g, q, 2, ph, hx[q].real(), hx[q].imag(), &t->t2x[2 * q], &t->t2x[2 * q + 1]);
-        table_entry(p, g, q, 2, ph, hyc.real(), hyc.imag(), &t->t2y[2 * q], &t->t2y[2 * q + 1]);
-        table_entry(p, g, q, 3, ph, hx[q].real(), hx[q].imag(), &t->t3x[2 * q], &t->t3x[2 * q + 1]);
-        table_entry(p, g, q, 3, ph, hyc.real(), hyc.imag(), &t->t3y[2 * q], &t->t3y[2 * q + 1]);
+        // the arithmetic of table_entry, with the mode's phase factors formed once
+        const double dec = ((k & 1) ? -1.0 : 1.0) / ph / np;
+        const cd win1 = cis_ratio(-int64_t(k) * g.Lo, g.G);
+        const cd ctr1 = cis_ratio(-int64_t(k) * (g.n / 2), np);
+        const cd a1 = win1 * ctr1, a2 = std::conj(win1) * std::conj(ctr1);
+        auto put = [](double* dst, int i, const cd& v) {
+            dst[2 * i] = v.real();
+            dst[2 * i + 1] = v.imag();
+        };
+        put(t->t1x, q, a1 * dec * hx[q]);
+        put(t->t1y, q, a1 * dec * hyc);
+        put(t->t2x, q, a2 * dec * hx[q]);
+        put(t->t2y, q, a2 * dec * hyc);
+        const double dec3 = 1.0 / (ph * ph * np);
+        put(t->t3x, q, cd(hx[q].real() * dec3, hx[q].imag() * dec3));
+        put(t->t3y, q, cd(hyc.real() * dec3, hyc.imag() * dec3));
         const double f = double(k) / (double(np) * p.pitch);
         t->s[q] = p.lambda * p.lambda * f * f;
     }
     t->rc = p.z / (2.0 * p.lambda);
     t->rmax = nonsep_rmax(p, g);
     fit_kernel_poly(g, &t->poly);
-    for (int i = 0; i < G; ++i) twiddle(i, G, &t->tw[2 * i], &t->tw[2 * i + 1]);
+    if (t->tw)
+        for (int i = 0; i < G; ++i) twiddle(i, G, &t->tw[2 * i], &t->tw[2 * i + 1]);
+}
+
+size_t table_bytes(const Geometry& g, bool f64, bool with_twiddles) {
+    const size_t eb = f64 ? 16 : 8, sb = f64 ? sizeof(double) : 2 * sizeof(float);
+    return 6 * size_t(g.np) * eb + size_t(g.np) * sb + (with_twiddles ? size_t(g.G) * eb : 0);
+}
+
+// Device image of the tables: T1x T1y T2x T2y T3x T3y (complex, plan precision),
+// s (double, or float hi/lo pairs), then the twiddles when present.
+void pack_tables(const HostTables& t, const Geometry& g, bool f64, bool with_twiddles, void* dst) {
+    const int np = g.np;
+    const size_t eb = f64 ? 16 : 8;
+    char* out = static_cast<char*>(dst);
+    auto put_c = [&](size_t off, const double* src, int count) {
+        if (f64) std::memcpy(out + off, src, sizeof(double) * 2 * count);
+        else {
+            float* d = reinterpret_cast<float*>(out + off);
+            for (int i = 0; i < 2 * count; ++i) d[i] = float(src[i]);
+        }
+    };
+    const double* six[6] = {t.t1x, t.t1y, t.t2x, t.t2y, t.t3x, t.t3y};
+    for (int i = 0; i < 6; ++i) put_c(size_t(i) * np * eb, six[i], np);
+    const size_t soff = 6 * size_t(np) * eb;
+    if (f64) std::memcpy(out + soff, t.s, sizeof(double) * np);
+    else {
+        float* d = reinterpret_cast<float*>(out + soff);
+        for (int i = 0; i < np; ++i) {
+            const float hi = float(t.s[i]);
+            d[2 * i] = hi;
+            d[2 * i + 1] = float(t.s[i] - double(hi));
+        }
+    }
+    if (with_twiddles && t.tw) put_c(soff + size_t(np) * (f64 ? sizeof(double) : 2 * sizeof(float)), t.tw, g.G);
+}
+
+int choose_nonsep_mode(const nuasm_params_t& p, double rmax) {
+    if (p.kind != NUASM_KIND_ASM || p.z == 0.0) return 0;
+    if (p.prec == NUASM_PREC_F64 || rmax <= 0.5) return 1;
+    return 2;
 }
 
 // Chebyshev interpolation of each tap phi(i + f - w/2), f in [0, 1), at

@@ -104,8 +104,33 @@ bool kernel_shape(double tol, int prec, int kernel, int* w, double* beta);
 double kernel_value(const Geometry& g, double t);
 void band_range(const nuasm_params_t& p, int out[4]);
 Geometry make_geometry(const nuasm_params_t& p);
-void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t);
+// FP64 tables for the plan parameters; `phihat` (N' values of the kernel's
+// Fourier transform at k/G, see phihat_table) may be passed in when cached,
+// twiddles are left out (t->tw = nullptr) when with_twiddles is false.
+void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t, const double* phihat = nullptr,
+                  bool with_twiddles = true);
+void phihat_table(const Geometry& g, double* out);
 void free_tables(HostTables* t);
+size_t table_bytes(const Geometry& g, bool f64, bool with_twiddles);
+void pack_tables(const HostTables& t, const Geometry& g, bool f64, bool with_twiddles, void* dst);
+// ASM non-separable phase evaluation: 0 none, 1 plain, 2 double-float
+int choose_nonsep_mode(const nuasm_params_t& p, double rmax);
+
+// plan life cycle and device-pointer execute chains (capi.cu).  A plan made
+// without workspace holds tables, twiddles and bins only; it is executed
+// through a view that supplies the workspace (batch.cu, serve.cu).
+nuasm_status plan_create(nuasm_plan_s** out, const nuasm_params_t* p, int64_t m, const double* x,
+                         const double* y, const double* w, cudaStream_t st, bool workspace);
+void plan_release(nuasm_plan_s* P);
+bool same_problem(const nuasm_params_t& a, const nuasm_params_t& b);
+bool device_accessible(const void* p);
+cudaError_t chain_type1(nuasm_plan_s* P, const void* c, void* u2, cudaStream_t s);
+cudaError_t chain_type2(nuasm_plan_s* P, const void* u1, void* v, cudaStream_t s);
+cudaError_t chain_type3(nuasm_plan_s* P, const nuasm_plan_s* Q, const void* c, void* v, cudaStream_t s);
+// workspace elements (complex) of a geometry: window W x Wp, bufA N' x Wp, bufB N' x N
+inline size_t ws_win_elems(const Geometry& g) { return size_t(g.W) * g.Wp; }
+inline size_t ws_bufA_elems(const Geometry& g) { return size_t(g.np) * g.Wp; }
+inline size_t ws_bufB_elems(const Geometry& g) { return size_t(g.np) * g.n; }
 
 // launchers (gridding.cu / passes.cu); all asynchronous on `s`
 // (the device error word P->d.err: bit 1 = point outside the window at plan

@@ -31,6 +31,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "fft_engine.cuh"
 #include "nuasm_internal.h"
@@ -552,7 +554,8 @@ cudaError_t launch_col_tma(const nuasm_plan_s* P, const void* src, void* dst, in
         const size_t sm = Cf::smem();
         cudaError_t e = set_smem(col_tma_kernel<LOGNP, MODE>, sm);
         if (e != cudaSuccess) return e;
-        static int ctas = 0;   // persistent grid: resident CTAs on the whole GPU
+        static std::atomic<int> resident{0};   // persistent grid: resident CTAs on the whole GPU
+        int ctas = resident.load(std::memory_order_relaxed);
         if (ctas == 0) {
             int dev = 0, nsm = 0, per = 0;
             if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -561,6 +564,7 @@ cudaError_t launch_col_tma(const nuasm_plan_s* P, const void* src, void* dst, in
                 cudaSuccess)
                 return e;
             ctas = nsm * (per > 0 ? per : 1);
+            resident.store(ctas, std::memory_order_relaxed);
         }
         const int nstrips = (ncols + Cf::C - 1) / Cf::C;
         const int nboxes = (load_rows + Cf::BOXR - 1) / Cf::BOXR;

@@ -53,6 +53,32 @@ class PlanInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("type", ctypes.c_int32),
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("device", ctypes.c_int32), ("hbm_budget", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("p", Params), ("type", ctypes.c_int32), ("points_id", ctypes.c_uint64), ("m", ctypes.c_int64),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reused_points", ctypes.c_int32), ("latency_ms", ctypes.c_double),
+                ("queue_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "failed", "points")] + \
+               [("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("wall_s", ctypes.c_double)] + \
+               [(f, ctypes.c_int64) for f in ("resident_sets", "resident_bytes", "bins_built", "bins_reused",
+                                              "evictions", "peak_bytes")]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -83,6 +109,18 @@ _SIGS = {
     "nuasm_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "nuasm2_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int64, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "nuasm_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(BatchItem),
+                                          ctypes.c_int32, ctypes.c_int32]),
+    "nuasm_batch_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "nuasm_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    "nuasm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "nuasm_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ServerConfig)]),
+    "nuasm_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]),
+    "nuasm_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                         ctypes.POINTER(RequestResult)]),
+    "nuasm_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats), ctypes.c_int32]),
+    "nuasm_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
 
@@ -354,3 +392,128 @@ def nuasm2_solve_noalloc(params: Params, x, y, u1, v, stream=None):
     _check(lib().nuasm2_solve_noalloc(ctypes.byref(params), m, _ptr(x), _ptr(y), _ptr(u1), _ptr(v),
                                       _stream(stream)), "nuasm2_solve_noalloc")
     return v
+
+
+# ---------------------------------------------------------------- batches
+class Batch:
+    """Owner of a nuasm_batch_t handle; keeps the plans and arrays it records alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def execute(self, stream=None):
+        return nuasm_batch_execute(self, stream)
+
+    def info(self) -> tuple:
+        return nuasm_batch_info(self)
+
+    def destroy(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            _check(lib().nuasm_batch_destroy(h), "nuasm_batch_destroy")
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def nuasm_batch_create(items, lanes: int = 0) -> Batch:
+    """items: sequence of (plan, type, in, out) or (plan, type, in, out, dst) with device arrays."""
+    arr = (BatchItem * len(items))()
+    keep = []
+    for i, it in enumerate(items):
+        plan, type_, inp, out = it[:4]
+        dst = it[4] if len(it) > 4 else None
+        n_in = plan.m if type_ in (1, 3) else plan.n * plan.n
+        n_out = plan.n * plan.n if type_ == 1 else (plan.m if type_ == 2 else (dst.m if dst else 0))
+        _expect(inp, n_in, plan.complex_dtype, f"items[{i}].in")
+        _expect(out, n_out, plan.complex_dtype, f"items[{i}].out")
+        arr[i] = BatchItem(plan._h, dst._h if dst is not None else None, int(type_), _ptr(inp), _ptr(out))
+        keep += [plan, dst, inp, out]
+    h = ctypes.c_void_p()
+    _check(lib().nuasm_batch_create(ctypes.byref(h), arr, len(items), int(lanes)), "nuasm_batch_create")
+    return Batch(h, keep)
+
+
+def nuasm_batch_execute(batch: Batch, stream=None):
+    _check(lib().nuasm_batch_execute(batch.handle, _stream(stream)), "nuasm_batch_execute")
+
+
+def nuasm_batch_info(batch: Batch) -> tuple:
+    """(lanes used, kernel launches per execute)."""
+    lanes, kernels = ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().nuasm_batch_info(batch.handle, ctypes.byref(lanes), ctypes.byref(kernels)), "nuasm_batch_info")
+    return int(lanes.value), int(kernels.value)
+
+
+def nuasm_batch_destroy(batch: Batch):
+    batch.destroy()
+
+
+# ---------------------------------------------------------------- serving
+class Server:
+    """Owner of a nuasm_server_t handle.  Submitted arrays are referenced until
+    their wait returns."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self._pending = {}
+
+    def destroy(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            _check(lib().nuasm_server_destroy(h), "nuasm_server_destroy")
+            self._pending.clear()
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def nuasm_server_create(slots: int = 0, device: int = 0, hbm_budget: int = 0) -> Server:
+    cfg = ServerConfig(int(slots), int(device), int(hbm_budget))
+    h = ctypes.c_void_p()
+    _check(lib().nuasm_server_create(ctypes.byref(h), ctypes.byref(cfg)), "nuasm_server_create")
+    return Server(h)
+
+
+def nuasm_server_submit(server: Server, params: Params, type_: int, x, y, inp, out, points_id: int = 0) -> int:
+    """Queue one solve; x, y: float64 (M), inp/out: host or device arrays.  Returns the ticket."""
+    m = _numel(x)
+    _expect(y, m, "float64", "y")
+    _expect(x, m, "float64", "x")
+    cdt = "complex128" if params.prec == PREC_F64 else "complex64"
+    nn = params.n * params.n
+    _expect(inp, m if type_ == 1 else nn, cdt, "in")
+    _expect(out, nn if type_ == 1 else m, cdt, "out")
+    req = Request(params, int(type_), int(points_id), m, _ptr(x), _ptr(y), _ptr(inp), _ptr(out))
+    t = ctypes.c_int64()
+    _check(lib().nuasm_server_submit(server.handle, ctypes.byref(req), ctypes.byref(t)), "nuasm_server_submit")
+    server._pending[int(t.value)] = (x, y, inp, out)
+    return int(t.value)
+
+
+def nuasm_server_wait(server: Server, ticket: int, timeout_s: float = -1.0) -> dict:
+    """Block until the request completes; returns its status and timings
+    (raises NuasmError with NUASM_ETIMEOUT when the limit passes first)."""
+    r = RequestResult()
+    _check(lib().nuasm_server_wait(server.handle, int(ticket), float(timeout_s), ctypes.byref(r)),
+           "nuasm_server_wait")
+    server._pending.pop(int(ticket), None)
+    return {"status": int(r.status), "reused_points": bool(r.reused_points), "latency_ms": float(r.latency_ms),
+            "queue_ms": float(r.queue_ms)}
+
+
+def nuasm_server_stats(server: Server, reset: bool = False) -> dict:
+    st = ServerStats()
+    _check(lib().nuasm_server_stats(server.handle, ctypes.byref(st), 1 if reset else 0), "nuasm_server_stats")
+    return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+
+def nuasm_server_destroy(server: Server):
+    server.destroy()

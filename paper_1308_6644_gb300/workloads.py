@@ -223,3 +223,33 @@ def mixed_plane(seed: int, plane: int) -> Workload:
         vals = random_phasor(rng, (n, n))
     return Workload(f"mixed{plane}_n{n}_t{type_}_m{len(x)}", "asm", type_, n, pitch, lam, z,
                     x=x, y=y, values=vals)
+
+
+def serving_point_set(seed: int, k: int, max_points: int = 16_000_000) -> Workload:
+    """Point set k of the serving workload: N in {512, 1024, 2048, 4096},
+    M/N^2 log-uniform in [1/4, 1] (at most max_points), jittered-lattice or
+    clustered points, 8 um pitch.  Wavelength and distance belong to the
+    requests, not to the set."""
+    rng = np.random.default_rng(seed + 100 + k)
+    n = int(rng.choice([512, 1024, 2048, 4096]))
+    pitch = 8e-6
+    m = min(max_points, max(1, int(np.exp(rng.uniform(np.log(0.25), 0.0)) * n * n)))
+    half = 0.5 * n * pitch
+    if rng.random() < 0.5:
+        side = max(1, int(np.sqrt(m)))
+        x, y = jittered_lattice(rng, side, 2 * half / side, 0.4)
+    else:
+        x, y = clustered_points(rng, m, half)
+    x, y = clamp_window(x, n, pitch), clamp_window(y, n, pitch)
+    return Workload(f"serve_set{k}_n{n}_m{len(x)}", "asm", 0, n, pitch, 0.0, 0.0, x=x, y=y, values=None)
+
+
+def serving_trace(seed: int, count: int, sets: int) -> list:
+    """count requests: (point-set index, type 1/2, z ~ U[1, 50] cm, lambda in
+    {450, 532, 633} nm, unit-mean exponential gap before the arrival)."""
+    rng = np.random.default_rng(seed + 7)
+    out = []
+    for _ in range(count):
+        out.append((int(rng.integers(0, sets)), int(rng.integers(1, 3)), float(rng.uniform(0.01, 0.50)),
+                    float(rng.choice([450e-9, 532e-9, 633e-9])), float(rng.exponential(1.0))))
+    return out

@@ -159,3 +159,24 @@ def test_gaussian_kernel_limits(P):
     with pytest.raises(P.NuasmError) as ei:
         P.nuasm_plan(bad, x, x)
     assert ei.value.code == 1
+
+
+def test_batch_and_server_reject_bad_arguments_before_device_work(P):
+    lib = P.lib()
+    h = ctypes.c_void_p()
+    assert lib.nuasm_batch_create(ctypes.byref(h), None, 1, 0) == 1
+    items = (P.nuasm.BatchItem * 1)()
+    assert lib.nuasm_batch_create(ctypes.byref(h), items, 0, 0) == 1        # empty batch
+    assert lib.nuasm_batch_create(ctypes.byref(h), items, 1, 65) == 1       # too many lanes
+    assert lib.nuasm_batch_create(ctypes.byref(h), items, 1, 0) == 1        # NULL plan
+    assert lib.nuasm_batch_execute(None, None) == 1
+    assert lib.nuasm_batch_destroy(None) == 0
+    cfg = P.nuasm.ServerConfig(33, 0, 0)
+    assert lib.nuasm_server_create(ctypes.byref(h), ctypes.byref(cfg)) == 1  # too many slots
+    cfg = P.nuasm.ServerConfig(2, -1, 0)
+    assert lib.nuasm_server_create(ctypes.byref(h), ctypes.byref(cfg)) == 1  # bad device
+    t = ctypes.c_int64()
+    req = P.nuasm.Request()
+    assert lib.nuasm_server_submit(None, ctypes.byref(req), ctypes.byref(t)) == 1
+    assert lib.nuasm_server_wait(None, 1, 0.0, ctypes.byref(P.nuasm.RequestResult())) == 1
+    assert lib.nuasm_server_destroy(None) == 0
