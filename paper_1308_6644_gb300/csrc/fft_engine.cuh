@@ -124,19 +124,37 @@ template <> struct Log2<1> { static constexpr int v = 0; };
 // w[r] = exp(-2 pi i k r / (Ns R)) = tw[(k r) << sh] for r in [1, R).  FP64
 // reads every power from the table; FP32 reads w^1 and w^4 (w^1 and w^2 for
 // R = 4) and forms the others by complex products (at most four roundings,
-// about 2.4e-7 relative), which trades table loads for FMA-pipe work.
+// about 2.4e-7 relative), which trades table loads for FMA-pipe work.  The
+// table reads are split from the products (twiddle_base / twiddle_powers) so
+// a pass can issue them before its barrier.
+template <typename V, int R> struct TwBase {
+    static constexpr int N = (sizeof(V) == 16 || R == 2) ? R - 1 : 2;
+    V t[N > 0 ? N : 1];
+};
+
 template <typename V, int R>
-__device__ __forceinline__ void twiddle_powers(const V* __restrict__ tw, int k, int sh, V* w) {
+__device__ __forceinline__ void twiddle_base(const V* __restrict__ tw, int k, int sh, TwBase<V, R>& b) {
     if constexpr (sizeof(V) == 16 || R == 2) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) w[r] = __ldg(&tw[(k * r) << sh]);
+        for (int r = 1; r < R; ++r) b.t[r - 1] = __ldg(&tw[(k * r) << sh]);
+    } else {
+        b.t[0] = __ldg(&tw[k << sh]);
+        b.t[1] = __ldg(&tw[((R == 4 ? 2 : 4) * k) << sh]);
+    }
+}
+
+template <typename V, int R>
+__device__ __forceinline__ void twiddle_powers(const TwBase<V, R>& b, V* w) {
+    if constexpr (sizeof(V) == 16 || R == 2) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[r] = b.t[r - 1];
     } else if constexpr (R == 4) {
-        w[1] = __ldg(&tw[k << sh]);
-        w[2] = __ldg(&tw[(2 * k) << sh]);
+        w[1] = b.t[0];
+        w[2] = b.t[1];
         w[3] = cmul(w[2], w[1]);
     } else {
-        w[1] = __ldg(&tw[k << sh]);
-        w[4] = __ldg(&tw[(4 * k) << sh]);
+        w[1] = b.t[0];
+        w[4] = b.t[1];
         w[2] = cmul(w[1], w[1]);
         w[3] = cmul(w[2], w[1]);
         w[5] = cmul(w[4], w[1]);
@@ -167,6 +185,7 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
     const int tid = threadIdx.x;
     V v[E];
     int jj[NB], cc[NB];
+    TwBase<V, R> twb[LOGNS > 0 ? NB : 1];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int beta = tid + b * P;
@@ -175,6 +194,7 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
         else { c = beta & (C - 1); j = beta >> LOGC; }
         jj[b] = j;
         cc[b] = c;
+        if constexpr (LOGNS > 0) twiddle_base<V, R>(tw, j & (NS - 1), SH, twb[b]);   // in flight across the barrier
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int p = j + r * LDR;
@@ -185,10 +205,9 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
     if (!FIRST) __syncthreads();
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        if (LOGNS > 0) {
-            const int k = jj[b] & (NS - 1);
+        if constexpr (LOGNS > 0) {
             V w[R];
-            twiddle_powers<V, R>(tw, k, SH, w);
+            twiddle_powers<V, R>(twb[b], w);
 #pragma unroll
             for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], DIR > 0 ? cconj(w[r]) : w[r]);
         }

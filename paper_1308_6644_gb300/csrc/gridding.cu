@@ -290,58 +290,95 @@ __global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::ty
 // --------------------------------------------------------------- interpolation (type 2)
 // The tile plus its (w-1) halo is staged with a row stride rounded up to 16
 // elements, so bank classes depend on the column only (see order_tile_kernel).
+// The first kInterpPrefetch records of every thread are loaded before the
+// staging loads so that their latency overlaps the tile's; FP32 tiles are
+// staged two complex values (16 B) per load.
+constexpr int kInterpThreads = 256, kInterpPrefetch = 4;
+
+template <typename S, int WMAX, bool EXACT, typename Rec, typename V>
+__device__ __forceinline__ void interp_point(const Rec& r, const V* __restrict__ tl, int THP, int x0, int y0, int w,
+                                             S beta, const KernelPoly& kp, V* __restrict__ v) {
+    const int lx = int(r.cell & 0xffffu) - x0, ly = int(r.cell >> 16) - y0;
+    S wx[WMAX], wy[WMAX];
+    tap_weights<WMAX>(S(r.fx), w, beta, kp, wx);
+    tap_weights<WMAX>(S(r.fy), w, beta, kp, wy);
+    S ar = S(0), ai = S(0);
+#pragma unroll
+    for (int qy = 0; qy < WMAX; ++qy) {
+        if (qy >= w) continue;
+        const V* row = tl + (ly + qy) * THP + lx;
+        S rr = S(0), ri = S(0);
+#pragma unroll
+        for (int qx = 0; qx < WMAX; ++qx) {
+            if (qx >= w) continue;
+            const V g = row[qx];
+            rr = fma(g.x, wx[qx], rr);
+            ri = fma(g.y, wx[qx], ri);
+        }
+        ar = fma(rr, wy[qy], ar);
+        ai = fma(ri, wy[qy], ai);
+    }
+    V out;
+    out.x = ar;
+    out.y = ai;
+    v[r.j] = out;
+}
+
 template <typename S, int WMAX, bool EXACT>
-__global__ void __launch_bounds__(256) interp_kernel(const typename RecOf<S>::type* __restrict__ rec,
-                                                     const int* __restrict__ off, const int* __restrict__ home,
-                                                     const typename VecOf<S>::type* __restrict__ win,
-                                                     typename VecOf<S>::type* __restrict__ v, GridArgs a,
-                                                     const KernelPoly kp) {
+__global__ void __launch_bounds__(kInterpThreads) interp_kernel(const typename RecOf<S>::type* __restrict__ rec,
+                                                                const int* __restrict__ off,
+                                                                const int* __restrict__ home,
+                                                                const typename VecOf<S>::type* __restrict__ win,
+                                                                typename VecOf<S>::type* __restrict__ v, GridArgs a,
+                                                                const KernelPoly kp) {
     using V = typename VecOf<S>::type;
+    using Rec = typename RecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
     V* tl = reinterpret_cast<V*>(smem_raw);
     const int T = a.T, w = EXACT ? WMAX : a.w, TH = T + w - 1, THP = (TH + 15) & ~15;
     const int tile = blockIdx.x;
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
-    for (int i = threadIdx.x; i < TH * THP; i += blockDim.x) {
-        const int yy = i / THP, xx = i - yy * THP;
-        const int gy = y0 + yy, gx = x0 + xx;
-        V val;
-        val.x = S(0);
-        val.y = S(0);
-        if (xx < TH && gy < a.W && gx < a.W) val = win[gy * a.Wp + gx];
-        tl[i] = val;
+    const int b = off[tile], e = b + home[tile];
+    Rec pre[kInterpPrefetch];
+#pragma unroll
+    for (int k = 0; k < kInterpPrefetch; ++k) {
+        const int i = b + threadIdx.x + k * kInterpThreads;
+        if (i < e) pre[k] = rec[i];
+    }
+    if constexpr (sizeof(V) == 8) {
+        // pairs of complex64: x0 and the row pitch are even, so every pair is
+        // 16-byte aligned, and W is even, so a pair never straddles the window edge
+        const int HP = THP / 2;
+        float4* tl4 = reinterpret_cast<float4*>(tl);
+        for (int i = threadIdx.x; i < TH * HP; i += kInterpThreads) {
+            const int yy = i / HP, u = i - yy * HP;
+            const int gy = y0 + yy, gx = x0 + 2 * u;
+            float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (2 * u < TH && gy < a.W && gx < a.W)
+                val = *reinterpret_cast<const float4*>(&win[size_t(gy) * a.Wp + gx]);
+            tl4[i] = val;
+        }
+    } else {
+        for (int i = threadIdx.x; i < TH * THP; i += kInterpThreads) {
+            const int yy = i / THP, xx = i - yy * THP;
+            const int gy = y0 + yy, gx = x0 + xx;
+            V val;
+            val.x = S(0);
+            val.y = S(0);
+            if (xx < TH && gy < a.W && gx < a.W) val = win[size_t(gy) * a.Wp + gx];
+            tl[i] = val;
+        }
     }
     __syncthreads();
     const S beta = S(a.beta);
-    const int b = off[tile], e = b + home[tile];
-    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
-        const auto r = rec[i];
-        const int lx = int(r.cell & 0xffffu) - x0, ly = int(r.cell >> 16) - y0;
-        S wx[WMAX], wy[WMAX];
-        tap_weights<WMAX>(S(r.fx), w, beta, kp, wx);
-        tap_weights<WMAX>(S(r.fy), w, beta, kp, wy);
-        S ar = S(0), ai = S(0);
 #pragma unroll
-        for (int qy = 0; qy < WMAX; ++qy) {
-            if (qy >= w) continue;
-            const V* row = tl + (ly + qy) * THP + lx;
-            S rr = S(0), ri = S(0);
-#pragma unroll
-            for (int qx = 0; qx < WMAX; ++qx) {
-                if (qx >= w) continue;
-                const V g = row[qx];
-                rr = fma(g.x, wx[qx], rr);
-                ri = fma(g.y, wx[qx], ri);
-            }
-            ar = fma(rr, wy[qy], ar);
-            ai = fma(ri, wy[qy], ai);
-        }
-        V out;
-        out.x = ar;
-        out.y = ai;
-        v[r.j] = out;
+    for (int k = 0; k < kInterpPrefetch; ++k) {
+        const int i = b + threadIdx.x + k * kInterpThreads;
+        if (i < e) interp_point<S, WMAX, EXACT>(pre[k], tl, THP, x0, y0, w, beta, kp, v);
     }
+    for (int i = b + threadIdx.x + kInterpPrefetch * kInterpThreads; i < e; i += kInterpThreads)
+        interp_point<S, WMAX, EXACT>(rec[i], tl, THP, x0, y0, w, beta, kp, v);
 }
 
 GridArgs grid_args(const nuasm_plan_s* P) {
@@ -387,7 +424,7 @@ cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
     const size_t sm = size_t(TH) * THP * sizeof(V);
     cudaError_t e = set_smem(interp_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
-    interp_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
+    interp_kernel<S, WMAX, EXACT><<<P->g.ntiles, kInterpThreads, sm, st>>>(
         static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.tile_home,
         static_cast<const V*>(P->d.win), static_cast<V*>(v), a, taps_arg(P));
     return cudaGetLastError();

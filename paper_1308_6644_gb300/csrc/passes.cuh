@@ -95,8 +95,7 @@ struct ColArgs {
 };
 
 // --------------------------------------------------------------- non-separable ASM factor
-__device__ __forceinline__ float2 nonsep_factor(const float2* __restrict__ s, int qx, int qy, const RowArgs& a) {
-    const float2 sa = __ldg(&s[qx]), sb = __ldg(&s[qy]);
+__device__ __forceinline__ float2 nonsep_factor(float2 sa, float2 sb, const RowArgs& a) {
     float fr;
     if (a.nonsep == 1) {
         // |r| <= 1/2 cycle: fast-math evaluation, phase error below 2e-6 rad
@@ -121,8 +120,8 @@ __device__ __forceinline__ float2 nonsep_factor(const float2* __restrict__ s, in
     return make_float2(cs, sn);
 }
 
-__device__ __forceinline__ double2 nonsep_factor(const double* __restrict__ s, int qx, int qy, const RowArgs& a) {
-    const double sv = __ldg(&s[qx]) + __ldg(&s[qy]);
+__device__ __forceinline__ double2 nonsep_factor(double sa, double sb, const RowArgs& a) {
+    const double sv = sa + sb;
     if (sv >= 1.0) return make_double2(0.0, 0.0);
     const double q = sv / (1.0 + sqrt(1.0 - sv));
     const double r = a.rc * q * q;
@@ -131,13 +130,40 @@ __device__ __forceinline__ double2 nonsep_factor(const double* __restrict__ s, i
     return make_double2(cs, sn);
 }
 
-// Tx(q) Ty(r) E(q, r): the per-mode factor applied between the row transforms
+// Tx(q) Ty(r) E(q, r): the per-mode factor applied between the row transforms.
+// A row's Ty(r) and s(r) are loaded once per row (RowConst) and passed in.
+template <typename V> struct RowConst {
+    V ty;
+    typename STable<V>::type s;
+};
+
+template <typename V>
+__device__ __forceinline__ RowConst<V> row_const(int r, const V* __restrict__ ty,
+                                                 const typename STable<V>::type* __restrict__ s) {
+    return RowConst<V>{__ldg(&ty[r]), __ldg(&s[r])};
+}
+
+template <typename V>
+__device__ __forceinline__ V mode_factor(int q, const RowConst<V>& rc, const V* __restrict__ tx,
+                                         const typename STable<V>::type* __restrict__ s, const RowArgs& a) {
+    V f = cmul(__ldg(&tx[q]), rc.ty);
+    if (a.nonsep && (f.x != 0 || f.y != 0)) f = cmul(f, nonsep_factor(__ldg(&s[q]), rc.s, a));
+    return f;
+}
+
 template <typename V>
 __device__ __forceinline__ V mode_factor(int q, int r, const V* __restrict__ tx, const V* __restrict__ ty,
                                          const typename STable<V>::type* __restrict__ s, const RowArgs& a) {
-    V f = cmul(__ldg(&tx[q]), __ldg(&ty[r]));
-    if (a.nonsep && (f.x != 0 || f.y != 0)) f = cmul(f, nonsep_factor(s, q, r, a));
-    return f;
+    return mode_factor<V>(q, row_const<V>(r, ty, s), tx, s, a);
+}
+
+// the factor of mode q in the CTA's row `row` (ROWS == 1: the constants held in registers)
+template <typename V, int ROWS>
+__device__ __forceinline__ V row_factor(int q, int row, int r0, const RowConst<V>& rc0, const V* __restrict__ tx,
+                                        const V* __restrict__ ty, const typename STable<V>::type* __restrict__ s,
+                                        const RowArgs& a) {
+    if constexpr (ROWS == 1) return mode_factor<V>(q, rc0, tx, s, a);
+    else return mode_factor<V>(q, r0 + row, tx, ty, s, a);
 }
 
 // --------------------------------------------------------------- type-1 row pass
@@ -163,10 +189,11 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
         const V t = p + NP < W ? x[p + NP] : zero;
         return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
     };
+    const RowConst<V> rc0 = row_const<V>(r0, ty, s);
     auto put = [&](int row, int pk, int sgn, V v) {
         const int pb = 2 * pk + sgn;
         const int q = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
-        if (q >= 0) M[row * NP + q] = cmul(v, mode_factor<V>(q, r0 + row, tx, ty, s, a));
+        if (q >= 0) M[row * NP + q] = cmul(v, row_factor<V, ROWS>(q, row, r0, rc0, tx, ty, s, a));
     };
     if constexpr (Cf::MERGE) {
         block_fft<V, -1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false>(
@@ -204,9 +231,10 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     const int r0 = blockIdx.x * ROWS;
     const int n = a.n, W = a.W, Wp = a.Wp;
     const V zero = CTraits<V>::zero();
+    const RowConst<V> rc0 = row_const<V>(r0, ty, s);
     block_fft<V, -1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
         S, tw, [&](int p, int c) { return p < n ? B[(r0 + c) * n + p] : zero; },
-        [&](int p, int c, V v) { M[c * NP + p] = cmul(v, mode_factor<V>(p, r0 + c, tx, ty, s, a)); });
+        [&](int p, int c, V v) { M[c * NP + p] = cmul(v, row_factor<V, ROWS>(p, c, r0, rc0, tx, ty, s, a)); });
     __syncthreads();
     auto get = [&](int row, int q, int sgn) -> V {
         const V y = M[row * NP + q];
@@ -255,10 +283,11 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
         const V t = p + NP < W ? x[p + NP] : zero;
         return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
     };
+    const RowConst<V> rc0 = row_const<V>(r0, ty, s);
     auto put_mode = [&](int row, int pk, int sgn, V v) {
         const int pb = 2 * pk + sgn;
         const int q = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
-        if (q >= 0) M[row * NP + q] = cmul(v, mode_factor<V>(q, r0 + row, tx, ty, s, a));
+        if (q >= 0) M[row * NP + q] = cmul(v, row_factor<V, ROWS>(q, row, r0, rc0, tx, ty, s, a));
     };
     auto get_mode = [&](int row, int q, int sgn) -> V {
         const V y = M[row * NP + q];
