@@ -124,7 +124,7 @@ void nuasm::plan_release(nuasm_plan_s* P) {
                 }
         delete X;
     }
-    void* ptrs[] = {P->d.tables, P->d.rec, P->d.wpt, P->d.tile_off, P->d.tile_home,
+    void* ptrs[] = {P->d.tables, P->d.rec, P->d.wpt, P->d.tile_off, P->d.tile_home, P->d.tile_order,
                     P->d.win, P->d.bufA, P->d.bufB, P->d.stage_in, P->d.stage_out, P->d.err};
     for (void* q : ptrs)
         if (q) cudaFree(q);

@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <numeric>
+#include <vector>
 
 #include "common.cuh"
 #include "nuasm_internal.h"
@@ -235,6 +237,7 @@ struct GridArgs {
 template <typename S, int WMAX, bool EXACT>
 __global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::type* __restrict__ rec,
                                                      const int* __restrict__ off, const double* __restrict__ wpt,
+                                                     const int* __restrict__ order,
                                                      const typename VecOf<S>::type* __restrict__ c,
                                                      typename VecOf<S>::type* __restrict__ win, GridArgs a,
                                                      const KernelPoly kp) {
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::ty
     const int T = a.T, w = EXACT ? WMAX : a.w;
     S* sre = reinterpret_cast<S*>(smem_raw);
     S* sim = sre + T * T;
-    const int tile = blockIdx.x;
+    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) { sre[i] = S(0); sim[i] = S(0); }
@@ -328,6 +331,7 @@ template <typename S, int WMAX, bool EXACT>
 __global__ void __launch_bounds__(kInterpThreads) interp_kernel(const typename RecOf<S>::type* __restrict__ rec,
                                                                 const int* __restrict__ off,
                                                                 const int* __restrict__ home,
+                                                                const int* __restrict__ order,
                                                                 const typename VecOf<S>::type* __restrict__ win,
                                                                 typename VecOf<S>::type* __restrict__ v, GridArgs a,
                                                                 const KernelPoly kp) {
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(kInterpThreads) interp_kernel(const typename R
     extern __shared__ unsigned char smem_raw[];
     V* tl = reinterpret_cast<V*>(smem_raw);
     const int T = a.T, w = EXACT ? WMAX : a.w, TH = T + w - 1, THP = (TH + 15) & ~15;
-    const int tile = blockIdx.x;
+    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
     const int b = off[tile], e = b + home[tile];
@@ -372,13 +376,20 @@ __global__ void __launch_bounds__(kInterpThreads) interp_kernel(const typename R
     }
     __syncthreads();
     const S beta = S(a.beta);
+    // a ring of kInterpPrefetch records in flight: each slot is refilled with
+    // the record kInterpPrefetch strides ahead before its point is computed
+    constexpr int AHEAD = kInterpPrefetch * kInterpThreads;
+    for (int base = b + threadIdx.x; base < e; base += AHEAD) {
 #pragma unroll
-    for (int k = 0; k < kInterpPrefetch; ++k) {
-        const int i = b + threadIdx.x + k * kInterpThreads;
-        if (i < e) interp_point<S, WMAX, EXACT>(pre[k], tl, THP, x0, y0, w, beta, kp, v);
+        for (int k = 0; k < kInterpPrefetch; ++k) {
+            const int i = base + k * kInterpThreads;
+            if (i < e) {
+                const Rec r = pre[k];
+                if (i + AHEAD < e) pre[k] = rec[i + AHEAD];
+                interp_point<S, WMAX, EXACT>(r, tl, THP, x0, y0, w, beta, kp, v);
+            }
+        }
     }
-    for (int i = b + threadIdx.x + kInterpPrefetch * kInterpThreads; i < e; i += kInterpThreads)
-        interp_point<S, WMAX, EXACT>(rec[i], tl, THP, x0, y0, w, beta, kp, v);
 }
 
 GridArgs grid_args(const nuasm_plan_s* P) {
@@ -411,7 +422,7 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     cudaError_t e = set_smem(spread_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
     spread_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
-        static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.wpt,
+        static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.wpt, P->d.tile_order,
         static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg(P));
     return cudaGetLastError();
 }
@@ -425,7 +436,7 @@ cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
     cudaError_t e = set_smem(interp_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
     interp_kernel<S, WMAX, EXACT><<<P->g.ntiles, kInterpThreads, sm, st>>>(
-        static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.tile_home,
+        static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.tile_home, P->d.tile_order,
         static_cast<const V*>(P->d.win), static_cast<V*>(v), a, taps_arg(P));
     return cudaGetLastError();
 }
@@ -459,6 +470,25 @@ template <bool SPREAD> cudaError_t gridding(const nuasm_plan_s* P, const void* i
 static nuasm_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return NUASM_OK;
     return e == cudaErrorMemoryAllocation ? NUASM_ENOMEM : NUASM_ECUDA;
+}
+
+// Tiles in decreasing record count (ties by index): the launch order of the
+// one-CTA-per-tile kernels, so the heaviest tiles start first and the last
+// wave holds the lightest.
+cudaError_t make_tile_order(nuasm_plan_s* P, cudaStream_t st) {
+    const int nt = P->g.ntiles;
+    std::vector<int> off(size_t(nt) + 1), order(nt);
+    cudaError_t e = cudaMemcpyAsync(off.data(), P->d.tile_off, sizeof(int) * (size_t(nt) + 1),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    if ((e = cudaMalloc(&P->d.tile_order, sizeof(int) * size_t(nt))) != cudaSuccess) return e;
+    P->device_bytes += int64_t(sizeof(int)) * nt;
+    e = cudaMemcpyAsync(P->d.tile_order, order.data(), sizeof(int) * size_t(nt), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);   // the host vector goes out of scope
 }
 
 nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, const double* w, cudaStream_t st) {
@@ -495,6 +525,7 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
         return NUASM_ERANGE;
     }
     P->nrec = total;
+    if ((e = make_tile_order(P, st)) != cudaSuccess) return fail(e);
     const size_t rsz = P->f64 ? sizeof(RecD) : sizeof(RecF);
     if ((e = cudaMalloc(&P->d.rec, rsz * size_t(total > 0 ? total : 1))) != cudaSuccess) return fail(e);
     P->device_bytes += int64_t(rsz) * (total > 0 ? total : 1);

@@ -51,6 +51,7 @@ struct PlanDevice {
     double* wpt = nullptr;      // optional per-point weights, in point order
     int* tile_off = nullptr;    // ntiles + 1 offsets into rec
     int* tile_home = nullptr;   // home-record count per tile
+    int* tile_order = nullptr;  // launch order of the tiles (heaviest first); null = index order
     void* win = nullptr;        // W x Wp fine-grid window
     void* bufA = nullptr;       // N' x Wp
     void* bufB = nullptr;       // N' x N
