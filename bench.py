@@ -135,22 +135,45 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline bookkeeping
-def stage_bytes(info: dict, m: int) -> dict:
-    """Algorithmic HBM bytes per launch of each type-2 stage (complex64 = 8 B):
-    each input read once, each output written once, records 16 B per point."""
+def stage_bytes(info: dict, m: int, type_: int = 2, eb: int = 8) -> dict:
+    """Algorithmic HBM bytes per launch of each stage (eb = 8 for complex64,
+    16 for complex128): each input read once, each output written once,
+    records 16 B (24 B in FP64) per record."""
     n, np_, W = info["n"], info["n_pad"], info["window"]
+    rb = 16 if eb == 8 else 24
+    if type_ == 1:
+        return {
+            "spread": (rb + eb) * info["records"] + eb * W * W,
+            "col_fwd_fold": eb * (2 * W * W + np_ * W),
+            "row_t1": eb * (np_ * W + np_ * n),
+            "col_inv": eb * (np_ * n + n * n),
+        }
     return {
-        "col_fwd": 8 * (n * n + np_ * n),
-        "row_t2": 8 * (np_ * n + np_ * W),
-        "col_inv_fold": 8 * (np_ * W + W * W),
-        "interp": 8 * W * W + 16 * m + 8 * m,
+        "col_fwd": eb * (n * n + np_ * n),
+        "row_t2": eb * (np_ * n + np_ * W),
+        "col_inv_fold": eb * (np_ * W + W * W),
+        "interp": eb * W * W + (rb + eb) * m,
     }
 
 
-KERNEL_OF_STAGE = {"col_fwd": "col_kernel<float2, 11, 2>", "row_t2": "row_t2_kernel<float2, 11>",
-                   "col_inv_fold": "col_tma_kernel<11, 3>", "interp": "interp_kernel<float, 7, true>"}
+def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
+    """Name of the kernel a stage launches for this geometry (as ncu lists it)."""
+    lognp = int(np.log2(info["n_pad"]))
+    v, s = ("double2", "double") if f64 else ("float2", "float")
+    w = info["kernel_width"]
+    tap = f"{s}, {8 if w <= 8 else 16}, false" if f64 else (f"float, {w}, true" if 4 <= w <= 8 else "float, 16, false")
+    tma = not f64 and info["n_pad"] >= 512
+    return {"col_fwd": f"col_kernel<{v}, {lognp}, 2>", "row_t2": f"row_t2_kernel<{v}, {lognp}>",
+            "col_inv_fold": f"col_tma_kernel<{lognp}, 3>" if tma else f"col_kernel<{v}, {lognp}, 3>",
+            "interp": f"interp_kernel<{tap}>", "spread": f"spread_kernel<{tap}>",
+            "col_fwd_fold": f"col_tma_kernel<{lognp}, 0>" if tma else f"col_kernel<{v}, {lognp}, 0>",
+            "row_t1": f"row_t1_kernel<{v}, {lognp}>", "col_inv": f"col_kernel<{v}, {lognp}, 1>"}[stage]
+
+
 STAGE_SOURCES = {"col_fwd": ["passes.cuh", "fft_engine.cuh"], "row_t2": ["passes.cuh", "fft_engine.cuh"],
-                 "col_inv_fold": ["passes.cuh", "fft_engine.cuh", "tma.cuh"], "interp": ["gridding.cu"]}
+                 "col_inv_fold": ["passes.cuh", "fft_engine.cuh", "tma.cuh"], "interp": ["gridding.cu"],
+                 "spread": ["gridding.cu"], "col_fwd_fold": ["passes.cuh", "fft_engine.cuh", "tma.cuh"],
+                 "row_t1": ["passes.cuh", "fft_engine.cuh"], "col_inv": ["passes.cuh", "fft_engine.cuh"]}
 
 
 def source_hash(stage: str) -> str:
@@ -163,7 +186,7 @@ def source_hash(stage: str) -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(stage: str):
+def measured_traffic(stage: str, workload: str = "nuasm2"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -172,7 +195,7 @@ def measured_traffic(stage: str):
             t = json.load(fh)
     except Exception:
         return None
-    rec = t.get(stage)
+    rec = t.get(stage if workload == "nuasm2" else f"{workload}:{stage}")
     if not rec or rec.get("source_hash") != source_hash(stage):
         return None
     return rec.get("dram_bytes_per_launch")
@@ -244,8 +267,60 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
+SINGLE = {
+    # key: (generator, precision, workload label)
+    "nuasm2": (lambda W: W.nuasm2_graded(seed=1002, n=1024, pitch=8e-6), "f32", WORKLOAD),
+    "c1": (lambda W: W.nuasm1_small(1001), "f64", "nuasm1_n64_m4864_dense_core_lambda633nm_z5cm"),
+    "c3t1": (lambda W: W.fresnel_clustered(1003, type_=1), "f32", "nufre1_n2048_m4194304_clusters_lambda633nm_z1m"),
+    "c3t2": (lambda W: W.fresnel_clustered(1003, type_=2), "f32", "nufre2_n2048_m4194304_clusters_lambda633nm_z1m"),
+    "c3t1f64": (lambda W: W.fresnel_clustered(1003, type_=1), "f64",
+                "nufre1_n2048_m4194304_clusters_lambda633nm_z1m"),
+    "c3t2f64": (lambda W: W.fresnel_clustered(1003, type_=2), "f64",
+                "nufre2_n2048_m4194304_clusters_lambda633nm_z1m"),
+}
+
+
+def oracle_sample_type1(wl, n_points: int, rng_seed: int = 5):
+    """Time the FP64 oracle's direct NUFFT_1 (every mode) for a sample of the
+    points; the cost is linear in the point count."""
+    import oracle as O
+    rng = np.random.default_rng(rng_seed)
+    idx = np.sort(rng.choice(wl.m, n_points, replace=False))
+    c = np.asarray(wl.values).reshape(-1)[idx].astype(np.complex128)
+    t0 = time.perf_counter()
+    O.nudft_type1(wl.x[idx] / wl.pitch, wl.y[idx] / wl.pitch, c, 2 * wl.n)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_single(wl, prec: str):
+    """The oracle on a bounded sample of a single-solve workload (see the
+    `sample` string of the returned record)."""
+    import oracle as O
+    if wl.type == 2 and wl.kind == "asm" and wl.n <= 1024:
+        return cpu_baseline(wl)
+    if wl.type == 2:
+        rng = np.random.default_rng(5)
+        n_pad = 2 * wl.n
+        a = rng.normal(size=(n_pad, n_pad)) + 1j * rng.normal(size=(n_pad, n_pad))
+        idx = np.sort(rng.choice(wl.m, 256, replace=False))
+        t0 = time.perf_counter()
+        O.nudft_type2(a, wl.x[idx] / wl.pitch, wl.y[idx] / wl.pitch, n_pad)
+        t = (time.perf_counter() - t0) * wl.m / 256
+        return ({"value": wl.m / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                 "sample": f"FP64 direct NUFFT_2 at 256 of {wl.m} points, extrapolated (the spectrum's "
+                           f"dense-DFT cost at N' = {n_pad} is left out, so this overstates the oracle)"},
+                None, None)
+    n_pts = wl.m if wl.m <= 8192 else 256
+    t = oracle_sample_type1(wl, n_pts) * wl.m / n_pts
+    what = "every point" if n_pts == wl.m else f"{n_pts} of {wl.m} points, extrapolated"
+    return ({"value": wl.m / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+             "sample": f"FP64 direct NUFFT_1 over all {(2 * wl.n) ** 2} modes for {what} (the inverse DFT "
+                       "to the plane is left out, so this overstates the oracle)"}, None, None)
+
+
 def run_ours(args):
     import torch
+    from paper_1308_6644_gb300 import workloads as WL
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -258,8 +333,11 @@ def run_ours(args):
     _build.build()
     import paper_1308_6644_gb300 as P
 
-    wl = _workload()
-    params = P.make_params(wl.n, wl.pitch, wl.lam, wl.z, ox=wl.ox, oy=wl.oy, kind="asm", prec="f32")
+    make, prec, label = SINGLE[args.workload]
+    wl = make(WL)
+    f64 = prec == "f64"
+    cdt, tdt, eb = (np.complex128, torch.complex128, 16) if f64 else (np.complex64, torch.complex64, 8)
+    params = P.make_params(wl.n, wl.pitch, wl.lam, wl.z, ox=wl.ox, oy=wl.oy, kind=wl.kind, prec=prec)
     stream = torch.cuda.current_stream(dev)
     x = torch.from_numpy(wl.x).to(dev)
     y = torch.from_numpy(wl.y).to(dev)
@@ -267,12 +345,18 @@ def run_ours(args):
     plan = P.nuasm_plan(params, x, y, stream=stream)
     plan_s = time.perf_counter() - t_plan0
     info = plan.info()
-    u1 = torch.from_numpy(wl.values.astype(np.complex64).reshape(-1)).to(dev)
-    v = torch.empty(wl.m, dtype=torch.complex64, device=dev)
+    n_out = wl.n * wl.n if wl.type == 1 else wl.m
+    inp = torch.from_numpy(np.ascontiguousarray(np.asarray(wl.values).astype(cdt).reshape(-1))).to(dev)
+    out = torch.empty(n_out, dtype=tdt, device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    if wl.kind == "asm":
+        execute = P.nuasm1_execute if wl.type == 1 else P.nuasm2_execute
+    else:
+        def execute(pl, i, o, stream=None):
+            return P.nufresnel_execute(pl, wl.type, i, o, stream=stream)
 
     def solve():
-        P.nuasm2_execute(plan, u1, v, stream=stream)
+        execute(plan, inp, out, stream=stream)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -301,10 +385,10 @@ def run_ours(args):
     value = points / (total_ms * 1e-3)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
-    hu1 = torch.from_numpy(wl.values.astype(np.complex64).reshape(-1)).pin_memory()
-    hv = torch.empty(wl.m, dtype=torch.complex64).pin_memory()
+    h_in = inp.cpu().pin_memory()
+    h_out = torch.empty(n_out, dtype=tdt).pin_memory()
     for _ in range(2):
-        P.nuasm2_execute(plan, hu1, hv, stream=stream)
+        execute(plan, h_in, h_out, stream=stream)
     torch.cuda.synchronize()
     e2e_ms = []
     aux_steps = min(args.steps, 200)
@@ -312,7 +396,7 @@ def run_ours(args):
         flush.zero_()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        P.nuasm2_execute(plan, hu1, hv, stream=stream)
+        execute(plan, h_in, h_out, stream=stream)
         e.record(stream)
         e.synchronize()
         e2e_ms.append(s.elapsed_time(e))
@@ -327,7 +411,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     prof = P.nuasm_profile_read(plan)
     P.nuasm_profile_enable(plan, False)
-    sbytes = stage_bytes(info, wl.m)
+    sbytes = stage_bytes(info, wl.m, wl.type, eb)
     stages = {}
     for name, b in sbytes.items():
         ms, cnt = prof[name]
@@ -338,7 +422,7 @@ def run_ours(args):
     peak, peak_kind = hbm_peak()
     ach = stages[dom]["gbs"]
     roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": measured_traffic(dom), "kernel": KERNEL_OF_STAGE[dom],
+                "traffic": measured_traffic(dom, args.workload), "kernel": kernel_of_stage(dom, info, f64),
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "stages": {k: {"ms": round(s["ms"], 5), "GB/s": round(s["gbs"], 1),
@@ -346,22 +430,29 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": wl.n, "n_pad": info["n_pad"], "points": wl.m,
-                       "kernel_width": info["kernel_width"], "precision": "complex64 + FP64-derived phase",
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": label, "n": wl.n, "n_pad": info["n_pad"], "points": wl.m,
+                       "kernel_width": info["kernel_width"],
+                       "precision": "complex128" if f64 else "complex64 + FP64-derived phase",
                        "l2": "flushed (256 MB write) before every step", "plan_s": round(plan_s, 3),
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hu1.numel() * 8),
-                    "d2h_bytes_per_step": int(hv.numel() * 8)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h_in.numel() * eb),
+                    "d2h_bytes_per_step": int(h_out.numel() * eb)},
             "gpu_launches": 4 * args.steps,
             "roofline": roofline,
             "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rec, idx, ref = cpu_baseline(wl)
-        got = v.cpu().numpy()[idx]
+        rec, idx, ref = cpu_baseline_single(wl, prec)
         line["cpu_baseline"] = rec
-        line["rel_l2_vs_fp64_sample"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        if ref is not None:
+            got = out.cpu().numpy()[idx]
+            line["rel_l2_vs_fp64_sample"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        elif args.workload == "c1":
+            import oracle as O
+            want = O.nuasm1(wl.x, wl.y, np.asarray(wl.values).astype(cdt).astype(np.complex128),
+                            dict(n=wl.n, pitch=wl.pitch, lam=wl.lam, z=wl.z)).reshape(-1)
+            line["rel_l2_vs_fp64"] = float(O.rel_l2(out.cpu().numpy(), want))
     plan.destroy()
     if rank == 0:
         print(json.dumps(line))
@@ -611,9 +702,10 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["nuasm2", "batch64", "serve"], default="nuasm2",
-                    help="nuasm2: the single-solve benchmark (default); batch64: 64 mixed planes in one "
-                         "graph; serve: Poisson-arrival serving loop")
+    ap.add_argument("--workload", choices=list(SINGLE) + ["batch64", "serve"], default="nuasm2",
+                    help="nuasm2: the NU-ASM_2 single-solve benchmark (default); c1: NU-ASM_1 64^2 FP64; "
+                         "c3t1/c3t2(f64): NU-FRE types 1/2 at N = 2048, 4M clustered points; batch64: 64 mixed "
+                         "planes in one graph; serve: Poisson-arrival serving loop")
     ap.add_argument("--planes", type=int, default=64)
     ap.add_argument("--lanes", type=int, default=8)
     ap.add_argument("--requests", type=int, default=1000)
