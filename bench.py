@@ -494,10 +494,17 @@ def run_batch(args):
     import paper_1308_6644_gb300 as P
     stream = torch.cuda.current_stream(dev)
     planes, items, total_m, in_bytes, out_bytes = [], [], 0, 0, 0
+    tiles = {}
     for i in range(args.planes):
         wl = WL.mixed_plane(1004, i)
         params = P.make_params(wl.n, wl.pitch, wl.lam, wl.z, kind="asm", prec="f32")
-        plan = P.nuasm_plan(params, torch.from_numpy(wl.x).to(dev), torch.from_numpy(wl.y).to(dev), stream=stream)
+        xd, yd = torch.from_numpy(wl.x).to(dev), torch.from_numpy(wl.y).to(dev)
+        if args.autotune:
+            params.tile, _ = P.nuasm_autotune_tile(params, xd, yd, wl.type, stream=stream)
+        plan = P.nuasm_plan(params, xd, yd, stream=stream)
+        t_used = plan.info()["tile"]
+        tiles[t_used] = tiles.get(t_used, 0) + 1
+        del xd, yd
         inp = torch.from_numpy(np.ascontiguousarray(wl.values.astype(np.complex64).reshape(-1))).to(dev)
         out = torch.empty(wl.n * wl.n if wl.type == 1 else wl.m, dtype=torch.complex64, device=dev)
         planes.append((plan, wl.type, inp, out))
@@ -555,6 +562,8 @@ def run_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"mixed{args.planes}_planes_n256-2048_types1+2", "planes": args.planes,
                        "points_per_step": total_m, "lanes": lanes, "graph_kernels": kernels,
+                       "tiles": ("autotuned per plane: " if args.autotune else "library rule: ") +
+                       ", ".join(f"T={k} x{v}" for k, v in sorted(tiles.items())),
                        "plain_points_per_s": plain_value, "batched_over_plain": value / plain_value,
                        "plain": "one execute call per plane, back to back on one stream",
                        "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{ws}"},
@@ -712,6 +721,8 @@ def main(argv=None):
     ap.add_argument("--sets", type=int, default=12)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--plain-requests", type=int, default=60)
+    ap.add_argument("--autotune", action="store_true",
+                    help="batch64: time every tile side per plane (nuasm_autotune_tile) instead of the library's rule")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -94,6 +94,11 @@ typedef struct {
     int32_t prec;       /* nuasm_prec */
     double  tol;        /* requested NUFFT relative tolerance; 0 selects 1e-6 (F32) or 1e-12 (F64) */
     int32_t kernel;     /* nuasm_kernel: spreading kernel of the NUFFT gridding */
+    int32_t tile;       /* side of the gridding tiles (bins) in fine-grid cells: 16, 32 or 64;
+                           0 = the library's rule (the largest side giving at least 608
+                           tiles over the fine-grid window, else 16).  Results agree to
+                           rounding for every choice; nuasm_autotune_tile measures which
+                           is fastest. */
 } nuasm_params_t;
 
 /* Geometry of a plan (read-only report). */
@@ -217,6 +222,17 @@ nuasm_status nufresnel3_execute(nuasm_plan_t src, nuasm_plan_t dst, const void* 
 nuasm_status nuasm_rs_direct(const nuasm_params_t* p, int64_t m1, const double* x1, const double* y1,
                              const void* c, const double* area, int64_t m2, const double* x2, const double* y2,
                              void* out, void* stream);
+
+/*
+ * nuasm_autotune_tile -- time one solve of `type` (1 or 2) on the given
+ * points for each tile side (16, 32, 64) and return the fastest in *tile
+ * (and its time in *ms, may be NULL).  The paper has no counterpart.  p->tile
+ * is ignored; x, y (device, m entries) as for nuasm_plan.  Builds and
+ * destroys temporary plans and zero-filled input/output arrays; synchronises
+ * `stream`.  Errors as nuasm_plan.
+ */
+nuasm_status nuasm_autotune_tile(const nuasm_params_t* p, int64_t m, const double* x, const double* y, int32_t type,
+                                 void* stream, int32_t* tile, double* ms);
 
 /* Release every resource of the plan (synchronises the plan's device work). NULL is a no-op. */
 nuasm_status nuasm_destroy(nuasm_plan_t plan);

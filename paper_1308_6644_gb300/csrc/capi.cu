@@ -29,7 +29,7 @@ bool device_accessible(const void* p) {
 bool same_problem(const nuasm_params_t& a, const nuasm_params_t& b) {
     bool same = a.n == b.n && a.n_pad == b.n_pad && a.pitch == b.pitch && a.lambda == b.lambda && a.z == b.z &&
                 a.ox == b.ox && a.oy == b.oy && a.band_auto == b.band_auto && a.kind == b.kind &&
-                a.prec == b.prec && a.tol == b.tol && a.kernel == b.kernel;
+                a.prec == b.prec && a.tol == b.tol && a.kernel == b.kernel && a.tile == b.tile;
     if (same && !a.band_auto)
         same = a.c_m == b.c_m && a.c_n == b.c_n && a.w_m == b.w_m && a.w_n == b.w_n;
     return same;
@@ -454,6 +454,61 @@ nuasm_status nufresnel3_execute(nuasm_plan_t src, nuasm_plan_t dst, const void* 
     if (!src || !dst) return NUASM_EINVAL;
     if (src->p.kind != NUASM_KIND_FRESNEL) return NUASM_EINVAL;
     return exec_type3(src, dst, c, v, static_cast<cudaStream_t>(stream));
+}
+
+nuasm_status nuasm_autotune_tile(const nuasm_params_t* p, int64_t m, const double* x, const double* y, int32_t type,
+                                 void* stream, int32_t* tile, double* ms) {
+    if (!p || !tile || (type != 1 && type != 2)) return NUASM_EINVAL;
+    nuasm_params_t rp;
+    nuasm_status s = validate(*p, m, &rp);
+    if (s != NUASM_OK) return s;
+    if (m > 0 && (!x || !y || !device_accessible(x) || !device_accessible(y))) return NUASM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t eb = rp.prec == NUASM_PREC_F64 ? 16 : 8;
+    const size_t nn = size_t(rp.n) * rp.n;
+    void* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, eb * (nn + size_t(m > 0 ? m : 1)));
+    if (e != cudaSuccess) return cuda_status(e);
+    char* in = static_cast<char*>(buf);
+    char* out = in + eb * (type == 1 ? size_t(m) : nn);
+    e = cudaMemsetAsync(buf, 0, eb * (nn + size_t(m > 0 ? m : 1)), st);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    int best = 0;
+    float best_ms = 0.f;
+    for (int cand : {16, 32, 64}) {
+        if (e != cudaSuccess) break;
+        nuasm_params_t q = rp;
+        q.tile = cand;
+        nuasm_plan_s* P = nullptr;
+        s = plan_create(&P, &q, m, x, y, nullptr, st, true);
+        if (s != NUASM_OK) break;
+        float total = 0.f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // first run untimed
+            e = cudaEventRecord(t0, st);
+            if (e == cudaSuccess) e = type == 1 ? chain_type1(P, in, out, st) : chain_type2(P, in, out, st);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, t0, t1);
+            if (rep > 0) total += t;
+        }
+        plan_release(P);
+        if (e == cudaSuccess && (best == 0 || total / 3 < best_ms)) {
+            best = cand;
+            best_ms = total / 3;
+        }
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (s != NUASM_OK) return s;
+    if (e != cudaSuccess) return cuda_status(e);
+    *tile = best;
+    if (ms) *ms = best_ms;
+    return NUASM_OK;
 }
 
 nuasm_status nuasm_destroy(nuasm_plan_t plan) {

@@ -261,6 +261,7 @@ nuasm_status validate(const nuasm_params_t& p0, int64_t m, nuasm_params_t* out) 
         double beta;
         if (!kernel_shape(p.tol, p.prec, p.kernel, &w, &beta)) return NUASM_EUNSUPPORTED;
     }
+    if (p.tile != 0 && p.tile != 16 && p.tile != 32 && p.tile != 64) return NUASM_EINVAL;
     if (p.n_pad != 0 && (p.n_pad < 2 * p.n || !is_pow2(p.n_pad))) return NUASM_EINVAL;
     // what this build implements: power-of-two planes, N' <= 8192 (F32) / 4096 (F64)
     if (!is_pow2(p.n) || p.n < 16) return NUASM_EUNSUPPORTED;
@@ -298,7 +299,19 @@ Geometry make_geometry(const nuasm_params_t& p) {
     g.W = 2 * p.n + 2 * g.h;
     g.Wp = (g.W + 31) & ~31;
     g.Lo = p.n_pad - p.n - g.h;
-    g.T = (p.prec == NUASM_PREC_F64 || g.W <= 512) ? 32 : 64;
+    // default tile: the largest side that still gives at least 608 tiles
+    // (four CTAs per SM on 152 SMs), else the smallest
+    g.T = p.tile;
+    if (!g.T) {
+        g.T = 16;
+        for (int t : {64, 32}) {
+            const int per_axis = (g.W + t - 1) / t;
+            if (per_axis * per_axis >= 608) {
+                g.T = t;
+                break;
+            }
+        }
+    }
     g.ntx = (g.W + g.T - 1) / g.T;
     g.ntiles = g.ntx * g.ntx;
     band_range(p, g.band);

@@ -44,16 +44,16 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 // Identity of a resident point set: the caller's key plus everything the bins depend on.
 struct SetKey {
     uint64_t id;
-    int n, n_pad, prec, kernel;
+    int n, n_pad, prec, kernel, tile;
     double pitch, tol;
     bool operator==(const SetKey& o) const {
         return id == o.id && n == o.n && n_pad == o.n_pad && prec == o.prec && kernel == o.kernel &&
-               pitch == o.pitch && tol == o.tol;
+               tile == o.tile && pitch == o.pitch && tol == o.tol;
     }
 };
 
 SetKey key_of(uint64_t id, const nuasm_params_t& rp) {
-    return SetKey{id, rp.n, rp.n_pad, rp.prec, rp.kernel, rp.pitch, rp.tol};
+    return SetKey{id, rp.n, rp.n_pad, rp.prec, rp.kernel, rp.tile, rp.pitch, rp.tol};
 }
 
 struct PointSet {

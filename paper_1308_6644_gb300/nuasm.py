@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
                 ("oy", ctypes.c_double), ("band_auto", ctypes.c_int32), ("c_m", ctypes.c_double),
                 ("c_n", ctypes.c_double), ("w_m", ctypes.c_double), ("w_n", ctypes.c_double),
                 ("kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("kernel", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("tile", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -109,6 +109,9 @@ _SIGS = {
     "nuasm_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "nuasm2_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int64, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "nuasm_autotune_tile": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_double)]),
     "nuasm_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(BatchItem),
                                           ctypes.c_int32, ctypes.c_int32]),
     "nuasm_batch_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -197,9 +200,10 @@ KERNEL_ES, KERNEL_GAUSSIAN = 0, 1
 
 
 def make_params(n, pitch, lam, z, ox=0.0, oy=0.0, kind="asm", prec="f32", tol=0.0, n_pad=0,
-                band=None, kernel="es") -> Params:
+                band=None, kernel="es", tile=0) -> Params:
     """nuasm_params_t from keyword values; band = (c_m, c_n, w_m, w_n) or None
-    (auto rule); kernel = "es" (exponential of semicircle) or "gaussian"."""
+    (auto rule); kernel = "es" (exponential of semicircle) or "gaussian";
+    tile = gridding tile side (0: the library's rule)."""
     p = Params()
     p.n, p.n_pad, p.pitch, p.lambda_, p.z, p.ox, p.oy = int(n), int(n_pad), pitch, lam, z, ox, oy
     if band is None:
@@ -211,6 +215,7 @@ def make_params(n, pitch, lam, z, ox=0.0, oy=0.0, kind="asm", prec="f32", tol=0.
     p.prec = PREC_F64 if prec in ("f64", PREC_F64) else PREC_F32_F64PHASE
     p.tol = float(tol)
     p.kernel = KERNEL_GAUSSIAN if kernel in ("gaussian", KERNEL_GAUSSIAN) else KERNEL_ES
+    p.tile = int(tile)
     return p
 
 
@@ -392,6 +397,17 @@ def nuasm2_solve_noalloc(params: Params, x, y, u1, v, stream=None):
     _check(lib().nuasm2_solve_noalloc(ctypes.byref(params), m, _ptr(x), _ptr(y), _ptr(u1), _ptr(v),
                                       _stream(stream)), "nuasm2_solve_noalloc")
     return v
+
+
+def nuasm_autotune_tile(params: Params, x, y, type_: int, stream=None) -> tuple:
+    """(fastest tile side, its solve time in ms) for these device points."""
+    m = _numel(x)
+    _expect(x, m, "float64", "x")
+    _expect(y, m, "float64", "y")
+    t, ms = ctypes.c_int32(), ctypes.c_double()
+    _check(lib().nuasm_autotune_tile(ctypes.byref(params), m, _ptr(x), _ptr(y), int(type_), _stream(stream),
+                                     ctypes.byref(t), ctypes.byref(ms)), "nuasm_autotune_tile")
+    return int(t.value), float(ms.value)
 
 
 # ---------------------------------------------------------------- batches

@@ -180,3 +180,11 @@ def test_batch_and_server_reject_bad_arguments_before_device_work(P):
     assert lib.nuasm_server_submit(None, ctypes.byref(req), ctypes.byref(t)) == 1
     assert lib.nuasm_server_wait(None, 1, 0.0, ctypes.byref(P.nuasm.RequestResult())) == 1
     assert lib.nuasm_server_destroy(None) == 0
+
+
+@pytest.mark.parametrize("tile", [8, 48, 128, -16])
+def test_plan_rejects_unsupported_tiles(P, tile):
+    x = np.zeros(2)
+    with pytest.raises(P.NuasmError) as ei:
+        P.nuasm_plan(P.make_params(32, 10e-6, 633e-9, 0.01, tile=tile), x, x)
+    assert ei.value.code == 1

@@ -30,11 +30,11 @@ def _t(a, dev="cuda"):
 
 
 def run_gpu(P, kind, type_, prec, n, pitch, lam, z, x, y, values, ox=0.0, oy=0.0, w=None, n_pad=0,
-            band=None, tol=0.0, host=False, kernel="es"):
+            band=None, tol=0.0, host=False, kernel="es", tile=0):
     """One plan + one execute; returns the output as a numpy array."""
     import torch
     params = P.make_params(n, pitch, lam, z, ox=ox, oy=oy, kind=kind, prec=prec, tol=tol,
-                           n_pad=n_pad, band=band, kernel=kernel)
+                           n_pad=n_pad, band=band, kernel=kernel, tile=tile)
     cdt = CDT[prec]
     tdt = torch.complex64 if prec == "f32" else torch.complex128
     if host:
@@ -226,3 +226,26 @@ def test_gaussian_kernel_parity(P, kind, type_, prec, tol, bound):
     got = run_gpu(P, kind, type_, prec, 64, x=x, y=y, values=vals, tol=tol, kernel="gaussian", **kw)
     ref = run_oracle(kind, type_, 64, x=x, y=y, values=vals, prec=prec, **kw)
     assert O.rel_l2(got, ref) < bound
+
+
+# ---------------------------------------------------------------- gridding tile sides
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_tile_sides_agree(P, prec):
+    """Type 2 is the same gather whatever the tile side (bit for bit); type 1
+    differs only by the accumulation order / fixed-point quantum."""
+    kw = dict(pitch=10e-6, lam=633e-9, z=0.03, ox=25e-6)
+    x, y, u1 = random_case(61, 128, 5000, type_=2)
+    outs2 = [run_gpu(P, "asm", 2, prec, 128, x=x, y=y, values=u1, tile=t, **kw) for t in (16, 32, 64)]
+    assert np.array_equal(outs2[0], outs2[1]) and np.array_equal(outs2[0], outs2[2])
+    x, y, c = random_case(62, 128, 5000, type_=1)
+    outs1 = [run_gpu(P, "asm", 1, prec, 128, x=x, y=y, values=c, tile=t, **kw) for t in (16, 32, 64)]
+    ref = run_oracle("asm", 1, 128, x=x, y=y, values=c, prec=prec, **kw)
+    for o in outs1:
+        assert O.rel_l2(o, ref) < TOL[prec]
+
+
+def test_autotune_tile_picks_a_supported_side(P):
+    w = WL.nuasm2_graded(n=256)
+    params = P.make_params(w.n, w.pitch, w.lam, w.z, ox=w.ox)
+    tile, ms = P.nuasm_autotune_tile(params, _t(w.x), _t(w.y), 2)
+    assert tile in (16, 32, 64) and ms > 0
