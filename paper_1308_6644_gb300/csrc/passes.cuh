@@ -412,17 +412,30 @@ template <int LOGNP, int MODE> struct TmaColCfg {
     static constexpr int NP = Base::NP;
     static constexpr int C = Base::C < NUASM_TMA_C ? Base::C : NUASM_TMA_C;
     static constexpr int LOGC = Log2<C>::v;
+    // up to N' = 2048 the folded modes transform both halves of every column
+    // at once (sequence cs = 2 c + half, 2C sequences per strip, twice the
+    // warps); beyond, 1024 threads would spill, so the halves run in turn
+    static constexpr bool FOLDED = MODE == COL_FWD_FOLD || MODE == COL_INV_FOLD;
+    static constexpr bool MERGED = FOLDED && LOGNP <= 11;
+    static constexpr int SEQ = MERGED ? 2 * C : C;
+    static constexpr int LOGSEQ = Log2<SEQ>::v;
     static constexpr int E = Base::E;
-    static constexpr int P = (NP * C) / E;
+    static constexpr int P = (NP * SEQ) / E;
     static constexpr int BOXR = NP < 256 ? NP : 256;
     static constexpr int RAW_ROWS = MODE == COL_FWD_FOLD ? NP + BOXR : NP;
     static constexpr size_t RAW_BYTES = size_t(RAW_ROWS) * C * sizeof(float2);
-    static constexpr size_t WORK_BYTES = ((size_t(spad_size<float2>(NP * C)) * sizeof(float2)) + 127) & ~size_t(127);
-    static size_t smem() { return 128 + RAW_BYTES + WORK_BYTES + 16; }
+    static constexpr size_t WORK_BYTES = ((size_t(spad_size<float2>(NP * SEQ)) * sizeof(float2)) + 127) & ~size_t(127);
+    static constexpr size_t SMEM = 128 + RAW_BYTES + WORK_BYTES + 16;
+    static size_t smem() { return SMEM; }
+    // CTAs per SM that shared memory allows (228 KB per SM, 1 KB reserved per
+    // CTA): registers are capped only as far as that occupancy needs
+    static constexpr int BY_SMEM = int((228u * 1024u) / (SMEM + 1024u));
+    static constexpr int BY_REGS = 65536 / (P * 64);
+    static constexpr int MINB = BY_SMEM < 1 ? 1 : (BY_SMEM < BY_REGS ? BY_SMEM : (BY_REGS < 1 ? 1 : BY_REGS));
 };
 
 template <int LOGNP, int MODE>
-__global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, 65536 / (TmaColCfg<LOGNP, MODE>::P * 64))
+__global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MODE>::MINB)
     col_tma_kernel(const __grid_constant__ CUtensorMap map, float2* __restrict__ dst, const float2* __restrict__ tw,
                    ColArgs a, int nstrips, int nboxes, int* __restrict__ err) {
     using Cf = TmaColCfg<LOGNP, MODE>;
@@ -458,42 +471,63 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, 65536 / (TmaColCfg<
         auto prefetch = [&] {
             if (tid == 0 && next < nstrips) issue(next);
         };
-        auto nothing = [] {};
         if constexpr (MODE == COL_FWD_FOLD) {
-            // raw: window rows [0, NP + BOXR) of C columns (zero beyond the window)
+            // raw: window rows [0, NP + BOXR) of C columns (zero beyond the window);
+            // half 0 transforms x(p) + x(p + N'), half 1 (x(p) - x(p + N')) w^p
+            auto fold = [&](int p, int c, int sgn) -> float2 {
+                // rows p + N' < W lie within the first BOXR rows past N' (W - N' = 2h <= 16)
+                const float2 u = raw[p * C + c], t = p < BOXR ? raw[(p + NP) * C + c] : zero;
+                const float sg = sgn ? -1.f : 1.f;
+                const float2 v = make_float2(fmaf(sg, t.x, u.x), fmaf(sg, t.y, u.y));
+                return sgn ? cmul(v, __ldg(&tw[p])) : v;
+            };
+            auto put = [&](int pk, int c, int sgn, float2 v) {
+                const int col = col0 + c;
+                const int pb = 2 * pk + sgn;
+                const int r = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
+                if (r >= 0 && col < W) dst[r * Wp + col] = v;
+            };
+            if constexpr (Cf::MERGED) {
+                block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGSEQ, false>(
+                    S, tw, [&](int p, int cs) { return fold(p, cs >> 1, cs & 1); },
+                    [&](int pk, int cs, float2 v) { put(pk, cs >> 1, cs & 1, v); }, prefetch);
+            } else {
+                auto nothing = [] {};
 #pragma unroll 1
-            for (int sgn = 0; sgn < 2; ++sgn) {
-                auto load = [&](int p, int c) -> float2 {
-                    // rows p + N' < W lie within the first BOXR rows past N' (W - N' = 2h <= 16)
-                    const float2 u = raw[p * C + c], t = p < BOXR ? raw[(p + NP) * C + c] : zero;
-                    return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
-                };
-                auto store = [&](int pk, int c, float2 v) {
-                    const int col = col0 + c;
-                    const int pb = 2 * pk + sgn;
-                    const int r = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
-                    if (r >= 0 && col < W) dst[r * Wp + col] = v;
-                };
-                if (sgn == 0) block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, nothing);
-                else block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, prefetch);
+                for (int sgn = 0; sgn < 2; ++sgn) {
+                    auto load = [&](int p, int c) { return fold(p, c, sgn); };
+                    auto store = [&](int pk, int c, float2 v) { put(pk, c, sgn, v); };
+                    if (sgn == 0) block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, nothing);
+                    else block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, prefetch);
+                }
             }
         } else if constexpr (MODE == COL_INV_FOLD) {
-            // raw: rows [0, N') of A, C columns (zero beyond the window's columns)
+            // raw: rows [0, N') of A, C columns (zero beyond the window's columns);
+            // half 1 is pre-twiddled for the odd outputs
+            auto get = [&](int q, int c, int sgn) -> float2 {
+                const float2 y = raw[q * C + c];
+                if (sgn == 0) return y;
+                const int pg = q < HALF ? q : q + NP;
+                return cmul(y, cconj(__ldg(&tw[pg])));
+            };
+            auto put = [&](int k, int c, int sgn, float2 v) {
+                const int col = col0 + c;
+                const int u = 2 * k + sgn;
+                if (u < W && col < W) dst[u * Wp + col] = v;
+            };
+            if constexpr (Cf::MERGED) {
+                block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGSEQ, false>(
+                    S, tw, [&](int q, int cs) { return get(q, cs >> 1, cs & 1); },
+                    [&](int k, int cs, float2 v) { put(k, cs >> 1, cs & 1, v); }, prefetch);
+            } else {
+                auto nothing = [] {};
 #pragma unroll 1
-            for (int sgn = 0; sgn < 2; ++sgn) {
-                auto load = [&](int q, int c) -> float2 {
-                    const float2 y = raw[q * C + c];
-                    if (sgn == 0) return y;
-                    const int pg = q < HALF ? q : q + NP;
-                    return cmul(y, cconj(__ldg(&tw[pg])));
-                };
-                auto store = [&](int k, int c, float2 v) {
-                    const int col = col0 + c;
-                    const int u = 2 * k + sgn;
-                    if (u < W && col < W) dst[u * Wp + col] = v;
-                };
-                if (sgn == 0) block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, nothing);
-                else block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, prefetch);
+                for (int sgn = 0; sgn < 2; ++sgn) {
+                    auto load = [&](int q, int c) { return get(q, c, sgn); };
+                    auto store = [&](int k, int c, float2 v) { put(k, c, sgn, v); };
+                    if (sgn == 0) block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, nothing);
+                    else block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, prefetch);
+                }
             }
         } else if constexpr (MODE == COL_INV) {
             block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGC, false>(
