@@ -162,12 +162,17 @@ def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
     v, s = ("double2", "double") if f64 else ("float2", "float")
     w = info["kernel_width"]
     tap = f"{s}, {8 if w <= 8 else 16}, false" if f64 else (f"float, {w}, true" if 4 <= w <= 8 else "float, 16, false")
-    tma = not f64 and info["n_pad"] >= 512
-    return {"col_fwd": f"col_kernel<{v}, {lognp}, 2>", "row_t2": f"row_t2_kernel<{v}, {lognp}>",
+    tma = not f64 and 512 <= info["n_pad"] <= 4096          # folded column passes
+    tma_wide = not f64 and info["n_pad"] == 4096              # unfolded ones too
+    spread = f"spread_fx_kernel<{w if 4 <= w <= 8 else 16}, {'true' if 4 <= w <= 8 else 'false'}>" if not f64 \
+        else f"spread_kernel<{tap}>"
+    return {"col_fwd": f"col_tma_kernel<{lognp}, 2>" if tma_wide else f"col_kernel<{v}, {lognp}, 2>",
+            "row_t2": f"row_t2_kernel<{v}, {lognp}>",
             "col_inv_fold": f"col_tma_kernel<{lognp}, 3>" if tma else f"col_kernel<{v}, {lognp}, 3>",
-            "interp": f"interp_kernel<{tap}>", "spread": f"spread_kernel<{tap}>",
+            "interp": f"interp_kernel<{tap}>", "spread": spread,
             "col_fwd_fold": f"col_tma_kernel<{lognp}, 0>" if tma else f"col_kernel<{v}, {lognp}, 0>",
-            "row_t1": f"row_t1_kernel<{v}, {lognp}>", "col_inv": f"col_kernel<{v}, {lognp}, 1>"}[stage]
+            "row_t1": f"row_t1_kernel<{v}, {lognp}>",
+            "col_inv": f"col_tma_kernel<{lognp}, 1>" if tma_wide else f"col_kernel<{v}, {lognp}, 1>"}[stage]
 
 
 STAGE_SOURCES = {"col_fwd": ["passes.cuh", "fft_engine.cuh"], "row_t2": ["passes.cuh", "fft_engine.cuh"],

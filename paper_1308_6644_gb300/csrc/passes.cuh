@@ -398,13 +398,17 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP>::P, ColCfg<V, LOGNP>::MINB)
 // from one load.  Waits are bounded: a wait that gives up sets bit 2 of the
 // plan's error word, waits once more for its own copy and the CTA returns.
 // Tuning knobs: columns per TMA strip (NUASM_TMA_C) and the column modes that
-// use the TMA pipeline (bit MODE of NUASM_TMA_MODES; by default the two folded
-// passes, whose strips are numerous enough to keep a persistent pipeline busy).
+// use the TMA pipeline (bit MODE of NUASM_TMA_MODES up to N' = 2048, of
+// NUASM_TMA_MODES_WIDE beyond; measured: at N' = 2048 the unfolded passes are
+// faster without TMA, at N' = 4096 with it).
 #ifndef NUASM_TMA_C
 #define NUASM_TMA_C 4
 #endif
 #ifndef NUASM_TMA_MODES
-#define NUASM_TMA_MODES 0x9
+#define NUASM_TMA_MODES 0x9        // N' <= 2048
+#endif
+#ifndef NUASM_TMA_MODES_WIDE
+#define NUASM_TMA_MODES_WIDE 0xF   // N' >= 4096: the unfolded passes have 1024+ strips too
 #endif
 
 template <int LOGNP, int MODE> struct TmaColCfg {
@@ -609,7 +613,8 @@ template <int LOGNP, int MODE>
 cudaError_t launch_col_tma(const nuasm_plan_s* P, const void* src, void* dst, int ncols, int src_cols,
                            int src_rows, int src_pitch, int load_rows, cudaStream_t st) {
     using Cf = TmaColCfg<LOGNP, MODE>;
-    if constexpr (Cf::C < 2 || Cf::NP < 512 || !((NUASM_TMA_MODES >> MODE) & 1)) {
+    constexpr int modes = LOGNP >= 12 ? NUASM_TMA_MODES_WIDE : NUASM_TMA_MODES;
+    if constexpr (Cf::C < 2 || Cf::NP < 512 || !((modes >> MODE) & 1)) {
         return cudaErrorNotSupported;
     } else {
         CUtensorMap map;
