@@ -300,12 +300,15 @@ __global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::ty
 // (kernel taps are at most 1), so the integers stay below 2^31; rounding
 // costs at most q_k / 2 per tap, about 1e-7 of a typical cell value.
 constexpr int kBandRows = 8, kMaxBands = 8;   // tiles of at most 64 rows
+#ifndef NUASM_SPREAD_MINB
+#define NUASM_SPREAD_MINB 1
+#endif
 #ifndef NUASM_SPREAD_FX
 #define NUASM_SPREAD_FX 1   // 0: FP32 plans spread with float atomics like FP64 plans
 #endif
 
 template <int WMAX, bool EXACT>
-__global__ void __launch_bounds__(256) spread_fx_kernel(const RecF* __restrict__ rec, const int* __restrict__ off,
+__global__ void __launch_bounds__(256, NUASM_SPREAD_MINB) spread_fx_kernel(const RecF* __restrict__ rec, const int* __restrict__ off,
                                                         const double* __restrict__ wpt, const int* __restrict__ order,
                                                         const float2* __restrict__ c, float2* __restrict__ win,
                                                         GridArgs a, const KernelPoly kp) {
@@ -401,6 +404,9 @@ __global__ void __launch_bounds__(256) spread_fx_kernel(const RecF* __restrict__
 // staging loads so that their latency overlaps the tile's; FP32 tiles are
 // staged two complex values (16 B) per load.
 constexpr int kInterpThreads = 256, kInterpPrefetch = 4;
+#ifndef NUASM_INTERP_MINB
+#define NUASM_INTERP_MINB 4   // CTAs per SM the register budget is sized for (64 registers)
+#endif
 
 template <typename S, int WMAX, bool EXACT, typename Rec, typename V>
 __device__ __forceinline__ void interp_point(const Rec& r, const V* __restrict__ tl, int THP, int x0, int y0, int w,
@@ -432,7 +438,7 @@ __device__ __forceinline__ void interp_point(const Rec& r, const V* __restrict__
 }
 
 template <typename S, int WMAX, bool EXACT>
-__global__ void __launch_bounds__(kInterpThreads) interp_kernel(const typename RecOf<S>::type* __restrict__ rec,
+__global__ void __launch_bounds__(kInterpThreads, NUASM_INTERP_MINB) interp_kernel(const typename RecOf<S>::type* __restrict__ rec,
                                                                 const int* __restrict__ off,
                                                                 const int* __restrict__ home,
                                                                 const int* __restrict__ order,

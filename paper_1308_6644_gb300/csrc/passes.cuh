@@ -43,15 +43,20 @@ namespace passes {
 
 // --------------------------------------------------------------- launch configuration
 template <typename V> struct Prec;
+#ifndef NUASM_ROW_REGS
+#define NUASM_ROW_REGS 64   // FP32 register budget per thread that sets the row passes' CTAs per SM
+#endif
 template <> struct Prec<float2> {
     static constexpr bool f64 = false;
     static constexpr int col_e = 16, col_budget = 8192;   // elements per thread / per CTA
     static constexpr int regs = 64;
+    static constexpr int row_regs = NUASM_ROW_REGS;
 };
 template <> struct Prec<double2> {
     static constexpr bool f64 = true;
     static constexpr int col_e = 8, col_budget = 4096;
     static constexpr int regs = 128;
+    static constexpr int row_regs = 128;
 };
 
 template <typename V, int LOGNP> struct RowCfg {
@@ -63,7 +68,7 @@ template <typename V, int LOGNP> struct RowCfg {
     static constexpr int EF = (!Prec<V>::f64 && LOGNP >= 13) ? 16 : 8;   // single-sequence engines
     static constexpr int EM = 16;                                         // merged engines
     static constexpr int P = (NP * ROWS) / EF;
-    static constexpr int MINB = (65536 / (P * Prec<V>::regs)) > 0 ? 65536 / (P * Prec<V>::regs) : 1;
+    static constexpr int MINB = (65536 / (P * Prec<V>::row_regs)) > 0 ? 65536 / (P * Prec<V>::row_regs) : 1;
     static constexpr int SEQ = MERGE ? 2 * ROWS : ROWS;                  // sequences in the work buffer
     static size_t smem() { return (size_t(spad_size<V>(NP * SEQ)) + size_t(NP) * ROWS) * sizeof(V); }
 };
