@@ -424,7 +424,32 @@ def run_ours(args):
         e.record(stream)
         e.synchronize()
         e2e_ms.append(s.elapsed_time(e))
-    e2e_value = wl.m / (np.mean(e2e_ms) * 1e-3)
+    e2e_serial = wl.m / (np.mean(e2e_ms) * 1e-3)
+
+    # pipelined: a second plan on a second stream and steps alternating between
+    # them, so one step's host copies overlap the other's kernels; every step
+    # still copies its input in, flushes L2 on its stream and reads its result back
+    plan2 = P.nuasm_plan(params, x, y, stream=stream)
+    s2 = torch.cuda.Stream(dev)
+    lanes = [(plan, stream, h_in, h_out),
+             (plan2, s2, inp.cpu().pin_memory(), torch.empty(n_out, dtype=tdt).pin_memory())]
+    for pl, st, hi, ho in lanes:
+        execute(pl, hi, ho, stream=st)
+    torch.cuda.synchronize()
+    t_a, t_b, t_j = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    t_a.record(stream)
+    s2.wait_event(t_a)
+    for k in range(aux_steps):
+        pl, st, hi, ho = lanes[k % 2]
+        with torch.cuda.stream(st):
+            flush.zero_()
+        execute(pl, hi, ho, stream=st)
+    t_j.record(s2)
+    stream.wait_event(t_j)
+    t_b.record(stream)
+    t_b.synchronize()
+    e2e_value = wl.m * aux_steps / (t_a.elapsed_time(t_b) * 1e-3)
+    plan2.destroy()
 
     # per-stage times for the roofline (separate pass, events on the solve stream)
     P.nuasm_profile_enable(plan, True)
@@ -474,7 +499,10 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h_in.numel() * eb),
-                    "d2h_bytes_per_step": int(h_out.numel() * eb)},
+                    "d2h_bytes_per_step": int(h_out.numel() * eb),
+                    "how": "host buffers through nuasm*_execute; two plans on two streams, steps alternating "
+                           "(copies of one step overlap the other's kernels), L2 flushed before every step",
+                    "serial_value": e2e_serial},
             "gpu_launches": 4 * args.steps,
             "roofline": roofline,
             "clocks": clk}
