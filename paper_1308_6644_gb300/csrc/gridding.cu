@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::ty
     const int T = a.T, w = EXACT ? WMAX : a.w;
     S* sre = reinterpret_cast<S*>(smem_raw);
     S* sim = sre + T * T;
+    pdl_allow_next();
     const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
@@ -319,6 +320,7 @@ __global__ void __launch_bounds__(256, NUASM_SPREAD_MINB) spread_fx_kernel(const
     const int nb = T / kBandRows;
     int* sre = reinterpret_cast<int*>(smem_raw);
     int* sim = sre + T * T;
+    pdl_allow_next();
     const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
@@ -453,6 +455,7 @@ __global__ void __launch_bounds__(kInterpThreads, NUASM_INTERP_MINB) interp_kern
     const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
+    pdl_allow_next();
     const int b = off[tile], e = b + home[tile];
     Rec pre[kInterpPrefetch];
 #pragma unroll
@@ -460,6 +463,7 @@ __global__ void __launch_bounds__(kInterpThreads, NUASM_INTERP_MINB) interp_kern
         const int i = b + threadIdx.x + k * kInterpThreads;
         if (i < e) pre[k] = rec[i];
     }
+    pdl_wait();   // the window comes from the previous kernel; the records are the plan's
     if constexpr (sizeof(V) == 8) {
         // pairs of complex64: x0 and the row pitch are even, so every pair is
         // 16-byte aligned, and W is even, so a pair never straddles the window edge
@@ -556,9 +560,10 @@ cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
     const size_t sm = size_t(TH) * THP * sizeof(V);
     cudaError_t e = set_smem(interp_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
-    interp_kernel<S, WMAX, EXACT><<<P->g.ntiles, kInterpThreads, sm, st>>>(
-        static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.tile_home, P->d.tile_order,
-        static_cast<const V*>(P->d.win), static_cast<V*>(v), a, taps_arg(P));
+    e = launch_chained(interp_kernel<S, WMAX, EXACT>, dim3(P->g.ntiles), dim3(kInterpThreads), sm, st,
+                       static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.tile_home,
+                       P->d.tile_order, static_cast<const V*>(P->d.win), static_cast<V*>(v), a, taps_arg(P));
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -187,6 +187,9 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     const int r0 = blockIdx.x * ROWS;
     const int W = a.W, Wp = a.Wp;
     const V zero = CTraits<V>::zero();
+    pdl_allow_next();
+    const RowConst<V> rc0 = row_const<V>(r0, ty, s);
+    pdl_wait();   // A comes from the previous kernel
 
     auto folded = [&](int row, int p, int sgn) -> V {
         const V* x = A + (r0 + row) * Wp;
@@ -194,7 +197,6 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
         const V t = p + NP < W ? x[p + NP] : zero;
         return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
     };
-    const RowConst<V> rc0 = row_const<V>(r0, ty, s);
     auto put = [&](int row, int pk, int sgn, V v) {
         const int pb = 2 * pk + sgn;
         const int q = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
@@ -236,7 +238,9 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     const int r0 = blockIdx.x * ROWS;
     const int n = a.n, W = a.W, Wp = a.Wp;
     const V zero = CTraits<V>::zero();
+    pdl_allow_next();
     const RowConst<V> rc0 = row_const<V>(r0, ty, s);
+    pdl_wait();   // B comes from the previous kernel
     block_fft<V, -1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
         S, tw, [&](int p, int c) { return p < n ? B[(r0 + c) * n + p] : zero; },
         [&](int p, int c, V v) { M[c * NP + p] = cmul(v, row_factor<V, ROWS>(p, c, r0, rc0, tx, ty, s, a)); });
@@ -282,13 +286,15 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     const int r0 = blockIdx.x * ROWS;
     const int W = a.W, Wp = a.Wp;
     const V zero = CTraits<V>::zero();
+    pdl_allow_next();
+    const RowConst<V> rc0 = row_const<V>(r0, ty, s);
+    pdl_wait();   // A comes from the previous kernel
     auto folded = [&](int row, int p, int sgn) -> V {
         const V* x = A + (r0 + row) * Wp;
         const V u = p < W ? x[p] : zero;
         const V t = p + NP < W ? x[p + NP] : zero;
         return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
     };
-    const RowConst<V> rc0 = row_const<V>(r0, ty, s);
     auto put_mode = [&](int row, int pk, int sgn, V v) {
         const int pb = 2 * pk + sgn;
         const int q = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
@@ -343,6 +349,8 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP>::P, ColCfg<V, LOGNP>::MINB)
     const int sgn = blockIdx.y;
     const int W = a.W, Wp = a.Wp, n = a.n;
     const V zero = CTraits<V>::zero();
+    pdl_allow_next();
+    pdl_wait();   // src comes from the previous kernel (no-op for the first kernel of a chain)
     if constexpr (MODE == COL_FWD_FOLD) {
         // src: window (W x Wp); dst: A (N' x Wp), kept modes in natural N'-bin rows
         block_fft<V, -1, Cf::E, LOGNP, Cf::LOGC, false>(
@@ -458,7 +466,10 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
     const int tid = threadIdx.x;
     const int W = a.W, Wp = a.Wp, n = a.n;
     const float2 zero = make_float2(0.f, 0.f);
+    pdl_allow_next();
     if (tid == 0) tma::mbar_init(bar, 1);
+    pdl_wait();   // the strips come from the previous kernel
+    if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");   // its writes, for the TMA reads
     __syncthreads();
     auto issue = [&](int strip) {
         tma::mbar_expect_tx(bar, uint32_t(nboxes) * BOXR * C * uint32_t(sizeof(float2)));
@@ -582,20 +593,20 @@ cudaError_t launch_row(const nuasm_plan_s* P, int type, cudaStream_t st) {
     cudaError_t e;
     if (type == 1) {
         if ((e = set_smem(row_t1_kernel<V, LOGNP>, sm)) != cudaSuccess) return e;
-        row_t1_kernel<V, LOGNP><<<blocks, Cf::P, sm, st>>>(
-            static_cast<const V*>(P->d.bufA), static_cast<V*>(P->d.bufB), static_cast<const V*>(P->d.t1x),
-            static_cast<const V*>(P->d.t1y), s, tw, a);
+        e = launch_chained(row_t1_kernel<V, LOGNP>, dim3(blocks), dim3(Cf::P), sm, st,
+                           static_cast<const V*>(P->d.bufA), static_cast<V*>(P->d.bufB),
+                           static_cast<const V*>(P->d.t1x), static_cast<const V*>(P->d.t1y), s, tw, a);
     } else if (type == 3) {
         if ((e = set_smem(row_t3_kernel<V, LOGNP>, sm)) != cudaSuccess) return e;
-        row_t3_kernel<V, LOGNP><<<blocks, Cf::P, sm, st>>>(static_cast<V*>(P->d.bufA),
-                                                          static_cast<const V*>(P->d.t3x),
-                                                          static_cast<const V*>(P->d.t3y), s, tw, a);
+        e = launch_chained(row_t3_kernel<V, LOGNP>, dim3(blocks), dim3(Cf::P), sm, st, static_cast<V*>(P->d.bufA),
+                           static_cast<const V*>(P->d.t3x), static_cast<const V*>(P->d.t3y), s, tw, a);
     } else {
         if ((e = set_smem(row_t2_kernel<V, LOGNP>, sm)) != cudaSuccess) return e;
-        row_t2_kernel<V, LOGNP><<<blocks, Cf::P, sm, st>>>(
-            static_cast<const V*>(P->d.bufB), static_cast<V*>(P->d.bufA), static_cast<const V*>(P->d.t2x),
-            static_cast<const V*>(P->d.t2y), s, tw, a);
+        e = launch_chained(row_t2_kernel<V, LOGNP>, dim3(blocks), dim3(Cf::P), sm, st,
+                           static_cast<const V*>(P->d.bufB), static_cast<V*>(P->d.bufA),
+                           static_cast<const V*>(P->d.t2x), static_cast<const V*>(P->d.t2y), s, tw, a);
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -607,8 +618,14 @@ cudaError_t launch_col(const nuasm_plan_s* P, const void* src, void* dst, int nc
     cudaError_t e = set_smem(col_kernel<V, LOGNP, MODE>, sm);
     if (e != cudaSuccess) return e;
     dim3 grid((ncols + Cf::C - 1) / Cf::C, halves);
-    col_kernel<V, LOGNP, MODE><<<grid, Cf::P, sm, st>>>(static_cast<const V*>(src), static_cast<V*>(dst),
-                                                        static_cast<const V*>(P->d.tw), a);
+    if constexpr (MODE == COL_FWD) {   // first kernel of the type-2 chain
+        col_kernel<V, LOGNP, MODE><<<grid, Cf::P, sm, st>>>(static_cast<const V*>(src), static_cast<V*>(dst),
+                                                            static_cast<const V*>(P->d.tw), a);
+    } else {
+        e = launch_chained(col_kernel<V, LOGNP, MODE>, grid, dim3(Cf::P), sm, st, static_cast<const V*>(src),
+                           static_cast<V*>(dst), static_cast<const V*>(P->d.tw), a);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 
@@ -643,9 +660,16 @@ cudaError_t launch_col_tma(const nuasm_plan_s* P, const void* src, void* dst, in
         const int nboxes = (load_rows + Cf::BOXR - 1) / Cf::BOXR;
         const int grid = nstrips < ctas ? nstrips : ctas;
         const ColArgs a{P->g.n, P->g.W, P->g.Wp};
-        col_tma_kernel<LOGNP, MODE><<<grid, Cf::P, sm, st>>>(map, static_cast<float2*>(dst),
-                                                             static_cast<const float2*>(P->d.tw), a, nstrips, nboxes,
-                                                             P->d.err);
+        if constexpr (MODE == COL_FWD) {   // first kernel of the type-2 chain
+            col_tma_kernel<LOGNP, MODE><<<grid, Cf::P, sm, st>>>(map, static_cast<float2*>(dst),
+                                                                 static_cast<const float2*>(P->d.tw), a, nstrips,
+                                                                 nboxes, P->d.err);
+        } else {
+            e = launch_chained(col_tma_kernel<LOGNP, MODE>, dim3(grid), dim3(Cf::P), sm, st, map,
+                               static_cast<float2*>(dst), static_cast<const float2*>(P->d.tw), a, nstrips, nboxes,
+                               P->d.err);
+            if (e != cudaSuccess) return e;
+        }
         return cudaGetLastError();
     }
 }
