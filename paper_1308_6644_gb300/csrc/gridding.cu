@@ -406,6 +406,9 @@ __global__ void __launch_bounds__(256, NUASM_SPREAD_MINB) spread_fx_kernel(const
 // staging loads so that their latency overlaps the tile's; FP32 tiles are
 // staged two complex values (16 B) per load.
 constexpr int kInterpThreads = 256, kInterpPrefetch = 4;
+#ifndef NUASM_F64_EXACT13
+#define NUASM_F64_EXACT13 1
+#endif
 #ifndef NUASM_INTERP_MINB
 #define NUASM_INTERP_MINB 4   // CTAs per SM the register budget is sized for (64 registers)
 #endif
@@ -440,7 +443,7 @@ __device__ __forceinline__ void interp_point(const Rec& r, const V* __restrict__
 }
 
 template <typename S, int WMAX, bool EXACT>
-__global__ void __launch_bounds__(kInterpThreads, NUASM_INTERP_MINB) interp_kernel(const typename RecOf<S>::type* __restrict__ rec,
+__global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_MINB : 2) interp_kernel(const typename RecOf<S>::type* __restrict__ rec,
                                                                 const int* __restrict__ off,
                                                                 const int* __restrict__ home,
                                                                 const int* __restrict__ order,
@@ -580,7 +583,13 @@ template <bool SPREAD> cudaError_t gridding(const nuasm_plan_s* P, const void* i
         if constexpr (SPREAD) return spread_impl<typename Tg::S, Tg::W, Tg::X>(P, in, st);
         else return interp_impl<typename Tg::S, Tg::W, Tg::X>(P, out, st);
     };
-    if (P->f64) return P->g.w <= 8 ? run(GTag<double, 8, false>{}) : run(GTag<double, 16, false>{});
+    if (P->f64) {
+        // the FP64 default tolerance (1e-12) gives w = 13: an exact instantiation
+#if NUASM_F64_EXACT13
+        if (P->g.w == 13) return run(GTag<double, 13, true>{});
+#endif
+        return P->g.w <= 8 ? run(GTag<double, 8, false>{}) : run(GTag<double, 16, false>{});
+    }
     switch (P->g.w) {
         case 4: return run(GTag<float, 4, true>{});
         case 5: return run(GTag<float, 5, true>{});
