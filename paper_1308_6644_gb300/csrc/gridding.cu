@@ -196,7 +196,7 @@ template <> __device__ __forceinline__ double es_eval<double>(double t, double i
 // exponential itself for FP64.
 template <int WMAX> __device__ __forceinline__ void tap_weights(float f, int w, float beta, const KernelPoly& kp,
                                                                  float* out) {
-    constexpr int DMAX = WMAX + 3 < kPolyMaxD ? WMAX + 3 : kPolyMaxD;
+    constexpr int DMAX = WMAX + 2 < kPolyMaxD ? WMAX + 2 : kPolyMaxD;
     (void)w;
     (void)beta;
     const float x = fmaf(2.f, f, -1.f);

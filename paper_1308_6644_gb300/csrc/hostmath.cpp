@@ -452,7 +452,7 @@ int choose_nonsep_mode(const nuasm_params_t& p, double rmax) {
 // evaluation of the exponential).
 void fit_kernel_poly(const Geometry& g, KernelPoly* kp) {
     std::memset(kp, 0, sizeof(*kp));
-    int d = g.w + 2;
+    int d = g.w + 1;
     if (d > kPolyMaxD - 1) d = kPolyMaxD - 1;
     kp->deg = d;
     const int K = 2 * d + 2;
