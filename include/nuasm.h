@@ -234,6 +234,16 @@ nuasm_status nuasm_rs_direct(const nuasm_params_t* p, int64_t m1, const double* 
 nuasm_status nuasm_autotune_tile(const nuasm_params_t* p, int64_t m, const double* x, const double* y, int32_t type,
                                  void* stream, int32_t* tile, double* ms);
 
+/*
+ * nuasm_debug_bounded_wait -- diagnostic for the failure path of the bounded
+ * device waits (the paper has no counterpart).  Runs one CTA that waits, with
+ * the loop the TMA column passes use, on an mbarrier nothing completes,
+ * giving up after `spins` try-waits (1 .. 2^24).  Returns NUASM_ETIMEOUT when
+ * the wait gave up (always, unless the device fails), after which the device
+ * context stays usable; NUASM_EINVAL for a bad count.  Synchronises `stream`.
+ */
+nuasm_status nuasm_debug_bounded_wait(int32_t spins, void* stream);
+
 /* Release every resource of the plan (synchronises the plan's device work). NULL is a no-op. */
 nuasm_status nuasm_destroy(nuasm_plan_t plan);
 

@@ -4,6 +4,7 @@
 // deconvolution, twiddles) -> device allocations (tables, workspace, staging)
 // -> point binning on the device.  Execute: stream-ordered launches only.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -82,12 +83,16 @@ void ring_consume_oldest(nuasm_plan_s* P, int stage) {
     r.count -= 1;
 }
 
+// One stage of an execute chain: an NVTX range on the host thread (named as
+// nuasm_stage_name; free when no tool is attached) and, when the plan's
+// profiling is on, CUDA events around the stage on its stream.
 struct StageScope {
     nuasm_plan_s* P;
     int stage;
     cudaStream_t st;
     int slot = -1;
     StageScope(nuasm_plan_s* p, int s, cudaStream_t stream) : P(p), stage(s), st(stream) {
+        nvtxRangePushA(nuasm_stage_name(s));
         if (!P->prof) return;
         ProfRing& r = extra_of(P)->ring[stage];
         if (!r.created) {
@@ -102,6 +107,7 @@ struct StageScope {
         cudaEventRecord(r.start[slot], st);
     }
     ~StageScope() {
+        nvtxRangePop();
         if (slot < 0) return;
         ProfRing& r = extra_of(P)->ring[stage];
         cudaEventRecord(r.stop[slot], st);

@@ -1,0 +1,46 @@
+// Diagnostic entry point for the bounded-wait failure path (declared in
+// include/nuasm.h).  One CTA waits on an mbarrier that no thread or copy will
+// ever complete, with the same bounded try-wait loop the TMA column passes
+// use; when the bound runs out it sets bit 2 of the error word, exactly as a
+// stalled copy would, and returns.  Nothing is in flight, so there is nothing
+// else to wait for or release.
+#include <cuda_runtime.h>
+
+#include "nuasm_internal.h"
+#include "tma.cuh"
+
+namespace {
+
+__global__ void bounded_wait_kernel(int spins, int* __restrict__ err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    nuasm::tma::mbar_init(&bar, 1);   // expects one arrival that never comes
+    if (!nuasm::tma::mbar_wait(&bar, 0, spins)) atomicOr(err, 2);
+}
+
+nuasm_status status_of(cudaError_t e) {
+    if (e == cudaSuccess) return NUASM_OK;
+    return e == cudaErrorMemoryAllocation ? NUASM_ENOMEM : NUASM_ECUDA;
+}
+
+}  // namespace
+
+extern "C" nuasm_status nuasm_debug_bounded_wait(int32_t spins, void* stream) {
+    if (spins < 1 || spins > nuasm::tma::kSpinLimit) return NUASM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* err = nullptr;
+    cudaError_t e = cudaMallocAsync(&err, sizeof(int), st);
+    if (e != cudaSuccess) return status_of(e);
+    int host = 0;
+    e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        bounded_wait_kernel<<<1, 32, 0, st>>>(spins, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(err, st);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess) return status_of(e);
+    return (host & 2) ? NUASM_ETIMEOUT : NUASM_OK;
+}

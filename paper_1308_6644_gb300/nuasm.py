@@ -112,6 +112,7 @@ _SIGS = {
     "nuasm_autotune_tile": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_double)]),
+    "nuasm_debug_bounded_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p]),
     "nuasm_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(BatchItem),
                                           ctypes.c_int32, ctypes.c_int32]),
     "nuasm_batch_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -408,6 +409,15 @@ def nuasm_autotune_tile(params: Params, x, y, type_: int, stream=None) -> tuple:
     _check(lib().nuasm_autotune_tile(ctypes.byref(params), m, _ptr(x), _ptr(y), int(type_), _stream(stream),
                                      ctypes.byref(t), ctypes.byref(ms)), "nuasm_autotune_tile")
     return int(t.value), float(ms.value)
+
+
+def nuasm_debug_bounded_wait(spins: int, stream=None) -> int:
+    """Status of a device wait that is made to run out after `spins` tries
+    (NUASM_ETIMEOUT = 5 is the expected answer)."""
+    code = lib().nuasm_debug_bounded_wait(int(spins), _stream(stream))
+    if code not in (0, 5):
+        _check(code, "nuasm_debug_bounded_wait")
+    return int(code)
 
 
 # ---------------------------------------------------------------- batches

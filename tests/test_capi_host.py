@@ -188,3 +188,9 @@ def test_plan_rejects_unsupported_tiles(P, tile):
     with pytest.raises(P.NuasmError) as ei:
         P.nuasm_plan(P.make_params(32, 10e-6, 633e-9, 0.01, tile=tile), x, x)
     assert ei.value.code == 1
+
+
+def test_bounded_wait_diagnostic_rejects_bad_counts(P):
+    lib = P.lib()
+    assert lib.nuasm_debug_bounded_wait(0, None) == 1
+    assert lib.nuasm_debug_bounded_wait((1 << 24) + 1, None) == 1

@@ -216,6 +216,21 @@ def test_type2_is_deterministic(P):
     assert np.array_equal(a, b)
 
 
+def test_fp32_type1_is_deterministic(P):
+    """FP32 spreading adds integers (fixed point), so the order in which the
+    taps land does not change a bit, even with many points per cell."""
+    rng = np.random.default_rng(43)
+    n, pitch = 64, 10e-6
+    x = WL.clamp_window(rng.normal(0, 20e-6, 20000), n, pitch)   # ~5 points per fine-grid cell near the centre
+    y = WL.clamp_window(rng.normal(0, 20e-6, 20000), n, pitch)
+    c = rng.normal(size=20000) + 1j * rng.normal(size=20000)
+    kw = dict(pitch=pitch, lam=633e-9, z=0.02)
+    a = run_gpu(P, "asm", 1, "f32", n, x=x, y=y, values=c, **kw)
+    b = run_gpu(P, "asm", 1, "f32", n, x=x, y=y, values=c, **kw)
+    assert np.array_equal(a, b)
+    assert O.rel_l2(a, run_oracle("asm", 1, n, x=x, y=y, values=c, **kw)) < TOL["f32"]
+
+
 # ---------------------------------------------------------------- Gaussian (Greengard-Lee) kernel option
 @pytest.mark.parametrize("kind", ["asm", "fresnel"])
 @pytest.mark.parametrize("type_", [1, 2])
