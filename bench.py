@@ -183,8 +183,7 @@ def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
     tap = f"{s}, {8 if w <= 8 else 16}, false" if f64 else (f"float, {w}, true" if 4 <= w <= 8 else "float, 16, false")
     tma = not f64 and 512 <= info["n_pad"] <= 4096          # folded column passes
     tma_wide = not f64 and info["n_pad"] == 4096              # unfolded ones too
-    spread = f"spread_fx_kernel<{w if 4 <= w <= 8 else 16}, {'true' if 4 <= w <= 8 else 'false'}>" if not f64 \
-        else f"spread_kernel<{tap}>"
+    spread = f"spread_kernel<{tap}>"
     return {"col_fwd": f"col_tma_kernel<{lognp}, 2>" if tma_wide else f"col_kernel<{v}, {lognp}, 2>",
             "row_t2": f"row_t2_kernel<{v}, {lognp}>",
             "col_inv_fold": f"col_tma_kernel<{lognp}, 3>" if tma else f"col_kernel<{v}, {lognp}, 3>",

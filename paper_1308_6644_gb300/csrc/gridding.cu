@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -234,8 +235,20 @@ struct GridArgs {
 
 // --------------------------------------------------------------- spreading (type 1)
 // EXACT: the kernel width is WMAX itself (compile-time loops); else w <= WMAX at run time.
+// Taps accumulate with shared-memory atomicAdd in the plan's precision.  (On
+// sm_103a a float shared-memory atomicAdd is a compare-and-swap loop -- 9.4
+// instructions and 2 wavefronts per add, against one native operation for a
+// 32-bit integer.  Fixed-point integer accumulation with a bound per 8-row
+// band was measured: one word spread 4M clustered points 1.6x faster but
+// lost ~1e-9 of the band's |c| sum per tap, 1.1e-5 end to end where
+// thousands of random-phase points crowd a few cells; two words (high and
+// remainder) were accurate but slower than float; a per-tile switch chose
+// float for most dense tiles.  Float accumulation stays.)
+#ifndef NUASM_SPREAD_MINB
+#define NUASM_SPREAD_MINB 1
+#endif
 template <typename S, int WMAX, bool EXACT>
-__global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::type* __restrict__ rec,
+__global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) spread_kernel(const typename RecOf<S>::type* __restrict__ rec,
                                                      const int* __restrict__ off, const double* __restrict__ wpt,
                                                      const int* __restrict__ order,
                                                      const typename VecOf<S>::type* __restrict__ c,
@@ -289,114 +302,6 @@ __global__ void __launch_bounds__(256) spread_kernel(const typename RecOf<S>::ty
             win[size_t(gy) * a.Wp + gx] = v;
         }
     }
-}
-
-// FP32 spreading in fixed point.  Shared-memory float atomicAdd is a
-// compare-and-swap loop on this architecture while 32-bit integer atomicAdd is
-// a single native operation, so each tile accumulates integers: the tile's
-// rows are split into bands of kBandRows, band k gets the quantum
-// q_k = S_k (1 + 2^-8) / 2^30 with S_k the sum of |Re c| + |Im c| (times the
-// point weight) over the records whose taps reach the band, and every tap
-// adds round(contribution / q_k).  Each cell's true sum is bounded by S_k
-// (kernel taps are at most 1), so the integers stay below 2^31; rounding
-// costs at most q_k / 2 per tap, about 1e-7 of a typical cell value.
-constexpr int kBandRows = 8, kMaxBands = 8;   // tiles of at most 64 rows
-#ifndef NUASM_SPREAD_MINB
-#define NUASM_SPREAD_MINB 1
-#endif
-#ifndef NUASM_SPREAD_FX
-#define NUASM_SPREAD_FX 1   // 0: FP32 plans spread with float atomics like FP64 plans
-#endif
-
-template <int WMAX, bool EXACT>
-__global__ void __launch_bounds__(256, NUASM_SPREAD_MINB) spread_fx_kernel(const RecF* __restrict__ rec, const int* __restrict__ off,
-                                                        const double* __restrict__ wpt, const int* __restrict__ order,
-                                                        const float2* __restrict__ c, float2* __restrict__ win,
-                                                        GridArgs a, const KernelPoly kp) {
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ float band_part[8][kMaxBands];
-    __shared__ float band_inv[kMaxBands], band_q[kMaxBands];
-    const int T = a.T, w = EXACT ? WMAX : a.w;
-    const int nb = T / kBandRows;
-    int* sre = reinterpret_cast<int*>(smem_raw);
-    int* sim = sre + T * T;
-    pdl_allow_next();
-    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
-    const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
-    const int x0 = tx * T, y0 = ty * T;
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) { sre[i] = 0; sim[i] = 0; }
-    const int b = off[tile], e = off[tile + 1];
-
-    // band bounds: per-thread partial sums, then warp and block reductions
-    float part[kMaxBands];
-#pragma unroll
-    for (int k = 0; k < kMaxBands; ++k) part[k] = 0.f;
-    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
-        const RecF r = rec[i];
-        const int ly = int(r.cell >> 16) - y0;
-        const float2 v = c[r.j];
-        float mag = fabsf(v.x) + fabsf(v.y);
-        if (wpt) mag *= fabsf(float(wpt[r.j]));
-        const int ra = max(0, ly), rb = min(T, ly + w) - 1;   // rows reached
-        const int ka = ra / kBandRows, kb = rb / kBandRows;
-#pragma unroll
-        for (int k = 0; k < kMaxBands; ++k) part[k] += (k >= ka && k <= kb) ? mag : 0.f;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kMaxBands; ++k) {
-        float v = part[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) band_part[warp][k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < kMaxBands) {
-        float sk = 0.f;
-        for (int wv = 0; wv < int(blockDim.x >> 5); ++wv) sk += band_part[wv][threadIdx.x];
-        const float bound = sk * (1.f + 0.00390625f);
-        band_q[threadIdx.x] = bound * 9.3132257461547852e-10f;                 // / 2^30
-        band_inv[threadIdx.x] = bound > 0.f ? 1073741824.f / bound : 0.f;      // 2^30 / bound
-    }
-    __syncthreads();
-
-    const float beta = float(a.beta);
-    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
-        const RecF r = rec[i];
-        const int lx = int(r.cell & 0xffffu) - x0, ly = int(r.cell >> 16) - y0;
-        float2 val = c[r.j];
-        if (wpt) { const float wt = float(wpt[r.j]); val.x *= wt; val.y *= wt; }
-        float wx[WMAX], wy[WMAX];
-        tap_weights<WMAX>(r.fx, w, beta, kp, wx);
-        tap_weights<WMAX>(r.fy, w, beta, kp, wy);
-        const int ya = max(0, -ly), yb = min(w, T - ly);
-        const int xa = max(0, -lx), xb = min(w, T - lx);
-#pragma unroll
-        for (int qy = 0; qy < WMAX; ++qy) {
-            if (qy < ya || qy >= yb) continue;
-            const int row = ly + qy;
-            const float sc = band_inv[row / kBandRows] * wy[qy];
-            const float vr = val.x * sc, vi = val.y * sc;
-            int* rowr = sre + row * T + lx;
-            int* rowi = sim + row * T + lx;
-#pragma unroll
-            for (int qx = 0; qx < WMAX; ++qx) {
-                if (qx < xa || qx >= xb) continue;
-                atomicAdd(rowr + qx, __float2int_rn(vr * wx[qx]));
-                atomicAdd(rowi + qx, __float2int_rn(vi * wx[qx]));
-            }
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
-        const int yy = i / T, xx = i - yy * T;
-        const int gy = y0 + yy, gx = x0 + xx;
-        if (gy < a.W && gx < a.W) {
-            const float q = band_q[yy / kBandRows];
-            win[size_t(gy) * a.Wp + gx] = make_float2(float(sre[i]) * q, float(sim[i]) * q);
-        }
-    }
-    (void)nb;
 }
 
 // --------------------------------------------------------------- interpolation (type 2)
@@ -535,17 +440,6 @@ template <typename S, int WMAX, bool EXACT>
 cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     using V = typename VecOf<S>::type;
     GridArgs a = grid_args(P);
-    if constexpr (sizeof(S) == 4 && NUASM_SPREAD_FX) {
-        if (a.T <= kBandRows * kMaxBands) {
-            const size_t sm = size_t(2) * a.T * a.T * sizeof(int);
-            cudaError_t e = set_smem(spread_fx_kernel<WMAX, EXACT>, sm);
-            if (e != cudaSuccess) return e;
-            spread_fx_kernel<WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
-                static_cast<const RecF*>(P->d.rec), P->d.tile_off, P->d.wpt, P->d.tile_order,
-                static_cast<const float2*>(c), static_cast<float2*>(P->d.win), a, taps_arg(P));
-            return cudaGetLastError();
-        }
-    }
     const size_t sm = size_t(2) * a.T * a.T * sizeof(S);
     cudaError_t e = set_smem(spread_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;

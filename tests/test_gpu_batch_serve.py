@@ -3,10 +3,9 @@
 
 Each result is checked against the same solve run alone through the plain
 entry points (nuasm_plan + nuasm*_execute) and, for a sample, against the FP64
-oracle.  Type 2 runs and FP32 type 1 runs (fixed-point spreading) are
-deterministic; FP64 spreading accumulates with double atomics whose order
-varies, so type 1 results are compared to rounding (rel-L2 1e-6 in FP32,
-1e-13 in FP64)."""
+oracle.  Type 2 runs are deterministic and must agree bit for bit; type 1
+spreading accumulates with shared-memory atomics whose order varies, so type 1
+results agree to rounding (rel-L2 1e-6 in FP32, 1e-13 in FP64)."""
 import numpy as np
 import pytest
 

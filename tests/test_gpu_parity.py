@@ -216,19 +216,22 @@ def test_type2_is_deterministic(P):
     assert np.array_equal(a, b)
 
 
-def test_fp32_type1_is_deterministic(P):
-    """FP32 spreading adds integers (fixed point), so the order in which the
-    taps land does not change a bit, even with many points per cell."""
+def test_fp32_type1_dense_random_phase_cluster(P):
+    """20000 random-phase points within a few fine-grid cells (hundreds per
+    cell): the shared-memory accumulation must keep the FP32 tolerance where
+    the cell sums cancel far below the sum of magnitudes, and two runs agree
+    to rounding (float atomics add in varying order)."""
     rng = np.random.default_rng(43)
-    n, pitch = 64, 10e-6
-    x = WL.clamp_window(rng.normal(0, 20e-6, 20000), n, pitch)   # ~5 points per fine-grid cell near the centre
-    y = WL.clamp_window(rng.normal(0, 20e-6, 20000), n, pitch)
-    c = rng.normal(size=20000) + 1j * rng.normal(size=20000)
+    n, pitch, m = 64, 10e-6, 20000
+    x = WL.clamp_window(rng.normal(0, 20e-6, m), n, pitch)
+    y = WL.clamp_window(rng.normal(0, 20e-6, m), n, pitch)
+    c = rng.normal(size=m) + 1j * rng.normal(size=m)
     kw = dict(pitch=pitch, lam=633e-9, z=0.02)
     a = run_gpu(P, "asm", 1, "f32", n, x=x, y=y, values=c, **kw)
     b = run_gpu(P, "asm", 1, "f32", n, x=x, y=y, values=c, **kw)
-    assert np.array_equal(a, b)
-    assert O.rel_l2(a, run_oracle("asm", 1, n, x=x, y=y, values=c, **kw)) < TOL["f32"]
+    ref = run_oracle("asm", 1, n, x=x, y=y, values=c, **kw)
+    assert O.rel_l2(a, ref) < TOL["f32"] and O.rel_l2(b, ref) < TOL["f32"]
+    assert O.rel_l2(a, b) < 1e-6
 
 
 # ---------------------------------------------------------------- Gaussian (Greengard-Lee) kernel option
