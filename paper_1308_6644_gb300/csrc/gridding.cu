@@ -243,7 +243,8 @@ struct GridArgs {
 // lost ~1e-9 of the band's |c| sum per tap, 1.1e-5 end to end where
 // thousands of random-phase points crowd a few cells; two words (high and
 // remainder) were accurate but slower than float; a per-tile switch chose
-// float for most dense tiles.  Float accumulation stays.)
+// float for most dense tiles; one 64-bit compare-and-swap per (re, im) pair
+// was 3.9x slower than two float adds.  Float accumulation stays.)
 #ifndef NUASM_SPREAD_MINB
 #define NUASM_SPREAD_MINB 1
 #endif
