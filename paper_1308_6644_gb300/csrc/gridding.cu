@@ -248,6 +248,9 @@ struct GridArgs {
 #ifndef NUASM_SPREAD_MINB
 #define NUASM_SPREAD_MINB 1
 #endif
+#ifndef NUASM_SPREAD_PRIVATE
+#define NUASM_SPREAD_PRIVATE 1   // per-warp private tiles where they fit (T <= 32 F32, <= 16 F64)
+#endif
 template <typename S, int WMAX, bool EXACT>
 __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) spread_kernel(const typename RecOf<S>::type* __restrict__ rec,
                                                      const int* __restrict__ off, const double* __restrict__ wpt,
@@ -300,6 +303,101 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
             V v;
             v.x = sre[i];
             v.y = sim[i];
+            win[size_t(gy) * a.Wp + gx] = v;
+        }
+    }
+}
+
+// Spreading into per-warp private copies of the tile, without atomics.  Each
+// warp takes 32 consecutive records and adds their taps into its own T x T
+// copy with plain loads and stores, one tap offset (qy, qx) at a time for all
+// lanes, with a __syncwarp between offsets so that every store of one offset
+// is seen by the loads of the next.  Within one offset two lanes touch the
+// same cell only if their records share the first-tap cell; such a batch
+// (found with __match_any_sync) adds with atomics instead.  The copies are
+// summed at the end.  Shared memory: 8 warps x T^2 complex, so T <= 32 (F32)
+// or T <= 16 (F64).
+template <typename S, int WMAX, bool EXACT>
+__global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename RecOf<S>::type* __restrict__ rec,
+                                                             const int* __restrict__ off,
+                                                             const double* __restrict__ wpt,
+                                                             const int* __restrict__ order,
+                                                             const typename VecOf<S>::type* __restrict__ c,
+                                                             typename VecOf<S>::type* __restrict__ win, GridArgs a,
+                                                             const KernelPoly kp) {
+    using V = typename VecOf<S>::type;
+    using Rec = typename RecOf<S>::type;
+    extern __shared__ unsigned char smem_raw[];
+    V* copies = reinterpret_cast<V*>(smem_raw);
+    const int T = a.T, w = EXACT ? WMAX : a.w, TT = T * T;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    V* mine = copies + warp * TT;
+    pdl_allow_next();
+    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
+    const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
+    const int x0 = tx * T, y0 = ty * T;
+    const V zero = CTraits<V>::zero();
+    for (int i = threadIdx.x; i < 8 * TT; i += blockDim.x) copies[i] = zero;
+    __syncthreads();
+    const S beta = S(a.beta);
+    const int b = off[tile], e = off[tile + 1];
+    for (int i0 = b + warp * 32; i0 < e; i0 += 256) {
+        const int i = i0 + lane;
+        const bool live = i < e;
+        Rec r{};
+        if (live) r = rec[i];
+        // lanes whose records share a first-tap cell would add to one cell in the same step
+        const uint32_t key = live ? r.cell : 0xffffffffu - uint32_t(lane);
+        const bool clash = __any_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, key)) > 1);
+        const int lx = live ? int(r.cell & 0xffffu) - x0 : 0, ly = live ? int(r.cell >> 16) - y0 : 0;
+        V val = zero;
+        if (live) {
+            val = c[r.j];
+            if (wpt) { const S wt = S(wpt[r.j]); val.x *= wt; val.y *= wt; }
+        }
+        S wx[WMAX], wy[WMAX];
+        tap_weights<WMAX>(S(r.fx), w, beta, kp, wx);
+        tap_weights<WMAX>(S(r.fy), w, beta, kp, wy);
+        const int ya = max(0, -ly), yb = min(w, T - ly);
+        const int xa = max(0, -lx), xb = min(w, T - lx);
+#pragma unroll
+        for (int qy = 0; qy < WMAX; ++qy) {
+            if (qy >= w) continue;   // warp-uniform
+            const bool rowok = live && qy >= ya && qy < yb;
+            const S vr = val.x * wy[qy], vi = val.y * wy[qy];
+            V* row = mine + (ly + qy) * T + lx;
+#pragma unroll
+            for (int qx = 0; qx < WMAX; ++qx) {
+                if (qx >= w) continue;   // warp-uniform
+                const bool ok = rowok && qx >= xa && qx < xb;
+                if (!clash) {
+                    if (ok) {
+                        V g = row[qx];
+                        g.x += vr * wx[qx];
+                        g.y += vi * wx[qx];
+                        row[qx] = g;
+                    }
+                    __syncwarp();
+                } else if (ok) {
+                    atomicAdd(&row[qx].x, vr * wx[qx]);
+                    atomicAdd(&row[qx].y, vi * wx[qx]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < TT; i += blockDim.x) {
+        const int yy = i / T, xx = i - yy * T;
+        const int gy = y0 + yy, gx = x0 + xx;
+        if (gy < a.W && gx < a.W) {
+            V v = copies[i];
+#pragma unroll
+            for (int k = 1; k < 8; ++k) {
+                const V u = copies[k * TT + i];
+                v.x += u.x;
+                v.y += u.y;
+            }
             win[size_t(gy) * a.Wp + gx] = v;
         }
     }
@@ -441,6 +539,15 @@ template <typename S, int WMAX, bool EXACT>
 cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     using V = typename VecOf<S>::type;
     GridArgs a = grid_args(P);
+    if (NUASM_SPREAD_PRIVATE && a.T <= (sizeof(S) == 4 ? 32 : 16)) {
+        const size_t sm = size_t(8) * a.T * a.T * sizeof(V);
+        cudaError_t e = set_smem(spread_private_kernel<S, WMAX, EXACT>, sm);
+        if (e != cudaSuccess) return e;
+        spread_private_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
+            static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.wpt, P->d.tile_order,
+            static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg(P));
+        return cudaGetLastError();
+    }
     const size_t sm = size_t(2) * a.T * a.T * sizeof(S);
     cudaError_t e = set_smem(spread_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
