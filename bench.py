@@ -160,14 +160,16 @@ def stage_bytes(info: dict, m: int, type_: int = 2, eb: int = 8) -> dict:
 ALU_PEAK_TFLOPS = {False: 152 * 128 * 2 * 2.07e9 / 1e12, True: 1.25}
 
 
-def stage_flops(info: dict, m: int, type_: int = 2) -> dict:
+def stage_flops(info: dict, m: int, type_: int = 2, f64: bool = False) -> dict:
     """Algorithmic flops per launch of each stage: 5 L log2 L per L-point
     complex FFT, one complex multiply (6 flops) per kept mode for the
     transfer function, and per gridding point or record the Horner taps
-    (2 axes x w taps x (w + 3) FMA) plus w^2 complex-by-real MACs."""
+    (2 axes x w taps x d FMA, d = the tap polynomials' degree: w + 1 in FP32,
+    15 in FP64) plus w^2 complex-by-real MACs."""
     n, np_, W, w = info["n"], info["n_pad"], info["window"], info["kernel_width"]
     fft = 5.0 * np_ * np.log2(np_)
-    taps = 2 * 2 * w * (w + 3) + 4 * w * w + 4 * w
+    d = 15 if f64 else w + 1
+    taps = 2 * 2 * w * d + 4 * w * w + 4 * w
     if type_ == 1:
         return {"spread": taps * info["records"], "col_fwd_fold": 2 * W * fft,
                 "row_t1": 3 * np_ * fft + 6.0 * np_ * np_, "col_inv": n * fft}
@@ -460,7 +462,7 @@ def run_ours(args):
     prof = P.nuasm_profile_read(plan)
     P.nuasm_profile_enable(plan, False)
     sbytes = stage_bytes(info, wl.m, wl.type, eb)
-    sflops = stage_flops(info, wl.m, wl.type)
+    sflops = stage_flops(info, wl.m, wl.type, f64)
     peak, peak_kind = hbm_peak()
     alu_peak = ALU_PEAK_TFLOPS[f64]
     stages = {}

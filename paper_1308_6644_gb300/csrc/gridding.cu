@@ -12,13 +12,17 @@
 // integer cell and the fraction f is done in FP64 once per plan.
 //
 // The kernel is the exponential of semicircle
-//   phi(t) = exp(beta (sqrt(1 - (2t/w)^2) - 1)),  |t| <= w/2.
+//   phi(t) = exp(beta (sqrt(1 - (2t/w)^2) - 1)),  |t| <= w/2,
+// or the truncated Gaussian; each tap phi(i + f - w/2) is evaluated from a
+// polynomial in f fitted at plan time (the fit error sits below the kernel's
+// own truncation error in both precisions).
 //
 // Tiles: the W x W window is cut into T x T tiles.  Each point is binned to the
 // tile that holds its first tap l0 (its home tile) and duplicated into the +x,
 // +y and +x+y neighbours its taps reach.  Spreading is output-stationary: one
 // CTA owns one tile, accumulates every record of its bin into shared memory
-// (shared-memory atomics, no global atomics) clipping taps to the tile, and
+// (shared-memory atomics, or for small tiles one private copy per warp with
+// plain read-modify-writes; no global atomics) clipping taps to the tile, and
 // writes the tile once.  Interpolation loads the tile plus a (w-1) halo into
 // shared memory and evaluates its home records only.
 #include <cuda_runtime.h>
@@ -180,26 +184,11 @@ __global__ void order_tile_kernel(const Rec* __restrict__ src, Rec* __restrict__
 }
 
 // --------------------------------------------------------------- kernel values
-template <typename S> __device__ __forceinline__ S es_eval(S t, S inv_half_w, S beta);
-template <> __device__ __forceinline__ float es_eval<float>(float t, float ihw, float beta) {
-    const float s = t * ihw;
-    const float u = fmaxf((1.f - s) * (1.f + s), 0.f);
-    return expf(beta * (sqrtf(u) - 1.f));
-}
-template <> __device__ __forceinline__ double es_eval<double>(double t, double ihw, double beta) {
-    const double s = t * ihw;
-    const double u = fmax((1.0 - s) * (1.0 + s), 0.0);
-    return exp(beta * (sqrt(u) - 1.0));
-}
-
-// Tap weights of one axis: polynomial form for FP32 (Horner in x = 2f - 1,
-// coefficients zero-padded to DMAX so the loop is fully unrolled), the
-// exponential itself for FP64.
-template <int WMAX> __device__ __forceinline__ void tap_weights(float f, int w, float beta, const KernelPoly& kp,
-                                                                 float* out) {
+// Tap weights of one axis as polynomials in x = 2f - 1 (Horner's rule; the
+// coefficients beyond the fitted degree and the taps beyond w are zero, so
+// the loops unroll fully): degree w + 1 in FP32, 15 in FP64.
+template <int WMAX> __device__ __forceinline__ void tap_weights(float f, const KernelPoly& kp, float* out) {
     constexpr int DMAX = WMAX + 2 < kPolyMaxD ? WMAX + 2 : kPolyMaxD;
-    (void)w;
-    (void)beta;
     const float x = fmaf(2.f, f, -1.f);
 #pragma unroll
     for (int i = 0; i < WMAX; ++i) {
@@ -209,20 +198,20 @@ template <int WMAX> __device__ __forceinline__ void tap_weights(float f, int w, 
         out[i] = acc;
     }
 }
-template <int WMAX> __device__ __forceinline__ void tap_weights(double f, int w, double beta, const KernelPoly& kp,
-                                                                 double* out) {
-    const double ihw = 2.0 / w, hw = 0.5 * w;
-    if (kp.deg < 0) {   // Gaussian kernel exp(-beta t^2)
+template <int WMAX> __device__ __forceinline__ void tap_weights(double f, const KernelPoly64& kp, double* out) {
+    const double x = fma(2.0, f, -1.0);
 #pragma unroll
-        for (int i = 0; i < WMAX; ++i) {
-            const double t = double(i) + f - hw;
-            out[i] = i < w ? exp(-beta * t * t) : 0.0;
-        }
-        return;
+    for (int i = 0; i < WMAX; ++i) {
+        double acc = kp.c[i][kPolyMaxD - 1];
+#pragma unroll
+        for (int k = kPolyMaxD - 2; k >= 0; --k) acc = fma(acc, x, kp.c[i][k]);
+        out[i] = acc;
     }
-#pragma unroll
-    for (int i = 0; i < WMAX; ++i) out[i] = i < w ? es_eval<double>(double(i) + f - hw, ihw, beta) : 0.0;
 }
+
+template <typename S> struct PolyOf;
+template <> struct PolyOf<float> { using type = KernelPoly; };
+template <> struct PolyOf<double> { using type = KernelPoly64; };
 
 template <typename S> struct VecOf;
 template <> struct VecOf<float> { using type = float2; };
@@ -230,7 +219,6 @@ template <> struct VecOf<double> { using type = double2; };
 
 struct GridArgs {
     int W, Wp, T, ntx, w;
-    double beta;
 };
 
 // --------------------------------------------------------------- spreading (type 1)
@@ -257,7 +245,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
                                                      const int* __restrict__ order,
                                                      const typename VecOf<S>::type* __restrict__ c,
                                                      typename VecOf<S>::type* __restrict__ win, GridArgs a,
-                                                     const KernelPoly kp) {
+                                                     const typename PolyOf<S>::type kp) {
     using V = typename VecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
     const int T = a.T, w = EXACT ? WMAX : a.w;
@@ -269,7 +257,6 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
     const int x0 = tx * T, y0 = ty * T;
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) { sre[i] = S(0); sim[i] = S(0); }
     __syncthreads();
-    const S beta = S(a.beta);
     const int b = off[tile], e = off[tile + 1];
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
         const auto r = rec[i];
@@ -277,8 +264,8 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
         V val = c[r.j];
         if (wpt) { const S wt = S(wpt[r.j]); val.x *= wt; val.y *= wt; }
         S wx[WMAX], wy[WMAX];
-        tap_weights<WMAX>(S(r.fx), w, beta, kp, wx);
-        tap_weights<WMAX>(S(r.fy), w, beta, kp, wy);
+        tap_weights<WMAX>(S(r.fx), kp, wx);
+        tap_weights<WMAX>(S(r.fy), kp, wy);
         const int ya = max(0, -ly), yb = min(w, T - ly);
         const int xa = max(0, -lx), xb = min(w, T - lx);
 #pragma unroll
@@ -324,7 +311,7 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
                                                              const int* __restrict__ order,
                                                              const typename VecOf<S>::type* __restrict__ c,
                                                              typename VecOf<S>::type* __restrict__ win, GridArgs a,
-                                                             const KernelPoly kp) {
+                                                             const typename PolyOf<S>::type kp) {
     using V = typename VecOf<S>::type;
     using Rec = typename RecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
@@ -339,7 +326,6 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
     const V zero = CTraits<V>::zero();
     for (int i = threadIdx.x; i < 8 * TT; i += blockDim.x) copies[i] = zero;
     __syncthreads();
-    const S beta = S(a.beta);
     const int b = off[tile], e = off[tile + 1];
     for (int i0 = b + warp * 32; i0 < e; i0 += 256) {
         const int i = i0 + lane;
@@ -356,8 +342,8 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
             if (wpt) { const S wt = S(wpt[r.j]); val.x *= wt; val.y *= wt; }
         }
         S wx[WMAX], wy[WMAX];
-        tap_weights<WMAX>(S(r.fx), w, beta, kp, wx);
-        tap_weights<WMAX>(S(r.fy), w, beta, kp, wy);
+        tap_weights<WMAX>(S(r.fx), kp, wx);
+        tap_weights<WMAX>(S(r.fy), kp, wy);
         const int ya = max(0, -ly), yb = min(w, T - ly);
         const int xa = max(0, -lx), xb = min(w, T - lx);
 #pragma unroll
@@ -419,11 +405,11 @@ constexpr int kInterpThreads = 256, kInterpPrefetch = 4;
 
 template <typename S, int WMAX, bool EXACT, typename Rec, typename V>
 __device__ __forceinline__ void interp_point(const Rec& r, const V* __restrict__ tl, int THP, int x0, int y0, int w,
-                                             S beta, const KernelPoly& kp, V* __restrict__ v) {
+                                             const typename PolyOf<S>::type& kp, V* __restrict__ v) {
     const int lx = int(r.cell & 0xffffu) - x0, ly = int(r.cell >> 16) - y0;
     S wx[WMAX], wy[WMAX];
-    tap_weights<WMAX>(S(r.fx), w, beta, kp, wx);
-    tap_weights<WMAX>(S(r.fy), w, beta, kp, wy);
+    tap_weights<WMAX>(S(r.fx), kp, wx);
+    tap_weights<WMAX>(S(r.fy), kp, wy);
     S ar = S(0), ai = S(0);
 #pragma unroll
     for (int qy = 0; qy < WMAX; ++qy) {
@@ -453,7 +439,7 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
                                                                 const int* __restrict__ order,
                                                                 const typename VecOf<S>::type* __restrict__ win,
                                                                 typename VecOf<S>::type* __restrict__ v, GridArgs a,
-                                                                const KernelPoly kp) {
+                                                                const typename PolyOf<S>::type kp) {
     using V = typename VecOf<S>::type;
     using Rec = typename RecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
@@ -496,7 +482,6 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
         }
     }
     __syncthreads();
-    const S beta = S(a.beta);
     // a ring of kInterpPrefetch records in flight: each slot is refilled with
     // the record kInterpPrefetch strides ahead before its point is computed
     constexpr int AHEAD = kInterpPrefetch * kInterpThreads;
@@ -507,7 +492,7 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
             if (i < e) {
                 const Rec r = pre[k];
                 if (i + AHEAD < e) pre[k] = rec[i + AHEAD];
-                interp_point<S, WMAX, EXACT>(r, tl, THP, x0, y0, w, beta, kp, v);
+                interp_point<S, WMAX, EXACT>(r, tl, THP, x0, y0, w, kp, v);
             }
         }
     }
@@ -520,7 +505,6 @@ GridArgs grid_args(const nuasm_plan_s* P) {
     a.T = P->g.T;
     a.ntx = P->g.ntx;
     a.w = P->g.w;
-    a.beta = P->g.beta;
     return a;
 }
 
@@ -528,11 +512,10 @@ template <typename K> cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
 }
 
-// FP64 taps evaluate the kernel itself; a negative degree marks the Gaussian
-KernelPoly taps_arg(const nuasm_plan_s* P) {
-    KernelPoly kp = P->poly;
-    if (P->f64 && P->g.kernel == NUASM_KERNEL_GAUSSIAN) kp.deg = -1;
-    return kp;
+// the tap polynomials of the plan's precision
+template <typename S> typename PolyOf<S>::type taps_arg(const nuasm_plan_s* P) {
+    if constexpr (sizeof(S) == 8) return P->poly64;
+    else return P->poly;
 }
 
 template <typename S, int WMAX, bool EXACT>
@@ -545,7 +528,7 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         spread_private_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
             static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.wpt, P->d.tile_order,
-            static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg(P));
+            static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg<S>(P));
         return cudaGetLastError();
     }
     const size_t sm = size_t(2) * a.T * a.T * sizeof(S);
@@ -553,7 +536,7 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     spread_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
         static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.wpt, P->d.tile_order,
-        static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg(P));
+        static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg<S>(P));
     return cudaGetLastError();
 }
 
@@ -567,7 +550,7 @@ cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     e = launch_chained(interp_kernel<S, WMAX, EXACT>, dim3(P->g.ntiles), dim3(kInterpThreads), sm, st,
                        static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.tile_home,
-                       P->d.tile_order, static_cast<const V*>(P->d.win), static_cast<V*>(v), a, taps_arg(P));
+                       P->d.tile_order, static_cast<const V*>(P->d.win), static_cast<V*>(v), a, taps_arg<S>(P));
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

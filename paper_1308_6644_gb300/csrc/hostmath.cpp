@@ -448,23 +448,23 @@ int choose_nonsep_mode(const nuasm_params_t& p, double rmax) {
 
 // Chebyshev interpolation of each tap phi(i + f - w/2), f in [0, 1), at
 // Chebyshev nodes of x = 2f - 1, converted to monomial coefficients in x (the
-// coefficients stay O(1), so Horner's rule in FP32 is as accurate as direct
-// evaluation of the exponential).
-void fit_kernel_poly(const Geometry& g, KernelPoly* kp) {
+// coefficients stay O(1), so Horner's rule is as accurate as direct
+// evaluation of the exponential: FP32 at degree w + 1, FP64 at degree 15).
+template <typename Poly, typename T>
+void fit_poly(const Geometry& g, int d, Poly* kp) {
     std::memset(kp, 0, sizeof(*kp));
-    int d = g.w + 1;
     if (d > kPolyMaxD - 1) d = kPolyMaxD - 1;
     kp->deg = d;
     const int K = 2 * d + 2;
     double xn[2 * kPolyMaxD + 2];
     for (int k = 0; k < K; ++k) xn[k] = std::cos(M_PI * (k + 0.5) / K);
     // monomial coefficients of the Chebyshev polynomials T_0..T_d
-    double T[kPolyMaxD][kPolyMaxD] = {};
-    T[0][0] = 1.0;
-    if (d >= 1) T[1][1] = 1.0;
+    double Tm[kPolyMaxD][kPolyMaxD] = {};
+    Tm[0][0] = 1.0;
+    if (d >= 1) Tm[1][1] = 1.0;
     for (int j = 2; j <= d; ++j)
         for (int m = 0; m <= d; ++m)
-            T[j][m] = (m > 0 ? 2.0 * T[j - 1][m - 1] : 0.0) - T[j - 2][m];
+            Tm[j][m] = (m > 0 ? 2.0 * Tm[j - 1][m - 1] : 0.0) - Tm[j - 2][m];
     for (int i = 0; i < g.w && i < kPolyMaxW; ++i) {
         double cheb[kPolyMaxD] = {};
         for (int k = 0; k < K; ++k) {
@@ -475,11 +475,14 @@ void fit_kernel_poly(const Geometry& g, KernelPoly* kp) {
         for (int j = 0; j <= d; ++j) cheb[j] *= (j == 0 ? 1.0 : 2.0) / K;
         for (int m = 0; m <= d; ++m) {
             double acc = 0.0;
-            for (int j = m; j <= d; ++j) acc += cheb[j] * T[j][m];
-            kp->c[i][m] = float(acc);
+            for (int j = m; j <= d; ++j) acc += cheb[j] * Tm[j][m];
+            kp->c[i][m] = T(acc);
         }
     }
 }
+
+void fit_kernel_poly(const Geometry& g, KernelPoly* kp) { fit_poly<KernelPoly, float>(g, g.w + 1, kp); }
+void fit_kernel_poly64(const Geometry& g, KernelPoly64* kp) { fit_poly<KernelPoly64, double>(g, kPolyMaxD - 1, kp); }
 
 void free_tables(HostTables* t) {
     delete[] t->t1x; delete[] t->t1y; delete[] t->t2x; delete[] t->t2y; delete[] t->t3x; delete[] t->t3y;

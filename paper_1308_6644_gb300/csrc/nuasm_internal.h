@@ -29,6 +29,12 @@ struct KernelPoly {
     float c[kPolyMaxW][kPolyMaxD];
     int deg;
 };
+// the same for FP64 gridding, always of degree kPolyMaxD - 1: the fit error
+// then sits at the kernel's own edge value (3.6e-14 for w = 13)
+struct KernelPoly64 {
+    double c[kPolyMaxW][kPolyMaxD];
+    int deg;
+};
 
 // Host tables in FP64 (complex as re/im pairs), natural N'-bin order.
 struct HostTables {
@@ -72,6 +78,7 @@ struct nuasm_plan_s {
     double rc = 0.0;            // z / (2 lambda)
     int nonsep_mode = 0;        // ASM non-separable phase: 0 none, 1 plain, 2 double-float
     nuasm::KernelPoly poly{};   // kernel taps as polynomials (F32 gridding)
+    nuasm::KernelPoly64 poly64{};   // the same in FP64 (F64 gridding)
     int64_t device_bytes = 0;
     nuasm::PlanDevice d;
     // profiling
@@ -100,6 +107,7 @@ void constant_factor(const nuasm_params_t& p, double* re, double* im);
 void twiddle(int i, int G, double* re, double* im);
 double nonsep_rmax(const nuasm_params_t& p, const Geometry& g);
 void fit_kernel_poly(const Geometry& g, KernelPoly* kp);
+void fit_kernel_poly64(const Geometry& g, KernelPoly64* kp);
 nuasm_status validate(const nuasm_params_t& p, int64_t m, nuasm_params_t* resolved);
 bool kernel_shape(double tol, int prec, int kernel, int* w, double* beta);
 double kernel_value(const Geometry& g, double t);
