@@ -138,19 +138,21 @@ class ClockSampler:
 def stage_bytes(info: dict, m: int, type_: int = 2, eb: int = 8) -> dict:
     """Algorithmic HBM bytes per launch of each stage (eb = 8 for complex64,
     16 for complex128): each input read once, each output written once,
-    records 16 B (24 B in FP64) per record."""
+    records 16 B (24 B in FP64) per record; the row pass also reads the
+    plan's table of the non-separable phase factor once, where it has one."""
     n, np_, W = info["n"], info["n_pad"], info["window"]
     rb = 16 if eb == 8 else 24
+    etab = info.get("phase_table_bytes", 0)
     if type_ == 1:
         return {
             "spread": (rb + eb) * info["records"] + eb * W * W,
             "col_fwd_fold": eb * (2 * W * W + np_ * W),
-            "row_t1": eb * (np_ * W + np_ * n),
+            "row_t1": eb * (np_ * W + np_ * n) + etab,
             "col_inv": eb * (np_ * n + n * n),
         }
     return {
         "col_fwd": eb * (n * n + np_ * n),
-        "row_t2": eb * (np_ * n + np_ * W),
+        "row_t2": eb * (np_ * n + np_ * W) + etab,
         "col_inv_fold": eb * (np_ * W + W * W),
         "interp": eb * W * W + (rb + eb) * m,
     }

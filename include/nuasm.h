@@ -115,6 +115,8 @@ typedef struct {
     int64_t points;            /* M */
     int64_t records;           /* binned records (points plus tile-halo duplicates) */
     int64_t device_bytes;      /* device memory owned by the plan */
+    int64_t phase_table_bytes; /* of which the tabulated non-separable ASM phase factor
+                                  (Eq. 4; 0 when the plan evaluates it per mode) */
 } nuasm_plan_info_t;
 
 /*
@@ -139,7 +141,11 @@ typedef struct {
  * range, pitch/lambda <= 0, Fresnel with z == 0, m < 0, NULL coordinates with
  * m > 0, tol outside (0, 0.1]), NUASM_ERANGE if any point is outside the
  * window, NUASM_ENOMEM, NUASM_ECUDA.  The plan allocates all the device memory
- * its execute calls will need.
+ * its execute calls will need.  For the ASM with z != 0 that includes a table
+ * of the transfer function's non-separable phase factor over |kx|, |ky| in
+ * [0, N'/2] (about N'^2/4 complex values in the plan precision, computed in
+ * FP64 during the call), which the execute calls read instead of evaluating a
+ * square root and a sine/cosine per mode.
  */
 nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m,
                         const double* x, const double* y, const double* w, void* stream);

@@ -130,8 +130,8 @@ void nuasm::plan_release(nuasm_plan_s* P) {
                 }
         delete X;
     }
-    void* ptrs[] = {P->d.tables, P->d.rec, P->d.wpt, P->d.tile_off, P->d.tile_home, P->d.tile_order,
-                    P->d.win, P->d.bufA, P->d.bufB, P->d.stage_in, P->d.stage_out, P->d.err};
+    void* ptrs[] = {P->d.tables, P->d.etab, P->d.rec, P->d.wpt, P->d.tile_off, P->d.tile_home,
+                    P->d.tile_order, P->d.win, P->d.bufA, P->d.bufB, P->d.stage_in, P->d.stage_out, P->d.err};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete P;
@@ -376,6 +376,12 @@ nuasm_status nuasm::plan_create(nuasm_plan_s** out, const nuasm_params_t* p, int
         if ((e = dalloc(P, &P->d.bufB, ws_bufB_elems(g) * eb)) != cudaSuccess) return bail(cuda_status(e));
         if ((e = dalloc(P, &P->d.stage_in, stage)) != cudaSuccess) return bail(cuda_status(e));
         if ((e = dalloc(P, &P->d.stage_out, stage)) != cudaSuccess) return bail(cuda_status(e));
+        if (P->nonsep_mode != 0) {
+            // the plan's transfer function is fixed: tabulate its non-separable factor once
+            const size_t ne = etab_elems(g, &P->etab_pitch);
+            if ((e = dalloc(P, &P->d.etab, ne * eb)) != cudaSuccess) return bail(cuda_status(e));
+            if ((e = build_etab(P, st)) != cudaSuccess) return bail(cuda_status(e));
+        }
     }
     if ((e = dalloc(P, &P->d.tile_off, sizeof(int) * (g.ntiles + 1))) != cudaSuccess) return bail(cuda_status(e));
     if ((e = dalloc(P, &P->d.tile_home, sizeof(int) * g.ntiles)) != cudaSuccess) return bail(cuda_status(e));
@@ -558,6 +564,9 @@ nuasm_status nuasm_plan_info(nuasm_plan_t plan, nuasm_plan_info_t* info) {
     info->points = plan->m;
     info->records = plan->nrec;
     info->device_bytes = plan->device_bytes;
+    int pitch = 0;
+    info->phase_table_bytes =
+        plan->d.etab ? int64_t(etab_elems(plan->g, &pitch) * (plan->f64 ? 16 : 8)) : 0;
     return NUASM_OK;
 }
 

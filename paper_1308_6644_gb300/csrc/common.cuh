@@ -19,6 +19,16 @@ namespace nuasm {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
+// 16-byte asynchronous global -> shared copies (both addresses 16-byte aligned).
+// The issuing thread waits with cp_async_wait_all; a barrier after that wait
+// makes the data visible to the block.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Off by default: measured on the NU-ASM_2 N = 1024 chain it cost 3.5 us per
 // solve (131.1 -> 134.6 us) and changed nothing at N = 2048 or in batches.
 #ifndef NUASM_PDL

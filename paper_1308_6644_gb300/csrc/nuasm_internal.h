@@ -53,6 +53,8 @@ struct PlanDevice {
     void* t3x = nullptr; void* t3y = nullptr;
     void* s = nullptr;          // float2 (hi, lo) per bin (F32) or double (F64)
     void* tw = nullptr;         // twiddles, G complex
+    void* etab = nullptr;       // ASM non-separable factor E(|kx|, |ky|): N'/2 + 1 rows of etab_pitch
+                                // entries in the plan precision (null: evaluated per mode)
     void* rec = nullptr;        // binned point records
     double* wpt = nullptr;      // optional per-point weights, in point order
     int* tile_off = nullptr;    // ntiles + 1 offsets into rec
@@ -77,6 +79,7 @@ struct nuasm_plan_s {
     bool f64 = false;
     double rc = 0.0;            // z / (2 lambda)
     int nonsep_mode = 0;        // ASM non-separable phase: 0 none, 1 plain, 2 double-float
+    int etab_pitch = 0;         // entries per row of d.etab
     nuasm::KernelPoly poly{};   // kernel taps as polynomials (F32 gridding)
     nuasm::KernelPoly64 poly64{};   // the same in FP64 (F64 gridding)
     int64_t device_bytes = 0;
@@ -157,6 +160,9 @@ cudaError_t launch_col_inv(const nuasm_plan_s* P, void* u2, cudaStream_t s);
 cudaError_t launch_col_fwd(const nuasm_plan_s* P, const void* u1, cudaStream_t s);
 cudaError_t launch_row_t2(const nuasm_plan_s* P, cudaStream_t s);
 cudaError_t launch_row_t3(const nuasm_plan_s* P, cudaStream_t s);
+// Fill P->d.etab (etab_elems entries, pitch P->etab_pitch) with the ASM non-separable factor.
+size_t etab_elems(const Geometry& g, int* pitch);
+cudaError_t build_etab(const nuasm_plan_s* P, cudaStream_t s);
 cudaError_t launch_col_inv_fold(const nuasm_plan_s* P, cudaStream_t s);
 
 }  // namespace nuasm

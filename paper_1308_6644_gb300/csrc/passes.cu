@@ -2,8 +2,10 @@
 // passes_{row,col}_{f32,f64}.cu).
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
+#include "common.cuh"
 #include "nuasm_internal.h"
 #include "tma.cuh"
 
@@ -57,6 +59,51 @@ cudaError_t launch_row_t2(const nuasm_plan_s* P, cudaStream_t s) {
 }
 cudaError_t launch_row_t3(const nuasm_plan_s* P, cudaStream_t s) {
     return P->f64 ? row_f64(P, 3, s) : row_f32(P, 3, s);
+}
+
+// The non-separable part of the ASM phase (Eq. 4), E = exp(-2 pi i rc Q(s)^2),
+// Q(s) = s / (1 + sqrt(1 - s)), s = lambda^2 |f|^2, tabulated once per plan in
+// FP64 for |kx| = a and |ky| = b in [0, N'/2] (s = c (a^2 + b^2),
+// c = (lambda / (N' pitch))^2); evanescent modes (s >= 1) hold 0.  Row b holds
+// `pitch` entries (N'/2 + 1 rounded up to even, so rows start 16-byte aligned).
+size_t etab_elems(const Geometry& g, int* pitch) {
+    const int half = g.np / 2;
+    *pitch = (half + 2) & ~1;
+    return size_t(half + 1) * size_t(*pitch);
+}
+
+namespace {
+template <typename V>
+__global__ void etab_kernel(V* __restrict__ out, int half, int pitch, double c, double rc) {
+    const int64_t total = int64_t(half + 1) * pitch;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int b = int(i / pitch), a = int(i - int64_t(b) * pitch);
+        double re = 0.0, im = 0.0;
+        if (a <= half) {
+            const double sv = c * (double(a) * a + double(b) * b);
+            if (sv < 1.0) {
+                const double q = sv / (1.0 + sqrt(1.0 - sv));
+                const double r = rc * q * q;
+                sincospi(-2.0 * (r - rint(r)), &im, &re);
+            }
+        }
+        out[i] = CTraits<V>::make(re, im);
+    }
+}
+}  // namespace
+
+cudaError_t build_etab(const nuasm_plan_s* P, cudaStream_t s) {
+    int pitch = 0;
+    const size_t n = etab_elems(P->g, &pitch);
+    if (!P->d.etab || pitch != P->etab_pitch) return cudaErrorInvalidValue;
+    const double k = P->p.lambda / (double(P->g.np) * P->p.pitch);
+    const int threads = 256;
+    const int blocks = int(std::min<size_t>((n + threads - 1) / threads, size_t(152) * 8));
+    if (P->f64)
+        etab_kernel<<<blocks, threads, 0, s>>>(static_cast<double2*>(P->d.etab), P->g.np / 2, pitch, k * k, P->rc);
+    else
+        etab_kernel<<<blocks, threads, 0, s>>>(static_cast<float2*>(P->d.etab), P->g.np / 2, pitch, k * k, P->rc);
+    return cudaGetLastError();
 }
 
 }  // namespace nuasm

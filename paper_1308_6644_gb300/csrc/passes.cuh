@@ -93,6 +93,9 @@ struct RowArgs {
     int nonsep;            // 0: none (Fresnel, z = 0); 1: plain (FP32 or FP64); 2: double-float FP32
     double rc;             // z / (2 lambda)
     float rc_hi, rc_lo;
+    const void* etab;      // E(|kx|, |ky|) table of the plan precision, or null (E evaluated per mode)
+    int ep;                // entries per table row
+    int np;                // N'
 };
 
 struct ColArgs {
@@ -136,30 +139,57 @@ __device__ __forceinline__ double2 nonsep_factor(double sa, double sb, const Row
 }
 
 // Tx(q) Ty(r) E(q, r): the per-mode factor applied between the row transforms.
-// A row's Ty(r) and s(r) are loaded once per row (RowConst) and passed in.
+// A row's Ty(r) and s(r) (or its row of the E table) are loaded once per row
+// (RowConst) and passed in.  E depends on |f|^2 only, so the table holds the
+// quadrant |kx|, |ky| in [0, N'/2]; natural bin q maps to |k| = min(q, N' - q).
 template <typename V> struct RowConst {
     V ty;
     typename STable<V>::type s;
+    const V* erow;
 };
 
 template <typename V>
 __device__ __forceinline__ RowConst<V> row_const(int r, const V* __restrict__ ty,
-                                                 const typename STable<V>::type* __restrict__ s) {
-    return RowConst<V>{__ldg(&ty[r]), __ldg(&s[r])};
+                                                 const typename STable<V>::type* __restrict__ s, const RowArgs& a) {
+    const V* erow = nullptr;
+    if (a.etab) erow = static_cast<const V*>(a.etab) + size_t(min(r, a.np - r)) * a.ep;
+    return RowConst<V>{__ldg(&ty[r]), __ldg(&s[r]), erow};
 }
 
 template <typename V>
 __device__ __forceinline__ V mode_factor(int q, const RowConst<V>& rc, const V* __restrict__ tx,
                                          const typename STable<V>::type* __restrict__ s, const RowArgs& a) {
     V f = cmul(__ldg(&tx[q]), rc.ty);
-    if (a.nonsep && (f.x != 0 || f.y != 0)) f = cmul(f, nonsep_factor(__ldg(&s[q]), rc.s, a));
+    if (rc.erow) {
+        f = cmul(f, __ldg(&rc.erow[min(q, a.np - q)]));   // both loads in flight together
+    } else if (a.nonsep && (f.x != 0 || f.y != 0)) {
+        f = cmul(f, nonsep_factor(__ldg(&s[q]), rc.s, a));
+    }
     return f;
 }
 
 template <typename V>
 __device__ __forceinline__ V mode_factor(int q, int r, const V* __restrict__ tx, const V* __restrict__ ty,
                                          const typename STable<V>::type* __restrict__ s, const RowArgs& a) {
-    return mode_factor<V>(q, row_const<V>(r, ty, s), tx, s, a);
+    return mode_factor<V>(q, row_const<V>(r, ty, s, a), tx, s, a);
+}
+
+// Copy the E-table rows of the CTA's rows r0 .. r0 + ROWS - 1 to shared memory at
+// `dst` (ep entries per row) with cp.async.  Returns false (nothing issued) when
+// the plan has no table or `dst` is not 16-byte aligned; the decision is the
+// same for every thread of the block.
+template <typename V, int ROWS>
+__device__ __forceinline__ bool stage_erows(V* dst, int r0, const RowArgs& a) {
+    if (!a.etab || (reinterpret_cast<uintptr_t>(dst) & 15)) return false;
+    const int chunks = int((size_t(a.ep) * sizeof(V)) / 16);   // ep * sizeof(V) is a multiple of 16
+    for (int i = threadIdx.x; i < ROWS * chunks; i += blockDim.x) {
+        const int c = i / chunks, k = i - c * chunks;
+        const int rr = min(r0 + c, a.np - r0 - c);
+        const char* src = static_cast<const char*>(a.etab) + size_t(rr) * a.ep * sizeof(V) + 16 * size_t(k);
+        cp_async16(reinterpret_cast<char*>(dst) + size_t(c) * a.ep * sizeof(V) + 16 * size_t(k), src);
+    }
+    cp_async_commit();
+    return true;
 }
 
 // the factor of mode q in the CTA's row `row` (ROWS == 1: the constants held in registers)
@@ -188,7 +218,7 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     const int W = a.W, Wp = a.Wp;
     const V zero = CTraits<V>::zero();
     pdl_allow_next();
-    const RowConst<V> rc0 = row_const<V>(r0, ty, s);
+    const RowConst<V> rc0 = row_const<V>(r0, ty, s, a);
     pdl_wait();   // A comes from the previous kernel
 
     auto folded = [&](int row, int p, int sgn) -> V {
@@ -239,11 +269,30 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     const int n = a.n, W = a.W, Wp = a.Wp;
     const V zero = CTraits<V>::zero();
     pdl_allow_next();
-    const RowConst<V> rc0 = row_const<V>(r0, ty, s);
+    const RowConst<V> rc0 = row_const<V>(r0, ty, s, a);
+    // With merged inverse engines S holds 2 ROWS sequences and the forward
+    // transform uses the first ROWS: the E rows are staged behind them while it
+    // runs (waited for after its first pass, whose successors synchronise).
+    static_assert(LOGNP > 3, "the staged E rows need a forward transform of at least two passes");
+    V* Es = S + ((spad_size<V>(NP * ROWS) + 1) & ~1);
+    bool staged = false;
+    if constexpr (Cf::MERGE) staged = stage_erows<V, ROWS>(Es, r0, a);
     pdl_wait();   // B comes from the previous kernel
     block_fft<V, -1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
         S, tw, [&](int p, int c) { return p < n ? B[(r0 + c) * n + p] : zero; },
-        [&](int p, int c, V v) { M[c * NP + p] = cmul(v, row_factor<V, ROWS>(p, c, r0, rc0, tx, ty, s, a)); });
+        [&](int p, int c, V v) {
+            V f;
+            if (staged) {
+                const V t = ROWS == 1 ? rc0.ty : __ldg(&ty[r0 + c]);
+                f = cmul(cmul(__ldg(&tx[p]), t), Es[c * a.ep + min(p, NP - p)]);
+            } else {
+                f = row_factor<V, ROWS>(p, c, r0, rc0, tx, ty, s, a);
+            }
+            M[c * NP + p] = cmul(v, f);
+        },
+        [&] {
+            if (staged) cp_async_wait_all();
+        });
     __syncthreads();
     auto get = [&](int row, int q, int sgn) -> V {
         const V y = M[row * NP + q];
@@ -287,7 +336,7 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     const int W = a.W, Wp = a.Wp;
     const V zero = CTraits<V>::zero();
     pdl_allow_next();
-    const RowConst<V> rc0 = row_const<V>(r0, ty, s);
+    const RowConst<V> rc0 = row_const<V>(r0, ty, s, a);
     pdl_wait();   // A comes from the previous kernel
     auto folded = [&](int row, int p, int sgn) -> V {
         const V* x = A + (r0 + row) * Wp;
@@ -578,6 +627,9 @@ inline RowArgs row_args(const nuasm_plan_s* P) {
     a.rc = P->rc;
     a.rc_hi = float(P->rc);
     a.rc_lo = float(P->rc - double(a.rc_hi));
+    a.etab = P->d.etab;
+    a.ep = P->etab_pitch;
+    a.np = P->g.np;
     return a;
 }
 

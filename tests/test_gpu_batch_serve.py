@@ -1,11 +1,15 @@
 """Batched planes (one CUDA graph over many plans) and the serving loop
 (continuous batching with resident point sets), through the C ABI.
 
-Each result is checked against the same solve run alone through the plain
-entry points (nuasm_plan + nuasm*_execute) and, for a sample, against the FP64
-oracle.  Type 2 runs are deterministic and must agree bit for bit; type 1
-spreading accumulates with shared-memory atomics whose order varies, so type 1
-results agree to rounding (rel-L2 1e-6 in FP32, 1e-13 in FP64)."""
+A batch item is checked against the same solve run alone through the plain
+entry points (nuasm_plan + nuasm*_execute), a served request against the same
+request served alone, and both, for a sample, against the FP64 oracle.  Type 2
+runs are deterministic and must agree bit for bit; type 1 spreading
+accumulates with shared-memory atomics whose order varies, so type 1 results
+agree to rounding (rel-L2 1e-6 in FP32, 1e-13 in FP64).  A served request and
+the plain path agree within the parity tolerance (1e-5 FP32, 1e-10 FP64): a
+plan tabulates the non-separable ASM phase factor, a request evaluates it per
+mode."""
 import numpy as np
 import pytest
 
@@ -209,7 +213,26 @@ def _requests(P):
     return reqs
 
 
+def _served_alone(P, reqs):
+    """Each request through a one-slot server with nothing else in flight."""
+    outs = []
+    srv = P.nuasm_server_create(slots=1)
+    try:
+        for r in reqs:
+            out = np.zeros_like(r["out"])
+            t = P.nuasm_server_submit(srv, r["params"], r["type"], r["x"], r["y"], r["inp"], out,
+                                      points_id=r["id"])
+            assert P.nuasm_server_wait(srv, t, 120.0)["status"] == 0
+            outs.append(out)
+    finally:
+        srv.destroy()
+    return outs
+
+
 def _alone(P, r):
+    """The request on the plain path: its own plan and one execute.  A plan
+    tabulates the non-separable ASM phase factor once, a served request
+    evaluates it per mode, so the two agree within the parity tolerance."""
     plan = P.nuasm_plan(r["params"], r["x"], r["y"])
     try:
         out = np.zeros_like(r["out"])
@@ -222,8 +245,12 @@ def _alone(P, r):
 
 
 def test_server_results_alone_and_in_the_mix(P):
+    """Every served result equals the same request served alone (bit for bit
+    for type 2; type 1 sums in floating point atomically) and the plain path
+    within the parity tolerance."""
     reqs = _requests(P)
-    alone = [_alone(P, r) for r in reqs]
+    plain = [_alone(P, r) for r in reqs]
+    alone = _served_alone(P, reqs)
     srv = P.nuasm_server_create(slots=4)
     try:
         tickets = [P.nuasm_server_submit(srv, r["params"], r["type"], r["x"], r["y"], r["inp"], r["out"],
@@ -232,9 +259,10 @@ def test_server_results_alone_and_in_the_mix(P):
         st = P.nuasm_server_stats(srv)
     finally:
         srv.destroy()
-    for r, res, a in zip(reqs, results, alone):
+    for r, res, a, q in zip(reqs, results, alone, plain):
         assert res["status"] == 0
         assert _same(r["out"], a, r["prec"], r["type"]), (r["id"], r["kind"], r["type"])
+        assert O.rel_l2(r["out"], q) < TOL[r["prec"]], (r["id"], r["kind"], r["type"])
     assert st["completed"] == len(reqs) and st["failed"] == 0
     kept = {r["id"] for r in reqs if r["id"]}
     unkept = sum(1 for r in reqs if not r["id"])
@@ -278,8 +306,10 @@ def test_server_evicts_under_a_small_budget(P):
         srv.destroy()
     assert all(res["status"] == 0 for res in results)
     assert st["evictions"] > 0 and st["bins_built"] > 6
-    for r in reqs[:3] + reqs[-3:]:
-        assert np.array_equal(r["out"], _alone(P, r))
+    again = _served_alone(P, reqs[:3] + reqs[-3:])
+    for r, a in zip(reqs[:3] + reqs[-3:], again):
+        assert np.array_equal(r["out"], a)
+        assert O.rel_l2(r["out"], _alone(P, r)) < TOL["f32"]
 
 
 def test_server_device_arrays_and_out_of_window_points(P):
@@ -311,7 +341,7 @@ def test_server_device_arrays_and_out_of_window_points(P):
         torch.cuda.synchronize()
     finally:
         plan.destroy()
-    assert np.array_equal(out_d.cpu().numpy(), ref.cpu().numpy())
+    assert O.rel_l2(out_d.cpu().numpy(), ref.cpu().numpy()) < TOL["f32"]
 
 
 def test_server_accepts_requests_from_several_threads(P):
@@ -319,7 +349,7 @@ def test_server_accepts_requests_from_several_threads(P):
     request solved alone."""
     import threading
     reqs = _requests(P)[:12]
-    alone = [_alone(P, r) for r in reqs]
+    alone = _served_alone(P, reqs)
     srv = P.nuasm_server_create(slots=3)
     errors = []
 

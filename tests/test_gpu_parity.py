@@ -144,6 +144,50 @@ def test_explicit_band_and_larger_padding(P, type_):
     assert O.rel_l2(got, ref) < TOL["f64"]
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("type_", [1, 2])
+def test_tabulated_phase_factor_large_phase(P, prec, type_):
+    """Eq. 4 with the full mode set kept (explicit band) and a non-separable
+    phase rc Q(s)^2 of about 1.6 cycles at the corner modes: the plan's FP64
+    table of that factor against the oracle, and (F32, type 2) against the
+    no-allocation path, which evaluates the factor per mode in double-float
+    FP32."""
+    import torch
+    n, m = 64, 900
+    x, y, vals = random_case(41 + type_, n, m, pitch=4e-6, type_=type_)
+    kw = dict(pitch=4e-6, lam=633e-9, z=0.05, ox=20e-6, oy=-8e-6, band=(0.0, 0.0, 128.0, 128.0))
+    got = run_gpu(P, "asm", type_, prec, n, x=x, y=y, values=vals, **kw)
+    ref = run_oracle("asm", type_, n, x=x, y=y, values=vals, prec=prec, **kw)
+    assert O.rel_l2(got, ref) < TOL[prec]
+    params = P.make_params(n, kw["pitch"], kw["lam"], kw["z"], ox=kw["ox"], oy=kw["oy"], band=kw["band"], prec=prec)
+    plan = P.nuasm_plan(params, _t(x), _t(y))
+    try:
+        half = 64
+        assert plan.info()["phase_table_bytes"] == (half + 1) * (half + 2) * (8 if prec == "f32" else 16)
+    finally:
+        plan.destroy()
+    if prec == "f32" and type_ == 2:
+        v = torch.zeros(m, dtype=torch.complex64, device="cuda")
+        P.nuasm2_solve_noalloc(params, _t(x), _t(y), _t(np.asarray(vals, np.complex64).reshape(-1)), v)
+        torch.cuda.synchronize()
+        per_mode = v.cpu().numpy()
+        assert O.rel_l2(per_mode, ref) < TOL["f32"]
+        assert O.rel_l2(per_mode, got) < TOL["f32"]
+
+
+def test_phase_table_only_where_the_phase_is_not_separable(P):
+    x, y, _ = random_case(5, 32, 100)
+    for kind, z, expect in (("asm", 0.03, True), ("asm", 0.0, False), ("fresnel", 0.03, False)):
+        params = P.make_params(32, 10e-6, 633e-9, z, kind=kind)
+        plan = P.nuasm_plan(params, _t(x), _t(y))
+        try:
+            info = plan.info()
+            assert (info["phase_table_bytes"] > 0) == expect
+            assert info["device_bytes"] > info["phase_table_bytes"]
+        finally:
+            plan.destroy()
+
+
 def test_window_edges_and_single_tile(P):
     """Points exactly on the lower window edge, just inside the upper edge and
     all crowded into one tile."""
