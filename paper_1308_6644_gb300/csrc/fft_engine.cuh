@@ -23,6 +23,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "nuasm_internal.h"
 
 namespace nuasm {
 
@@ -121,25 +122,36 @@ template <int R> struct Log2 { static constexpr int v = R <= 1 ? 0 : 1 + Log2<R 
 template <> struct Log2<1> { static constexpr int v = 0; };
 
 // ---------------------------------------------------------------- twiddle powers
-// w[r] = exp(-2 pi i k r / (Ns R)) = tw[(k r) << sh] for r in [1, R).  FP64
-// reads every power from the table; FP32 reads w^1 and w^4 (w^1 and w^2 for
-// R = 4) and forms the others by complex products (at most four roundings,
-// about 2.4e-7 relative), which trades table loads for FMA-pipe work.  The
-// table reads are split from the products (twiddle_base / twiddle_powers) so
-// a pass can issue them before its barrier.
+// w[r] = exp(-2 pi i k r / (Ns R)) for r in [1, R).  FP64 reads every power;
+// FP32 reads w^1 and w^4 (w^1 and w^2 for R = 4) and forms the others by
+// complex products (at most four roundings, about 2.4e-7 relative), which
+// trades table loads for FMA-pipe work.  The reads come from the pass's own
+// compact table (the pass twiddles that follow the full 2L-entry table; the
+// layout is given with twp_pass_offset): one butterfly group's bases are
+// adjacent, so FP32 reads them with one 16-byte load and a pass's table is a
+// few KB of L1.  The table reads are split from the products (twiddle_base /
+// twiddle_powers) so a pass can issue them before its barrier.
 template <typename V, int R> struct TwBase {
     static constexpr int N = (sizeof(V) == 16 || R == 2) ? R - 1 : 2;
     V t[N > 0 ? N : 1];
 };
 
+// offset of a pass's table from the start of the full table
+template <typename V, int LE, int LOGL, int PASS> struct TwpOffset {
+    static_assert(LE == 3 || LE == 4, "pass twiddles exist for the radix-8 and radix-16 schedules");
+    static constexpr int v = (2 << LOGL) + twp_pass_offset(sizeof(V) == 16, LE, LOGL, PASS);
+};
+
 template <typename V, int R>
-__device__ __forceinline__ void twiddle_base(const V* __restrict__ tw, int k, int sh, TwBase<V, R>& b) {
-    if constexpr (sizeof(V) == 16 || R == 2) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) b.t[r - 1] = __ldg(&tw[(k * r) << sh]);
+__device__ __forceinline__ void twiddle_base(const V* __restrict__ tp, int k, TwBase<V, R>& b) {
+    constexpr int N = TwBase<V, R>::N;
+    if constexpr (sizeof(V) == 8 && N == 2) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(tp) + k);
+        b.t[0] = CTraits<V>::make(q.x, q.y);
+        b.t[1] = CTraits<V>::make(q.z, q.w);
     } else {
-        b.t[0] = __ldg(&tw[k << sh]);
-        b.t[1] = __ldg(&tw[((R == 4 ? 2 : 4) * k) << sh]);
+#pragma unroll
+        for (int r = 0; r < N; ++r) b.t[r] = __ldg(&tp[k * N + r]);
     }
 }
 
@@ -169,7 +181,8 @@ __device__ __forceinline__ void twiddle_powers(const TwBase<V, R>& b, V* w) {
 }
 
 // ---------------------------------------------------------------- one pass
-// Twiddle table: tw[t] = exp(-2 pi i t / 2L), t in [0, 2L).
+// Twiddle table: tw[t] = exp(-2 pi i t / 2L), t in [0, 2L), followed by the
+// pass twiddles of the radix-8 and radix-16 schedules.
 template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, int LR, int LOGNS, bool FIRST,
           bool LAST, class LoadF, class StoreF>
 __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __restrict__ tw, LoadF& load,
@@ -181,7 +194,10 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
     constexpr int NS = 1 << LOGNS;
     constexpr int C = 1 << LOGC;
     constexpr int P = (L * C) / E;
-    constexpr int SH = LOGL + 1 - LOGNS - LR;
+    constexpr int LE = Log2<E>::v;
+    static_assert(LOGNS % LE == 0, "passes start at multiples of the schedule's radix");
+    const V* __restrict__ tp = tw;
+    if constexpr (LOGNS > 0) tp = tw + TwpOffset<V, LE, LOGL, LOGNS / LE>::v;
     const int tid = threadIdx.x;
     V v[E];
     int jj[NB], cc[NB];
@@ -194,7 +210,7 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
         else { c = beta & (C - 1); j = beta >> LOGC; }
         jj[b] = j;
         cc[b] = c;
-        if constexpr (LOGNS > 0) twiddle_base<V, R>(tw, j & (NS - 1), SH, twb[b]);   // in flight across the barrier
+        if constexpr (LOGNS > 0) twiddle_base<V, R>(tp, j & (NS - 1), twb[b]);   // in flight across the barrier
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int p = j + r * LDR;

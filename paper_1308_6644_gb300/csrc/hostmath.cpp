@@ -407,9 +407,43 @@ void build_tables(const nuasm_params_t& p, const Geometry& g, HostTables* t, con
         for (int i = 0; i < G; ++i) twiddle(i, G, &t->tw[2 * i], &t->tw[2 * i + 1]);
 }
 
+namespace {
+int log2_of(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+}  // namespace
+
 size_t table_bytes(const Geometry& g, bool f64, bool with_twiddles) {
     const size_t eb = f64 ? 16 : 8, sb = f64 ? sizeof(double) : 2 * sizeof(float);
-    return 6 * size_t(g.np) * eb + size_t(g.np) * sb + (with_twiddles ? size_t(g.G) * eb : 0);
+    const size_t tw = with_twiddles ? size_t(g.G) + size_t(twp_entries(f64, log2_of(g.np))) : 0;
+    return 6 * size_t(g.np) * eb + size_t(g.np) * sb + tw * eb;
+}
+
+void pack_twp(const double* tw, int logl, bool f64, void* dst) {
+    size_t idx = 0;
+    for (int le = 3; le <= 4; ++le) {
+        const int nfull = logl / le, rem = logl % le, npass = nfull + (rem ? 1 : 0);
+        for (int i = 1; i < npass; ++i) {
+            const int lr = i < nfull ? le : rem, ns = 1 << (i * le);
+            const int cnt = twp_per_k(f64, lr), sh = logl + 1 - i * le - lr;
+            for (int k = 0; k < ns; ++k)
+                for (int n = 0; n < cnt; ++n, ++idx) {
+                    const int pw = f64 ? n + 1 : (n == 0 ? 1 : (lr == 2 ? 2 : 4));
+                    const size_t t = size_t(k * pw) << sh;
+                    if (f64) {
+                        double* d = static_cast<double*>(dst);
+                        d[2 * idx] = tw[2 * t];
+                        d[2 * idx + 1] = tw[2 * t + 1];
+                    } else {
+                        float* d = static_cast<float*>(dst);
+                        d[2 * idx] = float(tw[2 * t]);
+                        d[2 * idx + 1] = float(tw[2 * t + 1]);
+                    }
+                }
+        }
+    }
 }
 
 // Device image of the tables: T1x T1y T2x T2y T3x T3y (complex, plan precision),
@@ -437,7 +471,11 @@ void pack_tables(const HostTables& t, const Geometry& g, bool f64, bool with_twi
             d[2 * i + 1] = float(t.s[i] - double(hi));
         }
     }
-    if (with_twiddles && t.tw) put_c(soff + size_t(np) * (f64 ? sizeof(double) : 2 * sizeof(float)), t.tw, g.G);
+    if (with_twiddles && t.tw) {
+        const size_t toff = soff + size_t(np) * (f64 ? sizeof(double) : 2 * sizeof(float));
+        put_c(toff, t.tw, g.G);
+        pack_twp(t.tw, log2_of(np), f64, out + toff + size_t(g.G) * eb);
+    }
 }
 
 int choose_nonsep_mode(const nuasm_params_t& p, double rmax) {

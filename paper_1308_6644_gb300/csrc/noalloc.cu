@@ -111,7 +111,10 @@ extern "C" nuasm_status nuasm2_solve_noalloc(const nuasm_params_t* p, int64_t m,
     const Geometry& g = P.g;
     const int np = g.np;
     Carve cv{base};
-    float2* tables = static_cast<float2*>(cv.take(sizeof(float2) * (4 * size_t(np) + np + g.G)));
+    int logl = 0;
+    while ((1 << logl) < np) ++logl;
+    const size_t ntw = size_t(g.G) + size_t(twp_entries(false, logl));   // full table, then pass twiddles
+    float2* tables = static_cast<float2*>(cv.take(sizeof(float2) * (4 * size_t(np) + np + ntw)));
     P.d.t1x = tables;
     P.d.t1y = tables + np;
     P.d.t2x = tables + 2 * np;
@@ -131,7 +134,10 @@ extern "C" nuasm_status nuasm2_solve_noalloc(const nuasm_params_t* p, int64_t m,
     if (cv.used > kScratchBytes) return NUASM_EUNSUPPORTED;
 
     // type-2 tables (Eq. 4 separable part, deconvolution, twiddles), built on the stack
-    float2 host[4 * kMaxNp + kMaxNp + 2 * kMaxNp];
+    constexpr int kMaxLog = 9;   // log2(kMaxNp)
+    static_assert((1 << kMaxLog) == kMaxNp, "kMaxLog");
+    float2 host[4 * kMaxNp + kMaxNp + 2 * kMaxNp + twp_entries(false, kMaxLog)];
+    double twd[2 * 2 * kMaxNp];
     std::memset(host, 0, sizeof(host));
     KernelQuad qd;
     make_quad(g, &qd);
@@ -153,16 +159,16 @@ extern "C" nuasm_status nuasm2_solve_noalloc(const nuasm_params_t* p, int64_t m,
         host[4 * np + q] = make_float2(hi, float(sv - double(hi)));
     }
     for (int i = 0; i < g.G; ++i) {
-        double re, im;
-        twiddle(i, g.G, &re, &im);
-        host[5 * np + i] = make_float2(float(re), float(im));
+        twiddle(i, g.G, &twd[2 * i], &twd[2 * i + 1]);
+        host[5 * np + i] = make_float2(float(twd[2 * i]), float(twd[2 * i + 1]));
     }
+    pack_twp(twd, logl, false, host + 5 * np + g.G);
     P.rc = rp.z / (2.0 * rp.lambda);
     const double rmax = nonsep_rmax(rp, g);
     P.nonsep_mode = (rp.z == 0.0) ? 0 : (rmax <= 0.5 ? 1 : 2);
     fit_kernel_poly(g, &P.poly);
     // pageable source: the copy is staged before the call returns, so the stack buffer may go
-    e = cudaMemcpyAsync(tables, host, sizeof(float2) * (5 * size_t(np) + g.G), cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(tables, host, sizeof(float2) * (5 * size_t(np) + ntw), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return status_of(e);
 
     if ((e = bin_points_into(&P, x, y, cnt, rec_tmp, st)) != cudaSuccess) return status_of(e);

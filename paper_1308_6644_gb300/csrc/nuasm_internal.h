@@ -125,6 +125,34 @@ void phihat_table(const Geometry& g, double* out);
 void free_tables(HostTables* t);
 size_t table_bytes(const Geometry& g, bool f64, bool with_twiddles);
 void pack_tables(const HostTables& t, const Geometry& g, bool f64, bool with_twiddles, void* dst);
+
+// Pass twiddles.  The full twiddle table tw[t] = exp(-2 pi i t / 2N'),
+// t < 2N', is followed by the twiddle bases of every pass I >= 1 of the
+// radix-8 and then the radix-16 Stockham schedule of an N'-point transform
+// (fft_engine.cuh): for each butterfly group k < NS = 2^(I log2 E), the
+// twp_per_k entries a butterfly of radix R = 2^lr loads, contiguous
+// (FP64: w^k .. w^((R-1)k); FP32: w^k and w^4k, w^k and w^2k for R = 4, w^k
+// for R = 2; w = exp(-2 pi i / (NS R))).  One group's entries are one load.
+constexpr int twp_per_k(bool f64, int lr) { return (f64 || lr == 1) ? (1 << lr) - 1 : 2; }
+constexpr int twp_sched_entries(bool f64, int le, int logl) {
+    const int nfull = logl / le, rem = logl % le, npass = nfull + (rem ? 1 : 0);
+    int n = 0;
+    for (int i = 1; i < npass; ++i) n += (1 << (i * le)) * twp_per_k(f64, i < nfull ? le : rem);
+    return n;
+}
+// entries before pass `pass` of the radix-2^le schedule (le = 3 or 4)
+constexpr int twp_pass_offset(bool f64, int le, int logl, int pass) {
+    const int nfull = logl / le, rem = logl % le;
+    int off = le == 4 ? twp_sched_entries(f64, 3, logl) : 0;
+    for (int i = 1; i < pass; ++i) off += (1 << (i * le)) * twp_per_k(f64, i < nfull ? le : rem);
+    return off;
+}
+constexpr int twp_entries(bool f64, int logl) {
+    return twp_sched_entries(f64, 3, logl) + twp_sched_entries(f64, 4, logl);
+}
+// Gather the pass twiddles (twp_entries complex values in the plan precision)
+// from the full table `tw` (2^(logl+1) complex doubles, interleaved).
+void pack_twp(const double* tw, int logl, bool f64, void* dst);
 // ASM non-separable phase evaluation: 0 none, 1 plain, 2 double-float
 int choose_nonsep_mode(const nuasm_params_t& p, double rmax);
 
