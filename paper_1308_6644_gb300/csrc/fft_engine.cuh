@@ -183,8 +183,8 @@ __device__ __forceinline__ void twiddle_powers(const TwBase<V, R>& b, V* w) {
 // ---------------------------------------------------------------- one pass
 // Twiddle table: tw[t] = exp(-2 pi i t / 2L), t in [0, 2L), followed by the
 // pass twiddles of the radix-8 and radix-16 schedules.
-template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, int LR, int LOGNS, bool FIRST,
-          bool LAST, class LoadF, class StoreF>
+template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, bool SYNC_FIRST, int LR, int LOGNS,
+          bool FIRST, bool LAST, class LoadF, class StoreF>
 __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __restrict__ tw, LoadF& load,
                                               StoreF& store) {
     constexpr int R = 1 << LR;
@@ -218,7 +218,7 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
             else v[b * R + r] = sm[spad<V>(ROWMAJOR ? (c << LOGL) + p : (p << LOGC) + c)];
         }
     }
-    if (!FIRST) __syncthreads();
+    if (!FIRST || SYNC_FIRST) __syncthreads();
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         if constexpr (LOGNS > 0) {
@@ -245,8 +245,8 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
 }
 
 // passes of radix E, then the remainder (LOGL mod log2 E) as one smaller-radix pass
-template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, int I, class LoadF, class StoreF,
-          class HookF>
+template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, bool SYNC_FIRST, int I, class LoadF,
+          class StoreF, class HookF>
 __device__ __forceinline__ void run_passes(V* __restrict__ sm, const V* __restrict__ tw, LoadF& load,
                                            StoreF& store, HookF& after_first) {
     constexpr int LE = Log2<E>::v;
@@ -255,28 +255,33 @@ __device__ __forceinline__ void run_passes(V* __restrict__ sm, const V* __restri
     constexpr int NPASS = NFULL + (REM ? 1 : 0);
     if constexpr (I < NPASS) {
         constexpr int LR = I < NFULL ? LE : REM;
-        stockham_pass<V, DIR, E, LOGL, LOGC, ROWMAJOR, LR, I * LE, I == 0, I == NPASS - 1>(sm, tw, load, store);
+        stockham_pass<V, DIR, E, LOGL, LOGC, ROWMAJOR, SYNC_FIRST, LR, I * LE, I == 0, I == NPASS - 1>(sm, tw, load,
+                                                                                                     store);
         if constexpr (I == 0) after_first();
-        run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, I + 1>(sm, tw, load, store, after_first);
+        run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, SYNC_FIRST, I + 1>(sm, tw, load, store, after_first);
     }
 }
 
 // Full transform.  DIR = -1: forward (exp(-2 pi i ...)), +1: inverse, unnormalised.
 // The caller synchronises before the call if `sm` still holds data that other
-// threads read.  `after_first` runs on every thread once the first pass has
-// finished reading its inputs (after that pass's closing barrier when there
-// are further passes): the load functor's source may be reused from then on.
-template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, class LoadF, class StoreF,
-          class HookF>
+// threads read.  SYNC_FIRST: the first pass synchronises between reading its
+// inputs and writing `sm`, so the load functor may read `sm` itself (an
+// input staged in the exchange buffer).  `after_first` runs on every thread
+// once the first pass has finished reading its inputs (after that pass's
+// closing barrier when there are further passes): the load functor's source
+// may be reused from then on.
+template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, bool SYNC_FIRST = false, class LoadF,
+          class StoreF, class HookF>
 __device__ __forceinline__ void block_fft(V* __restrict__ sm, const V* __restrict__ tw, LoadF load, StoreF store,
                                           HookF after_first) {
-    run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, 0>(sm, tw, load, store, after_first);
+    run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, SYNC_FIRST, 0>(sm, tw, load, store, after_first);
 }
 
-template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, class LoadF, class StoreF>
+template <typename V, int DIR, int E, int LOGL, int LOGC, bool ROWMAJOR, bool SYNC_FIRST = false, class LoadF,
+          class StoreF>
 __device__ __forceinline__ void block_fft(V* __restrict__ sm, const V* __restrict__ tw, LoadF load, StoreF store) {
     auto none = [] {};
-    run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, 0>(sm, tw, load, store, none);
+    run_passes<V, DIR, E, LOGL, LOGC, ROWMAJOR, SYNC_FIRST, 0>(sm, tw, load, store, none);
 }
 
 }  // namespace nuasm

@@ -70,7 +70,14 @@ template <typename V, int LOGNP> struct RowCfg {
     static constexpr int P = (NP * ROWS) / EF;
     static constexpr int MINB = (65536 / (P * Prec<V>::row_regs)) > 0 ? 65536 / (P * Prec<V>::row_regs) : 1;
     static constexpr int SEQ = MERGE ? 2 * ROWS : ROWS;                  // sequences in the work buffer
-    static size_t smem() { return (size_t(spad_size<V>(NP * SEQ)) + size_t(NP) * ROWS) * sizeof(V); }
+    // The mode buffer M (NP x ROWS) between the forward and inverse transforms
+    // lives inside the work buffer when the engines are merged (the forward
+    // transform's last pass writes it after its last read of the buffer, the
+    // inverse one's first pass reads it all before its first write); the
+    // sequential engines read it twice, so it gets its own space.
+    static size_t smem() {
+        return (size_t(spad_size<V>(NP * SEQ)) + (MERGE ? size_t(0) : size_t(NP) * ROWS)) * sizeof(V);
+    }
 };
 
 template <typename V, int LOGNP> struct ColCfg {
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     constexpr int NP = Cf::NP, ROWS = Cf::ROWS, HALF = NP / 2;
     extern __shared__ unsigned char smem_raw[];
     V* S = reinterpret_cast<V*>(smem_raw);
-    V* M = S + spad_size<V>(NP * Cf::SEQ);
+    V* M = Cf::MERGE ? S : S + spad_size<V>(NP * Cf::SEQ);
     const int r0 = blockIdx.x * ROWS;
     const int W = a.W, Wp = a.Wp;
     const V zero = CTraits<V>::zero();
@@ -245,7 +252,7 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     }
     __syncthreads();
     const int n = a.n;
-    block_fft<V, +1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
+    block_fft<V, +1, Cf::EF, LOGNP, Cf::LOGROWS, true, Cf::MERGE>(
         S, tw, [&](int p, int c) { return M[c * NP + p]; },
         [&](int p, int c, V v) {
             if (p < n) B[(r0 + c) * n + p] = v;
@@ -264,7 +271,7 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     constexpr int NP = Cf::NP, ROWS = Cf::ROWS, HALF = NP / 2;
     extern __shared__ unsigned char smem_raw[];
     V* S = reinterpret_cast<V*>(smem_raw);
-    V* M = S + spad_size<V>(NP * Cf::SEQ);
+    V* M = Cf::MERGE ? S : S + spad_size<V>(NP * Cf::SEQ);
     const int r0 = blockIdx.x * ROWS;
     const int n = a.n, W = a.W, Wp = a.Wp;
     const V zero = CTraits<V>::zero();
@@ -272,7 +279,8 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     const RowConst<V> rc0 = row_const<V>(r0, ty, s, a);
     // With merged inverse engines S holds 2 ROWS sequences and the forward
     // transform uses the first ROWS: the E rows are staged behind them while it
-    // runs (waited for after its first pass, whose successors synchronise).
+    // runs (waited for after its first pass, whose successors synchronise),
+    // clear of M, which its last pass writes at the start of S.
     static_assert(LOGNP > 3, "the staged E rows need a forward transform of at least two passes");
     V* Es = S + ((spad_size<V>(NP * ROWS) + 1) & ~1);
     bool staged = false;
@@ -305,7 +313,7 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
         if (u < W) A[(r0 + row) * Wp + u] = v;
     };
     if constexpr (Cf::MERGE) {
-        block_fft<V, +1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false>(
+        block_fft<V, +1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false, true>(
             S, tw, [&](int q, int cs) { return get(cs >> 1, q, cs & 1); },
             [&](int k, int cs, V v) { put(cs >> 1, k, cs & 1, v); });
     } else {
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     constexpr int NP = Cf::NP, ROWS = Cf::ROWS, HALF = NP / 2;
     extern __shared__ unsigned char smem_raw[];
     V* S = reinterpret_cast<V*>(smem_raw);
-    V* M = S + spad_size<V>(NP * Cf::SEQ);
+    V* M = Cf::MERGE ? S : S + spad_size<V>(NP * Cf::SEQ);
     const int r0 = blockIdx.x * ROWS;
     const int W = a.W, Wp = a.Wp;
     const V zero = CTraits<V>::zero();
@@ -364,7 +372,7 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
             S, tw, [&](int p, int cs) { return folded(cs >> 1, p, cs & 1); },
             [&](int pk, int cs, V v) { put_mode(cs >> 1, pk, cs & 1, v); });
         __syncthreads();
-        block_fft<V, +1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false>(
+        block_fft<V, +1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false, true>(
             S, tw, [&](int q, int cs) { return get_mode(cs >> 1, q, cs & 1); },
             [&](int k, int cs, V v) { put_row(cs >> 1, k, cs & 1, v); });
     } else {
