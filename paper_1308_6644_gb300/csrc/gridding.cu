@@ -236,6 +236,12 @@ struct GridArgs {
 #ifndef NUASM_SPREAD_MINB
 #define NUASM_SPREAD_MINB 1
 #endif
+#ifndef NUASM_SPREAD_FIXED
+#define NUASM_SPREAD_FIXED 1       // FP32 tiles beyond the private-copy sizes: batched integer accumulation
+#endif
+#ifndef NUASM_SPREAD_FIXED_RPB
+#define NUASM_SPREAD_FIXED_RPB 2   // records per thread per batch (4: 4% faster, 1.6x the error of dense cancelling sums)
+#endif
 #ifndef NUASM_SPREAD_PRIVATE
 #define NUASM_SPREAD_PRIVATE 1   // per-warp private tiles where they fit (T <= 32 F32, <= 16 F64)
 #endif
@@ -292,6 +298,131 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
             v.y = sim[i];
             win[size_t(gy) * a.Wp + gx] = v;
         }
+    }
+}
+
+// Spreading for large FP32 tiles with integer accumulation in batches.  On
+// sm_103a a shared-memory float atomicAdd is a compare-and-swap loop while a
+// 32-bit integer atomicAdd is native.  The CTA takes its records in batches of
+// RPB x 256; per batch it sums S = sum(|re| + |im|) of the batch's values
+// (weights included) and adds every tap contribution v wx wy / q, q = S 2^-30,
+// rounded to an integer, into int32 planes: a batch's sum at one cell is at
+// most S / q = 2^30 in magnitude because the kernel is at most 1.  The planes
+// are then folded into FP32 totals (tot += q acc) and cleared.  A contribution
+// is thus rounded to within max(q/2, its own FP32 rounding), q being a 2^-30
+// share of one batch's magnitude, where a float atomic rounds to the running
+// cell value.  A batch whose S is zero is skipped; one whose S is not a normal
+// finite number (infinities, NaNs, or values so small that q would underflow)
+// adds to the totals with float atomics, so non-finite inputs propagate as in
+// the float path.
+constexpr int kFixedThreads = 256;
+template <int WMAX, bool EXACT, int RPB>
+__global__ void __launch_bounds__(kFixedThreads, 2) spread_fixed_kernel(const RecF* __restrict__ rec,
+                                                                      const int* __restrict__ off,
+                                                                      const double* __restrict__ wpt,
+                                                                      const int* __restrict__ order,
+                                                                      const float2* __restrict__ c,
+                                                                      float2* __restrict__ win, GridArgs a,
+                                                                      const KernelPoly kp) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ float red[kFixedThreads / 32];
+    __shared__ float batch_sum;
+    const int T = a.T, w = EXACT ? WMAX : a.w, TT = T * T;
+    int* are = reinterpret_cast<int*>(smem_raw);
+    int* aim = are + TT;
+    float* tre = reinterpret_cast<float*>(aim + TT);
+    float* tim = tre + TT;
+    pdl_allow_next();
+    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
+    const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
+    const int x0 = tx * T, y0 = ty * T;
+    for (int i = threadIdx.x; i < TT; i += kFixedThreads) {
+        are[i] = 0;
+        aim[i] = 0;
+        tre[i] = 0.f;
+        tim[i] = 0.f;
+    }
+    const int b = off[tile], e = off[tile + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i0 = b; i0 < e; i0 += RPB * kFixedThreads) {
+        RecF r[RPB];
+        float2 val[RPB];
+        float part = 0.f;
+#pragma unroll
+        for (int k = 0; k < RPB; ++k) {
+            const int i = i0 + threadIdx.x + k * kFixedThreads;
+            val[k] = make_float2(0.f, 0.f);
+            r[k].cell = 0;
+            if (i < e) {
+                r[k] = rec[i];
+                val[k] = c[r[k].j];
+                if (wpt) {
+                    const float wt = float(wpt[r[k].j]);
+                    val[k].x *= wt;
+                    val[k].y *= wt;
+                }
+                part += fabsf(val[k].x) + fabsf(val[k].y);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();   // also orders the clearing above and the previous batch's fold
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+#pragma unroll
+            for (int k = 0; k < kFixedThreads / 32; ++k) t += red[k];
+            batch_sum = t;
+        }
+        __syncthreads();
+        const float S = batch_sum;
+        if (S == 0.f) continue;   // every value of the batch is zero (uniform)
+        const bool fixed = S >= 1e-30f && S <= 3.0e38f;
+        const float q = ldexpf(S, -30), inv = fixed ? 1.f / q : 1.f;
+#pragma unroll
+        for (int k = 0; k < RPB; ++k) {
+            const int i = i0 + threadIdx.x + k * kFixedThreads;
+            if (i >= e) continue;
+            const int lx = int(r[k].cell & 0xffffu) - x0, ly = int(r[k].cell >> 16) - y0;
+            float wx[WMAX], wy[WMAX];
+            tap_weights<WMAX>(r[k].fx, kp, wx);
+            tap_weights<WMAX>(r[k].fy, kp, wy);
+            const float sr = val[k].x * inv, si = val[k].y * inv;
+            const int ya = max(0, -ly), yb = min(w, T - ly);
+            const int xa = max(0, -lx), xb = min(w, T - lx);
+#pragma unroll
+            for (int qy = 0; qy < WMAX; ++qy) {
+                if (qy < ya || qy >= yb) continue;
+                const float vr = sr * wy[qy], vi = si * wy[qy];
+                const int rowi = (ly + qy) * T + lx;
+#pragma unroll
+                for (int qx = 0; qx < WMAX; ++qx) {
+                    if (qx < xa || qx >= xb) continue;
+                    if (fixed) {
+                        atomicAdd(&are[rowi + qx], __float2int_rn(vr * wx[qx]));
+                        atomicAdd(&aim[rowi + qx], __float2int_rn(vi * wx[qx]));
+                    } else {
+                        atomicAdd(&tre[rowi + qx], vr * wx[qx]);
+                        atomicAdd(&tim[rowi + qx], vi * wx[qx]);
+                    }
+                }
+            }
+        }
+        if (fixed) {
+            __syncthreads();
+            for (int j = threadIdx.x; j < TT; j += kFixedThreads) {
+                tre[j] = fmaf(float(are[j]), q, tre[j]);
+                tim[j] = fmaf(float(aim[j]), q, tim[j]);
+                are[j] = 0;
+                aim[j] = 0;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < TT; i += kFixedThreads) {
+        const int yy = i / T, xx = i - yy * T;
+        const int gy = y0 + yy, gx = x0 + xx;
+        if (gy < a.W && gx < a.W) win[size_t(gy) * a.Wp + gx] = make_float2(tre[i], tim[i]);
     }
 }
 
@@ -530,6 +661,18 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
             static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.wpt, P->d.tile_order,
             static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg<S>(P));
         return cudaGetLastError();
+    }
+    if constexpr (sizeof(S) == 4) {
+        if (NUASM_SPREAD_FIXED) {
+            constexpr int RPB = NUASM_SPREAD_FIXED_RPB;
+            const size_t sm = size_t(4) * a.T * a.T * sizeof(float);
+            cudaError_t e = set_smem(spread_fixed_kernel<WMAX, EXACT, RPB>, sm);
+            if (e != cudaSuccess) return e;
+            spread_fixed_kernel<WMAX, EXACT, RPB><<<P->g.ntiles, kFixedThreads, sm, st>>>(
+                static_cast<const RecF*>(P->d.rec), P->d.tile_off, P->d.wpt, P->d.tile_order,
+                static_cast<const float2*>(c), static_cast<float2*>(P->d.win), a, taps_arg<S>(P));
+            return cudaGetLastError();
+        }
     }
     const size_t sm = size_t(2) * a.T * a.T * sizeof(S);
     cudaError_t e = set_smem(spread_kernel<S, WMAX, EXACT>, sm);

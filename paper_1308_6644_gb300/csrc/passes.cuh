@@ -46,9 +46,12 @@ template <typename V> struct Prec;
 #ifndef NUASM_ROW_REGS
 #define NUASM_ROW_REGS 64   // FP32 register budget per thread that sets the row passes' CTAs per SM
 #endif
+#ifndef NUASM_COL_BUDGET
+#define NUASM_COL_BUDGET 8192   // FP32 column passes: complex elements per CTA (columns = budget / N')
+#endif
 template <> struct Prec<float2> {
     static constexpr bool f64 = false;
-    static constexpr int col_e = 16, col_budget = 8192;   // elements per thread / per CTA
+    static constexpr int col_e = 16, col_budget = NUASM_COL_BUDGET;   // elements per thread / per CTA
     static constexpr int regs = 64;
     static constexpr int row_regs = NUASM_ROW_REGS;
 };

@@ -260,22 +260,49 @@ def test_type2_is_deterministic(P):
     assert np.array_equal(a, b)
 
 
-def test_fp32_type1_dense_random_phase_cluster(P):
+@pytest.mark.parametrize("tile", [16, 32, 64])
+def test_fp32_type1_dense_random_phase_cluster(P, tile):
     """20000 random-phase points within a few fine-grid cells (hundreds per
-    cell): the shared-memory accumulation must keep the FP32 tolerance where
-    the cell sums cancel far below the sum of magnitudes, and two runs agree
-    to rounding (float atomics add in varying order)."""
+    cell): every shared-memory accumulation (warp-private copies for 16 and
+    32, batched integer sums for 64) must keep the FP32 tolerance where the
+    cell sums cancel far below the sum of magnitudes, and two runs agree to
+    rounding (atomics add in varying order)."""
     rng = np.random.default_rng(43)
     n, pitch, m = 64, 10e-6, 20000
     x = WL.clamp_window(rng.normal(0, 20e-6, m), n, pitch)
     y = WL.clamp_window(rng.normal(0, 20e-6, m), n, pitch)
     c = rng.normal(size=m) + 1j * rng.normal(size=m)
-    kw = dict(pitch=pitch, lam=633e-9, z=0.02)
+    kw = dict(pitch=pitch, lam=633e-9, z=0.02, tile=tile)
     a = run_gpu(P, "asm", 1, "f32", n, x=x, y=y, values=c, **kw)
     b = run_gpu(P, "asm", 1, "f32", n, x=x, y=y, values=c, **kw)
+    del kw["tile"]
     ref = run_oracle("asm", 1, n, x=x, y=y, values=c, **kw)
     assert O.rel_l2(a, ref) < TOL["f32"] and O.rel_l2(b, ref) < TOL["f32"]
     assert O.rel_l2(a, b) < 1e-6
+
+
+def test_fp32_type1_large_tiles_dynamic_range_and_non_finite(P):
+    """Batched integer spreading (tile 64): values spanning eight decades in
+    one batch and weights keep the FP32 tolerance; an all-zero input gives
+    zeros; a NaN or an infinity among the values reaches the output as in
+    float arithmetic."""
+    rng = np.random.default_rng(47)
+    n, pitch, m = 128, 10e-6, 6000
+    x, y, c = random_case(47, n, m, pitch=pitch)
+    c[:7] *= 1e4
+    c[7:20] *= 1e-4
+    wts = rng.uniform(0.2, 2.0, m)
+    kw = dict(pitch=pitch, lam=633e-9, z=0.03, ox=10e-6)
+    got = run_gpu(P, "asm", 1, "f32", n, x=x, y=y, values=c, w=wts, tile=64, **kw)
+    ref = run_oracle("asm", 1, n, x=x, y=y, values=c, w=wts, **kw)
+    assert O.rel_l2(got, ref) < TOL["f32"]
+    zero = run_gpu(P, "asm", 1, "f32", n, x=x, y=y, values=np.zeros(m), tile=64, **kw)
+    assert not np.any(zero)
+    for bad in (np.nan, np.inf):
+        cb = c.copy()
+        cb[100] = bad
+        out = run_gpu(P, "asm", 1, "f32", n, x=x, y=y, values=cb, tile=64, **kw)
+        assert not np.all(np.isfinite(out))
 
 
 # ---------------------------------------------------------------- Gaussian (Greengard-Lee) kernel option
