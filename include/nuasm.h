@@ -117,6 +117,8 @@ typedef struct {
     int64_t device_bytes;      /* device memory owned by the plan */
     int64_t phase_table_bytes; /* of which the tabulated non-separable ASM phase factor
                                   (Eq. 4; 0 when the plan evaluates it per mode) */
+    int32_t bank_skew;         /* shared-memory bank skew of the gridding tiles (0 or 2),
+                                  chosen from the points' distribution */
 } nuasm_plan_info_t;
 
 /*

@@ -567,6 +567,7 @@ nuasm_status nuasm_plan_info(nuasm_plan_t plan, nuasm_plan_info_t* info) {
     int pitch = 0;
     info->phase_table_bytes =
         plan->d.etab ? int64_t(etab_elems(plan->g, &pitch) * (plan->f64 ? 16 : 8)) : 0;
+    info->bank_skew = plan->skew;
     return NUASM_OK;
 }
 

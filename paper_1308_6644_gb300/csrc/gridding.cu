@@ -145,20 +145,69 @@ __global__ void bin_scatter_kernel(const double* __restrict__ x, const double* _
     }
 }
 
-// Order each tile's records so that consecutive records have distinct
-// first-tap columns modulo 32 (round-robin over the 32 classes lx mod 32, home
-// records and halo duplicates separately).  A warp then gathers (type 2) or
-// accumulates (type 1) its w x w taps at 32 distinct shared-memory banks for
-// every tap offset: the tile rows are a multiple of 32 banks apart.  One CTA
+// Shared-memory tile rows are laid out `skew` words (32-bit planes), 8-byte or
+// 16-byte elements apart modulo the 32 banks: a tap at tile cell (x, y) sits in
+// bank class (skew y + x) mod 32 (mod 16 for 8-byte, mod 8 for 16-byte
+// elements), and the records are ordered by that class of their first tap.
+// With skew 0 the class is the column alone, which repeats whenever points sit
+// on a lattice coarser than the fine grid (every 4th column at the 16 um edge
+// of the graded NU-ASM_2 plane); skew 2 mixes in the row.  The plan takes
+// skew 2 only where it balances the classes clearly better (class_balance),
+// since on unstructured clusters skew 0 measured faster at equal balance.
+__host__ __device__ constexpr int plane_stride(int T, int skew) { return T + skew; }   // T = 32, 64: = skew mod 32
+__host__ __device__ constexpr int halo_pitch(int th, int skew) { return th + (((skew - th) % 16) + 16) % 16; }
+
+// Sum over tiles of the largest bank-class count of the tile's home records
+// (the ones interpolation visits and most of what spreading visits), for skew
+// 0 (sums[0]) and skew 2 (sums[1]): the record slots a perfectly balanced warp
+// schedule would need, up to a factor 32.
+template <typename Rec>
+__global__ void class_balance_kernel(const Rec* __restrict__ rec, const int* __restrict__ off,
+                                     const int* __restrict__ home, int T, int ntx,
+                                     unsigned long long* __restrict__ sums) {
+    __shared__ int cnt[2][32];
+    const int tile = blockIdx.x;
+    const int x0 = (tile - (tile / ntx) * ntx) * T, y0 = (tile / ntx) * T;
+    if (threadIdx.x < 64) (&cnt[0][0])[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = off[tile] + threadIdx.x; i < off[tile] + home[tile]; i += blockDim.x) {
+        const uint32_t cell = rec[i].cell;
+        const int lx = int(cell & 0xffffu) - x0, ly = int(cell >> 16) - y0;
+        atomicAdd(&cnt[0][lx & 31], 1);
+        atomicAdd(&cnt[1][(2 * ly + lx) & 31], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int m0 = cnt[0][threadIdx.x], m1 = cnt[1][threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+            m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        }
+        if (threadIdx.x == 0) {
+            atomicAdd(&sums[0], (unsigned long long)m0);
+            atomicAdd(&sums[1], (unsigned long long)m1);
+        }
+    }
+}
+
+// Order each tile's records so that consecutive records have distinct bank
+// classes (skew ly + lx) mod 32 of their first tap (round-robin over the
+// 32 classes, home records and halo duplicates separately).  A warp then
+// gathers (type 2) or accumulates (type 1) its w x w taps at distinct banks
+// for every tap offset, as far as the tile's classes are balanced.  One CTA
 // per tile, reading the unordered copy `src` and writing `dst`; the order
 // within a class is arbitrary (results do not depend on record order in
 // type 2; type 1 sums in shared memory whatever the order).
 template <typename Rec>
 __global__ void order_tile_kernel(const Rec* __restrict__ src, Rec* __restrict__ dst, const int* __restrict__ off,
-                                  const int* __restrict__ home, int T, int ntx) {
+                                  const int* __restrict__ home, int T, int ntx, int skew) {
     __shared__ int cnt[2][32], cur[2][32];
     const int tile = blockIdx.x;
-    const int x0 = (tile - (tile / ntx) * ntx) * T;
+    const int x0 = (tile - (tile / ntx) * ntx) * T, y0 = (tile / ntx) * T;
+    auto bank_class = [&](uint32_t cell) {
+        return (skew * (int(cell >> 16) - y0) + (int(cell & 0xffffu) - x0)) & 31;
+    };
     const int b = off[tile], e = off[tile + 1], eh = b + home[tile];
     if (threadIdx.x < 64) {
         (&cnt[0][0])[threadIdx.x] = 0;
@@ -166,12 +215,12 @@ __global__ void order_tile_kernel(const Rec* __restrict__ src, Rec* __restrict__
     }
     __syncthreads();
     for (int i = b + threadIdx.x; i < e; i += blockDim.x)
-        atomicAdd(&cnt[i >= eh][(int(src[i].cell & 0xffffu) - x0) & 31], 1);
+        atomicAdd(&cnt[i >= eh][bank_class(src[i].cell)], 1);
     __syncthreads();
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
         const Rec r = src[i];
         const int seg = i >= eh;
-        const int c = (int(r.cell & 0xffffu) - x0) & 31;
+        const int c = bank_class(r.cell);
         const int rank = atomicAdd(&cur[seg][c], 1);
         int pos = 0;   // records of lower rank, then same rank and lower class
 #pragma unroll 8
@@ -219,6 +268,7 @@ template <> struct VecOf<double> { using type = double2; };
 
 struct GridArgs {
     int W, Wp, T, ntx, w;
+    int skew;   // bank skew of the tile layouts (plane_stride, halo_pitch)
 };
 
 // --------------------------------------------------------------- spreading (type 1)
@@ -254,14 +304,14 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
                                                      const typename PolyOf<S>::type kp) {
     using V = typename VecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
-    const int T = a.T, w = EXACT ? WMAX : a.w;
+    const int T = a.T, w = EXACT ? WMAX : a.w, TS = plane_stride(T, a.skew), TT = T * TS;
     S* sre = reinterpret_cast<S*>(smem_raw);
-    S* sim = sre + T * T;
+    S* sim = sre + TT;
     pdl_allow_next();
     const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) { sre[i] = S(0); sim[i] = S(0); }
+    for (int i = threadIdx.x; i < TT; i += blockDim.x) { sre[i] = S(0); sim[i] = S(0); }
     __syncthreads();
     const int b = off[tile], e = off[tile + 1];
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
@@ -278,8 +328,8 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
         for (int qy = 0; qy < WMAX; ++qy) {
             if (qy < ya || qy >= yb) continue;
             const S vr = val.x * wy[qy], vi = val.y * wy[qy];
-            S* rowr = sre + (ly + qy) * T + lx;
-            S* rowi = sim + (ly + qy) * T + lx;
+            S* rowr = sre + (ly + qy) * TS + lx;
+            S* rowi = sim + (ly + qy) * TS + lx;
 #pragma unroll
             for (int qx = 0; qx < WMAX; ++qx) {
                 if (qx < xa || qx >= xb) continue;
@@ -294,8 +344,8 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
         const int gy = y0 + yy, gx = x0 + xx;
         if (gy < a.W && gx < a.W) {
             V v;
-            v.x = sre[i];
-            v.y = sim[i];
+            v.x = sre[yy * TS + xx];
+            v.y = sim[yy * TS + xx];
             win[size_t(gy) * a.Wp + gx] = v;
         }
     }
@@ -327,7 +377,7 @@ __global__ void __launch_bounds__(kFixedThreads, 2) spread_fixed_kernel(const Re
     extern __shared__ unsigned char smem_raw[];
     __shared__ float red[kFixedThreads / 32];
     __shared__ float batch_sum;
-    const int T = a.T, w = EXACT ? WMAX : a.w, TT = T * T;
+    const int T = a.T, w = EXACT ? WMAX : a.w, TS = plane_stride(T, a.skew), TT = T * TS;
     int* are = reinterpret_cast<int*>(smem_raw);
     int* aim = are + TT;
     float* tre = reinterpret_cast<float*>(aim + TT);
@@ -394,7 +444,7 @@ __global__ void __launch_bounds__(kFixedThreads, 2) spread_fixed_kernel(const Re
             for (int qy = 0; qy < WMAX; ++qy) {
                 if (qy < ya || qy >= yb) continue;
                 const float vr = sr * wy[qy], vi = si * wy[qy];
-                const int rowi = (ly + qy) * T + lx;
+                const int rowi = (ly + qy) * TS + lx;
 #pragma unroll
                 for (int qx = 0; qx < WMAX; ++qx) {
                     if (qx < xa || qx >= xb) continue;
@@ -419,10 +469,10 @@ __global__ void __launch_bounds__(kFixedThreads, 2) spread_fixed_kernel(const Re
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < TT; i += kFixedThreads) {
+    for (int i = threadIdx.x; i < T * T; i += kFixedThreads) {
         const int yy = i / T, xx = i - yy * T;
         const int gy = y0 + yy, gx = x0 + xx;
-        if (gy < a.W && gx < a.W) win[size_t(gy) * a.Wp + gx] = make_float2(tre[i], tim[i]);
+        if (gy < a.W && gx < a.W) win[size_t(gy) * a.Wp + gx] = make_float2(tre[yy * TS + xx], tim[yy * TS + xx]);
     }
 }
 
@@ -447,7 +497,7 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
     using Rec = typename RecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
     V* copies = reinterpret_cast<V*>(smem_raw);
-    const int T = a.T, w = EXACT ? WMAX : a.w, TT = T * T;
+    const int T = a.T, w = EXACT ? WMAX : a.w, TS = plane_stride(T, a.skew), TT = T * TS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     V* mine = copies + warp * TT;
     pdl_allow_next();
@@ -482,7 +532,7 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
             if (qy >= w) continue;   // warp-uniform
             const bool rowok = live && qy >= ya && qy < yb;
             const S vr = val.x * wy[qy], vi = val.y * wy[qy];
-            V* row = mine + (ly + qy) * T + lx;
+            V* row = mine + (ly + qy) * TS + lx;
 #pragma unroll
             for (int qx = 0; qx < WMAX; ++qx) {
                 if (qx >= w) continue;   // warp-uniform
@@ -504,14 +554,15 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
         __syncwarp();
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < TT; i += blockDim.x) {
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
         const int yy = i / T, xx = i - yy * T;
         const int gy = y0 + yy, gx = x0 + xx;
         if (gy < a.W && gx < a.W) {
-            V v = copies[i];
+            const int si = yy * TS + xx;
+            V v = copies[si];
 #pragma unroll
             for (int k = 1; k < 8; ++k) {
-                const V u = copies[k * TT + i];
+                const V u = copies[k * TT + si];
                 v.x += u.x;
                 v.y += u.y;
             }
@@ -521,8 +572,8 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
 }
 
 // --------------------------------------------------------------- interpolation (type 2)
-// The tile plus its (w-1) halo is staged with a row stride rounded up to 16
-// elements, so bank classes depend on the column only (see order_tile_kernel).
+// The tile plus its (w-1) halo is staged with a row stride = skew mod 16
+// elements (halo_pitch), matching the record order's bank classes.
 // The first kInterpPrefetch records of every thread are loaded before the
 // staging loads so that their latency overlaps the tile's; FP32 tiles are
 // staged two complex values (16 B) per load.
@@ -575,7 +626,7 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
     using Rec = typename RecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
     V* tl = reinterpret_cast<V*>(smem_raw);
-    const int T = a.T, w = EXACT ? WMAX : a.w, TH = T + w - 1, THP = (TH + 15) & ~15;
+    const int T = a.T, w = EXACT ? WMAX : a.w, TH = T + w - 1, THP = halo_pitch(TH, a.skew);
     const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
@@ -636,6 +687,7 @@ GridArgs grid_args(const nuasm_plan_s* P) {
     a.T = P->g.T;
     a.ntx = P->g.ntx;
     a.w = P->g.w;
+    a.skew = P->skew;
     return a;
 }
 
@@ -654,7 +706,7 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     using V = typename VecOf<S>::type;
     GridArgs a = grid_args(P);
     if (NUASM_SPREAD_PRIVATE && a.T <= (sizeof(S) == 4 ? 32 : 16)) {
-        const size_t sm = size_t(8) * a.T * a.T * sizeof(V);
+        const size_t sm = size_t(8) * a.T * plane_stride(a.T, a.skew) * sizeof(V);
         cudaError_t e = set_smem(spread_private_kernel<S, WMAX, EXACT>, sm);
         if (e != cudaSuccess) return e;
         spread_private_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
@@ -665,7 +717,7 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     if constexpr (sizeof(S) == 4) {
         if (NUASM_SPREAD_FIXED) {
             constexpr int RPB = NUASM_SPREAD_FIXED_RPB;
-            const size_t sm = size_t(4) * a.T * a.T * sizeof(float);
+            const size_t sm = size_t(4) * a.T * plane_stride(a.T, a.skew) * sizeof(float);
             cudaError_t e = set_smem(spread_fixed_kernel<WMAX, EXACT, RPB>, sm);
             if (e != cudaSuccess) return e;
             spread_fixed_kernel<WMAX, EXACT, RPB><<<P->g.ntiles, kFixedThreads, sm, st>>>(
@@ -674,7 +726,7 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
             return cudaGetLastError();
         }
     }
-    const size_t sm = size_t(2) * a.T * a.T * sizeof(S);
+    const size_t sm = size_t(2) * a.T * plane_stride(a.T, a.skew) * sizeof(S);
     cudaError_t e = set_smem(spread_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
     spread_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
@@ -687,7 +739,7 @@ template <typename S, int WMAX, bool EXACT>
 cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
     using V = typename VecOf<S>::type;
     GridArgs a = grid_args(P);
-    const int TH = a.T + a.w - 1, THP = (TH + 15) & ~15;
+    const int TH = a.T + a.w - 1, THP = halo_pitch(TH, a.skew);
     const size_t sm = size_t(TH) * THP * sizeof(V);
     cudaError_t e = set_smem(interp_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
@@ -808,16 +860,35 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
         if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     }
     if (P->m > 0 && total > 0) {
+        // bank skew: 2 where it balances the record classes at least 5% better
+        unsigned long long* sums = nullptr;
+        unsigned long long hs[2] = {0, 0};
+        if ((e = cudaMallocAsync(&sums, sizeof(hs), st)) != cudaSuccess) return fail(e);
+        e = cudaMemsetAsync(sums, 0, sizeof(hs), st);
+        if (e == cudaSuccess) {
+            if (P->f64)
+                class_balance_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(P->d.rec), P->d.tile_off,
+                                                               P->d.tile_home, g.T, g.ntx, sums);
+            else
+                class_balance_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(P->d.rec), P->d.tile_off,
+                                                               P->d.tile_home, g.T, g.ntx, sums);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFreeAsync(sums, st);
+        if (e != cudaSuccess) return fail(e);
+        P->skew = double(hs[1]) < 0.95 * double(hs[0]) ? 2 : 0;
         void* tmp = nullptr;
         if ((e = cudaMallocAsync(&tmp, rsz * size_t(total), st)) != cudaSuccess) return fail(e);
         e = cudaMemcpyAsync(tmp, P->d.rec, rsz * size_t(total), cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) {
             if (P->f64)
                 order_tile_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(tmp), static_cast<RecD*>(P->d.rec),
-                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew);
             else
                 order_tile_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(tmp), static_cast<RecF*>(P->d.rec),
-                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew);
             e = cudaGetLastError();
         }
         cudaFreeAsync(tmp, st);
@@ -857,12 +928,12 @@ cudaError_t bin_points_into(const nuasm_plan_s* P, const double* x, const double
         bin_scatter_kernel<RecD, double><<<blocks, 256, 0, st>>>(x, y, a, P->d.tile_off, home_cnt, cur_home,
                                                                  cur_dup, static_cast<RecD*>(rec_tmp));
         order_tile_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(rec_tmp), static_cast<RecD*>(P->d.rec),
-                                                    P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+                                                    P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew);
     } else {
         bin_scatter_kernel<RecF, float><<<blocks, 256, 0, st>>>(x, y, a, P->d.tile_off, home_cnt, cur_home,
                                                                 cur_dup, static_cast<RecF*>(rec_tmp));
         order_tile_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(rec_tmp), static_cast<RecF*>(P->d.rec),
-                                                    P->d.tile_off, P->d.tile_home, g.T, g.ntx);
+                                                    P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew);
     }
     return cudaGetLastError();
 }

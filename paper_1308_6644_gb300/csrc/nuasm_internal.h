@@ -80,6 +80,7 @@ struct nuasm_plan_s {
     double rc = 0.0;            // z / (2 lambda)
     int nonsep_mode = 0;        // ASM non-separable phase: 0 none, 1 plain, 2 double-float
     int etab_pitch = 0;         // entries per row of d.etab
+    int skew = 0;               // bank skew of the gridding tile layouts and record order (0 or 2)
     nuasm::KernelPoly poly{};   // kernel taps as polynomials (F32 gridding)
     nuasm::KernelPoly64 poly64{};   // the same in FP64 (F64 gridding)
     int64_t device_bytes = 0;

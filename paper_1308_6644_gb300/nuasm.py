@@ -50,7 +50,8 @@ class PlanInfo(ctypes.Structure):
                 ("band_lo_x", ctypes.c_int32), ("band_hi_x", ctypes.c_int32),
                 ("band_lo_y", ctypes.c_int32), ("band_hi_y", ctypes.c_int32),
                 ("points", ctypes.c_int64), ("records", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("phase_table_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("phase_table_bytes", ctypes.c_int64),
+                ("bank_skew", ctypes.c_int32)]
 
 
 class BatchItem(ctypes.Structure):

@@ -188,6 +188,30 @@ def test_phase_table_only_where_the_phase_is_not_separable(P):
             plan.destroy()
 
 
+def test_bank_skew_follows_the_point_distribution(P):
+    """A graded lattice (points every few fine-grid columns, as at the edge of
+    the NU-ASM_2 benchmark plane) gets the skewed tile layout, uniformly random
+    points the plain one; type 2 gives the same bits either way (each point's
+    taps are summed in a fixed order) and both agree with the oracle."""
+    wl = WL.nuasm2_graded(seed=7, n=256, pitch=8e-6)
+    xr, yr, _ = random_case(8, 256, wl.m, pitch=8e-6)
+    params = P.make_params(256, 8e-6, 532e-9, 0.05, tile=64)
+    skews = []
+    for x, y in ((wl.x, wl.y), (xr, yr)):
+        plan = P.nuasm_plan(params, _t(x), _t(y))
+        try:
+            skews.append(plan.info()["bank_skew"])
+        finally:
+            plan.destroy()
+    assert skews == [2, 0]
+    u1 = np.random.default_rng(9).normal(size=(256, 256)) + 0j
+    kw = dict(pitch=8e-6, lam=532e-9, z=0.05)
+    got = run_gpu(P, "asm", 2, "f32", 256, x=wl.x, y=wl.y, values=u1, tile=64, **kw)
+    idx = np.random.default_rng(10).choice(wl.m, 4000, replace=False)
+    ref = run_oracle("asm", 2, 256, x=wl.x[idx], y=wl.y[idx], values=u1, **kw)
+    assert O.rel_l2(got[idx], ref) < TOL["f32"]
+
+
 def test_window_edges_and_single_tile(P):
     """Points exactly on the lower window edge, just inside the upper edge and
     all crowded into one tile."""
