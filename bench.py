@@ -184,10 +184,19 @@ def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
     lognp = int(np.log2(info["n_pad"]))
     v, s = ("double2", "double") if f64 else ("float2", "float")
     w = info["kernel_width"]
-    tap = f"{s}, {8 if w <= 8 else 16}, false" if f64 else (f"float, {w}, true" if 4 <= w <= 8 else "float, 16, false")
+    if f64:
+        tap = "double, 13, true" if w == 13 else f"double, {8 if w <= 8 else 16}, false"
+    else:
+        tap = f"float, {w}, true" if 4 <= w <= 8 else "float, 16, false"
     tma = not f64 and 512 <= info["n_pad"] <= 4096          # folded column passes
     tma_wide = not f64 and info["n_pad"] == 4096              # unfolded ones too
-    spread = f"spread_kernel<{tap}>"
+    tile = info.get("tile", 64)
+    if f64:
+        spread = f"spread_private_kernel<{tap}>" if tile <= 16 else f"spread_kernel<{tap}>"
+    elif tile <= 32:
+        spread = f"spread_private_kernel<{tap}>"
+    else:
+        spread = f"spread_fixed_kernel<{w}, true, 2>" if 4 <= w <= 8 else "spread_fixed_kernel<16, false, 2>"
     return {"col_fwd": f"col_tma_kernel<{lognp}, 2>" if tma_wide else f"col_kernel<{v}, {lognp}, 2>",
             "row_t2": f"row_t2_kernel<{v}, {lognp}>",
             "col_inv_fold": f"col_tma_kernel<{lognp}, 3>" if tma else f"col_kernel<{v}, {lognp}, 3>",
