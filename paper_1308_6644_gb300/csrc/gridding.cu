@@ -273,16 +273,18 @@ struct GridArgs {
 
 // --------------------------------------------------------------- spreading (type 1)
 // EXACT: the kernel width is WMAX itself (compile-time loops); else w <= WMAX at run time.
-// Taps accumulate with shared-memory atomicAdd in the plan's precision.  (On
-// sm_103a a float shared-memory atomicAdd is a compare-and-swap loop -- 9.4
-// instructions and 2 wavefronts per add, against one native operation for a
-// 32-bit integer.  Fixed-point integer accumulation with a bound per 8-row
-// band was measured: one word spread 4M clustered points 1.6x faster but
-// lost ~1e-9 of the band's |c| sum per tap, 1.1e-5 end to end where
-// thousands of random-phase points crowd a few cells; two words (high and
-// remainder) were accurate but slower than float; a per-tile switch chose
-// float for most dense tiles; one 64-bit compare-and-swap per (re, im) pair
-// was 3.9x slower than two float adds.  Float accumulation stays.)
+// Three accumulation schemes, picked by precision and tile side in spread_impl:
+// warp-private copies (small tiles), batched int32 sums (FP32, T = 64) and,
+// here, shared-memory atomicAdd in the plan's precision (FP64 large tiles; on
+// sm_103a a float or double shared-memory atomicAdd is a compare-and-swap
+// loop -- 9.4 instructions and 2 wavefronts per float add, against one native
+// operation for a 32-bit integer).  Also measured and not kept: one int32
+// word per value at a single quantum per 8-row band for all of a tile's
+// records (1.6x faster than float but 1.1e-5 end to end where thousands of
+// random-phase points crowd a few cells -- the batched scheme fixes this by a
+// quantum per batch), two words (value and remainder; slower than float), and
+// one 64-bit compare-and-swap per (re, im) pair (3.9x slower than two float
+// adds).
 #ifndef NUASM_SPREAD_MINB
 #define NUASM_SPREAD_MINB 1
 #endif
