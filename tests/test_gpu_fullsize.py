@@ -137,3 +137,49 @@ def test_mixed_planes(P, plane):
         got = _solve(P, w, 1, c).reshape(w.n, w.n)
         p = dict(n=w.n, pitch=w.pitch, lam=w.lam, z=w.z)
         assert O.rel_l2(got, O.nuasm1(w.x[nz], w.y[nz], c[nz].astype(np.complex64), p)) < TOL
+
+
+def test_asm_n4096_exact_helmholtz_solution(P):
+    """N = 4096 (N' = 8192: the row passes run their two transforms in turn
+    and read the phase-factor table from L2): NU-ASM_2 of a complex-source-
+    point beam, an exact solution of the Helmholtz equation, against that
+    solution at 200,000 random points, 2 mm away (a non-separable phase of
+    ~50 cycles at the band edge), through a plan (tabulated factor, FP64) and
+    through the server (factor evaluated per mode in double-float FP32)."""
+    n, pitch, lam, w0, z, m = 4096, 0.2e-6, 0.5e-6, 20e-6, 2e-3, 200_000
+    k, b = 2 * np.pi / lam, np.pi * w0 ** 2 / lam
+
+    def csp(x, y, zz):
+        R = -1j * np.sqrt(b * b - (x * x + y * y) + 0j) if zz == 0 else np.sqrt(x * x + y * y + (zz - 1j * b) ** 2)
+        return np.exp(1j * k * (R + 1j * b)) / R
+
+    g = (np.arange(n) - n // 2) * pitch
+    gx, gy = np.meshgrid(g, g)
+    u1 = csp(gx, gy, 0.0)
+    scale = np.abs(u1).max()
+    u1 = (u1 / scale).astype(np.complex64)
+    rng = np.random.default_rng(4096)
+    half = 0.25 * n * pitch   # the beam (width ~25 um at z) sits well inside
+    x = rng.uniform(-half, half, m)
+    y = rng.uniform(-half, half, m)
+    want = csp(x, y, z) / scale
+    params = P.make_params(n, pitch, lam, z)
+    import torch
+    plan = P.nuasm_plan(params, _dev(x), _dev(y))
+    try:
+        assert plan.info()["phase_table_bytes"] > 0
+        v = torch.zeros(m, dtype=torch.complex64, device="cuda")
+        P.nuasm2_execute(plan, _dev(u1.reshape(-1)), v)
+        torch.cuda.synchronize()
+        got = v.cpu().numpy()
+    finally:
+        plan.destroy()
+    assert O.rel_l2(got, want) < TOL
+    srv = P.nuasm_server_create(slots=1)
+    try:
+        served = np.zeros(m, np.complex64)
+        t = P.nuasm_server_submit(srv, params, 2, x, y, u1.reshape(-1), served, points_id=0)
+        assert P.nuasm_server_wait(srv, t, 120.0)["status"] == 0
+    finally:
+        srv.destroy()
+    assert O.rel_l2(served, want) < TOL
