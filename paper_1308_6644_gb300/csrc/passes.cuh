@@ -18,15 +18,17 @@
 // Type 2 (Eq. 9):  u1 --col_fwd--> B (N' x N) --row_t2--> A (N' x W)
 //                  --col_inv_fold--> window.
 //
-// The non-separable part of the ASM phase is evaluated per mode:
+// The non-separable part of the ASM phase:
 //   z sqrt(1/lambda^2 - |f|^2) = z/lambda - (z lambda/2)|f|^2 - (z/(2 lambda)) q^2,
 //   q = s / (1 + sqrt(1 - s)),  s = lambda^2 |f|^2,
 // an exact rearrangement whose first two terms are separable (folded into the
-// per-axis tables in FP64 on the host) and whose last term r is small.  r is
-// computed in FP64 (F64 plans), with FP32 fast-math intrinsics when the plan's
-// largest |r| is at most 1/2 cycle (phase error below 2e-6 rad), else in
-// double-float FP32 reduced mod 1 and passed to sincospi.  Evanescent modes
-// (s >= 1) are zeroed.
+// per-axis tables in FP64 on the host) and whose last term r is small.  A plan
+// tabulates E = exp(-2 pi i r) once in FP64 over |kx|, |ky| in [0, N'/2]
+// (E depends on |f|^2 only); without the table (served requests, the
+// allocation-free solve) r is computed per mode in FP64 (F64 plans), with FP32
+// fast-math intrinsics when the largest |r| is at most 1/2 cycle (phase error
+// below 2e-6 rad), else in double-float FP32 reduced mod 1 and passed to
+// sincospi.  Evanescent modes (s >= 1) are zeroed either way.
 #pragma once
 
 #include <cuda_runtime.h>
