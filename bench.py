@@ -144,17 +144,21 @@ def stage_bytes(info: dict, m: int, type_: int = 2, eb: int = 8) -> dict:
     plan's table of the non-separable phase factor once, where it has one."""
     n, np_, W = info["n"], info["n_pad"], info["window"]
     rb = 16 if eb == 8 else 24
-    etab = info.get("phase_table_bytes", 0)
+    # the plan's phase tables: E over the |k| quadrant, plus (FP32) type 2's
+    # Tx-folded rows; each row pass reads one of them once
+    tables = info.get("phase_table_bytes", 0)
+    equad = (np_ // 2 + 1) * (np_ // 2 + 2) * eb if tables else 0
+    etab2 = tables - equad
     if type_ == 1:
         return {
             "spread": (rb + eb) * info["records"] + eb * W * W,
             "col_fwd_fold": eb * (2 * W * W + np_ * W),
-            "row_t1": eb * (np_ * W + np_ * n) + etab,
+            "row_t1": eb * (np_ * W + np_ * n) + equad,
             "col_inv": eb * (np_ * n + n * n),
         }
     return {
         "col_fwd": eb * (n * n + np_ * n),
-        "row_t2": eb * (np_ * n + np_ * W) + etab,
+        "row_t2": eb * (np_ * n + np_ * W) + (etab2 if etab2 > 0 else equad),
         "col_inv_fold": eb * (np_ * W + W * W),
         "interp": eb * W * W + (rb + eb) * m,
     }

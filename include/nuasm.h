@@ -116,7 +116,8 @@ typedef struct {
     int64_t records;           /* binned records (points plus tile-halo duplicates) */
     int64_t device_bytes;      /* device memory owned by the plan */
     int64_t phase_table_bytes; /* of which the tabulated non-separable ASM phase factor
-                                  (Eq. 4; 0 when the plan evaluates it per mode) */
+                                  (Eq. 4) and its type-2 product with the per-column
+                                  factor (0 when the plan evaluates it per mode) */
     int32_t bank_skew;         /* shared-memory bank skew of the gridding tiles (0 or 2),
                                   chosen from the points' distribution */
 } nuasm_plan_info_t;
@@ -147,7 +148,8 @@ typedef struct {
  * of the transfer function's non-separable phase factor over |kx|, |ky| in
  * [0, N'/2] (about N'^2/4 complex values in the plan precision, computed in
  * FP64 during the call), which the execute calls read instead of evaluating a
- * square root and a sine/cosine per mode.
+ * square root and a sine/cosine per mode; FP32 plans with N' <= 4096 add the
+ * same factor times type 2's per-column table (about N'^2/2 complex64).
  */
 nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m,
                         const double* x, const double* y, const double* w, void* stream);

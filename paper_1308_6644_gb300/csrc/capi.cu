@@ -14,6 +14,10 @@
 
 #include "nuasm_internal.h"
 
+#ifndef NUASM_ETAB2
+#define NUASM_ETAB2 1   // FP32 plans also tabulate T2x E for the type-2 row pass
+#endif
+
 using namespace nuasm;
 
 namespace nuasm {
@@ -130,7 +134,7 @@ void nuasm::plan_release(nuasm_plan_s* P) {
                 }
         delete X;
     }
-    void* ptrs[] = {P->d.tables, P->d.etab, P->d.rec, P->d.wpt, P->d.tile_off, P->d.tile_home,
+    void* ptrs[] = {P->d.tables, P->d.etab, P->d.etab2, P->d.rec, P->d.wpt, P->d.tile_off, P->d.tile_home,
                     P->d.tile_order, P->d.win, P->d.bufA, P->d.bufB, P->d.stage_in, P->d.stage_out, P->d.err};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -381,6 +385,12 @@ nuasm_status nuasm::plan_create(nuasm_plan_s** out, const nuasm_params_t* p, int
             const size_t ne = etab_elems(g, &P->etab_pitch);
             if ((e = dalloc(P, &P->d.etab, ne * eb)) != cudaSuccess) return bail(cuda_status(e));
             if ((e = build_etab(P, st)) != cudaSuccess) return bail(cuda_status(e));
+            if (NUASM_ETAB2 && !P->f64 && g.np <= 4096) {
+                // type 2's row pass stages T2x E rows (merged row engines: N' <= 4096 in FP32)
+                const size_t n2 = size_t(g.np / 2 + 1) * g.np;
+                if ((e = dalloc(P, &P->d.etab2, n2 * eb)) != cudaSuccess) return bail(cuda_status(e));
+                if ((e = build_etab2(P, st)) != cudaSuccess) return bail(cuda_status(e));
+            }
         }
     }
     if ((e = dalloc(P, &P->d.tile_off, sizeof(int) * (g.ntiles + 1))) != cudaSuccess) return bail(cuda_status(e));
@@ -566,7 +576,8 @@ nuasm_status nuasm_plan_info(nuasm_plan_t plan, nuasm_plan_info_t* info) {
     info->device_bytes = plan->device_bytes;
     int pitch = 0;
     info->phase_table_bytes =
-        plan->d.etab ? int64_t(etab_elems(plan->g, &pitch) * (plan->f64 ? 16 : 8)) : 0;
+        (plan->d.etab ? int64_t(etab_elems(plan->g, &pitch) * (plan->f64 ? 16 : 8)) : 0) +
+        (plan->d.etab2 ? int64_t(plan->g.np / 2 + 1) * plan->g.np * 8 : 0);
     info->bank_skew = plan->skew;
     return NUASM_OK;
 }

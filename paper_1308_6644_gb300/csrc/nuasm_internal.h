@@ -55,6 +55,8 @@ struct PlanDevice {
     void* tw = nullptr;         // twiddles, G complex
     void* etab = nullptr;       // ASM non-separable factor E(|kx|, |ky|): N'/2 + 1 rows of etab_pitch
                                 // entries in the plan precision (null: evaluated per mode)
+    void* etab2 = nullptr;      // type 2's T2x(kx) E(|kx|, |ky|): N'/2 + 1 rows of N' entries (FP32 plans
+                                // with merged row engines; null: row_t2 uses etab and T2x)
     void* rec = nullptr;        // binned point records
     double* wpt = nullptr;      // optional per-point weights, in point order
     int* tile_off = nullptr;    // ntiles + 1 offsets into rec
@@ -192,6 +194,8 @@ cudaError_t launch_row_t3(const nuasm_plan_s* P, cudaStream_t s);
 // Fill P->d.etab (etab_elems entries, pitch P->etab_pitch) with the ASM non-separable factor.
 size_t etab_elems(const Geometry& g, int* pitch);
 cudaError_t build_etab(const nuasm_plan_s* P, cudaStream_t s);
+// Fill P->d.etab2 ((N'/2 + 1) x N' entries) from d.etab and the type-2 Tx table.
+cudaError_t build_etab2(const nuasm_plan_s* P, cudaStream_t s);
 cudaError_t launch_col_inv_fold(const nuasm_plan_s* P, cudaStream_t s);
 
 }  // namespace nuasm

@@ -92,6 +92,28 @@ __global__ void etab_kernel(V* __restrict__ out, int half, int pitch, double c, 
 }
 }  // namespace
 
+namespace {
+__global__ void etab2_kernel(float2* __restrict__ out, const float2* __restrict__ etab, const float2* __restrict__ tx,
+                             int np, int pitch) {
+    const int64_t total = int64_t(np / 2 + 1) * np;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int b = int(i / np), q = int(i - int64_t(b) * np);
+        out[i] = cmul(tx[q], etab[size_t(b) * pitch + min(q, np - q)]);
+    }
+}
+}  // namespace
+
+cudaError_t build_etab2(const nuasm_plan_s* P, cudaStream_t s) {
+    if (!P->d.etab || !P->d.etab2 || P->f64) return cudaErrorInvalidValue;
+    const int np = P->g.np;
+    const size_t n = size_t(np / 2 + 1) * np;
+    const int threads = 256;
+    const int blocks = int(std::min<size_t>((n + threads - 1) / threads, size_t(152) * 8));
+    etab2_kernel<<<blocks, threads, 0, s>>>(static_cast<float2*>(P->d.etab2), static_cast<const float2*>(P->d.etab),
+                                            static_cast<const float2*>(P->d.t2x), np, P->etab_pitch);
+    return cudaGetLastError();
+}
+
 cudaError_t build_etab(const nuasm_plan_s* P, cudaStream_t s) {
     int pitch = 0;
     const size_t n = etab_elems(P->g, &pitch);

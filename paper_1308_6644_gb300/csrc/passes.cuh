@@ -106,6 +106,7 @@ struct RowArgs {
     double rc;             // z / (2 lambda)
     float rc_hi, rc_lo;
     const void* etab;      // E(|kx|, |ky|) table of the plan precision, or null (E evaluated per mode)
+    const void* etab2;     // type 2: T2x(kx) E(|kx|, |ky|), rows of N' entries, or null
     int ep;                // entries per table row
     int np;                // N'
 };
@@ -187,7 +188,8 @@ __device__ __forceinline__ V mode_factor(int q, int r, const V* __restrict__ tx,
 }
 
 // Copy the E-table rows of the CTA's rows r0 .. r0 + ROWS - 1 to shared memory at
-// `dst` (ep entries per row) with cp.async.  Returns false (nothing issued) when
+// `dst` (ep entries per row) with cp.async (the caller commits the group and
+// waits for it).  Returns false (nothing issued) when
 // the plan has no table or `dst` is not 16-byte aligned; the decision is the
 // same for every thread of the block.
 template <typename V, int ROWS>
@@ -200,7 +202,6 @@ __device__ __forceinline__ bool stage_erows(V* dst, int r0, const RowArgs& a) {
         const char* src = static_cast<const char*>(a.etab) + size_t(rr) * a.ep * sizeof(V) + 16 * size_t(k);
         cp_async16(reinterpret_cast<char*>(dst) + size_t(c) * a.ep * sizeof(V) + 16 * size_t(k), src);
     }
-    cp_async_commit();
     return true;
 }
 
@@ -287,16 +288,34 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     // runs (waited for after its first pass, whose successors synchronise),
     // clear of M, which its last pass writes at the start of S.
     static_assert(LOGNP > 3, "the staged E rows need a forward transform of at least two passes");
+    // Where the plan has the combined T2x E table, its rows (N' entries,
+    // Tx folded in) are staged instead and the epilogue needs no Tx load.
     V* Es = S + ((spad_size<V>(NP * ROWS) + 1) & ~1);
-    bool staged = false;
-    if constexpr (Cf::MERGE) staged = stage_erows<V, ROWS>(Es, r0, a);
+    int staged = 0;   // 0: nothing staged, 1: E rows, 2: T2x E rows
+    if constexpr (Cf::MERGE) {
+        if (a.etab2 && !(reinterpret_cast<uintptr_t>(Es) & 15)) {
+            constexpr int chunks = int((size_t(NP) * sizeof(V)) / 16);
+            for (int i = threadIdx.x; i < ROWS * chunks; i += Cf::P) {
+                const int c = i / chunks, k = i - c * chunks;
+                const int rr = min(r0 + c, NP - r0 - c);
+                cp_async16(reinterpret_cast<char*>(Es) + (size_t(c) * NP * sizeof(V)) + 16 * size_t(k),
+                           static_cast<const char*>(a.etab2) + (size_t(rr) * NP * sizeof(V)) + 16 * size_t(k));
+            }
+            staged = 2;
+        } else if (stage_erows<V, ROWS>(Es, r0, a)) {
+            staged = 1;
+        }
+        if (staged) cp_async_commit();
+    }
     pdl_wait();   // B comes from the previous kernel
     block_fft<V, -1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
         S, tw, [&](int p, int c) { return p < n ? B[(r0 + c) * n + p] : zero; },
         [&](int p, int c, V v) {
             V f;
-            if (staged) {
-                const V t = ROWS == 1 ? rc0.ty : __ldg(&ty[r0 + c]);
+            const V t = ROWS == 1 ? rc0.ty : __ldg(&ty[r0 + c]);
+            if (staged == 2) {
+                f = cmul(Es[c * NP + p], t);
+            } else if (staged == 1) {
                 f = cmul(cmul(__ldg(&tx[p]), t), Es[c * a.ep + min(p, NP - p)]);
             } else {
                 f = row_factor<V, ROWS>(p, c, r0, rc0, tx, ty, s, a);
@@ -641,6 +660,7 @@ inline RowArgs row_args(const nuasm_plan_s* P) {
     a.rc_hi = float(P->rc);
     a.rc_lo = float(P->rc - double(a.rc_hi));
     a.etab = P->d.etab;
+    a.etab2 = P->d.etab2;
     a.ep = P->etab_pitch;
     a.np = P->g.np;
     return a;

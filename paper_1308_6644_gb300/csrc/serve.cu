@@ -325,6 +325,7 @@ nuasm_status run_job(Server& S, Slot& sl, const Job& j, PointSet* ps, bool build
     view.d.s = part[0] + 6 * np * eb;
     view.d.tw = B->d.tw;
     view.d.etab = nullptr;   // one solve per table: E is evaluated per mode
+    view.d.etab2 = nullptr;
     view.d.win = part[1];
     view.d.bufA = part[2];
     view.d.bufB = part[3];

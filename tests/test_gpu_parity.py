@@ -162,8 +162,9 @@ def test_tabulated_phase_factor_large_phase(P, prec, type_):
     params = P.make_params(n, kw["pitch"], kw["lam"], kw["z"], ox=kw["ox"], oy=kw["oy"], band=kw["band"], prec=prec)
     plan = P.nuasm_plan(params, _t(x), _t(y))
     try:
-        half = 64
-        assert plan.info()["phase_table_bytes"] == (half + 1) * (half + 2) * (8 if prec == "f32" else 16)
+        half = 64   # E over |k| in [0, 64]; FP32 plans add type 2's Tx-folded rows of N' = 128 entries
+        want = (half + 1) * (half + 2) * 16 if prec == "f64" else ((half + 1) * (half + 2) + (half + 1) * 128) * 8
+        assert plan.info()["phase_table_bytes"] == want
     finally:
         plan.destroy()
     if prec == "f32" and type_ == 2:
