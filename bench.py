@@ -173,10 +173,10 @@ def stage_flops(info: dict, m: int, type_: int = 2, f64: bool = False) -> dict:
     complex FFT, one complex multiply (6 flops) per kept mode for the
     transfer function, and per gridding point or record the Horner taps
     (2 axes x w taps x d FMA, d = the tap polynomials' degree: w + 1 in FP32,
-    15 in FP64) plus w^2 complex-by-real MACs."""
+    13 in FP64) plus w^2 complex-by-real MACs."""
     n, np_, W, w = info["n"], info["n_pad"], info["window"], info["kernel_width"]
     fft = 5.0 * np_ * np.log2(np_)
-    d = 15 if f64 else w + 1
+    d = 13 if f64 else w + 1
     taps = 2 * 2 * w * d + 4 * w * w + 4 * w
     if type_ == 1:
         return {"spread": taps * info["records"], "col_fwd_fold": 2 * W * fft,

@@ -235,7 +235,7 @@ __global__ void order_tile_kernel(const Rec* __restrict__ src, Rec* __restrict__
 // --------------------------------------------------------------- kernel values
 // Tap weights of one axis as polynomials in x = 2f - 1 (Horner's rule; the
 // coefficients beyond the fitted degree and the taps beyond w are zero, so
-// the loops unroll fully): degree w + 1 in FP32, 15 in FP64.
+// the loops unroll fully): degree w + 1 in FP32, kPoly64Deg in FP64.
 template <int WMAX> __device__ __forceinline__ void tap_weights(float f, const KernelPoly& kp, float* out) {
     constexpr int DMAX = WMAX + 2 < kPolyMaxD ? WMAX + 2 : kPolyMaxD;
     const float x = fmaf(2.f, f, -1.f);
@@ -251,9 +251,9 @@ template <int WMAX> __device__ __forceinline__ void tap_weights(double f, const 
     const double x = fma(2.0, f, -1.0);
 #pragma unroll
     for (int i = 0; i < WMAX; ++i) {
-        double acc = kp.c[i][kPolyMaxD - 1];
+        double acc = kp.c[i][kPoly64Deg];
 #pragma unroll
-        for (int k = kPolyMaxD - 2; k >= 0; --k) acc = fma(acc, x, kp.c[i][k]);
+        for (int k = kPoly64Deg - 1; k >= 0; --k) acc = fma(acc, x, kp.c[i][k]);
         out[i] = acc;
     }
 }

@@ -487,7 +487,7 @@ int choose_nonsep_mode(const nuasm_params_t& p, double rmax) {
 // Chebyshev interpolation of each tap phi(i + f - w/2), f in [0, 1), at
 // Chebyshev nodes of x = 2f - 1, converted to monomial coefficients in x (the
 // coefficients stay O(1), so Horner's rule is as accurate as direct
-// evaluation of the exponential: FP32 at degree w + 1, FP64 at degree 15).
+// evaluation of the exponential: FP32 at degree w + 1, FP64 at kPoly64Deg).
 template <typename Poly, typename T>
 void fit_poly(const Geometry& g, int d, Poly* kp) {
     std::memset(kp, 0, sizeof(*kp));
@@ -520,7 +520,7 @@ void fit_poly(const Geometry& g, int d, Poly* kp) {
 }
 
 void fit_kernel_poly(const Geometry& g, KernelPoly* kp) { fit_poly<KernelPoly, float>(g, g.w + 1, kp); }
-void fit_kernel_poly64(const Geometry& g, KernelPoly64* kp) { fit_poly<KernelPoly64, double>(g, kPolyMaxD - 1, kp); }
+void fit_kernel_poly64(const Geometry& g, KernelPoly64* kp) { fit_poly<KernelPoly64, double>(g, kPoly64Deg, kp); }
 
 void free_tables(HostTables* t) {
     delete[] t->t1x; delete[] t->t1y; delete[] t->t2x; delete[] t->t2y; delete[] t->t3x; delete[] t->t3y;

@@ -29,8 +29,14 @@ struct KernelPoly {
     float c[kPolyMaxW][kPolyMaxD];
     int deg;
 };
-// the same for FP64 gridding, always of degree kPolyMaxD - 1: the fit error
-// then sits at the kernel's own edge value (3.6e-14 for w = 13)
+#ifndef NUASM_POLY64_DEG
+#define NUASM_POLY64_DEG 13   // measured: 15 and 14 give the same end-to-end errors, 4% more FP64 time
+#endif
+constexpr int kPoly64Deg = NUASM_POLY64_DEG;   // degree of the FP64 tap polynomials
+static_assert(kPoly64Deg < kPolyMaxD, "FP64 tap degree");
+// the same for FP64 gridding, always of degree kPoly64Deg: the fit error
+// then sits near the kernel's own edge value (3.6e-14 at degree 15 for w = 13)
+// and below the default FP64 tolerance (1e-12)
 struct KernelPoly64 {
     double c[kPolyMaxW][kPolyMaxD];
     int deg;
