@@ -450,7 +450,7 @@ def run_ours(args):
     # more than twice the 129 MB L2 through the cache before a plan's data
     # recurs, no flush is needed; smaller workloads flush L2 before every step.
     ws_bytes = sum(stage_bytes(info, wl.m, wl.type, eb).values())
-    e2e_flush = (E2E_LANES - 1) * ws_bytes < 2 * L2_BYTES
+    e2e_flush = e2e_needs_flush(ws_bytes)
     lanes = [(plan, stream, h_in, h_out)]
     for _ in range(E2E_LANES - 1):
         lanes.append((P.nuasm_plan(params, x, y, stream=stream), torch.cuda.Stream(dev),
@@ -559,6 +559,13 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------- batched planes
+def e2e_needs_flush(step_bytes: float, lanes: int = E2E_LANES) -> bool:
+    """Whether the pipelined end-to-end loop must flush L2 before every step:
+    yes unless the other lanes' steps stream more than twice the L2 through
+    the cache before a lane's data recurs."""
+    return (lanes - 1) * step_bytes < 2 * L2_BYTES
+
+
 def _timed_steps(fn, steps, stream, flush):
     import torch
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]

@@ -1,0 +1,83 @@
+"""Host-side pieces of bench.py (no GPU): the algorithmic byte and flop models
+of the roofline, the kernel each stage names, the end-to-end flush rule and
+the rule that reports the committed ncu traffic figures."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import bench
+
+C2 = dict(n=1024, n_pad=2048, window=2056, records=1_200_000, kernel_width=7, tile=64)
+
+
+def test_stage_bytes_of_the_benchmark_geometry():
+    n, np_, W = 1024, 2048, 2056
+    b = bench.stage_bytes(dict(C2, phase_table_bytes=0), 1 << 20, 2, 8)
+    assert b["col_fwd"] == 8 * (n * n + np_ * n)
+    assert b["row_t2"] == 8 * (np_ * n + np_ * W)
+    assert b["col_inv_fold"] == 8 * (np_ * W + W * W)
+    assert b["interp"] == 8 * W * W + 24 * (1 << 20)
+    b1 = bench.stage_bytes(dict(C2, phase_table_bytes=0), 1 << 20, 1, 8)
+    assert b1["spread"] == 24 * C2["records"] + 8 * W * W
+
+
+def test_phase_tables_count_once_per_row_pass():
+    equad = 1025 * 1026 * 8
+    both = equad + 1025 * 2048 * 8
+    t2 = bench.stage_bytes(dict(C2, phase_table_bytes=both), 1 << 20, 2, 8)
+    t1 = bench.stage_bytes(dict(C2, phase_table_bytes=both), 1 << 20, 1, 8)
+    base2 = bench.stage_bytes(dict(C2, phase_table_bytes=0), 1 << 20, 2, 8)
+    base1 = bench.stage_bytes(dict(C2, phase_table_bytes=0), 1 << 20, 1, 8)
+    assert t2["row_t2"] - base2["row_t2"] == 1025 * 2048 * 8     # the Tx-folded rows
+    assert t1["row_t1"] - base1["row_t1"] == equad                # the E quadrant
+    only_e = bench.stage_bytes(dict(C2, phase_table_bytes=equad), 1 << 20, 2, 8)
+    assert only_e["row_t2"] - base2["row_t2"] == equad
+
+
+def test_stage_flops_model():
+    f = bench.stage_flops(C2, 1 << 20, 2)
+    fft = 5.0 * 2048 * np.log2(2048)
+    assert f["col_fwd"] == pytest.approx(1024 * fft)
+    assert f["row_t2"] == pytest.approx(3 * 2048 * fft + 6.0 * 2048 * 2048)
+    w = 7
+    assert f["interp"] == pytest.approx((4 * w * (w + 1) + 4 * w * w + 4 * w) * (1 << 20))
+    f64 = bench.stage_flops(dict(C2, kernel_width=13), 1000, 2, True)
+    assert f64["interp"] == pytest.approx((4 * 13 * 13 + 4 * 13 * 13 + 4 * 13) * 1000)
+
+
+@pytest.mark.parametrize("tile,f64,w,want", [
+    (64, False, 7, "spread_fixed_kernel<7, true, 2>"),
+    (32, False, 7, "spread_private_kernel<float, 7, true>"),
+    (64, False, 13, "spread_fixed_kernel<16, false, 2>"),
+    (16, True, 13, "spread_private_kernel<double, 13, true>"),
+    (64, True, 13, "spread_kernel<double, 13, true>"),
+])
+def test_spreading_kernel_names(tile, f64, w, want):
+    assert bench.kernel_of_stage("spread", dict(n_pad=2048, kernel_width=w, tile=tile), f64) == want
+
+
+def test_column_kernel_names_follow_the_tma_rule():
+    assert bench.kernel_of_stage("col_inv_fold", dict(n_pad=2048, kernel_width=7), False) == "col_tma_kernel<11, 3>"
+    assert bench.kernel_of_stage("col_fwd", dict(n_pad=2048, kernel_width=7), False) == "col_kernel<float2, 11, 2>"
+    assert bench.kernel_of_stage("col_fwd", dict(n_pad=4096, kernel_width=7), False) == "col_tma_kernel<12, 2>"
+    assert bench.kernel_of_stage("col_inv_fold", dict(n_pad=2048, kernel_width=13), True) == \
+        "col_kernel<double2, 11, 3>"
+
+
+def test_e2e_flush_rule():
+    assert bench.e2e_needs_flush(0.8e6)            # a 64^2 plane stays in L2
+    assert not bench.e2e_needs_flush(211e6)        # the benchmark plane does not
+    assert bench.e2e_needs_flush(211e6, lanes=2)   # one other lane: 211 MB < 2 x 129 MB
+
+
+def test_traffic_is_reported_only_for_the_profiled_source(monkeypatch):
+    with open(os.path.join(bench.ROOT, "profiles", "traffic.json")) as fh:
+        t = json.load(fh)
+    rec = t["row_t2"]
+    monkeypatch.setattr(bench, "source_hash", lambda stage: rec["source_hash"])
+    assert bench.measured_traffic("row_t2") == rec["dram_bytes_per_launch"]
+    monkeypatch.setattr(bench, "source_hash", lambda stage: "0" * 16)
+    assert bench.measured_traffic("row_t2") is None
+    assert bench.measured_traffic("no_such_stage") is None
