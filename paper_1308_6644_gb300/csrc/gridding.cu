@@ -578,10 +578,15 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
 // elements (halo_pitch), matching the record order's bank classes.
 // The first kInterpPrefetch records of every thread are loaded before the
 // staging loads so that their latency overlaps the tile's; FP32 tiles are
-// staged two complex values (16 B) per load.
+// staged two complex values (16 B) per cp.async copy, straight into shared
+// memory (measured against loads through registers: NU-ASM_2 interpolation
+// 32.0 -> 30.2 us, 4M clustered points 106.8 -> 96.6 us).
 constexpr int kInterpThreads = 256, kInterpPrefetch = 4;
 #ifndef NUASM_F64_EXACT13
 #define NUASM_F64_EXACT13 1
+#endif
+#ifndef NUASM_INTERP_CPASYNC
+#define NUASM_INTERP_CPASYNC 1   // FP32 tiles staged with cp.async (no register round trip)
 #endif
 #ifndef NUASM_INTERP_MINB
 #define NUASM_INTERP_MINB 4   // CTAs per SM the register budget is sized for (64 registers)
@@ -649,11 +654,20 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
         for (int i = threadIdx.x; i < TH * HP; i += kInterpThreads) {
             const int yy = i / HP, u = i - yy * HP;
             const int gy = y0 + yy, gx = x0 + 2 * u;
+#if NUASM_INTERP_CPASYNC
+            if (2 * u < TH && gy < a.W && gx < a.W) cp_async16(&tl4[i], &win[size_t(gy) * a.Wp + gx]);
+            else tl4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+#else
             float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
             if (2 * u < TH && gy < a.W && gx < a.W)
                 val = *reinterpret_cast<const float4*>(&win[size_t(gy) * a.Wp + gx]);
             tl4[i] = val;
+#endif
         }
+#if NUASM_INTERP_CPASYNC
+        cp_async_commit();
+        cp_async_wait_all();
+#endif
     } else {
         for (int i = threadIdx.x; i < TH * THP; i += kInterpThreads) {
             const int yy = i / THP, xx = i - yy * THP;
