@@ -194,3 +194,50 @@ def test_bounded_wait_diagnostic_rejects_bad_counts(P):
     lib = P.lib()
     assert lib.nuasm_debug_bounded_wait(0, None) == 1
     assert lib.nuasm_debug_bounded_wait((1 << 24) + 1, None) == 1
+
+
+_CTYPE_OF = {"int32_t": "c_int32", "int64_t": "c_int64", "uint64_t": "c_uint64", "double": "c_double",
+             "float": "c_float"}
+
+
+def _header_structs():
+    """name -> [(field, C type)] for every typedef'd struct of include/nuasm.h."""
+    src = open(os.path.join(ROOT, "include", "nuasm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(\w+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"(const\s+)?([\w]+)(\s*\*)?\s+(.*)", decl)
+            ctype, ptr, names = m.group(2), m.group(3), m.group(4)
+            for nm in names.split(","):
+                nm = nm.strip()
+                fields.append((nm.lstrip("*"), "ptr" if (ptr or nm.startswith("*") or ctype.endswith("_t")
+                                                            and ctype.startswith("nuasm_plan")) else ctype))
+        out[name] = fields
+    return out
+
+
+@pytest.mark.parametrize("c_name,py_name", [
+    ("nuasm_params_t", "Params"), ("nuasm_plan_info_t", "PlanInfo"), ("nuasm_batch_item_t", "BatchItem"),
+    ("nuasm_server_config_t", "ServerConfig"), ("nuasm_request_t", "Request"),
+    ("nuasm_request_result_t", "RequestResult"), ("nuasm_server_stats_t", "ServerStats"),
+])
+def test_binding_structs_mirror_the_header(c_name, py_name):
+    """The ctypes mirrors list the header's fields in the same order with the
+    same scalar types (pointers and handles as pointers), so the ABI cannot
+    drift silently."""
+    from paper_1308_6644_gb300 import nuasm as B
+    fields = _header_structs()[c_name]
+    py = getattr(B, py_name)._fields_
+    # a Python keyword gets a trailing underscore (lambda -> lambda_)
+    assert [f for f, _ in fields] == [f.rstrip("_") for f, _ in py], (c_name, fields, py)
+    for (fname, ctype), (pname, ptype) in zip(fields, py):
+        if ctype == "ptr":
+            assert ptype in (ctypes.c_void_p,) or issubclass(ptype, ctypes._Pointer) or ptype is ctypes.c_char_p, \
+                (c_name, fname, ptype)
+        elif ctype in _CTYPE_OF:
+            assert ptype is getattr(ctypes, _CTYPE_OF[ctype]), (c_name, fname, ctype, ptype)
