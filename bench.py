@@ -149,30 +149,46 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline bookkeeping
 def stage_bytes(info: dict, m: int, type_: int = 2, eb: int = 8) -> dict:
-    """Algorithmic HBM bytes per launch of each stage (eb = 8 for complex64,
-    16 for complex128): each input read once, each output written once,
-    records 16 B (24 B in FP64) per record; the row pass also reads the
-    plan's table of the non-separable phase factor once, where it has one."""
+    """Algorithmic HBM bytes per launch of each stage, the pruned chain's
+    figures: each grid input read once and each grid output written once
+    (eb = 8 B per complex64 value, 16 per complex128), and per non-uniform
+    point its value (eb) plus a 12-byte sorted record (two fractional offsets
+    and the packed cell; 20 B per point in complex64).  Plan-owned tables
+    (the transfer function's phase-factor table the row passes read, this
+    library's 16-byte record format, the halo duplicates of the tiles) are
+    not algorithmic bytes; see plan_table_bytes."""
     n, np_, W = info["n"], info["n_pad"], info["window"]
-    rb = 16 if eb == 8 else 24
-    # the plan's phase tables: E over the |k| quadrant, plus (FP32) type 2's
-    # Tx-folded rows; each row pass reads one of them once
-    tables = info.get("phase_table_bytes", 0)
-    equad = (np_ // 2 + 1) * (np_ // 2 + 2) * eb if tables else 0
-    etab2 = tables - equad
+    pt = eb + 12
     if type_ == 1:
         return {
-            "spread": (rb + eb) * info["records"] + eb * W * W,
+            "spread": pt * m + eb * W * W,
             "col_fwd_fold": eb * (2 * W * W + np_ * W),
-            "row_t1": eb * (np_ * W + np_ * n) + equad,
+            "row_t1": eb * (np_ * W + np_ * n),
             "col_inv": eb * (np_ * n + n * n),
         }
     return {
         "col_fwd": eb * (n * n + np_ * n),
-        "row_t2": eb * (np_ * n + np_ * W) + (etab2 if etab2 > 0 else equad),
+        "row_t2": eb * (np_ * n + np_ * W),
         "col_inv_fold": eb * (np_ * W + W * W),
-        "interp": eb * W * W + (rb + eb) * m,
+        "interp": eb * W * W + pt * m,
     }
+
+
+def plan_table_bytes(info: dict, type_: int = 2, eb: int = 8) -> dict:
+    """Bytes of plan-owned tables a stage reads on top of its algorithmic
+    bytes: the row pass's non-separable phase-factor table (E over the |k|
+    quadrant, or type 2's rows with the per-column factor folded in), and the
+    gridding stages' records beyond 12 B per point (16 B / 24 B records, halo
+    duplicates)."""
+    np_ = info["n_pad"]
+    tables = info.get("phase_table_bytes", 0)
+    equad = (np_ // 2 + 1) * (np_ // 2 + 2) * eb if tables else 0
+    etab2 = tables - equad
+    rb = 16 if eb == 8 else 24
+    extra_rec = rb * info["records"] - 12 * info["points"]
+    if type_ == 1:
+        return {"row_t1": equad, "spread": extra_rec + eb * (info["records"] - info["points"])}
+    return {"row_t2": etab2 if etab2 > 0 else equad, "interp": (rb - 12) * info["points"]}
 
 
 # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64: the part's nominal rate
@@ -239,9 +255,9 @@ def source_hash(stage: str) -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(stage: str, workload: str = "nuasm2"):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+def ncu_record(stage: str, workload: str = "nuasm2"):
+    """The committed ncu counters of a stage's kernel (profiles/traffic.json),
+    if they were taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -251,7 +267,26 @@ def measured_traffic(stage: str, workload: str = "nuasm2"):
     rec = t.get(stage if workload == "nuasm2" else f"{workload}:{stage}")
     if not rec or rec.get("source_hash") != source_hash(stage):
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec
+
+
+def measured_traffic(stage: str, workload: str = "nuasm2"):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    rec = ncu_record(stage, workload)
+    return None if rec is None else rec.get("dram_bytes_per_launch")
+
+
+def ncu_limiter(stage: str, workload: str = "nuasm2"):
+    """Issue-slot and pipe utilisation of a stage's kernel from the committed
+    ncu capture (fractions of the kernel's cycles), or None."""
+    rec = ncu_record(stage, workload)
+    if rec is None:
+        return None
+    keys = {"issue_active": "issue_active_pct", "fma_pipe": "fma_pipe_pct", "lsu_pipe": "lsu_pipe_pct",
+            "shared_pipe": "shared_pipe_pct", "dram_throughput": "dram_throughput_pct"}
+    out = {k: round(rec[v] / 100.0, 3) for k, v in keys.items() if v in rec}
+    return out or None
 
 
 def hbm_peak():
@@ -390,7 +425,8 @@ def run_ours(args):
     wl = make(WL)
     f64 = prec == "f64"
     cdt, tdt, eb = (np.complex128, torch.complex128, 16) if f64 else (np.complex64, torch.complex64, 8)
-    params = P.make_params(wl.n, wl.pitch, wl.lam, wl.z, ox=wl.ox, oy=wl.oy, kind=wl.kind, prec=prec)
+    params = P.make_params(wl.n, wl.pitch, wl.lam, wl.z, ox=wl.ox, oy=wl.oy, kind=wl.kind, prec=prec,
+                           kernel=args.kernel, tol=args.tol)
     stream = torch.cuda.current_stream(dev)
     x = torch.from_numpy(wl.x).to(dev)
     y = torch.from_numpy(wl.y).to(dev)
@@ -499,6 +535,7 @@ def run_ours(args):
     prof = P.nuasm_profile_read(plan)
     P.nuasm_profile_enable(plan, False)
     sbytes = stage_bytes(info, wl.m, wl.type, eb)
+    tbytes = plan_table_bytes(info, wl.type, eb)
     sflops = stage_flops(info, wl.m, wl.type, f64)
     peak, peak_kind = hbm_peak()
     alu_peak = ALU_PEAK_TFLOPS[f64]
@@ -510,7 +547,8 @@ def run_ours(args):
             gbs, tfs = b / (avg * 1e-3) / 1e9, sflops[name] / (avg * 1e-3) / 1e12
             # the binding roof: the one this stage's algorithmic work takes longest on
             bound = "alu" if sflops[name] / (alu_peak * 1e12) > b / (peak * 1e9) else "hbm"
-            stages[name] = {"ms": avg, "gbs": gbs, "tfs": tfs, "bound": bound,
+            stages[name] = {"ms": avg, "gbs": gbs, "tfs": tfs, "bound": bound, "hbm_frac": gbs / peak,
+                            "alu_frac": tfs / alu_peak,
                             "frac": (tfs / alu_peak) if bound == "alu" else (gbs / peak)}
     dom = max(stages, key=lambda s: stages[s]["ms"])
     d = stages[dom]
@@ -522,16 +560,34 @@ def run_ours(args):
         roofline = {"bound": "hbm", "achieved": d["gbs"], "peak": peak, "unit": "GB/s", "frac": d["frac"],
                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                     if peak_kind == "measured" else "fallback 6.8 TB/s"}
+
+    def stage_rec(k, v):
+        r = {"ms": round(v["ms"], 5), "GB/s": round(v["gbs"], 1), "TFLOP/s": round(v["tfs"], 2),
+             "bound": v["bound"], "frac": round(v["frac"], 3), "hbm_frac": round(v["hbm_frac"], 3),
+             "alu_frac": round(v["alu_frac"], 3), "algorithmic_bytes": int(sbytes[k])}
+        if tbytes.get(k):
+            r["plan_table_bytes"] = int(tbytes[k])
+        lim = ncu_limiter(k, args.workload)
+        if lim:
+            r["ncu"] = lim
+        return r
+
     roofline.update({"traffic": measured_traffic(dom, args.workload), "kernel": kernel_of_stage(dom, info, f64),
-                     "stages": {k: {"ms": round(v["ms"], 5), "GB/s": round(v["gbs"], 1),
-                                    "TFLOP/s": round(v["tfs"], 2), "bound": v["bound"],
-                                    "frac": round(v["frac"], 3)} for k, v in stages.items()}})
+                     "algorithmic_bytes": int(sbytes[dom]), "algorithmic_flops": float(sflops[dom]),
+                     "hbm_frac": round(d["hbm_frac"], 4), "alu_frac": round(d["alu_frac"], 4),
+                     "bytes_model": "grid values read and written once (8 B complex64) + 20 B per point "
+                                    "(value + 12-byte record); plan tables excluded",
+                     "stages": {k: stage_rec(k, v) for k, v in stages.items()}})
+    lim = ncu_limiter(dom, args.workload)
+    if lim:
+        roofline["ncu_limiter"] = lim
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
             "config": {"workload": label, "n": wl.n, "n_pad": info["n_pad"], "points": wl.m,
-                       "kernel_width": info["kernel_width"],
+                       "kernel": args.kernel, "tol": params.tol or (1e-12 if f64 else 1e-6),
+                       "kernel_width": info["kernel_width"], "tile": info["tile"],
                        "precision": "complex128" if f64 else "complex64 + FP64-derived phase",
                        "l2": "flushed (256 MB write) before every step", "plan_s": round(plan_s, 3),
                        "parallelism": f"replicas x{ws}"},
@@ -562,6 +618,18 @@ def run_ours(args):
                             dict(n=wl.n, pitch=wl.pitch, lam=wl.lam, z=wl.z)).reshape(-1)
             line["rel_l2_vs_fp64"] = float(O.rel_l2(out.cpu().numpy(), want))
     plan.destroy()
+    del flush, h_in, h_out
+    if rank == 0 and ws == 1 and args.workload == "nuasm2" and args.served_requests > 0:
+        # the served form on a bounded trace (continuous batching over resident
+        # point sets) beside the plain one-plane-per-call path on the same requests
+        torch.cuda.synchronize()
+        r = serve_session(P, local, args.served_requests, args.served_sets, args.slots, 12, 24, clocks=False)
+        line["served"] = {k: r[k] for k in (
+            "requests", "sets", "slots", "failed", "arrival_rate_per_s", "p50_ms", "p99_ms",
+            "served_points_per_s", "plain_points_per_s", "served_over_plain", "plain_resident_points_per_s",
+            "served_over_plain_resident", "plain", "plain_resident", "inputs")}
+        line["served"]["workload"] = (f"Poisson arrivals of {r['requests']} requests over {r['sets']} resident point "
+                                      "sets (N 1024-4096, 0.9M-10M points), type 1/2, z and lambda per request")
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -701,69 +769,67 @@ def run_batch(args):
 
 
 # ---------------------------------------------------------------- serving loop
-def run_serve(args):
+def serve_session(P, local: int, n_requests: int, n_sets: int, slots: int, plain_requests: int,
+                  resident_requests: int, clocks=True) -> dict:
     """Poisson arrivals of requests over resident point sets (N in
     {512..4096}, up to 16M points), each with its own wavelength, distance and
-    type, served with continuous batching; against the same requests run one
-    at a time through the plain path (plan, execute, destroy)."""
+    type, served with continuous batching, against the same requests run one
+    at a time by the plain path: (a) per request nuasm_plan from host
+    coordinates, execute with host buffers, destroy; (b) execute with host
+    buffers on plans built beforehand (resident), waiting for each."""
     import torch
     from paper_1308_6644_gb300 import workloads as WL
-    ws, rank, local = _dist()
-    if ws > 1 and rank != 0:
-        return 0          # one server per GPU; replicas add nothing to this line
-    torch.cuda.set_device(local)
-    from paper_1308_6644_gb300 import _build
-    _build.build()
-    import paper_1308_6644_gb300 as P
-    sets = [WL.serving_point_set(1005, k) for k in range(args.sets)]
-    trace = WL.serving_trace(1005, args.requests, len(sets))
+    sets = [WL.serving_point_set(1005, k) for k in range(n_sets)]
+    trace = WL.serving_trace(1005, n_requests, len(sets))
     rng = np.random.default_rng(1005)
     host = []
-    for s in sets:
-        nn = s.n * s.n
-        host.append({"in1": torch.from_numpy(WL.random_phasor(rng, s.m).astype(np.complex64)).pin_memory(),
+    for st_ in sets:
+        nn = st_.n * st_.n
+        host.append({"in1": torch.from_numpy(WL.random_phasor(rng, st_.m).astype(np.complex64)).pin_memory(),
                      "in2": torch.from_numpy(WL.random_phasor(rng, nn).astype(np.complex64)).pin_memory(),
                      "out1": [torch.empty(nn, dtype=torch.complex64).pin_memory() for _ in range(2)],
-                     "out2": [torch.empty(s.m, dtype=torch.complex64).pin_memory() for _ in range(2)]})
+                     "out2": [torch.empty(st_.m, dtype=torch.complex64).pin_memory() for _ in range(2)]})
 
     def request(i, rec):
         k, t, z, lam, _ = rec
-        s, h = sets[k], host[k]
-        params = P.make_params(s.n, s.pitch, lam, z, kind="asm", prec="f32")
+        st_, h = sets[k], host[k]
+        params = P.make_params(st_.n, st_.pitch, lam, z, kind="asm", prec="f32")
         inp = h["in1"] if t == 1 else h["in2"]
         out = (h["out1"] if t == 1 else h["out2"])[i % 2]
-        return s, params, t, inp, out
+        return st_, params, t, inp, out
 
-    srv = P.nuasm_server_create(slots=args.slots)
+    srv = P.nuasm_server_create(slots=slots)
     # every set binned once (resident from then on)
     warm = []
-    for k, s in enumerate(sets):
-        params = P.make_params(s.n, s.pitch, 532e-9, 0.1, kind="asm", prec="f32")
-        warm.append(P.nuasm_server_submit(srv, params, 2, s.x, s.y, host[k]["in2"], host[k]["out2"][0],
+    for k, st_ in enumerate(sets):
+        params = P.make_params(st_.n, st_.pitch, 532e-9, 0.1, kind="asm", prec="f32")
+        warm.append(P.nuasm_server_submit(srv, params, 2, st_.x, st_.y, host[k]["in2"], host[k]["out2"][0],
                                           points_id=k + 1))
     for t in warm:
         P.nuasm_server_wait(srv, t)
+
     def closed_burst(recs):
         t0 = time.perf_counter()
         tk, pts = [], 0
         for i, rec in enumerate(recs):
-            s, params, t, inp, out = request(i, rec)
-            tk.append(P.nuasm_server_submit(srv, params, t, s.x, s.y, inp, out, points_id=rec[0] + 1))
-            pts += s.m
+            st_, params, t, inp, out = request(i, rec)
+            tk.append(P.nuasm_server_submit(srv, params, t, st_.x, st_.y, inp, out, points_id=rec[0] + 1))
+            pts += st_.m
         for t in tk:
             P.nuasm_server_wait(srv, t)
         return time.perf_counter() - t0, pts
 
     # warm the pools and staging buffers, then probe the capacity with a closed burst
-    closed_burst(trace[: min(len(trace), 4 * args.slots)])
-    burst = trace[: min(len(trace), 16 * args.slots)]
+    closed_burst(trace[: min(len(trace), 4 * slots)])
+    burst = trace[: min(len(trace), 16 * slots)]
     el, pts = closed_burst(burst)
     rate = len(burst) / el                               # requests/s the GPU sustains
     capacity = pts / el
     P.nuasm_server_stats(srv, reset=True)
     # Poisson arrivals at the measured capacity (saturating)
-    clocks = ClockSampler(local)
-    clocks.start()
+    clk_s = ClockSampler(local) if clocks else None
+    if clk_s:
+        clk_s.start()
     t_start = time.perf_counter()
     arrival = 0.0
     tickets = []
@@ -772,49 +838,92 @@ def run_serve(args):
         delay = t_start + arrival - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        s, params, t, inp, out = request(i, rec)
-        tickets.append(P.nuasm_server_submit(srv, params, t, s.x, s.y, inp, out, points_id=rec[0] + 1))
+        st_, params, t, inp, out = request(i, rec)
+        tickets.append(P.nuasm_server_submit(srv, params, t, st_.x, st_.y, inp, out, points_id=rec[0] + 1))
     res = [P.nuasm_server_wait(srv, t) for t in tickets]
-    clk = clocks.stop()
+    clk = clk_s.stop() if clk_s else None
     st = P.nuasm_server_stats(srv)
     srv.destroy()
     failed = sum(1 for r in res if r["status"] != 0)
     served = st["points"] / st["wall_s"]
-    # plain path: the first requests of the same trace, one at a time
-    n_plain = min(len(trace), args.plain_requests)
+    # plain path (a): the first requests of the same trace, one at a time, plan per request
+    n_plain = min(len(trace), plain_requests)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     pts = 0
     for i, rec in enumerate(trace[:n_plain]):
-        s, params, t, inp, out = request(i, rec)
-        plan = P.nuasm_plan(params, s.x, s.y)
+        st_, params, t, inp, out = request(i, rec)
+        plan = P.nuasm_plan(params, st_.x, st_.y)
         (P.nuasm1_execute if t == 1 else P.nuasm2_execute)(plan, inp, out)
         plan.destroy()
-        pts += s.m
+        pts += st_.m
     plain = pts / (time.perf_counter() - t0)
+    # plain path (b): plans of the first requests built beforehand (resident),
+    # then one execute at a time with the same host buffers, each waited for
+    n_res = min(len(trace), resident_requests)
+    stream = torch.cuda.current_stream()
+    plans = []
+    for i, rec in enumerate(trace[:n_res]):
+        st_, params, t, inp, out = request(i, rec)
+        plans.append((P.nuasm_plan(params, torch.from_numpy(st_.x).cuda(), torch.from_numpy(st_.y).cuda()),
+                      t, inp, out, st_.m))
+    for plan, t, inp, out, _ in plans[:2]:
+        (P.nuasm1_execute if t == 1 else P.nuasm2_execute)(plan, inp, out, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pts = 0
+    for plan, t, inp, out, m in plans:
+        (P.nuasm1_execute if t == 1 else P.nuasm2_execute)(plan, inp, out, stream=stream)
+        stream.synchronize()
+        pts += m
+    plain_res = pts / (time.perf_counter() - t0)
+    for plan, *_ in plans:
+        plan.destroy()
     h2d = d2h = 0
     for rec in trace:
-        s = sets[rec[0]]
-        h2d += 8 * (s.m if rec[1] == 1 else s.n * s.n)
-        d2h += 8 * (s.n * s.n if rec[1] == 1 else s.m)
-    line = {"metric": METRIC, "value": served, "unit": UNIT, "n_gpus": 1, "steps": len(trace),
-            "warmup": len(burst), "ms_per_step": 1e3 * st["wall_s"] / len(trace), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"serve_poisson_{len(trace)}req_{len(sets)}sets_n512-4096",
-                       "slots": args.slots, "arrival_rate_per_s": rate, "closed_loop_points_per_s": capacity,
-                       "failed": failed,
-                       "points_served": st["points"], "bins_built_during_run": st["bins_built"],
-                       "resident_sets": st["resident_sets"], "resident_gb": st["resident_bytes"] / 1e9,
-                       "peak_budget_gb": st["peak_bytes"] / 1e9, "hbm_budget_gb": 150,
-                       "plain_points_per_s": plain, "plain_requests_timed": n_plain,
-                       "served_over_plain": served / plain,
-                       "plain": "per request: nuasm_plan from host coordinates, execute with host buffers, destroy",
-                       "inputs": "pinned host memory, copied in and out by every request"},
-            "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
-            "e2e": {"value": served, "unit": UNIT, "h2d_bytes_per_step": h2d // len(trace),
-                    "d2h_bytes_per_step": d2h // len(trace)},
-            "gpu_launches": 4 * len(trace),
+        st_ = sets[rec[0]]
+        h2d += 8 * (st_.m if rec[1] == 1 else st_.n * st_.n)
+        d2h += 8 * (st_.n * st_.n if rec[1] == 1 else st_.m)
+    return {"requests": len(trace), "sets": len(sets), "slots": slots, "warmup_requests": len(burst),
+            "failed": failed, "arrival_rate_per_s": rate, "closed_loop_points_per_s": capacity,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "wall_s": st["wall_s"],
+            "served_points_per_s": served, "points_served": st["points"],
+            "bins_built_during_run": st["bins_built"], "resident_sets": st["resident_sets"],
+            "resident_gb": st["resident_bytes"] / 1e9, "peak_budget_gb": st["peak_bytes"] / 1e9,
+            "hbm_budget_gb": 150,
+            "plain_points_per_s": plain, "plain_requests_timed": n_plain, "served_over_plain": served / plain,
+            "plain": "per request: nuasm_plan from host coordinates, execute with host buffers, destroy",
+            "plain_resident_points_per_s": plain_res, "plain_resident_requests_timed": n_res,
+            "served_over_plain_resident": served / plain_res,
+            "plain_resident": "per request: execute with host buffers on a plan built beforehand, waited for",
+            "inputs": "pinned host memory, copied in and out by every request",
+            "h2d_bytes_per_request": h2d // len(trace), "d2h_bytes_per_request": d2h // len(trace),
             "clocks": clk}
+
+
+def run_serve(args):
+    """The serving loop as its own bench line (see serve_session)."""
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1 and rank != 0:
+        return 0          # one server per GPU; replicas add nothing to this line
+    torch.cuda.set_device(local)
+    from paper_1308_6644_gb300 import _build
+    _build.build()
+    import paper_1308_6644_gb300 as P
+    r = serve_session(P, local, args.requests, args.sets, args.slots, args.plain_requests, args.plain_requests)
+    n = r["requests"]
+    line = {"metric": METRIC, "value": r["served_points_per_s"], "unit": UNIT, "n_gpus": 1, "steps": n,
+            "warmup": r["warmup_requests"], "ms_per_step": 1e3 * r["wall_s"] / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serve_poisson_{n}req_{r['sets']}sets_n512-4096",
+                       **{k: v for k, v in r.items() if k not in ("clocks", "p50_ms", "p99_ms")}},
+            "latency_ms": {"p50": r["p50_ms"], "p99": r["p99_ms"]},
+            "e2e": {"value": r["served_points_per_s"], "unit": UNIT,
+                    "h2d_bytes_per_step": r["h2d_bytes_per_request"],
+                    "d2h_bytes_per_step": r["d2h_bytes_per_request"]},
+            "gpu_launches": 4 * n,
+            "clocks": r["clocks"]}
     print(json.dumps(line))
     return 0
 
@@ -836,6 +945,13 @@ def main(argv=None):
     ap.add_argument("--sets", type=int, default=12)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--plain-requests", type=int, default=60)
+    ap.add_argument("--served-requests", type=int, default=200,
+                    help="default workload: requests of the bounded serving trace reported under 'served' (0: skip)")
+    ap.add_argument("--served-sets", type=int, default=6)
+    ap.add_argument("--kernel", choices=["es", "gaussian"], default="es",
+                    help="spreading kernel of the single-solve workloads (gaussian: the paper's Greengard-Lee kernel)")
+    ap.add_argument("--tol", type=float, default=0.0,
+                    help="NUFFT tolerance of the single-solve workloads (0: the precision's default)")
     ap.add_argument("--autotune", action="store_true",
                     help="batch64: time every tile side per plane (nuasm_autotune_tile) instead of the library's rule")
     args = ap.parse_args(argv)

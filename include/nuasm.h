@@ -36,6 +36,14 @@
  *    from a later call.
  *  - Errors are returned, never thrown or printed.  On any non-OK status no
  *    output has been written unless stated otherwise.
+ *  - Device waits are bounded.  When one gives up (a copy that never
+ *    arrived), the kernel sets a flag in the plan's host-mapped error word and
+ *    that launch's output is incomplete; the plan's next execute call (or
+ *    nuasm_batch_execute of a batch holding the plan, or nuasm_destroy)
+ *    returns NUASM_ETIMEOUT without doing any work and clears the flag, so
+ *    the call after it runs normally.  Reading the flag adds no
+ *    synchronisation: a wait still running when the next call starts is
+ *    reported by a later one.
  *  - A plan may be used by one stream at a time.
  */
 #ifndef NUASM_H
@@ -77,8 +85,11 @@ typedef enum {
 
 /* Problem definition (Eq. 4 / Eq. 5 parameters).  Plain old data. */
 typedef struct {
-    int32_t n;          /* N: side of the uniform plane; power of two, 16..4096 (F32) / 16..2048 (F64) */
-    int32_t n_pad;      /* N': 0 selects 2N (the paper's padding); else a power of two >= 2N */
+    int32_t n;          /* N: side of the uniform plane, even (the paper's N' = 2N padding); this build
+                           runs powers of two 16..4096 (F32) / 16..2048 (F64) and returns
+                           NUASM_EUNSUPPORTED for other even sizes */
+    int32_t n_pad;      /* N': 0 selects 2N (the paper's padding); else an even N' >= 2N, run when it
+                           is a power of two (else NUASM_EUNSUPPORTED) */
     double  pitch;      /* pitch of the uniform plane in metres (Delta_2 for type 1, Delta_1 for type 2) */
     double  lambda;     /* wavelength, metres, > 0 */
     double  z;          /* propagation distance, metres; != 0 for Fresnel */
@@ -140,10 +151,13 @@ typedef struct {
  *  stream   stream for the plan's device work; the call synchronises it
  *           before returning.
  *
- * Returns NUASM_EINVAL for bad parameters (N not a power of two or out of
- * range, pitch/lambda <= 0, Fresnel with z == 0, m < 0, NULL coordinates with
- * m > 0, tol outside (0, 0.1]), NUASM_ERANGE if any point is outside the
- * window, NUASM_ENOMEM, NUASM_ECUDA.  The plan allocates all the device memory
+ * Returns NUASM_EINVAL for bad parameters (N odd or < 2, N' odd or < 2N,
+ * pitch/lambda <= 0, Fresnel with z == 0, m < 0, NULL coordinates with
+ * m > 0, tol outside (0, 0.1]), NUASM_EUNSUPPORTED for valid problems this
+ * build does not run (N or N' not a power of two, N < 16, N' above 8192
+ * (F32) / 4096 (F64), a kernel needing more than 16 taps for the tolerance),
+ * NUASM_ERANGE if any point is outside the window, NUASM_ENOMEM, NUASM_ECUDA.
+ * A failure releases everything the call had acquired.  The plan allocates all the device memory
  * its execute calls will need.  For the ASM with z != 0 that includes a table
  * of the transfer function's non-separable phase factor over |kx|, |ky| in
  * [0, N'/2] (about N'^2/4 complex values in the plan precision, computed in
@@ -245,6 +259,36 @@ nuasm_status nuasm_autotune_tile(const nuasm_params_t* p, int64_t m, const doubl
                                  void* stream, int32_t* tile, double* ms);
 
 /*
+ * nuasm_debug_plan_wait -- the same diagnostic aimed at a plan (the paper has
+ * no counterpart): runs the bounded wait on an mbarrier nothing completes,
+ * with `plan`'s error word as the flag it sets when it gives up after
+ * `spins` try-waits (1 .. 2^24), exactly as a column pass whose copy never
+ * arrived would.  Synchronises `stream` and returns NUASM_OK; the plan's
+ * next execute call then returns NUASM_ETIMEOUT.  NUASM_EINVAL for a NULL
+ * plan or a bad count.
+ */
+nuasm_status nuasm_debug_plan_wait(nuasm_plan_t plan, int32_t spins, void* stream);
+
+/*
+ * nuasm_debug_fail_alloc -- test hook for the clean-up paths (the paper has
+ * no counterpart).  k > 0: the k-th resource acquisition of the library from
+ * now on -- a device, pool or pinned host allocation, a stream, an event or a
+ * graph instantiation, in any call and any thread -- fails as if the device
+ * were out of memory (the call that made it returns NUASM_ENOMEM, a server
+ * request that made it completes with that status); the hook then disarms.
+ * k = 0 disarms it.  NUASM_EINVAL for k < 0.  Host only.
+ */
+nuasm_status nuasm_debug_fail_alloc(int64_t k);
+
+/*
+ * nuasm_debug_live_resources -- number of the library's resource
+ * acquisitions (as counted by nuasm_debug_fail_alloc) not yet released, in
+ * *count.  After a failed call it is back where it was before the call.
+ * Host only.
+ */
+nuasm_status nuasm_debug_live_resources(int64_t* count);
+
+/*
  * nuasm_debug_bounded_wait -- diagnostic for the failure path of the bounded
  * device waits (the paper has no counterpart).  Runs one CTA that waits, with
  * the loop the TMA column passes use, on an mbarrier nothing completes,
@@ -302,12 +346,13 @@ const char* nuasm_stage_name(int32_t stage);
  * nuasm2_solve_noalloc -- NU-ASM_2 (the same result as nuasm_plan followed by
  * nuasm2_execute) in one call that allocates nothing.  The paper has no
  * counterpart: this exists for callers that must not call cudaMalloc or any
- * allocating routine -- code running while a stream is captured into a CUDA
- * graph, plug-ins whose host framework owns all device memory, real-time
- * loops that cannot take an allocation's latency or failure.  Those callers
- * cannot build a plan, so the plan work and the solve happen here, with every
- * intermediate in one 16 MiB file-scope device array that every GPU loading
- * the library holds until the process exits.
+ * allocating routine -- plug-ins whose host framework owns all device
+ * memory, real-time loops that cannot take an allocation's latency or
+ * failure.  Those callers cannot build a plan, so the plan work and the
+ * solve happen here, with every intermediate in one 16 MiB file-scope device
+ * array that every GPU loading the library holds until the process exits.
+ * The call copies its tables from host memory, reads its error word back and
+ * synchronises its stream before returning.
  *
  *  p         parameters; kind must be NUASM_KIND_ASM and prec
  *            NUASM_PREC_F32_F64PHASE (else NUASM_EINVAL).
@@ -319,7 +364,8 @@ const char* nuasm_stage_name(int32_t stage);
  *            returning (it reads back the out-of-window flag).
  *
  * Limits: N <= 256 and N' <= 512 and m <= 65536, else NUASM_EUNSUPPORTED;
- * host pointers give NUASM_EINVAL.  The device address of the array is looked
+ * host pointers give NUASM_EINVAL; a point outside the window gives
+ * NUASM_ERANGE and a bounded device wait that gave up NUASM_ETIMEOUT.  The device address of the array is looked
  * up on the first call made on each device; make that first call before any
  * stream capture begins.  Every call reuses the same array (counters are
  * cleared at the start of each call); calls whose device work overlaps --

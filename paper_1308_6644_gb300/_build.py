@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libnuasm.so")
 
-SOURCES = ["capi.cu", "passes.cu", "passes_row_f32.cu", "passes_col_f32.cu", "passes_row_f64.cu",
+SOURCES = ["capi.cu", "resources.cu", "passes.cu", "passes_row_f32.cu", "passes_col_f32.cu", "passes_row_f64.cu",
            "passes_col_f64.cu", "gridding.cu", "hostmath.cpp", "noalloc.cu", "rs.cu", "batch.cu", "serve.cu", "diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",

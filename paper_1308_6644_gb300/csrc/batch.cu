@@ -21,6 +21,7 @@ struct nuasm_batch_s {
     cudaGraphExec_t exec = nullptr;
     int lanes = 0;
     int64_t kernels = 0;
+    std::vector<nuasm_plan_s*> plans;   // plans whose workspace and error word the graph uses
 };
 
 namespace {
@@ -46,8 +47,8 @@ struct Streams {
     std::vector<cudaStream_t> s;
     std::vector<cudaEvent_t> ev;
     ~Streams() {
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        for (cudaStream_t q : s) cudaStreamDestroy(q);
+        for (cudaEvent_t e : ev) xevent_destroy(e);
+        for (cudaStream_t q : s) xstream_destroy(q);
     }
 };
 
@@ -103,17 +104,17 @@ nuasm_status nuasm_batch_create(nuasm_batch_t* out, const nuasm_batch_item_t* it
 
     Streams S;
     cudaStream_t origin = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+    cudaError_t e = xstream_create(&origin);
     if (e != cudaSuccess) return status_of(e);
     S.s.push_back(origin);
     for (int l = 0; l < nl; ++l) {
         cudaStream_t q = nullptr;
-        if ((e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking)) != cudaSuccess) return status_of(e);
+        if ((e = xstream_create(&q)) != cudaSuccess) return status_of(e);
         S.s.push_back(q);
     }
     for (int l = 0; l <= nl; ++l) {
         cudaEvent_t ev = nullptr;
-        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return status_of(e);
+        if ((e = xevent_create(&ev)) != cudaSuccess) return status_of(e);
         S.ev.push_back(ev);
     }
 
@@ -142,7 +143,7 @@ nuasm_status nuasm_batch_create(nuasm_batch_t* out, const nuasm_batch_item_t* it
         return status_of(ce != cudaSuccess ? ce : e);
     }
     cudaGraphExec_t exec = nullptr;
-    if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
+    if ((e = xgraph_instantiate(&exec, graph)) != cudaSuccess) {
         cudaGraphDestroy(graph);
         return status_of(e);
     }
@@ -158,7 +159,7 @@ nuasm_status nuasm_batch_create(nuasm_batch_t* out, const nuasm_batch_item_t* it
 
     nuasm_batch_s* B = new (std::nothrow) nuasm_batch_s();
     if (!B) {
-        cudaGraphExecDestroy(exec);
+        xgraph_exec_destroy(exec);
         cudaGraphDestroy(graph);
         return NUASM_ENOMEM;
     }
@@ -166,6 +167,14 @@ nuasm_status nuasm_batch_create(nuasm_batch_t* out, const nuasm_batch_item_t* it
     B->exec = exec;
     B->lanes = nl;
     B->kernels = kernels;
+    try {
+        B->plans = owners;
+    } catch (...) {
+        xgraph_exec_destroy(exec);
+        cudaGraphDestroy(graph);
+        delete B;
+        return NUASM_ENOMEM;
+    }
     *out = B;
     return NUASM_OK;
 }
@@ -177,6 +186,14 @@ nuasm_status nuasm_batch_execute(nuasm_batch_t batch, void* stream) {
         cudaGetLastError();
         return NUASM_ECUDA;
     }
+    // a bounded device wait of an earlier launch gave up (host-mapped error words; reported once)
+    bool timed_out = false;
+    for (nuasm_plan_s* P : batch->plans)
+        if (P->d.h_err && (*static_cast<volatile int*>(P->d.h_err) & 2)) {
+            __atomic_fetch_and(P->d.h_err, ~2, __ATOMIC_SEQ_CST);
+            timed_out = true;
+        }
+    if (timed_out) return NUASM_ETIMEOUT;
     return status_of(cudaGraphLaunch(batch->exec, static_cast<cudaStream_t>(stream)));
 }
 
@@ -190,7 +207,7 @@ nuasm_status nuasm_batch_info(nuasm_batch_t batch, int32_t* lanes, int64_t* kern
 nuasm_status nuasm_batch_destroy(nuasm_batch_t batch) {
     if (!batch) return NUASM_OK;
     const cudaError_t e = cudaDeviceSynchronize();
-    cudaGraphExecDestroy(batch->exec);
+    xgraph_exec_destroy(batch->exec);
     cudaGraphDestroy(batch->graph);
     delete batch;
     return status_of(e);

@@ -135,9 +135,10 @@ void nuasm::plan_release(nuasm_plan_s* P) {
         delete X;
     }
     void* ptrs[] = {P->d.tables, P->d.etab, P->d.etab2, P->d.rec, P->d.wpt, P->d.tile_off, P->d.tile_home,
-                    P->d.tile_order, P->d.win, P->d.bufA, P->d.bufB, P->d.stage_in, P->d.stage_out, P->d.err};
-    for (void* q : ptrs)
-        if (q) cudaFree(q);
+                    P->d.tile_order, P->d.win, P->d.bufA, P->d.bufB, P->d.stage_in, P->d.stage_out};
+    for (void* q : ptrs) xfree(q);
+    if (P->d.h_err) xfree_host(P->d.h_err);
+    else xfree(P->d.err);
     delete P;
 }
 
@@ -145,7 +146,7 @@ namespace {
 
 template <typename T> cudaError_t dalloc(nuasm_plan_s* P, T** out, size_t bytes) {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    cudaError_t e = xmalloc(&q, bytes);
     if (e == cudaSuccess) {
         *out = static_cast<T*>(q);
         P->device_bytes += int64_t(bytes);
@@ -184,13 +185,24 @@ cudaError_t device_copy(const double* src, int64_t m, double** dev_out, bool* ow
     *dev_out = const_cast<double*>(src);
     if (!src || m == 0 || device_accessible(src)) return cudaSuccess;
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, sizeof(double) * size_t(m));
+    cudaError_t e = xmalloc(&q, sizeof(double) * size_t(m));
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(q, src, sizeof(double) * size_t(m), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) { cudaFree(q); return e; }
+    if (e != cudaSuccess) { xfree(q); return e; }
     *dev_out = static_cast<double*>(q);
     *owned = true;
     return cudaSuccess;
+}
+
+// Bit 2 of a plan's host-mapped error word: a bounded device wait of an
+// earlier execute gave up.  Reading it needs no synchronisation (the device
+// writes the mapped word directly); it is reported once and cleared.
+bool take_timeout(nuasm_plan_s* P) {
+    if (!P->d.h_err) return false;
+    volatile int* w = P->d.h_err;
+    if (!(*w & 2)) return false;
+    __atomic_fetch_and(P->d.h_err, ~2, __ATOMIC_SEQ_CST);
+    return true;
 }
 
 nuasm_status check_plan_usable(nuasm_plan_s* P) {
@@ -201,6 +213,7 @@ nuasm_status check_plan_usable(nuasm_plan_s* P) {
         cudaGetLastError();
         return NUASM_ECUDA;
     }
+    if (take_timeout(P)) return NUASM_ETIMEOUT;
     return NUASM_OK;
 }
 
@@ -395,14 +408,24 @@ nuasm_status nuasm::plan_create(nuasm_plan_s** out, const nuasm_params_t* p, int
     }
     if ((e = dalloc(P, &P->d.tile_off, sizeof(int) * (g.ntiles + 1))) != cudaSuccess) return bail(cuda_status(e));
     if ((e = dalloc(P, &P->d.tile_home, sizeof(int) * g.ntiles)) != cudaSuccess) return bail(cuda_status(e));
-    if ((e = dalloc(P, &P->d.err, sizeof(int))) != cudaSuccess) return bail(cuda_status(e));
+    {
+        // the error word is host-mapped: execute calls read it without synchronising
+        void* h = nullptr;
+        if ((e = xmalloc_host(&h, sizeof(int), cudaHostAllocMapped)) != cudaSuccess) return bail(cuda_status(e));
+        P->d.h_err = static_cast<int*>(h);
+        *P->d.h_err = 0;
+        void* dp = nullptr;
+        if ((e = cudaHostGetDevicePointer(&dp, h, 0)) != cudaSuccess) return bail(cuda_status(e));
+        P->d.err = static_cast<int*>(dp);
+        P->device_bytes += int64_t(sizeof(int));
+    }
 
     double *dx = nullptr, *dy = nullptr, *dw = nullptr;
     bool ox = false, oy = false, ow = false;
     auto free_coords = [&]() {
-        if (ox) cudaFree(dx);
-        if (oy) cudaFree(dy);
-        if (ow) cudaFree(dw);
+        if (ox) xfree(dx);
+        if (oy) xfree(dy);
+        if (ow) xfree(dw);
     };
     if ((e = device_copy(x, m, &dx, &ox, st)) != cudaSuccess ||
         (e = device_copy(y, m, &dy, &oy, st)) != cudaSuccess ||
@@ -436,14 +459,14 @@ nuasm_status nuasm_plan_lattice(nuasm_plan_t* out, const nuasm_params_t* p, int3
     if (m == 0) return nuasm_plan(out, p, 0, nullptr, nullptr, nullptr, stream);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     double* xy = nullptr;
-    cudaError_t e = cudaMalloc(&xy, sizeof(double) * 2 * size_t(m));
+    cudaError_t e = xmalloc(reinterpret_cast<void**>(&xy), sizeof(double) * 2 * size_t(m));
     if (e != cudaSuccess) return cuda_status(e);
     const int blocks = int(std::min<int64_t>((m + 255) / 256, 152 * 8));
     lattice_kernel<<<blocks, 256, 0, st>>>(xy, xy + m, nx, m, pitch2, x0, y0);
     e = cudaGetLastError();
     nuasm_status r = e == cudaSuccess ? nuasm_plan(out, p, m, xy, xy + m, nullptr, stream) : cuda_status(e);
     cudaStreamSynchronize(st);
-    cudaFree(xy);
+    xfree(xy);
     return r;
 }
 
@@ -490,7 +513,7 @@ nuasm_status nuasm_autotune_tile(const nuasm_params_t* p, int64_t m, const doubl
     const size_t eb = rp.prec == NUASM_PREC_F64 ? 16 : 8;
     const size_t nn = size_t(rp.n) * rp.n;
     void* buf = nullptr;
-    cudaError_t e = cudaMalloc(&buf, eb * (nn + size_t(m > 0 ? m : 1)));
+    cudaError_t e = xmalloc(&buf, eb * (nn + size_t(m > 0 ? m : 1)));
     if (e != cudaSuccess) return cuda_status(e);
     char* in = static_cast<char*>(buf);
     char* out = in + eb * (type == 1 ? size_t(m) : nn);
@@ -526,7 +549,7 @@ nuasm_status nuasm_autotune_tile(const nuasm_params_t* p, int64_t m, const doubl
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     cudaStreamSynchronize(st);
-    cudaFree(buf);
+    xfree(buf);
     if (s != NUASM_OK) return s;
     if (e != cudaSuccess) return cuda_status(e);
     *tile = best;
@@ -537,7 +560,9 @@ nuasm_status nuasm_autotune_tile(const nuasm_params_t* p, int64_t m, const doubl
 nuasm_status nuasm_destroy(nuasm_plan_t plan) {
     if (!plan) return NUASM_OK;
     cudaError_t e = cudaDeviceSynchronize();
+    const bool timed_out = e == cudaSuccess && take_timeout(plan);
     plan_release(plan);
+    if (timed_out) return NUASM_ETIMEOUT;
     return cuda_status(e);
 }
 

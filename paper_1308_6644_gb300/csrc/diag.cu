@@ -29,7 +29,7 @@ extern "C" nuasm_status nuasm_debug_bounded_wait(int32_t spins, void* stream) {
     if (spins < 1 || spins > nuasm::tma::kSpinLimit) return NUASM_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int* err = nullptr;
-    cudaError_t e = cudaMallocAsync(&err, sizeof(int), st);
+    cudaError_t e = nuasm::xmalloc_async(reinterpret_cast<void**>(&err), sizeof(int), st);
     if (e != cudaSuccess) return status_of(e);
     int host = 0;
     e = cudaMemsetAsync(err, 0, sizeof(int), st);
@@ -38,9 +38,22 @@ extern "C" nuasm_status nuasm_debug_bounded_wait(int32_t spins, void* stream) {
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&host, err, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(err, st);
+    nuasm::xfree_async(err, st);
     const cudaError_t es = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = es;
     if (e != cudaSuccess) return status_of(e);
     return (host & 2) ? NUASM_ETIMEOUT : NUASM_OK;
+}
+
+// The same wait with a plan's own error word as the flag it sets: what a
+// column pass whose copy never arrived leaves behind, without a stalled copy
+// (nothing else is in flight).  The plan's next execute call reports it.
+extern "C" nuasm_status nuasm_debug_plan_wait(nuasm_plan_t plan, int32_t spins, void* stream) {
+    if (!plan || spins < 1 || spins > nuasm::tma::kSpinLimit) return NUASM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bounded_wait_kernel<<<1, 32, 0, st>>>(spins, plan->d.err);
+    cudaError_t e = cudaGetLastError();
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
+    return status_of(e);
 }

@@ -815,7 +815,7 @@ cudaError_t make_tile_order(nuasm_plan_s* P, cudaStream_t st) {
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
-    if ((e = cudaMalloc(&P->d.tile_order, sizeof(int) * size_t(nt))) != cudaSuccess) return e;
+    if ((e = xmalloc(reinterpret_cast<void**>(&P->d.tile_order), sizeof(int) * size_t(nt))) != cudaSuccess) return e;
     P->device_bytes += int64_t(sizeof(int)) * nt;
     e = cudaMemcpyAsync(P->d.tile_order, order.data(), sizeof(int) * size_t(nt), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
@@ -827,19 +827,20 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
     BinArgs a{g.n, g.W, g.T, g.ntx, g.w, g.h, P->p.pitch, P->m};
     const int nt = g.ntiles;
     int* cnt = nullptr;   // home_cnt, dup_cnt, cur_home, cur_dup
-    cudaError_t e = cudaMallocAsync(&cnt, sizeof(int) * 4 * size_t(nt), st);
+    cudaError_t e = xmalloc_async(reinterpret_cast<void**>(&cnt), sizeof(int) * 4 * size_t(nt), st);
     if (e != cudaSuccess) return cuda_status(e);
     int* home_cnt = cnt;
     int* dup_cnt = cnt + nt;
     int* cur_home = cnt + 2 * nt;
     int* cur_dup = cnt + 3 * nt;
     auto fail = [&](cudaError_t err) {
-        cudaFreeAsync(cnt, st);
+        xfree_async(cnt, st);
         cudaStreamSynchronize(st);
         return cuda_status(err);
     };
     if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * 4 * size_t(nt), st)) != cudaSuccess) return fail(e);
-    if ((e = cudaMemsetAsync(P->d.err, 0, sizeof(int), st)) != cudaSuccess) return fail(e);
+    if (P->d.h_err) *P->d.h_err = 0;   // host-mapped: no device work has touched it yet
+    else if ((e = cudaMemsetAsync(P->d.err, 0, sizeof(int), st)) != cudaSuccess) return fail(e);
     const int blocks = int(std::min<int64_t>((P->m + 255) / 256, 152 * 16));
     if (P->m > 0) {
         bin_count_kernel<<<blocks, 256, 0, st>>>(x, y, a, home_cnt, dup_cnt, P->d.err);
@@ -849,8 +850,11 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     int total = 0, errw = 0;
     if ((e = cudaMemcpyAsync(&total, P->d.tile_off + nt, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(e);
-    if ((e = cudaMemcpyAsync(&errw, P->d.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(e);
+    if (!P->d.h_err &&
+        (e = cudaMemcpyAsync(&errw, P->d.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    if (P->d.h_err) errw = *static_cast<volatile int*>(P->d.h_err);
     if (errw) {
         fail(cudaSuccess);
         return NUASM_ERANGE;
@@ -858,10 +862,11 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
     P->nrec = total;
     if ((e = make_tile_order(P, st)) != cudaSuccess) return fail(e);
     const size_t rsz = P->f64 ? sizeof(RecD) : sizeof(RecF);
-    if ((e = cudaMalloc(&P->d.rec, rsz * size_t(total > 0 ? total : 1))) != cudaSuccess) return fail(e);
+    if ((e = xmalloc(&P->d.rec, rsz * size_t(total > 0 ? total : 1))) != cudaSuccess) return fail(e);
     P->device_bytes += int64_t(rsz) * (total > 0 ? total : 1);
     if (w && P->m > 0) {
-        if ((e = cudaMalloc(&P->d.wpt, sizeof(double) * size_t(P->m))) != cudaSuccess) return fail(e);
+        if ((e = xmalloc(reinterpret_cast<void**>(&P->d.wpt), sizeof(double) * size_t(P->m))) != cudaSuccess)
+            return fail(e);
         P->device_bytes += int64_t(sizeof(double)) * P->m;
         e = cudaMemcpyAsync(P->d.wpt, w, sizeof(double) * size_t(P->m), cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return fail(e);
@@ -879,7 +884,7 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
         // bank skew: 2 where it balances the record classes at least 5% better
         unsigned long long* sums = nullptr;
         unsigned long long hs[2] = {0, 0};
-        if ((e = cudaMallocAsync(&sums, sizeof(hs), st)) != cudaSuccess) return fail(e);
+        if ((e = xmalloc_async(reinterpret_cast<void**>(&sums), sizeof(hs), st)) != cudaSuccess) return fail(e);
         e = cudaMemsetAsync(sums, 0, sizeof(hs), st);
         if (e == cudaSuccess) {
             if (P->f64)
@@ -892,11 +897,11 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        cudaFreeAsync(sums, st);
+        xfree_async(sums, st);
         if (e != cudaSuccess) return fail(e);
         P->skew = double(hs[1]) < 0.95 * double(hs[0]) ? 2 : 0;
         void* tmp = nullptr;
-        if ((e = cudaMallocAsync(&tmp, rsz * size_t(total), st)) != cudaSuccess) return fail(e);
+        if ((e = xmalloc_async(&tmp, rsz * size_t(total), st)) != cudaSuccess) return fail(e);
         e = cudaMemcpyAsync(tmp, P->d.rec, rsz * size_t(total), cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) {
             if (P->f64)
@@ -907,11 +912,10 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
                                                             P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew);
             e = cudaGetLastError();
         }
-        cudaFreeAsync(tmp, st);
+        xfree_async(tmp, st);
         if (e != cudaSuccess) return fail(e);
     }
-    e = cudaFreeAsync(cnt, st);
-    if (e != cudaSuccess) return cuda_status(e);
+    xfree_async(cnt, st);
     return cuda_status(cudaStreamSynchronize(st));
 }
 

@@ -262,9 +262,10 @@ nuasm_status validate(const nuasm_params_t& p0, int64_t m, nuasm_params_t* out) 
         if (!kernel_shape(p.tol, p.prec, p.kernel, &w, &beta)) return NUASM_EUNSUPPORTED;
     }
     if (p.tile != 0 && p.tile != 16 && p.tile != 32 && p.tile != 64) return NUASM_EINVAL;
-    if (p.n_pad != 0 && (p.n_pad < 2 * p.n || !is_pow2(p.n_pad))) return NUASM_EINVAL;
-    // what this build implements: power-of-two planes, N' <= 8192 (F32) / 4096 (F64)
-    if (!is_pow2(p.n) || p.n < 16) return NUASM_EUNSUPPORTED;
+    if (p.n_pad != 0 && (p.n_pad < 2 * p.n || (p.n_pad & 1))) return NUASM_EINVAL;
+    // what this build implements: power-of-two planes 16 <= N and N', N' <= 8192
+    // (F32) / 4096 (F64); other even sizes are valid problems it does not run
+    if (!is_pow2(p.n) || p.n < 16 || (p.n_pad != 0 && !is_pow2(p.n_pad))) return NUASM_EUNSUPPORTED;
     if (p.n_pad == 0) p.n_pad = 2 * p.n;
     const int np_max = p.prec == NUASM_PREC_F64 ? 4096 : 8192;
     if (p.n_pad > np_max) return NUASM_EUNSUPPORTED;

@@ -1,13 +1,14 @@
 // nuasm2_solve_noalloc: a one-shot NU-ASM_2 solve that allocates nothing.
 //
 // Who needs it: callers that must not call cudaMalloc or any allocating
-// routine -- code running while a stream is being captured into a CUDA graph
-// (allocation is not allowed there), plug-ins whose host framework owns every
-// byte of device memory through its own pool, and real-time loops that cannot
-// afford an allocation's latency or failure.  Such callers cannot build a plan
-// with nuasm_plan (which allocates its tables, bins and workspace), so this
-// entry point does the plan work and the solve in one call, with every
-// intermediate in one file-scope device array.
+// routine -- plug-ins whose host framework owns every byte of device memory
+// through its own pool, and real-time loops that cannot afford an
+// allocation's latency or its failure.  Such callers cannot build a plan with
+// nuasm_plan (which allocates its tables, bins and workspace), so this entry
+// point does the plan work and the solve in one call, with every intermediate
+// in one file-scope device array.  The call copies its tables from host
+// memory, reads the error word back and waits for its stream before it
+// returns.
 //
 // The array (kScratchBytes) is part of the library image: every GPU that loads
 // the library holds it until the process exits.  Its device address is looked
@@ -165,7 +166,7 @@ extern "C" nuasm_status nuasm2_solve_noalloc(const nuasm_params_t* p, int64_t m,
     pack_twp(twd, logl, false, host + 5 * np + g.G);
     P.rc = rp.z / (2.0 * rp.lambda);
     const double rmax = nonsep_rmax(rp, g);
-    P.nonsep_mode = (rp.z == 0.0) ? 0 : (rmax <= 0.5 ? 1 : 2);
+    P.nonsep_mode = choose_nonsep_mode(rp, rmax);
     fit_kernel_poly(g, &P.poly);
     // pageable source: the copy is staged before the call returns, so the stack buffer may go
     e = cudaMemcpyAsync(tables, host, sizeof(float2) * (5 * size_t(np) + ntw), cudaMemcpyHostToDevice, st);
@@ -181,5 +182,6 @@ extern "C" nuasm_status nuasm2_solve_noalloc(const nuasm_params_t* p, int64_t m,
     if ((e = cudaMemcpyAsync(&flag, P.d.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return status_of(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return status_of(e);
+    if (flag & 2) return NUASM_ETIMEOUT;   // a bounded wait of a column pass gave up
     return flag ? NUASM_ERANGE : NUASM_OK;
 }

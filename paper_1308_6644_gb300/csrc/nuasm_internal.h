@@ -73,7 +73,9 @@ struct PlanDevice {
     void* bufB = nullptr;       // N' x N
     void* stage_in = nullptr;   // host-pointer staging (max of M, N^2 complex)
     void* stage_out = nullptr;
-    int* err = nullptr;         // device error word
+    int* err = nullptr;         // device address of the error word
+    int* h_err = nullptr;       // host view of the error word when it is host-mapped (plans made by
+                                // plan_create); null when it lives in device memory (views, scratch)
 };
 
 }  // namespace nuasm
@@ -180,6 +182,27 @@ cudaError_t chain_type3(nuasm_plan_s* P, const nuasm_plan_s* Q, const void* c, v
 inline size_t ws_win_elems(const Geometry& g) { return size_t(g.W) * g.Wp; }
 inline size_t ws_bufA_elems(const Geometry& g) { return size_t(g.np) * g.Wp; }
 inline size_t ws_bufB_elems(const Geometry& g) { return size_t(g.np) * g.n; }
+
+// Resource acquisition (resources.cu): device, pool and pinned host
+// allocations, streams, events and graph instantiations, with a count of the
+// live ones and a test hook that fails the k-th acquisition
+// (nuasm_debug_fail_alloc).  A failed acquisition returns
+// cudaErrorMemoryAllocation and leaves the output null.
+cudaError_t xmalloc(void** p, size_t bytes);
+cudaError_t xmalloc_async(void** p, size_t bytes, cudaStream_t s);
+cudaError_t xmalloc_pool(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t s);
+cudaError_t xmalloc_host(void** p, size_t bytes, unsigned flags);
+void xfree(void* p);
+void xfree_async(void* p, cudaStream_t s);
+void xfree_host(void* p);
+cudaError_t xstream_create(cudaStream_t* s);
+void xstream_destroy(cudaStream_t s);
+cudaError_t xevent_create(cudaEvent_t* ev);
+void xevent_destroy(cudaEvent_t ev);
+cudaError_t xgraph_instantiate(cudaGraphExec_t* exec, cudaGraph_t graph);
+void xgraph_exec_destroy(cudaGraphExec_t exec);
+cudaError_t xpool_create(cudaMemPool_t* pool, const cudaMemPoolProps* props);
+cudaError_t xpool_destroy(cudaMemPool_t pool);
 
 // launchers (gridding.cu / passes.cu); all asynchronous on `s`
 // (the device error word P->d.err: bit 1 = point outside the window at plan

@@ -136,10 +136,10 @@ struct Slot {
     char* h_tab = nullptr;
     size_t h_tab_bytes = 0;
     ~Slot() {
-        if (st) cudaStreamDestroy(st);
-        if (d_err) cudaFree(d_err);
-        if (h_err) cudaFreeHost(h_err);
-        if (h_tab) cudaFreeHost(h_tab);
+        xstream_destroy(st);
+        xfree(d_err);
+        xfree_host(h_err);
+        xfree_host(h_tab);
     }
 };
 
@@ -215,7 +215,7 @@ nuasm_status build_set(Server& S, Slot& sl, const Job& j, PointSet* ps) {
     char* tmp = nullptr;
     cudaError_t e = cudaSuccess;
     if (m > 0 && (!device_accessible(j.r.x) || !device_accessible(j.r.y))) {
-        e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&tmp), sizeof(double) * 2 * size_t(m), S.pool, sl.st);
+        e = xmalloc_pool(reinterpret_cast<void**>(&tmp), sizeof(double) * 2 * size_t(m), S.pool, sl.st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(tmp, j.r.x, sizeof(double) * size_t(m), cudaMemcpyDefault, sl.st);
         if (e == cudaSuccess)
@@ -227,7 +227,7 @@ nuasm_status build_set(Server& S, Slot& sl, const Job& j, PointSet* ps) {
     nuasm_plan_s* P = nullptr;
     nuasm_status s = e == cudaSuccess ? plan_create(&P, &j.rp, m, dx, dy, nullptr, sl.st, false) : status_of(e);
     if (tmp) {
-        cudaFreeAsync(tmp, sl.st);
+        xfree_async(tmp, sl.st);
         cudaStreamSynchronize(sl.st);
     }
     std::vector<double> ph;
@@ -277,10 +277,10 @@ nuasm_status run_job(Server& S, Slot& sl, const Job& j, PointSet* ps, bool build
     build_tables(j.rp, g, &ht, ps->phihat.data(), false);
     const size_t tb = table_bytes(g, f64, false);
     if (sl.h_tab_bytes < tb) {
-        if (sl.h_tab) cudaFreeHost(sl.h_tab);
+        xfree_host(sl.h_tab);
         sl.h_tab = nullptr;
         sl.h_tab_bytes = 0;
-        if (cudaMallocHost(reinterpret_cast<void**>(&sl.h_tab), tb) != cudaSuccess) {
+        if (xmalloc_host(reinterpret_cast<void**>(&sl.h_tab), tb, cudaHostAllocDefault) != cudaSuccess) {
             free_tables(&ht);
             cudaGetLastError();
             return NUASM_ENOMEM;
@@ -301,7 +301,7 @@ nuasm_status run_job(Server& S, Slot& sl, const Job& j, PointSet* ps, bool build
     size_t total = 0;
     for (size_t v : sz) total += v;
     char* base = nullptr;
-    cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&base), total, S.pool, sl.st);
+    cudaError_t e = xmalloc_pool(reinterpret_cast<void**>(&base), total, S.pool, sl.st);
     if (e != cudaSuccess) return status_of(e);
     char* part[6];
     size_t off = 0;
@@ -331,6 +331,7 @@ nuasm_status run_job(Server& S, Slot& sl, const Job& j, PointSet* ps, bool build
     view.d.bufB = part[3];
     view.d.stage_in = view.d.stage_out = nullptr;
     view.d.err = sl.d_err;
+    view.d.h_err = nullptr;   // the slot's word is device memory, read back below
     view.prof = false;
     view.prof_state = nullptr;
     const void* din = in_dev ? j.r.in : part[4];
@@ -344,7 +345,7 @@ nuasm_status run_job(Server& S, Slot& sl, const Job& j, PointSet* ps, bool build
     if (e == cudaSuccess && !out_dev)
         e = cudaMemcpyAsync(j.r.out, part[5], size_t(no) * eb, cudaMemcpyDeviceToHost, sl.st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_err, sl.d_err, sizeof(int), cudaMemcpyDeviceToHost, sl.st);
-    cudaFreeAsync(base, sl.st);
+    xfree_async(base, sl.st);
     const cudaError_t es = cudaStreamSynchronize(sl.st);
     if (e == cudaSuccess) e = es;
     if (e != cudaSuccess) {
@@ -356,10 +357,13 @@ nuasm_status run_job(Server& S, Slot& sl, const Job& j, PointSet* ps, bool build
 
 void worker_main(Server* S) {
     Slot sl;
-    bool ok = cudaSetDevice(S->cfg.device) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaMalloc(&sl.d_err, sizeof(int)) == cudaSuccess &&
-              cudaMallocHost(reinterpret_cast<void**>(&sl.h_err), sizeof(int)) == cudaSuccess;
+    // a slot that cannot get its resources fails every request it takes
+    cudaError_t se = cudaSetDevice(S->cfg.device);
+    if (se == cudaSuccess) se = xstream_create(&sl.st);
+    if (se == cudaSuccess) se = xmalloc(reinterpret_cast<void**>(&sl.d_err), sizeof(int));
+    if (se == cudaSuccess) se = xmalloc_host(reinterpret_cast<void**>(&sl.h_err), sizeof(int), cudaHostAllocDefault);
+    const bool ok = se == cudaSuccess;
+    const nuasm_status slot_status = status_of(se);
     if (!ok) cudaGetLastError();
     for (;;) {
         Job j;
@@ -386,7 +390,7 @@ void worker_main(Server* S) {
         }
         for (nuasm_plan_s* v : victims) plan_release(v);
         bool reused = false;
-        const nuasm_status s = ok ? run_job(*S, sl, j, ps, build, &reused) : NUASM_ECUDA;
+        const nuasm_status s = ok ? run_job(*S, sl, j, ps, build, &reused) : slot_status;
         const Clock::time_point t_done = Clock::now();
         nuasm_plan_s* drop = nullptr;
         {
@@ -450,7 +454,7 @@ nuasm_status nuasm_server_create(nuasm_server_t* out, const nuasm_server_config_
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = c.device;
-    cudaError_t e = cudaMemPoolCreate(&S->pool, &props);
+    cudaError_t e = xpool_create(&S->pool, &props);
     if (e != cudaSuccess) {
         delete S;
         return status_of(e);
@@ -468,7 +472,7 @@ nuasm_status nuasm_server_create(nuasm_server_t* out, const nuasm_server_config_
         }
         S->cv_work.notify_all();
         for (auto& t : S->workers) t.join();
-        cudaMemPoolDestroy(S->pool);
+        xpool_destroy(S->pool);
         delete S;
         return NUASM_ENOMEM;
     }
@@ -561,7 +565,7 @@ nuasm_status nuasm_server_destroy(nuasm_server_t S) {
     for (auto& p : S->sets)
         if (p->plan) plan_release(p->plan);
     S->sets.clear();
-    const cudaError_t e = cudaMemPoolDestroy(S->pool);
+    const cudaError_t e = xpool_destroy(S->pool);
     delete S;
     return status_of(e);
 }

@@ -114,6 +114,9 @@ _SIGS = {
                                            ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_double)]),
     "nuasm_debug_bounded_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p]),
+    "nuasm_debug_plan_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "nuasm_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int64]),
+    "nuasm_debug_live_resources": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
     "nuasm_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(BatchItem),
                                           ctypes.c_int32, ctypes.c_int32]),
     "nuasm_batch_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -419,6 +422,25 @@ def nuasm_debug_bounded_wait(spins: int, stream=None) -> int:
     if code not in (0, 5):
         _check(code, "nuasm_debug_bounded_wait")
     return int(code)
+
+
+def nuasm_debug_plan_wait(plan: Plan, spins: int, stream=None):
+    """Leave `plan`'s error word as a column pass whose copy never arrived
+    would: its next execute call returns NUASM_ETIMEOUT."""
+    _check(lib().nuasm_debug_plan_wait(plan._h, int(spins), _stream(stream)), "nuasm_debug_plan_wait")
+
+
+def nuasm_debug_fail_alloc(k: int):
+    """Make the k-th resource acquisition of the library from now fail
+    (k = 0 disarms)."""
+    _check(lib().nuasm_debug_fail_alloc(int(k)), "nuasm_debug_fail_alloc")
+
+
+def nuasm_debug_live_resources() -> int:
+    """The library's resource acquisitions not yet released."""
+    n = ctypes.c_int64()
+    _check(lib().nuasm_debug_live_resources(ctypes.byref(n)), "nuasm_debug_live_resources")
+    return int(n.value)
 
 
 # ---------------------------------------------------------------- batches

@@ -13,27 +13,33 @@ C2 = dict(n=1024, n_pad=2048, window=2056, records=1_200_000, kernel_width=7, ti
 
 
 def test_stage_bytes_of_the_benchmark_geometry():
-    n, np_, W = 1024, 2048, 2056
-    b = bench.stage_bytes(dict(C2, phase_table_bytes=0), 1 << 20, 2, 8)
-    assert b["col_fwd"] == 8 * (n * n + np_ * n)
-    assert b["row_t2"] == 8 * (np_ * n + np_ * W)
-    assert b["col_inv_fold"] == 8 * (np_ * W + W * W)
-    assert b["interp"] == 8 * W * W + 24 * (1 << 20)
-    b1 = bench.stage_bytes(dict(C2, phase_table_bytes=0), 1 << 20, 1, 8)
-    assert b1["spread"] == 24 * C2["records"] + 8 * W * W
+    """The algorithmic model: grid values read and written once (8 B) and
+    20 B per point (8 B value + 12 B record), whatever the plan's tables."""
+    n, np_, W, m = 1024, 2048, 2056, 1 << 20
+    for tables in (0, 1025 * 1026 * 8 + 1025 * 2048 * 8):
+        b = bench.stage_bytes(dict(C2, phase_table_bytes=tables, points=m), m, 2, 8)
+        assert b["col_fwd"] == 8 * (n * n + np_ * n)
+        assert b["row_t2"] == 8 * (np_ * n + np_ * W)                 # 50.46 MB
+        assert b["col_inv_fold"] == 8 * (np_ * W + W * W)
+        assert b["interp"] == 8 * W * W + 20 * m
+        b1 = bench.stage_bytes(dict(C2, phase_table_bytes=tables, points=m), m, 1, 8)
+        assert b1["spread"] == 20 * m + 8 * W * W
+        assert b1["row_t1"] == 8 * (np_ * W + np_ * n)
+    assert b["row_t2"] == 50_462_720
 
 
-def test_phase_tables_count_once_per_row_pass():
+def test_plan_tables_are_reported_apart():
+    m = 1 << 20
     equad = 1025 * 1026 * 8
     both = equad + 1025 * 2048 * 8
-    t2 = bench.stage_bytes(dict(C2, phase_table_bytes=both), 1 << 20, 2, 8)
-    t1 = bench.stage_bytes(dict(C2, phase_table_bytes=both), 1 << 20, 1, 8)
-    base2 = bench.stage_bytes(dict(C2, phase_table_bytes=0), 1 << 20, 2, 8)
-    base1 = bench.stage_bytes(dict(C2, phase_table_bytes=0), 1 << 20, 1, 8)
-    assert t2["row_t2"] - base2["row_t2"] == 1025 * 2048 * 8     # the Tx-folded rows
-    assert t1["row_t1"] - base1["row_t1"] == equad                # the E quadrant
-    only_e = bench.stage_bytes(dict(C2, phase_table_bytes=equad), 1 << 20, 2, 8)
-    assert only_e["row_t2"] - base2["row_t2"] == equad
+    t2 = bench.plan_table_bytes(dict(C2, phase_table_bytes=both, points=m), 2, 8)
+    t1 = bench.plan_table_bytes(dict(C2, phase_table_bytes=both, points=m), 1, 8)
+    assert t2["row_t2"] == 1025 * 2048 * 8        # the Tx-folded rows
+    assert t1["row_t1"] == equad                   # the E quadrant
+    only_e = bench.plan_table_bytes(dict(C2, phase_table_bytes=equad, points=m), 2, 8)
+    assert only_e["row_t2"] == equad
+    assert t2["interp"] == 4 * m                   # 16-byte records against the 12-byte model
+    assert t1["spread"] == 16 * C2["records"] - 12 * m + 8 * (C2["records"] - m)
 
 
 def test_stage_flops_model():

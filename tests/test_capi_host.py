@@ -57,10 +57,13 @@ def test_strerror_names_every_status(P):
     (dict(n=64, pitch=0.0, lam=633e-9, z=0.1), 1),            # pitch <= 0
     (dict(n=63, pitch=10e-6, lam=633e-9, z=0.1), 1),          # odd N
     (dict(n=64, pitch=10e-6, lam=633e-9, z=0.0, kind="fresnel"), 1),   # Fresnel z = 0
-    (dict(n=64, pitch=10e-6, lam=633e-9, z=0.1, n_pad=96), 1),  # N' not a power of two
+    (dict(n=64, pitch=10e-6, lam=633e-9, z=0.1, n_pad=129), 1),  # N' odd
+    (dict(n=64, pitch=10e-6, lam=633e-9, z=0.1, n_pad=192), 6),  # N' even, not a power of two
     (dict(n=64, pitch=10e-6, lam=633e-9, z=0.1, n_pad=64), 1),  # N' < 2N
     (dict(n=64, pitch=10e-6, lam=633e-9, z=0.1, tol=0.5), 1),   # tolerance out of range
-    (dict(n=48, pitch=10e-6, lam=633e-9, z=0.1), 6),          # N not a power of two
+    (dict(n=48, pitch=10e-6, lam=633e-9, z=0.1), 6),          # N even, not a power of two
+    (dict(n=384, pitch=10e-6, lam=633e-9, z=0.1), 6),
+    (dict(n=1000, pitch=10e-6, lam=633e-9, z=0.1), 6),
     (dict(n=8192, pitch=10e-6, lam=633e-9, z=0.1), 6),        # N' beyond 8192
     (dict(n=4096, pitch=10e-6, lam=633e-9, z=0.1, prec="f64"), 6),
 ])
@@ -194,6 +197,22 @@ def test_bounded_wait_diagnostic_rejects_bad_counts(P):
     lib = P.lib()
     assert lib.nuasm_debug_bounded_wait(0, None) == 1
     assert lib.nuasm_debug_bounded_wait((1 << 24) + 1, None) == 1
+    assert lib.nuasm_debug_plan_wait(None, 10, None) == 1
+
+
+def test_allocation_failure_hook_is_host_only_and_arms_and_disarms(P):
+    lib = P.lib()
+    n = ctypes.c_int64(-1)
+    assert lib.nuasm_debug_live_resources(None) == 1
+    assert lib.nuasm_debug_live_resources(ctypes.byref(n)) == 0 and n.value >= 0
+    assert lib.nuasm_debug_fail_alloc(-1) == 1
+    assert lib.nuasm_debug_fail_alloc(3) == 0
+    assert lib.nuasm_debug_fail_alloc(0) == 0
+    # validation failures acquire nothing
+    before = n.value
+    with pytest.raises(P.NuasmError):
+        P.nuasm_plan(P.make_params(63, 10e-6, 633e-9, 0.1), np.zeros(2), np.zeros(2))
+    assert lib.nuasm_debug_live_resources(ctypes.byref(n)) == 0 and n.value == before
 
 
 _CTYPE_OF = {"int32_t": "c_int32", "int64_t": "c_int64", "uint64_t": "c_uint64", "double": "c_double",
