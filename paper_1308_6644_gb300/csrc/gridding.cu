@@ -366,7 +366,19 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
 // cell value.  A batch whose S is zero is skipped; one whose S is not a normal
 // finite number (infinities, NaNs, or values so small that q would underflow)
 // adds to the totals with float atomics, so non-finite inputs propagate as in
-// the float path.
+// the float path.  The last batch of a tile folds its planes straight into
+// the window write (no fold into the totals, no clearing), and folds work
+// on pairs of cells (8-byte shared accesses).
+//
+// Measured and not kept: planes extended by a (w - 1)-cell margin so that no
+// tap needs clipping (the 49 taps become straight-line atomics; 31% of the
+// kernel's instructions were the clipping branches): 295 -> 309 us on the 4M
+// clustered points, since the halo duplicates then add all their taps and the
+// larger planes leave two CTAs per SM instead of three.  The shared-memory
+// atomics take about two wavefronts each on that workload; a CPU model of the
+// bank pattern gives the same 1.8x: the round-robin record order cannot give
+// 32 distinct bank classes per warp once a tile's classes run unevenly
+// (Poisson counts in the sparse background tiles).
 constexpr int kFixedThreads = 256;
 template <int WMAX, bool EXACT, int RPB>
 __global__ void __launch_bounds__(kFixedThreads, 2) spread_fixed_kernel(const RecF* __restrict__ rec,
@@ -396,6 +408,7 @@ __global__ void __launch_bounds__(kFixedThreads, 2) spread_fixed_kernel(const Re
     }
     const int b = off[tile], e = off[tile + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int half = T / 2;   // cells are folded and written in pairs
     for (int i0 = b; i0 < e; i0 += RPB * kFixedThreads) {
         RecF r[RPB];
         float2 val[RPB];
@@ -462,19 +475,45 @@ __global__ void __launch_bounds__(kFixedThreads, 2) spread_fixed_kernel(const Re
         }
         if (fixed) {
             __syncthreads();
-            for (int j = threadIdx.x; j < TT; j += kFixedThreads) {
-                tre[j] = fmaf(float(are[j]), q, tre[j]);
-                tim[j] = fmaf(float(aim[j]), q, tim[j]);
-                are[j] = 0;
-                aim[j] = 0;
+            if (i0 + RPB * kFixedThreads >= e) {
+                // last batch: fold into the window write
+                for (int i = threadIdx.x; i < T * half; i += kFixedThreads) {
+                    const int yy = i / half, xx = 2 * (i - yy * half), j = yy * TS + xx;
+                    const int2 rr = *reinterpret_cast<const int2*>(&are[j]);
+                    const int2 mm = *reinterpret_cast<const int2*>(&aim[j]);
+                    const float2 tr = *reinterpret_cast<const float2*>(&tre[j]);
+                    const float2 ti = *reinterpret_cast<const float2*>(&tim[j]);
+                    const int gy = y0 + yy, gx = x0 + xx;
+                    if (gy < a.W && gx < a.W)   // W, x0 and xx are even: both cells or neither
+                        *reinterpret_cast<float4*>(&win[size_t(gy) * a.Wp + gx]) =
+                            make_float4(fmaf(float(rr.x), q, tr.x), fmaf(float(mm.x), q, ti.x),
+                                        fmaf(float(rr.y), q, tr.y), fmaf(float(mm.y), q, ti.y));
+                }
+                return;
+            }
+            for (int i = threadIdx.x; i < T * half; i += kFixedThreads) {
+                const int yy = i / half, xx = 2 * (i - yy * half), j = yy * TS + xx;
+                int2* pr = reinterpret_cast<int2*>(&are[j]);
+                int2* pm = reinterpret_cast<int2*>(&aim[j]);
+                float2* pa = reinterpret_cast<float2*>(&tre[j]);
+                float2* pb = reinterpret_cast<float2*>(&tim[j]);
+                const int2 rr = *pr, mm = *pm;
+                const float2 tr = *pa, ti = *pb;
+                *pa = make_float2(fmaf(float(rr.x), q, tr.x), fmaf(float(rr.y), q, tr.y));
+                *pb = make_float2(fmaf(float(mm.x), q, ti.x), fmaf(float(mm.y), q, ti.y));
+                *pr = make_int2(0, 0);
+                *pm = make_int2(0, 0);
             }
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < T * T; i += kFixedThreads) {
-        const int yy = i / T, xx = i - yy * T;
+    for (int i = threadIdx.x; i < T * half; i += kFixedThreads) {
+        const int yy = i / half, xx = 2 * (i - yy * half), j = yy * TS + xx;
+        const float2 tr = *reinterpret_cast<const float2*>(&tre[j]);
+        const float2 ti = *reinterpret_cast<const float2*>(&tim[j]);
         const int gy = y0 + yy, gx = x0 + xx;
-        if (gy < a.W && gx < a.W) win[size_t(gy) * a.Wp + gx] = make_float2(tre[yy * TS + xx], tim[yy * TS + xx]);
+        if (gy < a.W && gx < a.W)
+            *reinterpret_cast<float4*>(&win[size_t(gy) * a.Wp + gx]) = make_float4(tr.x, ti.x, tr.y, ti.y);
     }
 }
 

@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "common.cuh"
 #include "fft_engine.cuh"
@@ -85,10 +86,14 @@ template <typename V, int LOGNP> struct RowCfg {
     }
 };
 
-template <typename V, int LOGNP> struct ColCfg {
+#ifndef NUASM_COL_FWD_BUDGET
+#define NUASM_COL_FWD_BUDGET NUASM_COL_BUDGET   // FP32 budget of the type-2 forward column pass
+#endif
+template <typename V, int LOGNP, int MODE = 0> struct ColCfg {
     static constexpr int NP = 1 << LOGNP;
     static constexpr int E = Prec<V>::col_e;
-    static constexpr int CRAW = Prec<V>::col_budget / NP;
+    static constexpr int BUDGET = (MODE == 2 && !Prec<V>::f64) ? NUASM_COL_FWD_BUDGET : Prec<V>::col_budget;
+    static constexpr int CRAW = BUDGET / NP;
     static constexpr int C = CRAW > 16 ? 16 : (CRAW < 1 ? 1 : CRAW);
     static constexpr int LOGC = Log2<C>::v;
     static constexpr int P = (NP * C) / E;
@@ -420,9 +425,9 @@ enum ColMode { COL_FWD_FOLD = 0, COL_INV = 1, COL_FWD = 2, COL_INV_FOLD = 3 };
 // One CTA = C adjacent columns (blockIdx.x) and, for the folded modes, one
 // half (blockIdx.y: 0 even, 1 odd).
 template <typename V, int LOGNP, int MODE>
-__global__ void __launch_bounds__(ColCfg<V, LOGNP>::P, ColCfg<V, LOGNP>::MINB)
+__global__ void __launch_bounds__(ColCfg<V, LOGNP, MODE>::P, ColCfg<V, LOGNP, MODE>::MINB)
     col_kernel(const V* __restrict__ src, V* __restrict__ dst, const V* __restrict__ tw, ColArgs a) {
-    using Cf = ColCfg<V, LOGNP>;
+    using Cf = ColCfg<V, LOGNP, MODE>;
     constexpr int NP = Cf::NP, HALF = NP / 2, C = Cf::C;
     extern __shared__ unsigned char smem_raw[];
     V* S = reinterpret_cast<V*>(smem_raw);
@@ -504,6 +509,9 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP>::P, ColCfg<V, LOGNP>::MINB)
 #ifndef NUASM_TMA_MODES_WIDE
 #define NUASM_TMA_MODES_WIDE 0xF   // N' >= 4096: the unfolded passes have 1024+ strips too
 #endif
+#ifndef NUASM_TMA_HALF_TAIL
+#define NUASM_TMA_HALF_TAIL 1      // a last partial round of strips runs as half strips
+#endif
 
 template <int LOGNP, int MODE> struct TmaColCfg {
     using Base = ColCfg<float2, LOGNP>;
@@ -532,10 +540,17 @@ template <int LOGNP, int MODE> struct TmaColCfg {
     static constexpr int MINB = BY_SMEM < 1 ? 1 : (BY_SMEM < BY_REGS ? BY_SMEM : (BY_REGS < 1 ? 1 : BY_REGS));
 };
 
+// Work items: `nfull` strips of C columns, then half strips of C/2 columns
+// for the columns of a last partial round (the host passes nfull as a whole
+// number of rounds of the grid when that leaves a partial round).  A half
+// strip loads the same C-wide box (the columns beyond its own are not used)
+// and transforms its C/2 columns with half the elements per thread, so a last
+// round that would keep part of the GPU busy for a full strip's time takes
+// half of it on all of the GPU.
 template <int LOGNP, int MODE>
 __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MODE>::MINB)
     col_tma_kernel(const __grid_constant__ CUtensorMap map, float2* __restrict__ dst, const float2* __restrict__ tw,
-                   ColArgs a, int nstrips, int nboxes, int* __restrict__ err) {
+                   ColArgs a, int nfull, int nitems, int nboxes, int* __restrict__ err) {
     using Cf = TmaColCfg<LOGNP, MODE>;
     constexpr int NP = Cf::NP, HALF = NP / 2, C = Cf::C, BOXR = Cf::BOXR;
     extern __shared__ unsigned char smem_raw[];
@@ -552,26 +567,19 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
     pdl_wait();   // the strips come from the previous kernel
     if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");   // its writes, for the TMA reads
     __syncthreads();
-    auto issue = [&](int strip) {
+    auto col0_of = [&](int item) { return item < nfull ? item * C : nfull * C + (item - nfull) * (C / 2); };
+    auto issue = [&](int item) {
         tma::mbar_expect_tx(bar, uint32_t(nboxes) * BOXR * C * uint32_t(sizeof(float2)));
-        for (int b = 0; b < nboxes; ++b) tma::load_2d(raw + b * BOXR * C, &map, strip * C, b * BOXR, bar);
+        for (int b = 0; b < nboxes; ++b) tma::load_2d(raw + b * BOXR * C, &map, col0_of(item), b * BOXR, bar);
     };
-    if (tid == 0 && int(blockIdx.x) < nstrips) issue(blockIdx.x);
+    if (tid == 0 && int(blockIdx.x) < nitems) issue(blockIdx.x);
     uint32_t parity = 0;
-    for (int s = blockIdx.x; s < nstrips; s += gridDim.x) {
-        const bool ok = tma::mbar_wait(bar, parity);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(err, 2);
-                tma::mbar_wait(bar, parity);
-            }
-            return;
-        }
-        parity ^= 1;
-        const int col0 = s * C, next = s + gridDim.x;
-        auto prefetch = [&] {
-            if (tid == 0 && next < nstrips) issue(next);
-        };
+    // one item of CC columns (CC = C or C/2) with EE elements per thread
+    auto run_item = [&](auto cc_tag, auto prefetch, int col0) {
+        constexpr int CC = decltype(cc_tag)::value;
+        constexpr int EE = Cf::E * CC / C;
+        constexpr int LOGCC = Log2<CC>::v;
+        constexpr int LOGSEQ = Cf::MERGED ? LOGCC + 1 : LOGCC;
         if constexpr (MODE == COL_FWD_FOLD) {
             // raw: window rows [0, NP + BOXR) of C columns (zero beyond the window);
             // half 0 transforms x(p) + x(p + N'), half 1 (x(p) - x(p + N')) w^p
@@ -589,7 +597,7 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
                 if (r >= 0 && col < W) dst[r * Wp + col] = v;
             };
             if constexpr (Cf::MERGED) {
-                block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGSEQ, false>(
+                block_fft<float2, -1, EE, LOGNP, LOGSEQ, false>(
                     S, tw, [&](int p, int cs) { return fold(p, cs >> 1, cs & 1); },
                     [&](int pk, int cs, float2 v) { put(pk, cs >> 1, cs & 1, v); }, prefetch);
             } else {
@@ -598,8 +606,8 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
                 for (int sgn = 0; sgn < 2; ++sgn) {
                     auto load = [&](int p, int c) { return fold(p, c, sgn); };
                     auto store = [&](int pk, int c, float2 v) { put(pk, c, sgn, v); };
-                    if (sgn == 0) block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, nothing);
-                    else block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, prefetch);
+                    if (sgn == 0) block_fft<float2, -1, EE, LOGNP, LOGCC, false>(S, tw, load, store, nothing);
+                    else block_fft<float2, -1, EE, LOGNP, LOGCC, false>(S, tw, load, store, prefetch);
                 }
             }
         } else if constexpr (MODE == COL_INV_FOLD) {
@@ -617,7 +625,7 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
                 if (u < W && col < W) dst[u * Wp + col] = v;
             };
             if constexpr (Cf::MERGED) {
-                block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGSEQ, false>(
+                block_fft<float2, +1, EE, LOGNP, LOGSEQ, false>(
                     S, tw, [&](int q, int cs) { return get(q, cs >> 1, cs & 1); },
                     [&](int k, int cs, float2 v) { put(k, cs >> 1, cs & 1, v); }, prefetch);
             } else {
@@ -626,21 +634,60 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
                 for (int sgn = 0; sgn < 2; ++sgn) {
                     auto load = [&](int q, int c) { return get(q, c, sgn); };
                     auto store = [&](int k, int c, float2 v) { put(k, c, sgn, v); };
-                    if (sgn == 0) block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, nothing);
-                    else block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGC, false>(S, tw, load, store, prefetch);
+                    if (sgn == 0) block_fft<float2, +1, EE, LOGNP, LOGCC, false>(S, tw, load, store, nothing);
+                    else block_fft<float2, +1, EE, LOGNP, LOGCC, false>(S, tw, load, store, prefetch);
                 }
             }
         } else if constexpr (MODE == COL_INV) {
-            block_fft<float2, +1, Cf::E, LOGNP, Cf::LOGC, false>(
+            block_fft<float2, +1, EE, LOGNP, LOGCC, false>(
                 S, tw, [&](int p, int c) { return raw[p * C + c]; },
                 [&](int p, int c, float2 v) {
-                    if (p < n) dst[p * n + col0 + c] = v;
+                    if (p < n && col0 + c < n) dst[p * n + col0 + c] = v;
                 },
                 prefetch);
         } else {
-            block_fft<float2, -1, Cf::E, LOGNP, Cf::LOGC, false>(
+            block_fft<float2, -1, EE, LOGNP, LOGCC, false>(
                 S, tw, [&](int p, int c) { return p < n ? raw[p * C + c] : zero; },
-                [&](int p, int c, float2 v) { dst[p * n + col0 + c] = v; }, prefetch);
+                [&](int p, int c, float2 v) {
+                    if (col0 + c < n) dst[p * n + col0 + c] = v;
+                },
+                prefetch);
+        }
+    };
+    // the full strips, then (nfull being a whole number of rounds) the half strips
+    int s = blockIdx.x;
+    for (; s < nfull; s += gridDim.x) {
+        const bool ok = tma::mbar_wait(bar, parity);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(err, 2);
+                tma::mbar_wait(bar, parity);
+            }
+            return;
+        }
+        parity ^= 1;
+        const int next = s + gridDim.x;
+        auto prefetch = [&] {
+            if (tid == 0 && next < nitems) issue(next);
+        };
+        run_item(std::integral_constant<int, C>{}, prefetch, s * C);
+    }
+    if constexpr (C >= 4) {   // half strips start on an even column (16-byte TMA coordinate)
+        for (; s < nitems; s += gridDim.x) {
+            const bool ok = tma::mbar_wait(bar, parity);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicOr(err, 2);
+                    tma::mbar_wait(bar, parity);
+                }
+                return;
+            }
+            parity ^= 1;
+            const int next = s + gridDim.x;
+            auto prefetch = [&] {
+                if (tid == 0 && next < nitems) issue(next);
+            };
+            run_item(std::integral_constant<int, C / 2>{}, prefetch, col0_of(s));
         }
     }
 }
@@ -697,7 +744,7 @@ cudaError_t launch_row(const nuasm_plan_s* P, int type, cudaStream_t st) {
 
 template <typename V, int LOGNP, int MODE>
 cudaError_t launch_col(const nuasm_plan_s* P, const void* src, void* dst, int ncols, int halves, cudaStream_t st) {
-    using Cf = ColCfg<V, LOGNP>;
+    using Cf = ColCfg<V, LOGNP, MODE>;
     const ColArgs a{P->g.n, P->g.W, P->g.Wp};
     const size_t sm = Cf::smem();
     cudaError_t e = set_smem(col_kernel<V, LOGNP, MODE>, sm);
@@ -744,15 +791,24 @@ cudaError_t launch_col_tma(const nuasm_plan_s* P, const void* src, void* dst, in
         const int nstrips = (ncols + Cf::C - 1) / Cf::C;
         const int nboxes = (load_rows + Cf::BOXR - 1) / Cf::BOXR;
         const int grid = nstrips < ctas ? nstrips : ctas;
+        // a last partial round of strips runs as half strips over the whole grid
+        int nfull = nstrips, nitems = nstrips;
+        // (C >= 4: a half strip's first column, the TMA x coordinate, must stay even)
+        if (NUASM_TMA_HALF_TAIL && Cf::C >= 4 && nstrips > grid && nstrips % grid != 0) {
+            nfull = (nstrips / grid) * grid;
+            const int tail = ncols - nfull * Cf::C, hc = Cf::C / 2;
+            nitems = nfull + (tail + hc - 1) / hc;
+            if ((hc & 1) || ((nfull * Cf::C) & 1)) return cudaErrorNotSupported;   // an odd TMA x: never issued
+        }
         const ColArgs a{P->g.n, P->g.W, P->g.Wp};
         if constexpr (MODE == COL_FWD) {   // first kernel of the type-2 chain
             col_tma_kernel<LOGNP, MODE><<<grid, Cf::P, sm, st>>>(map, static_cast<float2*>(dst),
-                                                                 static_cast<const float2*>(P->d.tw), a, nstrips,
-                                                                 nboxes, P->d.err);
+                                                                 static_cast<const float2*>(P->d.tw), a, nfull,
+                                                                 nitems, nboxes, P->d.err);
         } else {
             e = launch_chained(col_tma_kernel<LOGNP, MODE>, dim3(grid), dim3(Cf::P), sm, st, map,
-                               static_cast<float2*>(dst), static_cast<const float2*>(P->d.tw), a, nstrips, nboxes,
-                               P->d.err);
+                               static_cast<float2*>(dst), static_cast<const float2*>(P->d.tw), a, nfull, nitems,
+                               nboxes, P->d.err);
             if (e != cudaSuccess) return e;
         }
         return cudaGetLastError();
