@@ -89,7 +89,7 @@ template <int DIR, typename V> __device__ __forceinline__ V mul_i(V a) {
 
 // shared-memory padding: one spare slot every 128 bytes breaks the power-of-two
 // strides of the first Stockham pass across banks
-template <typename V> __device__ __forceinline__ int spad(int q) {
+template <typename V> __host__ __device__ __forceinline__ constexpr int spad(int q) {
     return q + (q >> CTraits<V>::pad_shift);
 }
 template <typename V> __host__ __device__ constexpr int spad_size(int n) {

@@ -198,6 +198,13 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
     static_assert(LOGNS % LE == 0, "passes start at multiples of the schedule's radix");
     const V* __restrict__ tp = tw;
     if constexpr (LOGNS > 0) tp = tw + TwpOffset<V, LE, LOGL, LOGNS / LE>::v;
+    // Shared-memory indices: element (c, p) sits at spad(ROWMAJOR ? c L + p : p C + c).  Along
+    // one butterfly the unpadded index grows by a fixed step S (loads: L/R, stores: NS; times C
+    // when the sequences interleave) from a base b whose residue mod the padding period plus
+    // any multiple of S stays below the period, so spad(b + r S) = spad(b) + spad(r S): one
+    // padded base per butterfly and compile-time offsets.
+    constexpr int SLD = ROWMAJOR ? LDR : (LDR << LOGC);
+    constexpr int SST = ROWMAJOR ? NS : (NS << LOGC);
     const int tid = threadIdx.x;
     V v[E];
     int jj[NB], cc[NB];
@@ -211,11 +218,13 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
         jj[b] = j;
         cc[b] = c;
         if constexpr (LOGNS > 0) twiddle_base<V, R>(tp, j & (NS - 1), twb[b]);   // in flight across the barrier
+        if (FIRST) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int p = j + r * LDR;
-            if (FIRST) v[b * R + r] = load(p, c);
-            else v[b * R + r] = sm[spad<V>(ROWMAJOR ? (c << LOGL) + p : (p << LOGC) + c)];
+            for (int r = 0; r < R; ++r) v[b * R + r] = load(j + r * LDR, c);
+        } else {
+            const V* src = sm + spad<V>(ROWMAJOR ? (c << LOGL) + j : (j << LOGC) + c);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b * R + r] = src[spad<V>(r * SLD)];
         }
     }
     if (!FIRST || SYNC_FIRST) __syncthreads();
@@ -234,11 +243,13 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
         const int j = jj[b], c = cc[b];
         const int k = j & (NS - 1);
         const int base = ((j - k) << LR) + k;
+        if (LAST) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int p = base + r * NS;
-            if (LAST) store(p, c, v[b * R + r]);
-            else sm[spad<V>(ROWMAJOR ? (c << LOGL) + p : (p << LOGC) + c)] = v[b * R + r];
+            for (int r = 0; r < R; ++r) store(base + r * NS, c, v[b * R + r]);
+        } else {
+            V* dst = sm + spad<V>(ROWMAJOR ? (c << LOGL) + base : (base << LOGC) + c);
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[spad<V>(r * SST)] = v[b * R + r];
         }
     }
     if (!LAST) __syncthreads();

@@ -665,6 +665,7 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
                                                                 const int* __restrict__ off,
                                                                 const int* __restrict__ home,
                                                                 const int* __restrict__ order,
+                                                                const int4* __restrict__ items,
                                                                 const typename VecOf<S>::type* __restrict__ win,
                                                                 typename VecOf<S>::type* __restrict__ v, GridArgs a,
                                                                 const typename PolyOf<S>::type kp) {
@@ -673,11 +674,20 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
     extern __shared__ unsigned char smem_raw[];
     V* tl = reinterpret_cast<V*>(smem_raw);
     const int T = a.T, w = EXACT ? WMAX : a.w, TH = T + w - 1, THP = halo_pitch(TH, a.skew);
-    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
+    int tile, b, e;
+    if (items) {   // a chunk of a tile's home records
+        const int4 it = items[blockIdx.x];
+        tile = it.x;
+        b = it.y;
+        e = it.z;
+    } else {       // a whole tile, heaviest tiles first
+        tile = order ? order[blockIdx.x] : blockIdx.x;
+        b = off[tile];
+        e = b + home[tile];
+    }
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
     pdl_allow_next();
-    const int b = off[tile], e = b + home[tile];
     Rec pre[kInterpPrefetch];
 #pragma unroll
     for (int k = 0; k < kInterpPrefetch; ++k) {
@@ -798,9 +808,11 @@ cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
     const size_t sm = size_t(TH) * THP * sizeof(V);
     cudaError_t e = set_smem(interp_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
-    e = launch_chained(interp_kernel<S, WMAX, EXACT>, dim3(P->g.ntiles), dim3(kInterpThreads), sm, st,
+    const int grid = P->d.interp_items ? P->n_interp_items : P->g.ntiles;
+    e = launch_chained(interp_kernel<S, WMAX, EXACT>, dim3(grid), dim3(kInterpThreads), sm, st,
                        static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.tile_home,
-                       P->d.tile_order, static_cast<const V*>(P->d.win), static_cast<V*>(v), a, taps_arg<S>(P));
+                       P->d.tile_order, static_cast<const int4*>(P->d.interp_items), static_cast<const V*>(P->d.win),
+                       static_cast<V*>(v), a, taps_arg<S>(P));
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -845,11 +857,21 @@ static nuasm_status cuda_status(cudaError_t e) {
 // Tiles in decreasing record count (ties by index): the launch order of the
 // one-CTA-per-tile kernels, so the heaviest tiles start first and the last
 // wave holds the lightest.
+//
+// Interpolation items: a tile with more than NUASM_INTERP_CHUNK home records is
+// split into chunks of at most that many, each its own CTA (which stages the
+// same tile), so that the densest tiles do not hold the last wave; items are
+// launched heaviest first.  0 keeps one item per tile.
+#ifndef NUASM_INTERP_CHUNK
+#define NUASM_INTERP_CHUNK 0
+#endif
 cudaError_t make_tile_order(nuasm_plan_s* P, cudaStream_t st) {
     const int nt = P->g.ntiles;
-    std::vector<int> off(size_t(nt) + 1), order(nt);
+    std::vector<int> off(size_t(nt) + 1), home(nt), order(nt);
     cudaError_t e = cudaMemcpyAsync(off.data(), P->d.tile_off, sizeof(int) * (size_t(nt) + 1),
                                     cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(home.data(), P->d.tile_home, sizeof(int) * size_t(nt), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(),
@@ -857,8 +879,30 @@ cudaError_t make_tile_order(nuasm_plan_s* P, cudaStream_t st) {
     if ((e = xmalloc(reinterpret_cast<void**>(&P->d.tile_order), sizeof(int) * size_t(nt))) != cudaSuccess) return e;
     P->device_bytes += int64_t(sizeof(int)) * nt;
     e = cudaMemcpyAsync(P->d.tile_order, order.data(), sizeof(int) * size_t(nt), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
-    return cudaStreamSynchronize(st);   // the host vector goes out of scope
+    if (e != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return e;   // host vectors go out of scope
+    if (NUASM_INTERP_CHUNK > 0) {
+        const int ch = NUASM_INTERP_CHUNK;
+        std::vector<int4> items;
+        items.reserve(size_t(nt) + size_t(P->m / ch) + 1);
+        for (int t = 0; t < nt; ++t) {
+            const int b = off[t], e2 = off[t] + home[t];
+            if (b == e2) continue;   // no home records: nothing to interpolate
+            // chunks start on a multiple of 32 records from the tile start: the record order's
+            // bank classes repeat every 32 records, so each warp keeps its distinct classes
+            const int pieces = (e2 - b + ch - 1) / ch, step = (((e2 - b + pieces - 1) / pieces) + 31) & ~31;
+            for (int s = b; s < e2; s += step) items.push_back(make_int4(t, s, std::min(e2, s + step), 0));
+        }
+        std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
+        if (items.empty()) return cudaSuccess;
+        if ((e = xmalloc(reinterpret_cast<void**>(&P->d.interp_items), sizeof(int4) * items.size())) != cudaSuccess)
+            return e;
+        P->device_bytes += int64_t(sizeof(int4) * items.size());
+        P->n_interp_items = int(items.size());
+        e = cudaMemcpyAsync(P->d.interp_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        return cudaStreamSynchronize(st);
+    }
+    return cudaSuccess;
 }
 
 nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, const double* w, cudaStream_t st) {

@@ -68,6 +68,8 @@ struct PlanDevice {
     int* tile_off = nullptr;    // ntiles + 1 offsets into rec
     int* tile_home = nullptr;   // home-record count per tile
     int* tile_order = nullptr;  // launch order of the tiles (heaviest first); null = index order
+    int4* interp_items = nullptr;   // interpolation work items (tile, first record, end record, 0),
+                                    // heaviest first; null = one item per tile in tile_order
     void* win = nullptr;        // W x Wp fine-grid window
     void* bufA = nullptr;       // N' x Wp
     void* bufB = nullptr;       // N' x N
@@ -91,6 +93,7 @@ struct nuasm_plan_s {
     int nonsep_mode = 0;        // ASM non-separable phase: 0 none, 1 plain, 2 double-float
     int etab_pitch = 0;         // entries per row of d.etab
     int skew = 0;               // bank skew of the gridding tile layouts and record order (0 or 2)
+    int n_interp_items = 0;     // entries of d.interp_items
     nuasm::KernelPoly poly{};   // kernel taps as polynomials (F32 gridding)
     nuasm::KernelPoly64 poly64{};   // the same in FP64 (F64 gridding)
     int64_t device_bytes = 0;
