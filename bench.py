@@ -218,9 +218,9 @@ def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
     v, s = ("double2", "double") if f64 else ("float2", "float")
     w = info["kernel_width"]
     if f64:
-        tap = "double, 13, true" if w == 13 else f"double, {8 if w <= 8 else 16}, false"
+        tap = "double, 13, true" if w == 13 else f"double, {8 if w <= 8 else (16 if w <= 16 else 26)}, false"
     else:
-        tap = f"float, {w}, true" if 4 <= w <= 8 else "float, 16, false"
+        tap = f"float, {w}, true" if 4 <= w <= 8 else f"float, {16 if w <= 16 else 26}, false"
     tma = not f64 and 512 <= info["n_pad"] <= 4096          # folded column passes
     tma_wide = not f64 and info["n_pad"] == 4096              # unfolded ones too
     tile = info.get("tile", 64)
@@ -229,7 +229,8 @@ def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
     elif tile <= 32:
         spread = f"spread_private_kernel<{tap}>"
     else:
-        spread = f"spread_fixed_kernel<{w}, true, 2>" if 4 <= w <= 8 else "spread_fixed_kernel<16, false, 2>"
+        spread = (f"spread_fixed_kernel<{w}, true, 2>" if 4 <= w <= 8 else
+                  f"spread_fixed_kernel<{16 if w <= 16 else 26}, false, 2>")
     return {"col_fwd": f"col_tma_kernel<{lognp}, 2>" if tma_wide else f"col_kernel<{v}, {lognp}, 2>",
             "row_t2": f"row_t2_kernel<{v}, {lognp}>",
             "col_inv_fold": f"col_tma_kernel<{lognp}, 3>" if tma else f"col_kernel<{v}, {lognp}, 3>",
@@ -703,6 +704,15 @@ def run_batch(args):
         for plan, t, inp, out in planes:
             (P.nuasm1_execute if t == 1 else P.nuasm2_execute)(plan, inp, out, stream=stream)
 
+    # the planes whose every kernel launches at least a full wave of CTAs over the
+    # GPU (N >= 1024: >= 1024 rows / columns per pass, >= 1089 tiles); running the
+    # others side by side with them can hide at most the others' time
+    large = [it for it in planes if it[0].n >= 1024]
+
+    def plain_large():
+        for plan, t, inp, out in large:
+            (P.nuasm1_execute if t == 1 else P.nuasm2_execute)(plan, inp, out, stream=stream)
+
     def batched():
         batch.execute(stream)
 
@@ -717,6 +727,7 @@ def run_batch(args):
     b_ms = _timed_steps(batched, args.steps, stream, flush)
     clk = clocks.stop()
     p_ms = _timed_steps(plain, max(3, min(args.steps, 20)), stream, flush)
+    pl_ms = _timed_steps(plain_large, max(3, min(args.steps, 20)), stream, flush)
     total_ms, points = reduce_over_ranks(float(b_ms.sum()), float(total_m * args.steps), dev)
     value = points / (total_ms * 1e-3)
     plain_value = total_m / (float(p_ms.mean()) * 1e-3)
@@ -749,6 +760,11 @@ def run_batch(args):
                        ", ".join(f"T={k} x{v}" for k, v in sorted(tiles.items())),
                        "plain_points_per_s": plain_value, "batched_over_plain": value / plain_value,
                        "plain": "one execute call per plane, back to back on one stream",
+                       "large_planes": len(large),
+                       "plain_ms_all": float(p_ms.mean()), "plain_ms_large_planes_only": float(pl_ms.mean()),
+                       "batched_over_plain_bound": float(p_ms.mean() / pl_ms.mean()),
+                       "bound": "plain time of all planes / plain time of the N >= 1024 planes alone: the gain "
+                                "batching could reach if every smaller plane ran for free beside them",
                        "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": float(np.percentile(b_ms, 50)), "p99": float(np.percentile(b_ms, 99))},
             "e2e": {"value": total_m / (float(e_ms.mean()) * 1e-3), "unit": UNIT,

@@ -74,7 +74,7 @@ typedef enum { NUASM_KIND_ASM = 0, NUASM_KIND_FRESNEL = 1 } nuasm_kind;
 typedef enum {
     NUASM_KERNEL_ES = 0,        /* exponential of semicircle, width ceil(log10(1/tol)) + 1 */
     NUASM_KERNEL_GAUSSIAN = 1   /* Gaussian (the Greengard-Lee gridding the paper uses),
-                                   width ceil(ln(1/tol)/1.11) <= 16, so tol >= 2e-8 */
+                                   width ceil(ln(1/tol)/1.11) <= 26, so tol >= 3e-13 */
 } nuasm_kernel;
 
 typedef enum {
@@ -107,9 +107,10 @@ typedef struct {
     int32_t kernel;     /* nuasm_kernel: spreading kernel of the NUFFT gridding */
     int32_t tile;       /* side of the gridding tiles (bins) in fine-grid cells: 16, 32 or 64;
                            0 = the library's rule (the largest side giving at least 608
-                           tiles over the fine-grid window, else 16).  Results agree to
-                           rounding for every choice; nuasm_autotune_tile measures which
-                           is fastest. */
+                           tiles over the fine-grid window, else 16; at least w - 1 for
+                           a kernel of w taps).  A side below w - 1 returns
+                           NUASM_EUNSUPPORTED.  Results agree to rounding for every
+                           choice; nuasm_autotune_tile measures which is fastest. */
 } nuasm_params_t;
 
 /* Geometry of a plan (read-only report). */
@@ -321,7 +322,9 @@ nuasm_status nuasm_band(const nuasm_params_t* p, int32_t out[4]);
  * precision's default), precision and kernel (nuasm_kernel): exp(beta
  * (sqrt(1 - (2t/w)^2) - 1)) for the exponential of semicircle, exp(-beta t^2)
  * for the Gaussian, t in fine-grid cells, |t| <= w/2.  NUASM_EUNSUPPORTED
- * when the kernel needs more than 16 taps for the tolerance.  No device work.
+ * when the kernel needs more taps than this build runs for the tolerance (16
+ * for the exponential of semicircle, which reaches 1e-15 within them; 26 for
+ * the Gaussian).  No device work.
  */
 nuasm_status nuasm_kernel_shape(double tol, int32_t prec, int32_t kernel, int32_t* width, double* beta);
 

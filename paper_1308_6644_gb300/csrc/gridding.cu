@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
         tap_weights<WMAX>(S(r.fy), kp, wy);
         const int ya = max(0, -ly), yb = min(w, T - ly);
         const int xa = max(0, -lx), xb = min(w, T - lx);
-#pragma unroll
+#pragma unroll(WMAX <= 16 ? WMAX : 1)
         for (int qy = 0; qy < WMAX; ++qy) {
             if (qy < ya || qy >= yb) continue;
             const S vr = val.x * wy[qy], vi = val.y * wy[qy];
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(kFixedThreads, 2) spread_fixed_kernel(const Re
             const float sr = val[k].x * inv, si = val[k].y * inv;
             const int ya = max(0, -ly), yb = min(w, T - ly);
             const int xa = max(0, -lx), xb = min(w, T - lx);
-#pragma unroll
+#pragma unroll(WMAX <= 16 ? WMAX : 1)
             for (int qy = 0; qy < WMAX; ++qy) {
                 if (qy < ya || qy >= yb) continue;
                 const float vr = sr * wy[qy], vi = si * wy[qy];
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
         tap_weights<WMAX>(S(r.fy), kp, wy);
         const int ya = max(0, -ly), yb = min(w, T - ly);
         const int xa = max(0, -lx), xb = min(w, T - lx);
-#pragma unroll
+#pragma unroll(WMAX <= 16 ? WMAX : 1)
         for (int qy = 0; qy < WMAX; ++qy) {
             if (qy >= w) continue;   // warp-uniform
             const bool rowok = live && qy >= ya && qy < yb;
@@ -639,7 +639,7 @@ __device__ __forceinline__ void interp_point(const Rec& r, const V* __restrict__
     tap_weights<WMAX>(S(r.fx), kp, wx);
     tap_weights<WMAX>(S(r.fy), kp, wy);
     S ar = S(0), ai = S(0);
-#pragma unroll
+#pragma unroll(WMAX <= 16 ? WMAX : 1)
     for (int qy = 0; qy < WMAX; ++qy) {
         if (qy >= w) continue;
         const V* row = tl + (ly + qy) * THP + lx;
@@ -835,7 +835,8 @@ template <bool SPREAD> cudaError_t gridding(const nuasm_plan_s* P, const void* i
 #if NUASM_F64_EXACT13
         if (P->g.w == 13) return run(GTag<double, 13, true>{});
 #endif
-        return P->g.w <= 8 ? run(GTag<double, 8, false>{}) : run(GTag<double, 16, false>{});
+        if (P->g.w <= 8) return run(GTag<double, 8, false>{});
+        return P->g.w <= 16 ? run(GTag<double, 16, false>{}) : run(GTag<double, kPolyMaxW, false>{});
     }
     switch (P->g.w) {
         case 4: return run(GTag<float, 4, true>{});
@@ -843,7 +844,7 @@ template <bool SPREAD> cudaError_t gridding(const nuasm_plan_s* P, const void* i
         case 6: return run(GTag<float, 6, true>{});
         case 7: return run(GTag<float, 7, true>{});
         case 8: return run(GTag<float, 8, true>{});
-        default: return run(GTag<float, 16, false>{});
+        default: return P->g.w <= 16 ? run(GTag<float, 16, false>{}) : run(GTag<float, kPolyMaxW, false>{});
     }
 }
 
@@ -881,7 +882,7 @@ cudaError_t make_tile_order(nuasm_plan_s* P, cudaStream_t st) {
     e = cudaMemcpyAsync(P->d.tile_order, order.data(), sizeof(int) * size_t(nt), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return e;   // host vectors go out of scope
     if (NUASM_INTERP_CHUNK > 0) {
-        const int ch = NUASM_INTERP_CHUNK;
+        const int ch = NUASM_INTERP_CHUNK > 0 ? NUASM_INTERP_CHUNK : 1;
         std::vector<int4> items;
         items.reserve(size_t(nt) + size_t(P->m / ch) + 1);
         for (int t = 0; t < nt; ++t) {

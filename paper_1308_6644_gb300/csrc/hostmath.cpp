@@ -226,7 +226,7 @@ bool kernel_shape(double tol, int prec, int kernel, int* w, double* beta) {
         if (ww < 2) ww = 2;
         *w = ww;
         *beta = std::sqrt(2.0) * M_PI / ww;   // 1 / (2 s^2)
-        return ww <= 16;
+        return ww <= kPolyMaxW;               // 26 taps: tol >= 3e-13
     }
     ww = int(std::ceil(-std::log10(tol) - 1e-9)) + 1;
     if (ww < 2) ww = 2;
@@ -262,6 +262,12 @@ nuasm_status validate(const nuasm_params_t& p0, int64_t m, nuasm_params_t* out) 
         if (!kernel_shape(p.tol, p.prec, p.kernel, &w, &beta)) return NUASM_EUNSUPPORTED;
     }
     if (p.tile != 0 && p.tile != 16 && p.tile != 32 && p.tile != 64) return NUASM_EINVAL;
+    {
+        int w;
+        double beta;
+        kernel_shape(p.tol, p.prec, p.kernel, &w, &beta);
+        if (p.tile != 0 && p.tile < w - 1) return NUASM_EUNSUPPORTED;   // taps would reach two tiles away
+    }
     if (p.n_pad != 0 && (p.n_pad < 2 * p.n || (p.n_pad & 1))) return NUASM_EINVAL;
     // what this build implements: power-of-two planes 16 <= N and N', N' <= 8192
     // (F32) / 4096 (F64); other even sizes are valid problems it does not run
@@ -313,6 +319,8 @@ Geometry make_geometry(const nuasm_params_t& p) {
             }
         }
     }
+    // a point's taps may reach only the next tile on each axis: w - 1 <= T
+    while (g.T < g.w - 1) g.T *= 2;
     g.ntx = (g.W + g.T - 1) / g.T;
     g.ntiles = g.ntx * g.ntx;
     band_range(p, g.band);

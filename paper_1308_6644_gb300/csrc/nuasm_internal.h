@@ -24,7 +24,7 @@ struct Geometry {
 
 // Piecewise-polynomial form of the spreading kernel: tap i of a point with
 // fractional offset f in [0, 1) has weight sum_k c[i][k] x^k, x = 2f - 1.
-constexpr int kPolyMaxW = 16, kPolyMaxD = 16;
+constexpr int kPolyMaxW = 26, kPolyMaxD = 16;   // taps: 16 for the ES kernel, 26 for the Gaussian
 struct KernelPoly {
     float c[kPolyMaxW][kPolyMaxD];
     int deg;
@@ -109,7 +109,7 @@ namespace nuasm {
 
 // Gauss-Legendre quadrature of the kernel on [0, w/2] for its Fourier transform.
 struct KernelQuad {
-    static constexpr int kMax = 2 * 16 + 48;
+    static constexpr int kMax = 2 * kPolyMaxW + 48;
     int n;
     double t[kMax], f[kMax];   // nodes and weight x kernel value
 };

@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
         constexpr int CC = decltype(cc_tag)::value;
         constexpr int EE = Cf::E * CC / C;
         constexpr int LOGCC = Log2<CC>::v;
-        constexpr int LOGSEQ = Cf::MERGED ? LOGCC + 1 : LOGCC;
+        [[maybe_unused]] constexpr int LOGSEQ = Cf::MERGED ? LOGCC + 1 : LOGCC;
         if constexpr (MODE == COL_FWD_FOLD) {
             // raw: window rows [0, NP + BOXR) of C columns (zero beyond the window);
             // half 0 transforms x(p) + x(p + N'), half 1 (x(p) - x(p + N')) w^p

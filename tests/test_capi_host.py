@@ -143,7 +143,7 @@ def test_binding_checks_shapes_and_dtypes(P):
         plan.info()
 
 
-@pytest.mark.parametrize("tol,w", [(1e-3, 7), (1e-5, 11), (1e-6, 13), (1e-7, 15)])
+@pytest.mark.parametrize("tol,w", [(1e-3, 7), (1e-5, 11), (1e-6, 13), (1e-7, 15), (1e-10, 21), (1e-12, 25)])
 def test_gaussian_kernel_width_rule(P, tol, w):
     width, beta = P.nuasm_kernel_shape(tol, 0, P.KERNEL_GAUSSIAN)
     assert width == w and abs(beta - np.sqrt(2) * np.pi / w) < 1e-12
@@ -151,12 +151,17 @@ def test_gaussian_kernel_width_rule(P, tol, w):
 
 def test_gaussian_kernel_limits(P):
     with pytest.raises(P.NuasmError) as ei:
-        P.nuasm_kernel_shape(1e-10, 1, P.KERNEL_GAUSSIAN)
-    assert ei.value.code == 6
+        P.nuasm_kernel_shape(1e-13, 1, P.KERNEL_GAUSSIAN)
+    assert ei.value.code == 6        # 27 taps: beyond the 26 this build runs
+    assert P.nuasm_kernel_shape(0.0, 1, P.KERNEL_GAUSSIAN)[0] == 25   # the F64 default tolerance 1e-12
     x = np.zeros(2)
     with pytest.raises(P.NuasmError) as ei:
-        P.nuasm_plan(P.make_params(32, 10e-6, 633e-9, 0.01, prec="f64", kernel="gaussian"), x, x)
-    assert ei.value.code == 6        # the F64 default tolerance needs more than 16 taps
+        P.nuasm_plan(P.make_params(32, 10e-6, 633e-9, 0.01, prec="f64", kernel="gaussian", tol=1e-13), x, x)
+    assert ei.value.code == 6
+    with pytest.raises(P.NuasmError) as ei:   # a 16-cell tile is too small for 21 taps
+        P.nuasm_plan(P.make_params(32, 10e-6, 633e-9, 0.01, prec="f64", kernel="gaussian", tol=1e-10, tile=16),
+                     x, x)
+    assert ei.value.code == 6
     bad = P.make_params(32, 10e-6, 633e-9, 0.01)
     bad.kernel = 7
     with pytest.raises(P.NuasmError) as ei:

@@ -333,8 +333,12 @@ def test_fp32_type1_large_tiles_dynamic_range_and_non_finite(P):
 # ---------------------------------------------------------------- Gaussian (Greengard-Lee) kernel option
 @pytest.mark.parametrize("kind", ["asm", "fresnel"])
 @pytest.mark.parametrize("type_", [1, 2])
-@pytest.mark.parametrize("prec,tol,bound", [("f32", 0.0, 1e-5), ("f64", 1e-7, 1e-6)])
+@pytest.mark.parametrize("prec,tol,bound", [("f32", 0.0, 1e-5), ("f64", 1e-7, 1e-6), ("f64", 1e-10, 1e-10),
+                                            ("f64", 0.0, 1e-10)])
 def test_gaussian_kernel_parity(P, kind, type_, prec, tol, bound):
+    """The paper's Gaussian gridding kernel on every path: FP32 at its default
+    tolerance, FP64 at 1e-7 (15 taps), 1e-10 (21 taps) and the FP64 default
+    1e-12 (25 taps, tiles of at least 32 cells), against the oracle."""
     x, y, vals = random_case(51 + type_, 64, 600, type_=type_)
     kw = dict(pitch=10e-6, lam=633e-9, z=0.03, ox=25e-6, oy=-12e-6)
     got = run_gpu(P, kind, type_, prec, 64, x=x, y=y, values=vals, tol=tol, kernel="gaussian", **kw)
