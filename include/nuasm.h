@@ -130,8 +130,9 @@ typedef struct {
     int64_t phase_table_bytes; /* of which the tabulated non-separable ASM phase factor
                                   (Eq. 4) and its type-2 product with the per-column
                                   factor (0 when the plan evaluates it per mode) */
-    int32_t bank_skew;         /* shared-memory bank skew of the gridding tiles (0 or 2),
-                                  chosen from the points' distribution */
+    int32_t bank_skew;         /* shared-memory bank skew of the gridding tiles (0 or 2; 0 .. 8
+                                  in builds with a skew per tile, then the one most tiles
+                                  use), chosen from the points' distribution */
 } nuasm_plan_info_t;
 
 /*

@@ -154,8 +154,59 @@ __global__ void bin_scatter_kernel(const double* __restrict__ x, const double* _
 // of the graded NU-ASM_2 plane); skew 2 mixes in the row.  The plan takes
 // skew 2 only where it balances the classes clearly better (class_balance),
 // since on unstructured clusters skew 0 measured faster at equal balance.
+// A warp's 32 records can only have distinct classes while the tile's classes
+// are balanced, and in sparse tiles their counts are uneven (Poisson).  With
+// NUASM_TILE_SKEW each tile takes instead the even skew (0 .. 8) that
+// minimises the largest class count of its home records (tile_skew_kernel;
+// 0 unless another is strictly better).  A CPU model of the bank pattern
+// gives 18% fewer shared-memory wavefronts for the spreading atomics on the
+// 4M clustered points, but measured: spreading 283 -> 296 us there, the
+// interpolation 29.2 -> 28.7 us (NU-ASM_2 benchmark) and 95.3 -> 94.2 us
+// (4M clustered points); off by default.
+#ifndef NUASM_TILE_SKEW
+#define NUASM_TILE_SKEW 0   // 1: a bank skew per tile
+#endif
+constexpr int kNumSkews = 5, kMaxSkew = 8;
+__host__ __device__ constexpr int skew_candidate(int i) { return 2 * i; }   // 0, 2, 4, 6, 8
 __host__ __device__ constexpr int plane_stride(int T, int skew) { return T + skew; }   // T = 32, 64: = skew mod 32
 __host__ __device__ constexpr int halo_pitch(int th, int skew) { return th + (((skew - th) % 16) + 16) % 16; }
+
+// Per tile: the candidate skew whose largest class count over the tile's home
+// records is smallest (ties keep the smaller skew); hist[i] counts the tiles
+// that chose candidate i.
+template <typename Rec>
+__global__ void tile_skew_kernel(const Rec* __restrict__ rec, const int* __restrict__ off,
+                                 const int* __restrict__ home, int T, int ntx, int8_t* __restrict__ tskew,
+                                 unsigned long long* __restrict__ hist) {
+    __shared__ int cnt[kNumSkews][32];
+    __shared__ int best[kNumSkews];
+    const int tile = blockIdx.x;
+    const int x0 = (tile - (tile / ntx) * ntx) * T, y0 = (tile / ntx) * T;
+    for (int i = threadIdx.x; i < kNumSkews * 32; i += blockDim.x) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+    for (int i = off[tile] + threadIdx.x; i < off[tile] + home[tile]; i += blockDim.x) {
+        const uint32_t cell = rec[i].cell;
+        const int lx = int(cell & 0xffffu) - x0, ly = int(cell >> 16) - y0;
+#pragma unroll
+        for (int k = 0; k < kNumSkews; ++k) atomicAdd(&cnt[k][(skew_candidate(k) * ly + lx) & 31], 1);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < kNumSkews) {
+        int m = cnt[warp][lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) best[warp] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int bi = 0;
+        for (int k = 1; k < kNumSkews; ++k)
+            if (best[k] < best[bi]) bi = k;
+        tskew[tile] = int8_t(skew_candidate(bi));
+        atomicAdd(&hist[bi], 1ull);
+    }
+}
 
 // Sum over tiles of the largest bank-class count of the tile's home records
 // (the ones interpolation visits and most of what spreading visits), for skew
@@ -201,9 +252,11 @@ __global__ void class_balance_kernel(const Rec* __restrict__ rec, const int* __r
 // type 2; type 1 sums in shared memory whatever the order).
 template <typename Rec>
 __global__ void order_tile_kernel(const Rec* __restrict__ src, Rec* __restrict__ dst, const int* __restrict__ off,
-                                  const int* __restrict__ home, int T, int ntx, int skew) {
+                                  const int* __restrict__ home, int T, int ntx, int skew,
+                                  const int8_t* __restrict__ tskew) {
     __shared__ int cnt[2][32], cur[2][32];
     const int tile = blockIdx.x;
+    if (tskew) skew = tskew[tile];
     const int x0 = (tile - (tile / ntx) * ntx) * T, y0 = (tile / ntx) * T;
     auto bank_class = [&](uint32_t cell) {
         return (skew * (int(cell >> 16) - y0) + (int(cell & 0xffffu) - x0)) & 31;
@@ -268,7 +321,10 @@ template <> struct VecOf<double> { using type = double2; };
 
 struct GridArgs {
     int W, Wp, T, ntx, w;
-    int skew;   // bank skew of the tile layouts (plane_stride, halo_pitch)
+    int skew;   // bank skew of the tile layouts (plane_stride, halo_pitch) when tskew is null
+    const int8_t* tskew;   // per-tile skews, or null
+    int max_skew;          // largest skew any tile uses (sizes the shared memory)
+    __device__ int skew_of(int tile) const { return tskew ? int(tskew[tile]) : skew; }
 };
 
 // --------------------------------------------------------------- spreading (type 1)
@@ -306,11 +362,11 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
                                                      const typename PolyOf<S>::type kp) {
     using V = typename VecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
-    const int T = a.T, w = EXACT ? WMAX : a.w, TS = plane_stride(T, a.skew), TT = T * TS;
+    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
+    const int T = a.T, w = EXACT ? WMAX : a.w, TS = plane_stride(T, a.skew_of(tile)), TT = T * TS;
     S* sre = reinterpret_cast<S*>(smem_raw);
     S* sim = sre + TT;
     pdl_allow_next();
-    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
     for (int i = threadIdx.x; i < TT; i += blockDim.x) { sre[i] = S(0); sim[i] = S(0); }
@@ -391,13 +447,13 @@ __global__ void __launch_bounds__(kFixedThreads, 2) spread_fixed_kernel(const Re
     extern __shared__ unsigned char smem_raw[];
     __shared__ float red[kFixedThreads / 32];
     __shared__ float batch_sum;
-    const int T = a.T, w = EXACT ? WMAX : a.w, TS = plane_stride(T, a.skew), TT = T * TS;
+    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
+    const int T = a.T, w = EXACT ? WMAX : a.w, TS = plane_stride(T, a.skew_of(tile)), TT = T * TS;
     int* are = reinterpret_cast<int*>(smem_raw);
     int* aim = are + TT;
     float* tre = reinterpret_cast<float*>(aim + TT);
     float* tim = tre + TT;
     pdl_allow_next();
-    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
     for (int i = threadIdx.x; i < TT; i += kFixedThreads) {
@@ -538,11 +594,11 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
     using Rec = typename RecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
     V* copies = reinterpret_cast<V*>(smem_raw);
-    const int T = a.T, w = EXACT ? WMAX : a.w, TS = plane_stride(T, a.skew), TT = T * TS;
+    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
+    const int T = a.T, w = EXACT ? WMAX : a.w, TS = plane_stride(T, a.skew_of(tile)), TT = T * TS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     V* mine = copies + warp * TT;
     pdl_allow_next();
-    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
     const V zero = CTraits<V>::zero();
@@ -673,7 +729,7 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
     using Rec = typename RecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
     V* tl = reinterpret_cast<V*>(smem_raw);
-    const int T = a.T, w = EXACT ? WMAX : a.w, TH = T + w - 1, THP = halo_pitch(TH, a.skew);
+    const int T = a.T, w = EXACT ? WMAX : a.w, TH = T + w - 1;
     int tile, b, e;
     if (items) {   // a chunk of a tile's home records
         const int4 it = items[blockIdx.x];
@@ -685,6 +741,7 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
         b = off[tile];
         e = b + home[tile];
     }
+    const int THP = halo_pitch(TH, a.skew_of(tile));
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
     pdl_allow_next();
@@ -753,6 +810,8 @@ GridArgs grid_args(const nuasm_plan_s* P) {
     a.ntx = P->g.ntx;
     a.w = P->g.w;
     a.skew = P->skew;
+    a.tskew = P->d.tile_skew;
+    a.max_skew = P->d.tile_skew ? kMaxSkew : P->skew;
     return a;
 }
 
@@ -771,7 +830,7 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     using V = typename VecOf<S>::type;
     GridArgs a = grid_args(P);
     if (NUASM_SPREAD_PRIVATE && a.T <= (sizeof(S) == 4 ? 32 : 16)) {
-        const size_t sm = size_t(8) * a.T * plane_stride(a.T, a.skew) * sizeof(V);
+        const size_t sm = size_t(8) * a.T * plane_stride(a.T, a.max_skew) * sizeof(V);
         cudaError_t e = set_smem(spread_private_kernel<S, WMAX, EXACT>, sm);
         if (e != cudaSuccess) return e;
         spread_private_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
@@ -782,7 +841,7 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     if constexpr (sizeof(S) == 4) {
         if (NUASM_SPREAD_FIXED) {
             constexpr int RPB = NUASM_SPREAD_FIXED_RPB;
-            const size_t sm = size_t(4) * a.T * plane_stride(a.T, a.skew) * sizeof(float);
+            const size_t sm = size_t(4) * a.T * plane_stride(a.T, a.max_skew) * sizeof(float);
             cudaError_t e = set_smem(spread_fixed_kernel<WMAX, EXACT, RPB>, sm);
             if (e != cudaSuccess) return e;
             spread_fixed_kernel<WMAX, EXACT, RPB><<<P->g.ntiles, kFixedThreads, sm, st>>>(
@@ -791,7 +850,7 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
             return cudaGetLastError();
         }
     }
-    const size_t sm = size_t(2) * a.T * plane_stride(a.T, a.skew) * sizeof(S);
+    const size_t sm = size_t(2) * a.T * plane_stride(a.T, a.max_skew) * sizeof(S);
     cudaError_t e = set_smem(spread_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
     spread_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
@@ -804,7 +863,10 @@ template <typename S, int WMAX, bool EXACT>
 cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
     using V = typename VecOf<S>::type;
     GridArgs a = grid_args(P);
-    const int TH = a.T + a.w - 1, THP = halo_pitch(TH, a.skew);
+    int THP = 0;   // the largest staged row pitch over the skews in use
+    for (int k = 0; k <= a.max_skew; k += 2) THP = std::max(THP, halo_pitch(a.T + a.w - 1, k));
+    if (!a.tskew) THP = halo_pitch(a.T + a.w - 1, a.skew);
+    const int TH = a.T + a.w - 1;
     const size_t sm = size_t(TH) * THP * sizeof(V);
     cudaError_t e = set_smem(interp_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
@@ -965,35 +1027,64 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
         if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     }
     if (P->m > 0 && total > 0) {
-        // bank skew: 2 where it balances the record classes at least 5% better
-        unsigned long long* sums = nullptr;
-        unsigned long long hs[2] = {0, 0};
-        if ((e = xmalloc_async(reinterpret_cast<void**>(&sums), sizeof(hs), st)) != cudaSuccess) return fail(e);
-        e = cudaMemsetAsync(sums, 0, sizeof(hs), st);
-        if (e == cudaSuccess) {
-            if (P->f64)
-                class_balance_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(P->d.rec), P->d.tile_off,
-                                                               P->d.tile_home, g.T, g.ntx, sums);
-            else
-                class_balance_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(P->d.rec), P->d.tile_off,
-                                                               P->d.tile_home, g.T, g.ntx, sums);
-            e = cudaGetLastError();
+        if (NUASM_TILE_SKEW) {
+            // per-tile bank skew: the candidate that balances the tile's record classes best
+            unsigned long long* hist = nullptr;
+            unsigned long long hh[kNumSkews] = {};
+            if ((e = xmalloc(reinterpret_cast<void**>(&P->d.tile_skew), size_t(nt))) != cudaSuccess) return fail(e);
+            P->device_bytes += nt;
+            if ((e = xmalloc_async(reinterpret_cast<void**>(&hist), sizeof(hh), st)) != cudaSuccess) return fail(e);
+            e = cudaMemsetAsync(hist, 0, sizeof(hh), st);
+            if (e == cudaSuccess) {
+                if (P->f64)
+                    tile_skew_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(P->d.rec), P->d.tile_off,
+                                                               P->d.tile_home, g.T, g.ntx, P->d.tile_skew, hist);
+                else
+                    tile_skew_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(P->d.rec), P->d.tile_off,
+                                                               P->d.tile_home, g.T, g.ntx, P->d.tile_skew, hist);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            xfree_async(hist, st);
+            if (e != cudaSuccess) return fail(e);
+            int most = 0;
+            for (int k = 1; k < kNumSkews; ++k)
+                if (hh[k] > hh[most]) most = k;
+            P->skew = skew_candidate(most);
+        } else {
+            // one bank skew for every tile: 2 where it balances the record classes at least 5% better
+            unsigned long long* sums = nullptr;
+            unsigned long long hs[2] = {0, 0};
+            if ((e = xmalloc_async(reinterpret_cast<void**>(&sums), sizeof(hs), st)) != cudaSuccess) return fail(e);
+            e = cudaMemsetAsync(sums, 0, sizeof(hs), st);
+            if (e == cudaSuccess) {
+                if (P->f64)
+                    class_balance_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(P->d.rec),
+                                                                   P->d.tile_off, P->d.tile_home, g.T, g.ntx, sums);
+                else
+                    class_balance_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(P->d.rec),
+                                                                   P->d.tile_off, P->d.tile_home, g.T, g.ntx, sums);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            xfree_async(sums, st);
+            if (e != cudaSuccess) return fail(e);
+            P->skew = double(hs[1]) < 0.95 * double(hs[0]) ? 2 : 0;
         }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        xfree_async(sums, st);
-        if (e != cudaSuccess) return fail(e);
-        P->skew = double(hs[1]) < 0.95 * double(hs[0]) ? 2 : 0;
         void* tmp = nullptr;
         if ((e = xmalloc_async(&tmp, rsz * size_t(total), st)) != cudaSuccess) return fail(e);
         e = cudaMemcpyAsync(tmp, P->d.rec, rsz * size_t(total), cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) {
             if (P->f64)
                 order_tile_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(tmp), static_cast<RecD*>(P->d.rec),
-                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew);
+                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew,
+                                                    P->d.tile_skew);
             else
                 order_tile_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(tmp), static_cast<RecF*>(P->d.rec),
-                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew);
+                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew,
+                                                    P->d.tile_skew);
             e = cudaGetLastError();
         }
         xfree_async(tmp, st);
@@ -1032,12 +1123,14 @@ cudaError_t bin_points_into(const nuasm_plan_s* P, const double* x, const double
         bin_scatter_kernel<RecD, double><<<blocks, 256, 0, st>>>(x, y, a, P->d.tile_off, home_cnt, cur_home,
                                                                  cur_dup, static_cast<RecD*>(rec_tmp));
         order_tile_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(rec_tmp), static_cast<RecD*>(P->d.rec),
-                                                    P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew);
+                                                    P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew,
+                                                    P->d.tile_skew);
     } else {
         bin_scatter_kernel<RecF, float><<<blocks, 256, 0, st>>>(x, y, a, P->d.tile_off, home_cnt, cur_home,
                                                                 cur_dup, static_cast<RecF*>(rec_tmp));
         order_tile_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(rec_tmp), static_cast<RecF*>(P->d.rec),
-                                                    P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew);
+                                                    P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew,
+                                                    P->d.tile_skew);
     }
     return cudaGetLastError();
 }

@@ -68,6 +68,7 @@ struct PlanDevice {
     int* tile_off = nullptr;    // ntiles + 1 offsets into rec
     int* tile_home = nullptr;   // home-record count per tile
     int* tile_order = nullptr;  // launch order of the tiles (heaviest first); null = index order
+    int8_t* tile_skew = nullptr;    // bank skew of each tile's layouts and record order; null: skew for all
     int4* interp_items = nullptr;   // interpolation work items (tile, first record, end record, 0),
                                     // heaviest first; null = one item per tile in tile_order
     void* win = nullptr;        // W x Wp fine-grid window
@@ -92,7 +93,8 @@ struct nuasm_plan_s {
     double rc = 0.0;            // z / (2 lambda)
     int nonsep_mode = 0;        // ASM non-separable phase: 0 none, 1 plain, 2 double-float
     int etab_pitch = 0;         // entries per row of d.etab
-    int skew = 0;               // bank skew of the gridding tile layouts and record order (0 or 2)
+    int skew = 0;               // bank skew of the gridding tile layouts and record order: the one most
+                                // tiles use when d.tile_skew is set, else the one every tile uses
     int n_interp_items = 0;     // entries of d.interp_items
     nuasm::KernelPoly poly{};   // kernel taps as polynomials (F32 gridding)
     nuasm::KernelPoly64 poly64{};   // the same in FP64 (F64 gridding)
