@@ -121,6 +121,48 @@ template <int DIR, typename V> struct Dft<16, DIR, V> {
 template <int R> struct Log2 { static constexpr int v = R <= 1 ? 0 : 1 + Log2<R / 2>::v; };
 template <> struct Log2<1> { static constexpr int v = 0; };
 
+// exp(DIR i pi k / 16) for k in [0, 16): constants once k is known at compile time
+template <int DIR, typename V> __device__ __forceinline__ V cis_pi16(int k) {
+    using S = typename CTraits<V>::real;
+    // cos(pi k / 16), k = 0 .. 8
+    constexpr S c[9] = {S(1.0),
+                        S(0.98078528040323044912618223613424),
+                        S(0.92387953251128675612818318939679),
+                        S(0.83146961230254523707878837761791),
+                        S(0.70710678118654752440084436210485),
+                        S(0.55557023301960222474283081394853),
+                        S(0.38268343236508977172845998403040),
+                        S(0.19509032201612826784828486847702),
+                        S(0.0)};
+    const S re = k <= 8 ? c[k] : -c[16 - k];
+    const S im = k <= 8 ? c[8 - k] : c[k - 8];
+    return CTraits<V>::make(re, DIR > 0 ? im : -im);
+}
+
+// exp(DIR i pi q / L) for q in [0, L), for the load functor of the first pass of
+// an engine of radix E, whose radix R0 is E (or L if smaller): there
+// q = j + r L/R0 with j < L/R0 the same for
+// every input of a butterfly and r a compile-time constant of the unrolled
+// loop, so the factor is tw[j] (or its conjugate; tw[t] = exp(-i pi t / L))
+// times the constant exp(DIR i pi r / R0): one table load per butterfly
+// instead of one per input (FP32; on the FP64 pipe the extra complex product
+// costs more than the loads it saves, so FP64 reads tw[q] itself).
+template <typename V, int DIR, int LOGL, int E>
+__device__ __forceinline__ V half_bin(const V* __restrict__ tw, int q) {
+    if constexpr (sizeof(V) == 16) {
+        const V t = __ldg(&tw[q]);
+        return DIR < 0 ? t : cconj(t);
+    } else {
+        // the first pass has radix E, or 2^LOGL when the whole transform is shorter
+        constexpr int R0 = LOGL >= Log2<E>::v ? E : (1 << LOGL);
+        static_assert(R0 >= 2 && R0 <= 16, "first-pass radix");
+        constexpr int LOGLDR = LOGL - Log2<R0>::v;
+        const int j = q & ((1 << LOGLDR) - 1), r = q >> LOGLDR;
+        const V t = __ldg(&tw[j]);
+        return cmul(DIR < 0 ? t : cconj(t), cis_pi16<DIR, V>(r * (16 / R0)));
+    }
+}
+
 // ---------------------------------------------------------------- twiddle powers
 // w[r] = exp(-2 pi i k r / (Ns R)) for r in [1, R).  FP64 reads every power;
 // FP32 reads w^1 and w^4 (w^1 and w^2 for R = 4) and forms the others by
@@ -213,8 +255,11 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
     for (int b = 0; b < NB; ++b) {
         const int beta = tid + b * P;
         int c, j;
+        // tid < P, so j < LDR either way; the mask in the column case states it
+        // for the compiler, which then folds q >> log2(LDR) in a first-pass
+        // load functor to the constant r (see half_bin)
         if (ROWMAJOR) { j = beta & (LDR - 1); c = beta >> (LOGL - LR); }
-        else { c = beta & (C - 1); j = beta >> LOGC; }
+        else { c = beta & (C - 1); j = (beta >> LOGC) & (LDR - 1); }
         jj[b] = j;
         cc[b] = c;
         if constexpr (LOGNS > 0) twiddle_base<V, R>(tp, j & (NS - 1), twb[b]);   // in flight across the barrier

@@ -434,10 +434,18 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
 // atomics take about two wavefronts each on that workload; a CPU model of the
 // bank pattern gives the same 1.8x: the round-robin record order cannot give
 // 32 distinct bank classes per warp once a tile's classes run unevenly
-// (Poisson counts in the sparse background tiles).
+// (Poisson counts in the sparse background tiles).  Also measured and not
+// kept: ordering each tile's home records as those whose taps all lie in the
+// tile, then the others, so that whole warps spread without clipping (283 ->
+// 265 us there), since the second segment's bank classes crowd into the
+// tile's last columns and the interpolation over the same records slowed by
+// more (94.8 -> 109.5 us).
+#ifndef NUASM_SPREAD_FIXED_MINB
+#define NUASM_SPREAD_FIXED_MINB 3   // CTAs per SM the register budget is set for
+#endif
 constexpr int kFixedThreads = 256;
 template <int WMAX, bool EXACT, int RPB>
-__global__ void __launch_bounds__(kFixedThreads, 2) spread_fixed_kernel(const RecF* __restrict__ rec,
+__global__ void __launch_bounds__(kFixedThreads, NUASM_SPREAD_FIXED_MINB) spread_fixed_kernel(const RecF* __restrict__ rec,
                                                                       const int* __restrict__ off,
                                                                       const double* __restrict__ wpt,
                                                                       const int* __restrict__ order,
@@ -500,35 +508,46 @@ __global__ void __launch_bounds__(kFixedThreads, 2) spread_fixed_kernel(const Re
         if (S == 0.f) continue;   // every value of the batch is zero (uniform)
         const bool fixed = S >= 1e-30f && S <= 3.0e38f;
         const float q = ldexpf(S, -30), inv = fixed ? 1.f / q : 1.f;
+        // The batch's mode is uniform across the CTA: one copy of the tap loops
+        // per mode, so that the integer atomics of clipped taps are predicated
+        // instead of branching around the float path's compare-and-swap loops.
+        auto add_taps = [&](auto fixed_mode) {
+            constexpr bool FX = decltype(fixed_mode)::value;
+            auto add = [&](int cell, float vr, float vi) {
+                if constexpr (FX) {
+                    atomicAdd(&are[cell], __float2int_rn(vr));
+                    atomicAdd(&aim[cell], __float2int_rn(vi));
+                } else {
+                    atomicAdd(&tre[cell], vr);
+                    atomicAdd(&tim[cell], vi);
+                }
+            };
 #pragma unroll
-        for (int k = 0; k < RPB; ++k) {
-            const int i = i0 + threadIdx.x + k * kFixedThreads;
-            if (i >= e) continue;
-            const int lx = int(r[k].cell & 0xffffu) - x0, ly = int(r[k].cell >> 16) - y0;
-            float wx[WMAX], wy[WMAX];
-            tap_weights<WMAX>(r[k].fx, kp, wx);
-            tap_weights<WMAX>(r[k].fy, kp, wy);
-            const float sr = val[k].x * inv, si = val[k].y * inv;
-            const int ya = max(0, -ly), yb = min(w, T - ly);
-            const int xa = max(0, -lx), xb = min(w, T - lx);
+            for (int k = 0; k < RPB; ++k) {
+                const int i = i0 + threadIdx.x + k * kFixedThreads;
+                if (i >= e) continue;
+                const int lx = int(r[k].cell & 0xffffu) - x0, ly = int(r[k].cell >> 16) - y0;
+                float wx[WMAX], wy[WMAX];
+                tap_weights<WMAX>(r[k].fx, kp, wx);
+                tap_weights<WMAX>(r[k].fy, kp, wy);
+                const float sr = val[k].x * inv, si = val[k].y * inv;
+                const int ya = max(0, -ly), yb = min(w, T - ly);
+                const int xa = max(0, -lx), xb = min(w, T - lx);
 #pragma unroll(WMAX <= 16 ? WMAX : 1)
-            for (int qy = 0; qy < WMAX; ++qy) {
-                if (qy < ya || qy >= yb) continue;
-                const float vr = sr * wy[qy], vi = si * wy[qy];
-                const int rowi = (ly + qy) * TS + lx;
+                for (int qy = 0; qy < WMAX; ++qy) {
+                    if (qy < ya || qy >= yb) continue;
+                    const float vr = sr * wy[qy], vi = si * wy[qy];
+                    const int rowi = (ly + qy) * TS + lx;
 #pragma unroll
-                for (int qx = 0; qx < WMAX; ++qx) {
-                    if (qx < xa || qx >= xb) continue;
-                    if (fixed) {
-                        atomicAdd(&are[rowi + qx], __float2int_rn(vr * wx[qx]));
-                        atomicAdd(&aim[rowi + qx], __float2int_rn(vi * wx[qx]));
-                    } else {
-                        atomicAdd(&tre[rowi + qx], vr * wx[qx]);
-                        atomicAdd(&tim[rowi + qx], vi * wx[qx]);
+                    for (int qx = 0; qx < WMAX; ++qx) {
+                        if (qx < xa || qx >= xb) continue;
+                        add(rowi + qx, vr * wx[qx], vi * wx[qx]);
                     }
                 }
             }
-        }
+        };
+        if (fixed) add_taps(std::true_type{});
+        else add_taps(std::false_type{});
         if (fixed) {
             __syncthreads();
             if (i0 + RPB * kFixedThreads >= e) {

@@ -11,7 +11,8 @@
 
 namespace nuasm {
 
-bool encode_map_8b(CUtensorMap* map, const void* base, int cols, int rows, int pitch, int box_cols, int box_rows) {
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -24,6 +25,28 @@ bool encode_map_8b(CUtensorMap* map, const void* base, int cols, int rows, int p
         else
             cudaGetLastError();
     });
+    return encode;
+}
+}  // namespace
+
+bool encode_store_map_8b(CUtensorMap* map, void* base, int cols, int planes, int rows, int pitch, int box_cols,
+                         int box_planes, int box_rows) {
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = encoder();
+    if (!encode || !base || (reinterpret_cast<uintptr_t>(base) & 15) || ((int64_t(pitch) * 8) & 15)) return false;
+    if (box_cols < 2 || box_cols > 256 || ((box_cols * 8) & 15) || box_planes < 1 || box_planes > planes ||
+        box_rows < 1 || box_rows > 256 || cols < 1 || planes < 1 || rows < 1)
+        return false;
+    const cuuint64_t dims[3] = {cuuint64_t(cols), cuuint64_t(planes), cuuint64_t(rows)};
+    const cuuint64_t strides[2] = {cuuint64_t(pitch) * 8u, cuuint64_t(pitch) * 8u * cuuint64_t(planes)};
+    const cuuint32_t box[3] = {cuuint32_t(box_cols), cuuint32_t(box_planes), cuuint32_t(box_rows)};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, base, dims, strides, box, estride,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_map_8b(CUtensorMap* map, const void* base, int cols, int rows, int pitch, int box_cols, int box_rows) {
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = encoder();
     if (!encode || !base || (reinterpret_cast<uintptr_t>(base) & 15) || ((int64_t(pitch) * 8) & 15)) return false;
     if (box_cols < 2 || box_cols > 256 || box_rows < 1 || box_rows > 256 || ((box_cols * 8) & 15)) return false;
     const cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};

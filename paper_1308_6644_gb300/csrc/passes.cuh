@@ -239,11 +239,12 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     const RowConst<V> rc0 = row_const<V>(r0, ty, s, a);
     pdl_wait();   // A comes from the previous kernel
 
+    constexpr int R0 = Cf::MERGE ? Cf::EM : Cf::EF;   // first-pass radix of the forward engines
     auto folded = [&](int row, int p, int sgn) -> V {
         const V* x = A + (r0 + row) * Wp;
         const V u = p < W ? x[p] : zero;
         const V t = p + NP < W ? x[p + NP] : zero;
-        return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
+        return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), half_bin<V, -1, LOGNP, R0>(tw, p));
     };
     auto put = [&](int row, int pk, int sgn, V v) {
         const int pb = 2 * pk + sgn;
@@ -331,11 +332,14 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
             if (staged) cp_async_wait_all();
         });
     __syncthreads();
+    // pre-twiddle of the odd outputs: conj(tw[pg]), pg the 2N'-grid bin of q, is
+    // exp(i pi q / N') with a minus sign for q >= N'/2
+    constexpr int R0I = Cf::MERGE ? Cf::EM : Cf::EF;   // first-pass radix of the inverse engines
     auto get = [&](int row, int q, int sgn) -> V {
         const V y = M[row * NP + q];
         if (sgn == 0) return y;
-        const int pg = q < HALF ? q : q + NP;
-        return cmul(y, cconj(__ldg(&tw[pg])));
+        const V f = half_bin<V, +1, LOGNP, R0I>(tw, q);
+        return cmul(y, q < HALF ? f : CTraits<V>::make(-f.x, -f.y));
     };
     auto put = [&](int row, int k, int sgn, V v) {
         const int u = 2 * k + sgn;
@@ -375,11 +379,12 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     pdl_allow_next();
     const RowConst<V> rc0 = row_const<V>(r0, ty, s, a);
     pdl_wait();   // A comes from the previous kernel
+    constexpr int R0 = Cf::MERGE ? Cf::EM : Cf::EF;   // first-pass radix of the engines
     auto folded = [&](int row, int p, int sgn) -> V {
         const V* x = A + (r0 + row) * Wp;
         const V u = p < W ? x[p] : zero;
         const V t = p + NP < W ? x[p + NP] : zero;
-        return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
+        return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), half_bin<V, -1, LOGNP, R0>(tw, p));
     };
     auto put_mode = [&](int row, int pk, int sgn, V v) {
         const int pb = 2 * pk + sgn;
@@ -389,8 +394,8 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     auto get_mode = [&](int row, int q, int sgn) -> V {
         const V y = M[row * NP + q];
         if (sgn == 0) return y;
-        const int pg = q < HALF ? q : q + NP;
-        return cmul(y, cconj(__ldg(&tw[pg])));
+        const V f = half_bin<V, +1, LOGNP, R0>(tw, q);
+        return cmul(y, q < HALF ? f : CTraits<V>::make(-f.x, -f.y));
     };
     auto put_row = [&](int row, int k, int sgn, V v) {
         const int u = 2 * k + sgn;
@@ -446,7 +451,7 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP, MODE>::P, ColCfg<V, LOGNP, MO
                 if (col >= W) return zero;
                 const V u = p < W ? src[p * Wp + col] : zero;
                 const V t = p + NP < W ? src[(p + NP) * Wp + col] : zero;
-                return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), __ldg(&tw[p]));
+                return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), half_bin<V, -1, LOGNP, Cf::E>(tw, p));
             },
             [&](int pk, int c, V v) {
                 const int col = col0 + c;
@@ -475,8 +480,8 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP, MODE>::P, ColCfg<V, LOGNP, MO
                 if (col >= W) return zero;
                 const V y = src[q * Wp + col];
                 if (sgn == 0) return y;
-                const int pg = q < HALF ? q : q + NP;
-                return cmul(y, cconj(__ldg(&tw[pg])));
+                const V f = half_bin<V, +1, LOGNP, Cf::E>(tw, q);
+                return cmul(y, q < HALF ? f : CTraits<V>::make(-f.x, -f.y));
             },
             [&](int k, int c, V v) {
                 const int col = col0 + c;
@@ -513,6 +518,10 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP, MODE>::P, ColCfg<V, LOGNP, MO
 #define NUASM_TMA_HALF_TAIL 1      // a last partial round of strips runs as half strips
 #endif
 
+#ifndef NUASM_TMA_STORE
+#define NUASM_TMA_STORE 1          // 1: outputs staged in shared memory and written with bulk tensor stores
+#endif
+
 template <int LOGNP, int MODE> struct TmaColCfg {
     using Base = ColCfg<float2, LOGNP>;
     static constexpr int NP = Base::NP;
@@ -531,8 +540,25 @@ template <int LOGNP, int MODE> struct TmaColCfg {
     static constexpr int RAW_ROWS = MODE == COL_FWD_FOLD ? NP + BOXR : NP;
     static constexpr size_t RAW_BYTES = size_t(RAW_ROWS) * C * sizeof(float2);
     static constexpr size_t WORK_BYTES = ((size_t(spad_size<float2>(NP * SEQ)) * sizeof(float2)) + 127) & ~size_t(127);
-    static constexpr size_t SMEM = 128 + RAW_BYTES + WORK_BYTES + 16;
+    // Bulk stores: the output is viewed as {columns, PLANES, rows / PLANES}
+    // (the folded modes interleave their two halves by row: plane = half) and
+    // written in boxes of BOXZ rows, instead of 8-byte stores per thread that
+    // each cover half a 32-byte sector at C = 2.  A strip that runs one
+    // transform stages its output in the work buffer itself (the last pass has
+    // read it by then); the halves of a folded strip run in turn and stage in a
+    // buffer of their own.  Measured: the N' = 4096 folded passes 143 ->
+    // 120 us and 150 -> 127 us on the 4M-point plane; the merged N' = 2048
+    // fold 34.7 -> 36.8 us (its staging in the work buffer holds the next
+    // strip's first pass until the stores have read it), so it keeps
+    // per-thread stores.
+    static constexpr bool STORE = NUASM_TMA_STORE != 0 && !MERGED;
+    static constexpr bool OWN_STAGE = STORE && FOLDED;
+    static constexpr size_t STAGE_BYTES = OWN_STAGE ? size_t(NP) * C * sizeof(float2) : 0;
+    static constexpr int PLANES = FOLDED ? 2 : 1;
+    static constexpr int BOXZ = NP < 256 ? NP : 256;
+    static constexpr size_t SMEM = 128 + RAW_BYTES + WORK_BYTES + STAGE_BYTES + 16;
     static size_t smem() { return SMEM; }
+    static constexpr bool FITS = SMEM <= 227u * 1024u;
     // CTAs per SM that shared memory allows (228 KB per SM, 1 KB reserved per
     // CTA): registers are capped only as far as that occupancy needs
     static constexpr int BY_SMEM = int((228u * 1024u) / (SMEM + 1024u));
@@ -546,19 +572,24 @@ template <int LOGNP, int MODE> struct TmaColCfg {
 // strip loads the same C-wide box (the columns beyond its own are not used)
 // and transforms its C/2 columns with half the elements per thread, so a last
 // round that would keep part of the GPU busy for a full strip's time takes
-// half of it on all of the GPU.
+// half of it on all of the GPU.  `omap` and `omap_h` are the output's store
+// views with boxes C and C/2 columns wide; `nz` is the number of output rows
+// (per plane) that the stores cover.
 template <int LOGNP, int MODE>
 __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MODE>::MINB)
-    col_tma_kernel(const __grid_constant__ CUtensorMap map, float2* __restrict__ dst, const float2* __restrict__ tw,
-                   ColArgs a, int nfull, int nitems, int nboxes, int* __restrict__ err) {
+    col_tma_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap omap,
+                   const __grid_constant__ CUtensorMap omap_h, float2* __restrict__ dst,
+                   const float2* __restrict__ tw, ColArgs a, int nfull, int nitems, int nboxes, int nz,
+                   int* __restrict__ err) {
     using Cf = TmaColCfg<LOGNP, MODE>;
-    constexpr int NP = Cf::NP, HALF = NP / 2, C = Cf::C, BOXR = Cf::BOXR;
+    constexpr int NP = Cf::NP, HALF = NP / 2, C = Cf::C, BOXR = Cf::BOXR, BOXZ = Cf::BOXZ;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float2* raw = reinterpret_cast<float2*>(base);
     float2* S = reinterpret_cast<float2*>(base + Cf::RAW_BYTES);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(base + Cf::RAW_BYTES + Cf::WORK_BYTES);
+    float2* O = reinterpret_cast<float2*>(base + Cf::RAW_BYTES + Cf::WORK_BYTES);   // own staging, if any
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + Cf::RAW_BYTES + Cf::WORK_BYTES + Cf::STAGE_BYTES);
     const int tid = threadIdx.x;
     const int W = a.W, Wp = a.Wp, n = a.n;
     const float2 zero = make_float2(0.f, 0.f);
@@ -580,6 +611,24 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
         constexpr int EE = Cf::E * CC / C;
         constexpr int LOGCC = Log2<CC>::v;
         [[maybe_unused]] constexpr int LOGSEQ = Cf::MERGED ? LOGCC + 1 : LOGCC;
+        // staged output of the item's transform: plane `plane`, rows [0, nz) --
+        // make the staged data visible to the bulk copies and issue them
+        [[maybe_unused]] auto flush = [&](const float2* stage, int plane) {
+            tma::store_fence();
+            __syncthreads();
+            if (tid == 0) {
+                const CUtensorMap* om = CC == C ? &omap : &omap_h;
+                for (int z0 = 0; z0 < nz; z0 += BOXZ) tma::store_3d(om, col0, plane, z0, stage + z0 * CC);
+                tma::store_commit();
+            }
+        };
+        // the second half of a non-merged folded strip rewrites the staging
+        // buffer: its reads by the first half's stores end before the barriers
+        // that follow its first pass
+        [[maybe_unused]] auto second_half_hook = [&] {
+            if (tid == 0) tma::store_wait_read();
+            prefetch();
+        };
         if constexpr (MODE == COL_FWD_FOLD) {
             // raw: window rows [0, NP + BOXR) of C columns (zero beyond the window);
             // half 0 transforms x(p) + x(p + N'), half 1 (x(p) - x(p + N')) w^p
@@ -588,13 +637,18 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
                 const float2 u = raw[p * C + c], t = p < BOXR ? raw[(p + NP) * C + c] : zero;
                 const float sg = sgn ? -1.f : 1.f;
                 const float2 v = make_float2(fmaf(sg, t.x, u.x), fmaf(sg, t.y, u.y));
-                return sgn ? cmul(v, __ldg(&tw[p])) : v;
+                return sgn ? cmul(v, half_bin<float2, -1, LOGNP, EE>(tw, p)) : v;
             };
+            // output row r = 2 pk + sgn (first quarter of the bins) or 2 pk + sgn - N' (last quarter)
             auto put = [&](int pk, int c, int sgn, float2 v) {
-                const int col = col0 + c;
                 const int pb = 2 * pk + sgn;
                 const int r = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
-                if (r >= 0 && col < W) dst[r * Wp + col] = v;
+                if constexpr (Cf::STORE) {
+                    if (r >= 0) O[(r >> 1) * CC + c] = v;   // plane sgn, row r >> 1
+                } else {
+                    const int col = col0 + c;
+                    if (r >= 0 && col < W) dst[r * Wp + col] = v;
+                }
             };
             if constexpr (Cf::MERGED) {
                 block_fft<float2, -1, EE, LOGNP, LOGSEQ, false>(
@@ -607,7 +661,10 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
                     auto load = [&](int p, int c) { return fold(p, c, sgn); };
                     auto store = [&](int pk, int c, float2 v) { put(pk, c, sgn, v); };
                     if (sgn == 0) block_fft<float2, -1, EE, LOGNP, LOGCC, false>(S, tw, load, store, nothing);
+                    else if constexpr (Cf::STORE)
+                        block_fft<float2, -1, EE, LOGNP, LOGCC, false>(S, tw, load, store, second_half_hook);
                     else block_fft<float2, -1, EE, LOGNP, LOGCC, false>(S, tw, load, store, prefetch);
+                    if constexpr (Cf::STORE) flush(O, sgn);
                 }
             }
         } else if constexpr (MODE == COL_INV_FOLD) {
@@ -616,13 +673,18 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
             auto get = [&](int q, int c, int sgn) -> float2 {
                 const float2 y = raw[q * C + c];
                 if (sgn == 0) return y;
-                const int pg = q < HALF ? q : q + NP;
-                return cmul(y, cconj(__ldg(&tw[pg])));
+                const float2 f = half_bin<float2, +1, LOGNP, EE>(tw, q);
+                return cmul(y, q < HALF ? f : make_float2(-f.x, -f.y));
             };
+            // output row u = 2 k + sgn
             auto put = [&](int k, int c, int sgn, float2 v) {
-                const int col = col0 + c;
-                const int u = 2 * k + sgn;
-                if (u < W && col < W) dst[u * Wp + col] = v;
+                if constexpr (Cf::STORE) {
+                    O[k * CC + c] = v;   // plane sgn, row k
+                } else {
+                    const int col = col0 + c;
+                    const int u = 2 * k + sgn;
+                    if (u < W && col < W) dst[u * Wp + col] = v;
+                }
             };
             if constexpr (Cf::MERGED) {
                 block_fft<float2, +1, EE, LOGNP, LOGSEQ, false>(
@@ -635,34 +697,48 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
                     auto load = [&](int q, int c) { return get(q, c, sgn); };
                     auto store = [&](int k, int c, float2 v) { put(k, c, sgn, v); };
                     if (sgn == 0) block_fft<float2, +1, EE, LOGNP, LOGCC, false>(S, tw, load, store, nothing);
+                    else if constexpr (Cf::STORE)
+                        block_fft<float2, +1, EE, LOGNP, LOGCC, false>(S, tw, load, store, second_half_hook);
                     else block_fft<float2, +1, EE, LOGNP, LOGCC, false>(S, tw, load, store, prefetch);
+                    if constexpr (Cf::STORE) flush(O, sgn);
                 }
             }
         } else if constexpr (MODE == COL_INV) {
             block_fft<float2, +1, EE, LOGNP, LOGCC, false>(
                 S, tw, [&](int p, int c) { return raw[p * C + c]; },
                 [&](int p, int c, float2 v) {
-                    if (p < n && col0 + c < n) dst[p * n + col0 + c] = v;
+                    if constexpr (Cf::STORE) S[p * CC + c] = v;
+                    else if (p < n && col0 + c < n) dst[p * n + col0 + c] = v;
                 },
                 prefetch);
+            if constexpr (Cf::STORE) flush(S, 0);
         } else {
             block_fft<float2, -1, EE, LOGNP, LOGCC, false>(
                 S, tw, [&](int p, int c) { return p < n ? raw[p * C + c] : zero; },
                 [&](int p, int c, float2 v) {
-                    if (col0 + c < n) dst[p * n + col0 + c] = v;
+                    if constexpr (Cf::STORE) S[p * CC + c] = v;
+                    else if (col0 + c < n) dst[p * n + col0 + c] = v;
                 },
                 prefetch);
+            if constexpr (Cf::STORE) flush(S, 0);
+        }
+    };
+    // before a wait gives up and the CTA returns: its own copies in flight end first
+    auto give_up = [&] {
+        if (tid == 0) {
+            atomicOr(err, 2);
+            tma::mbar_wait(bar, parity);
+            if constexpr (Cf::STORE) tma::store_wait_all();
         }
     };
     // the full strips, then (nfull being a whole number of rounds) the half strips
     int s = blockIdx.x;
     for (; s < nfull; s += gridDim.x) {
+        // the previous strip's stores have read the staged output before this strip's first pass rewrites it
+        if (Cf::STORE && tid == 0) tma::store_wait_read();
         const bool ok = tma::mbar_wait(bar, parity);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(err, 2);
-                tma::mbar_wait(bar, parity);
-            }
+            give_up();
             return;
         }
         parity ^= 1;
@@ -674,12 +750,10 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
     }
     if constexpr (C >= 4) {   // half strips start on an even column (16-byte TMA coordinate)
         for (; s < nitems; s += gridDim.x) {
+            if (Cf::STORE && tid == 0) tma::store_wait_read();
             const bool ok = tma::mbar_wait(bar, parity);
             if (__syncthreads_or(!ok)) {
-                if (tid == 0) {
-                    atomicOr(err, 2);
-                    tma::mbar_wait(bar, parity);
-                }
+                give_up();
                 return;
             }
             parity ^= 1;
@@ -690,6 +764,7 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
             run_item(std::integral_constant<int, C / 2>{}, prefetch, col0_of(s));
         }
     }
+    if (Cf::STORE && tid == 0) tma::store_wait_all();
 }
 
 // --------------------------------------------------------------- launchers
@@ -768,11 +843,31 @@ cudaError_t launch_col_tma(const nuasm_plan_s* P, const void* src, void* dst, in
                            int src_rows, int src_pitch, int load_rows, cudaStream_t st) {
     using Cf = TmaColCfg<LOGNP, MODE>;
     constexpr int modes = LOGNP >= 12 ? NUASM_TMA_MODES_WIDE : NUASM_TMA_MODES;
-    if constexpr (Cf::C < 2 || Cf::NP < 512 || !((modes >> MODE) & 1)) {
+    if constexpr (Cf::C < 2 || Cf::NP < 512 || !((modes >> MODE) & 1) || !Cf::FITS) {
         return cudaErrorNotSupported;
     } else {
-        CUtensorMap map;
+        CUtensorMap map, omap, omap_h;
         if (!encode_map_8b(&map, src, src_cols, src_rows, src_pitch, Cf::C, Cf::BOXR)) return cudaErrorNotSupported;
+        // the output's store view: {columns, planes, rows per plane}, row pitch
+        const Geometry& g = P->g;
+        int ocols = g.n, orows = Cf::NP, opitch = g.n, nz = Cf::NP;
+        if constexpr (MODE == COL_FWD_FOLD) {
+            ocols = g.W, orows = Cf::NP / 2, opitch = g.Wp, nz = orows;
+        } else if constexpr (MODE == COL_INV_FOLD) {
+            if (g.W & 1) return cudaErrorNotSupported;   // the window's rows pair up as (2k, 2k + 1)
+            ocols = g.W, orows = g.W / 2, opitch = g.Wp, nz = orows < Cf::NP ? orows : Cf::NP;
+        } else if constexpr (MODE == COL_INV) {
+            orows = g.n, nz = g.n;
+        }
+        if constexpr (Cf::STORE) {
+            constexpr int hc = Cf::C >= 4 ? Cf::C / 2 : Cf::C;
+            if (!encode_store_map_8b(&omap, dst, ocols, Cf::PLANES, orows, opitch, Cf::C, 1, Cf::BOXZ) ||
+                !encode_store_map_8b(&omap_h, dst, ocols, Cf::PLANES, orows, opitch, hc, 1, Cf::BOXZ))
+                return cudaErrorNotSupported;
+        } else {
+            omap = map;
+            omap_h = map;
+        }
         const size_t sm = Cf::smem();
         cudaError_t e = set_smem(col_tma_kernel<LOGNP, MODE>, sm);
         if (e != cudaSuccess) return e;
@@ -802,13 +897,13 @@ cudaError_t launch_col_tma(const nuasm_plan_s* P, const void* src, void* dst, in
         }
         const ColArgs a{P->g.n, P->g.W, P->g.Wp};
         if constexpr (MODE == COL_FWD) {   // first kernel of the type-2 chain
-            col_tma_kernel<LOGNP, MODE><<<grid, Cf::P, sm, st>>>(map, static_cast<float2*>(dst),
+            col_tma_kernel<LOGNP, MODE><<<grid, Cf::P, sm, st>>>(map, omap, omap_h, static_cast<float2*>(dst),
                                                                  static_cast<const float2*>(P->d.tw), a, nfull,
-                                                                 nitems, nboxes, P->d.err);
+                                                                 nitems, nboxes, nz, P->d.err);
         } else {
-            e = launch_chained(col_tma_kernel<LOGNP, MODE>, dim3(grid), dim3(Cf::P), sm, st, map,
+            e = launch_chained(col_tma_kernel<LOGNP, MODE>, dim3(grid), dim3(Cf::P), sm, st, map, omap, omap_h,
                                static_cast<float2*>(dst), static_cast<const float2*>(P->d.tw), a, nfull, nitems,
-                               nboxes, P->d.err);
+                               nboxes, nz, P->d.err);
             if (e != cudaSuccess) return e;
         }
         return cudaGetLastError();

@@ -56,6 +56,24 @@ __device__ __forceinline__ void load_2d(void* dst, const CUtensorMap* map, int x
         : "memory");
 }
 
+// ---- bulk tensor stores (shared -> global), tracked by bulk async-groups
+// Each thread that wrote the staged data runs store_fence() before the barrier
+// after which one thread issues the stores; that thread waits with
+// store_wait_read() before the staging area is written again and with
+// store_wait_all() before the CTA exits.
+__device__ __forceinline__ void store_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// one 3-D box {x, y, z} of `map` from shared memory at src (128-byte aligned);
+// elements outside the tensor's extent are not written
+__device__ __forceinline__ void store_3d(const CUtensorMap* map, int x, int y, int z, const void* src) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void store_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 }  // namespace tma
 
 // Host: encode a 2-D tiled tensor map over a row-major array of 8-byte
@@ -64,5 +82,12 @@ __device__ __forceinline__ void load_2d(void* dst, const CUtensorMap* map, int x
 // driver entry point is unavailable or the array breaks the TMA alignment
 // rules (16-byte base and pitch).
 bool encode_map_8b(CUtensorMap* map, const void* base, int cols, int rows, int pitch, int box_cols, int box_rows);
+
+// Host: a 3-D view {cols, planes, rows} of a row-major array of 8-byte
+// elements for bulk stores: element (x, y, z) is base[(z * zstep + y) * pitch
+// + x] (zstep = planes: the planes interleave by row), boxes of box_cols x
+// box_planes x box_rows.  Same failure rules as encode_map_8b.
+bool encode_store_map_8b(CUtensorMap* map, void* base, int cols, int planes, int rows, int pitch, int box_cols,
+                         int box_planes, int box_rows);
 
 }  // namespace nuasm
