@@ -439,7 +439,11 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
 // tile, then the others, so that whole warps spread without clipping (283 ->
 // 265 us there), since the second segment's bank classes crowd into the
 // tile's last columns and the interpolation over the same records slowed by
-// more (94.8 -> 109.5 us).
+// more (94.8 -> 109.5 us).  And: the FP32 totals kept in the tile's own
+// window cells (read and written through L2 by the folds) instead of shared
+// memory, which leaves 32 KB per CTA and room for five CTAs per SM: 279 ->
+// 288 us (304 us at four CTAs, 320 us at six), so more resident tiles do not
+// make the shared atomics go faster.
 #ifndef NUASM_SPREAD_FIXED_MINB
 #define NUASM_SPREAD_FIXED_MINB 3   // CTAs per SM the register budget is set for
 #endif
