@@ -300,6 +300,21 @@ nuasm_status nuasm_debug_live_resources(int64_t* count);
  */
 nuasm_status nuasm_debug_bounded_wait(int32_t spins, void* stream);
 
+/*
+ * nuasm_debug_bounds -- bounds records of the debug library (the paper has no
+ * counterpart; a stand-in for a memory checker).  The library built with
+ * NUASM_DEBUG_BOUNDS=1 (libnuasm_debug.so) checks the shared- and
+ * global-memory indices and TMA coordinates its kernels compute against the
+ * extents of the buffers they address, skips any access that would fall
+ * outside and counts it.  After a device synchronisation, *hits receives the
+ * number of skipped accesses since the last reset (0 when every access was in
+ * range) and, when it is non-zero, *site / *index / *limit the check site
+ * code, the index and the extent of the first one (any of the three may be
+ * NULL).  reset != 0 clears the records.  hits NULL: NUASM_EINVAL.  The normal
+ * library has no checks: it sets *hits = -1 and returns NUASM_EUNSUPPORTED.
+ */
+nuasm_status nuasm_debug_bounds(int64_t* hits, int32_t* site, int64_t* index, int64_t* limit, int32_t reset);
+
 /* Release every resource of the plan (synchronises the plan's device work). NULL is a no-op. */
 nuasm_status nuasm_destroy(nuasm_plan_t plan);
 

@@ -50,8 +50,8 @@ def needs_build() -> bool:
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def _compile(nvcc: str, src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(nvcc: str, src: str, extra: list[str], build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -77,6 +77,29 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if verbose:
         print(f"built {LIB}")
     return LIB
+
+
+DEBUG_LIB = os.path.join(PKG, "libnuasm_debug.so")
+
+
+def build_debug(force: bool = False) -> str:
+    """Compile the bounds-checking debug library ``libnuasm_debug.so`` (every
+    translation unit with NUASM_DEBUG_BOUNDS=1, objects under _build/debug);
+    returns its path.  Selected at run time with NUASM_LIBRARY."""
+    if not force and os.path.exists(DEBUG_LIB) and \
+            not any(os.path.getmtime(f) > os.path.getmtime(DEBUG_LIB) for f in _deps()):
+        return DEBUG_LIB
+    nvcc = _nvcc()
+    bdir = os.path.join(BUILD, "debug")
+    os.makedirs(bdir, exist_ok=True)
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(lambda s: _compile(nvcc, s, ["-DNUASM_DEBUG_BOUNDS=1"], bdir), SOURCES))
+    tmp = DEBUG_LIB + ".tmp"
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, DEBUG_LIB)
+    return DEBUG_LIB
 
 
 if __name__ == "__main__":

@@ -51,6 +51,62 @@ cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// ---------------------------------------------------------------- debug bounds checks
+// The debug library (built with NUASM_DEBUG_BOUNDS=1) checks the shared- and
+// global-memory indices and the TMA coordinates its kernels compute against
+// the extents of the buffers they address, skips any access that would fall
+// outside, and records per translation unit how many were skipped and the
+// first one (site, index, extent); nuasm_debug_bounds reads and clears the
+// records.  It stands in for a memory checker.  In the normal build every
+// check is the constant true and compiles away.
+#ifndef NUASM_DEBUG_BOUNDS
+#define NUASM_DEBUG_BOUNDS 0
+#endif
+namespace dbg {
+enum Site : int {
+    kFftLoad = 1, kFftStore = 2, kTmaLoad = 3, kTmaStore = 4,
+    kColLoad = 10, kColStore = 11, kColRaw = 12, kColStage = 13,
+    kRowLoad = 20, kRowStore = 21, kRowModes = 22,
+    kBinRec = 30, kSpreadRec = 31, kSpreadValue = 32, kSpreadPlane = 33, kSpreadWindow = 34,
+    kInterpRec = 40, kInterpTile = 41, kInterpOut = 42,
+};
+struct Record {
+    unsigned int hits;
+    int site;
+    long long index, limit;
+};
+using Reader = cudaError_t (*)(Record*, bool reset);
+int add_reader(Reader r);   // diag.cu: every translation unit's reader
+}  // namespace dbg
+#if NUASM_DEBUG_BOUNDS
+namespace dbg {
+static __device__ Record rec_;   // one per translation unit
+static __device__ __noinline__ bool miss(long long i, long long n, int site) {
+    if (atomicAdd(&rec_.hits, 1u) == 0) {
+        rec_.site = site;
+        rec_.index = i;
+        rec_.limit = n;
+    }
+    return false;
+}
+__device__ __forceinline__ bool in_range(long long i, long long n, int site) {
+    return (i >= 0 && i < n) ? true : miss(i, n, site);
+}
+static cudaError_t read_rec(Record* out, bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, rec_, sizeof(Record));
+    if (e == cudaSuccess && reset) {
+        const Record zero = {0, 0, 0, 0};
+        e = cudaMemcpyToSymbol(rec_, &zero, sizeof(Record));
+    }
+    return e;
+}
+[[maybe_unused]] static const int registered_ = add_reader(&read_rec);
+}  // namespace dbg
+#define NUASM_IN_RANGE(i, n, site) ::nuasm::dbg::in_range((long long)(i), (long long)(n), (site))
+#else
+#define NUASM_IN_RANGE(i, n, site) true
+#endif
+
 // ---------------------------------------------------------------- complex
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

@@ -6,8 +6,26 @@
 // else to wait for or release.
 #include <cuda_runtime.h>
 
+#include <vector>
+
+#include "common.cuh"
 #include "nuasm_internal.h"
 #include "tma.cuh"
+
+namespace nuasm {
+namespace dbg {
+namespace {
+std::vector<Reader>& readers() {
+    static std::vector<Reader> r;   // filled during static initialisation, read afterwards
+    return r;
+}
+}  // namespace
+int add_reader(Reader r) {
+    readers().push_back(r);
+    return int(readers().size());
+}
+}  // namespace dbg
+}  // namespace nuasm
 
 namespace {
 
@@ -56,4 +74,43 @@ extern "C" nuasm_status nuasm_debug_plan_wait(nuasm_plan_t plan, int32_t spins, 
     const cudaError_t es = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = es;
     return status_of(e);
+}
+
+// Bounds records of the debug library (see the debug bounds checks in
+// common.cuh): the number of accesses the kernels skipped as out of range
+// since the last reset, summed over translation units, and the first one.
+extern "C" nuasm_status nuasm_debug_bounds(int64_t* hits, int32_t* site, int64_t* index, int64_t* limit,
+                                           int32_t reset) {
+    if (!hits) return NUASM_EINVAL;
+#if !NUASM_DEBUG_BOUNDS
+    (void)site;
+    (void)index;
+    (void)limit;
+    (void)reset;
+    *hits = -1;
+    return NUASM_EUNSUPPORTED;
+#else
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return status_of(e);
+    int64_t total = 0;
+    bool first = true;
+    for (nuasm::dbg::Reader rd : nuasm::dbg::readers()) {
+        nuasm::dbg::Record r{};
+        if ((e = rd(&r, reset != 0)) != cudaSuccess) return status_of(e);
+        total += r.hits;
+        if (r.hits && first) {
+            first = false;
+            if (site) *site = r.site;
+            if (index) *index = r.index;
+            if (limit) *limit = r.limit;
+        }
+    }
+    if (first) {
+        if (site) *site = 0;
+        if (index) *index = 0;
+        if (limit) *limit = 0;
+    }
+    *hits = total;
+    return NUASM_OK;
+#endif
 }

@@ -247,6 +247,7 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
     // padded base per butterfly and compile-time offsets.
     constexpr int SLD = ROWMAJOR ? LDR : (LDR << LOGC);
     constexpr int SST = ROWMAJOR ? NS : (NS << LOGC);
+    [[maybe_unused]] constexpr int NSM = spad_size<V>(L << LOGC);   // the transform's shared-memory extent
     const int tid = threadIdx.x;
     V v[E];
     int jj[NB], cc[NB];
@@ -267,9 +268,12 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
 #pragma unroll
             for (int r = 0; r < R; ++r) v[b * R + r] = load(j + r * LDR, c);
         } else {
-            const V* src = sm + spad<V>(ROWMAJOR ? (c << LOGL) + j : (j << LOGC) + c);
+            const int b0 = spad<V>(ROWMAJOR ? (c << LOGL) + j : (j << LOGC) + c);
+            const V* src = sm + b0;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[b * R + r] = src[spad<V>(r * SLD)];
+            for (int r = 0; r < R; ++r)
+                v[b * R + r] = NUASM_IN_RANGE(b0 + spad<V>(r * SLD), NSM, dbg::kFftLoad) ? src[spad<V>(r * SLD)]
+                                                                                        : CTraits<V>::zero();
         }
     }
     if (!FIRST || SYNC_FIRST) __syncthreads();
@@ -292,9 +296,11 @@ __device__ __forceinline__ void stockham_pass(V* __restrict__ sm, const V* __res
 #pragma unroll
             for (int r = 0; r < R; ++r) store(base + r * NS, c, v[b * R + r]);
         } else {
-            V* dst = sm + spad<V>(ROWMAJOR ? (c << LOGL) + base : (base << LOGC) + c);
+            const int d0 = spad<V>(ROWMAJOR ? (c << LOGL) + base : (base << LOGC) + c);
+            V* dst = sm + d0;
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[spad<V>(r * SST)] = v[b * R + r];
+            for (int r = 0; r < R; ++r)
+                if (NUASM_IN_RANGE(d0 + spad<V>(r * SST), NSM, dbg::kFftStore)) dst[spad<V>(r * SST)] = v[b * R + r];
         }
     }
     if (!LAST) __syncthreads();

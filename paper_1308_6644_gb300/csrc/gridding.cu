@@ -51,6 +51,7 @@ struct BinArgs {
     int n, W, T, ntx, w, h;
     double pitch;
     int64_t m;
+    int64_t cap = 0;   // record slots (extent for the debug library's checks)
 };
 
 struct PointSplit { int l0x, l0y; double fx, fy; bool ok; };
@@ -140,7 +141,7 @@ __global__ void bin_scatter_kernel(const double* __restrict__ x, const double* _
             int pos;
             if (q == 0) pos = off[t[0]] + atomicAdd(&cur_home[t[0]], 1);
             else pos = off[t[q]] + home_cnt[t[q]] + atomicAdd(&cur_dup[t[q]], 1);
-            rec[pos] = r;
+            if (NUASM_IN_RANGE(pos, a.cap, dbg::kBinRec)) rec[pos] = r;
         }
     }
 }
@@ -321,6 +322,7 @@ template <> struct VecOf<double> { using type = double2; };
 
 struct GridArgs {
     int W, Wp, T, ntx, w;
+    long long m, nrec;     // points and record slots (extents for the debug library's checks)
     int skew;   // bank skew of the tile layouts (plane_stride, halo_pitch) when tskew is null
     const int8_t* tskew;   // per-tile skews, or null
     int max_skew;          // largest skew any tile uses (sizes the shared memory)
@@ -373,7 +375,9 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
     __syncthreads();
     const int b = off[tile], e = off[tile + 1];
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+        if (!NUASM_IN_RANGE(i, a.nrec, dbg::kSpreadRec)) continue;
         const auto r = rec[i];
+        if (!NUASM_IN_RANGE(r.j, a.m, dbg::kSpreadValue)) continue;
         const int lx = int(r.cell & 0xffffu) - x0, ly = int(r.cell >> 16) - y0;
         V val = c[r.j];
         if (wpt) { const S wt = S(wpt[r.j]); val.x *= wt; val.y *= wt; }
@@ -391,6 +395,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
 #pragma unroll
             for (int qx = 0; qx < WMAX; ++qx) {
                 if (qx < xa || qx >= xb) continue;
+                if (!NUASM_IN_RANGE((ly + qy) * TS + lx + qx, TT, dbg::kSpreadPlane)) continue;
                 atomicAdd(rowr + qx, vr * wx[qx]);
                 atomicAdd(rowi + qx, vi * wx[qx]);
             }
@@ -400,7 +405,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
         const int yy = i / T, xx = i - yy * T;
         const int gy = y0 + yy, gx = x0 + xx;
-        if (gy < a.W && gx < a.W) {
+        if (gy < a.W && gx < a.W && NUASM_IN_RANGE(gy * (long long)a.Wp + gx, (long long)a.W * a.Wp, dbg::kSpreadWindow)) {
             V v;
             v.x = sre[yy * TS + xx];
             v.y = sim[yy * TS + xx];
@@ -486,8 +491,9 @@ __global__ void __launch_bounds__(kFixedThreads, NUASM_SPREAD_FIXED_MINB) spread
             const int i = i0 + threadIdx.x + k * kFixedThreads;
             val[k] = make_float2(0.f, 0.f);
             r[k].cell = 0;
-            if (i < e) {
+            if (i < e && NUASM_IN_RANGE(i, a.nrec, dbg::kSpreadRec)) {
                 r[k] = rec[i];
+                if (!NUASM_IN_RANGE(r[k].j, a.m, dbg::kSpreadValue)) r[k].j = 0;
                 val[k] = c[r[k].j];
                 if (wpt) {
                     const float wt = float(wpt[r[k].j]);
@@ -518,6 +524,7 @@ __global__ void __launch_bounds__(kFixedThreads, NUASM_SPREAD_FIXED_MINB) spread
         auto add_taps = [&](auto fixed_mode) {
             constexpr bool FX = decltype(fixed_mode)::value;
             auto add = [&](int cell, float vr, float vi) {
+                if (!NUASM_IN_RANGE(cell, TT, dbg::kSpreadPlane)) return;
                 if constexpr (FX) {
                     atomicAdd(&are[cell], __float2int_rn(vr));
                     atomicAdd(&aim[cell], __float2int_rn(vi));
@@ -563,7 +570,8 @@ __global__ void __launch_bounds__(kFixedThreads, NUASM_SPREAD_FIXED_MINB) spread
                     const float2 tr = *reinterpret_cast<const float2*>(&tre[j]);
                     const float2 ti = *reinterpret_cast<const float2*>(&tim[j]);
                     const int gy = y0 + yy, gx = x0 + xx;
-                    if (gy < a.W && gx < a.W)   // W, x0 and xx are even: both cells or neither
+                    if (gy < a.W && gx < a.W &&   // W, x0 and xx are even: both cells or neither
+                        NUASM_IN_RANGE(gy * (long long)a.Wp + gx + 1, (long long)a.W * a.Wp, dbg::kSpreadWindow))
                         *reinterpret_cast<float4*>(&win[size_t(gy) * a.Wp + gx]) =
                             make_float4(fmaf(float(rr.x), q, tr.x), fmaf(float(mm.x), q, ti.x),
                                         fmaf(float(rr.y), q, tr.y), fmaf(float(mm.y), q, ti.y));
@@ -591,7 +599,8 @@ __global__ void __launch_bounds__(kFixedThreads, NUASM_SPREAD_FIXED_MINB) spread
         const float2 tr = *reinterpret_cast<const float2*>(&tre[j]);
         const float2 ti = *reinterpret_cast<const float2*>(&tim[j]);
         const int gy = y0 + yy, gx = x0 + xx;
-        if (gy < a.W && gx < a.W)
+        if (gy < a.W && gx < a.W &&
+            NUASM_IN_RANGE(gy * (long long)a.Wp + gx + 1, (long long)a.W * a.Wp, dbg::kSpreadWindow))
             *reinterpret_cast<float4*>(&win[size_t(gy) * a.Wp + gx]) = make_float4(tr.x, ti.x, tr.y, ti.y);
     }
 }
@@ -630,7 +639,8 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
     const int b = off[tile], e = off[tile + 1];
     for (int i0 = b + warp * 32; i0 < e; i0 += 256) {
         const int i = i0 + lane;
-        const bool live = i < e;
+        const bool live = i < e && NUASM_IN_RANGE(i, a.nrec, dbg::kSpreadRec) &&
+                          NUASM_IN_RANGE(rec[i].j, a.m, dbg::kSpreadValue);
         Rec r{};
         if (live) r = rec[i];
         // lanes whose records share a first-tap cell would add to one cell in the same step
@@ -656,7 +666,8 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
 #pragma unroll
             for (int qx = 0; qx < WMAX; ++qx) {
                 if (qx >= w) continue;   // warp-uniform
-                const bool ok = rowok && qx >= xa && qx < xb;
+                const bool ok = rowok && qx >= xa && qx < xb &&
+                                (!rowok || NUASM_IN_RANGE((ly + qy) * TS + lx + qx, TT, dbg::kSpreadPlane));
                 if (!clash) {
                     if (ok) {
                         V g = row[qx];
@@ -677,7 +688,7 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
         const int yy = i / T, xx = i - yy * T;
         const int gy = y0 + yy, gx = x0 + xx;
-        if (gy < a.W && gx < a.W) {
+        if (gy < a.W && gx < a.W && NUASM_IN_RANGE(gy * (long long)a.Wp + gx, (long long)a.W * a.Wp, dbg::kSpreadWindow)) {
             const int si = yy * TS + xx;
             V v = copies[si];
 #pragma unroll
@@ -712,7 +723,8 @@ constexpr int kInterpThreads = 256, kInterpPrefetch = 4;
 
 template <typename S, int WMAX, bool EXACT, typename Rec, typename V>
 __device__ __forceinline__ void interp_point(const Rec& r, const V* __restrict__ tl, int THP, int x0, int y0, int w,
-                                             const typename PolyOf<S>::type& kp, V* __restrict__ v) {
+                                             const typename PolyOf<S>::type& kp, V* __restrict__ v,
+                                             [[maybe_unused]] int tl_n, [[maybe_unused]] long long m) {
     const int lx = int(r.cell & 0xffffu) - x0, ly = int(r.cell >> 16) - y0;
     S wx[WMAX], wy[WMAX];
     tap_weights<WMAX>(S(r.fx), kp, wx);
@@ -726,6 +738,7 @@ __device__ __forceinline__ void interp_point(const Rec& r, const V* __restrict__
 #pragma unroll
         for (int qx = 0; qx < WMAX; ++qx) {
             if (qx >= w) continue;
+            if (!NUASM_IN_RANGE((ly + qy) * THP + lx + qx, tl_n, dbg::kInterpTile)) continue;
             const V g = row[qx];
             rr = fma(g.x, wx[qx], rr);
             ri = fma(g.y, wx[qx], ri);
@@ -736,7 +749,7 @@ __device__ __forceinline__ void interp_point(const Rec& r, const V* __restrict__
     V out;
     out.x = ar;
     out.y = ai;
-    v[r.j] = out;
+    if (NUASM_IN_RANGE(r.j, m, dbg::kInterpOut)) v[r.j] = out;
 }
 
 template <typename S, int WMAX, bool EXACT>
@@ -772,7 +785,7 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
 #pragma unroll
     for (int k = 0; k < kInterpPrefetch; ++k) {
         const int i = b + threadIdx.x + k * kInterpThreads;
-        if (i < e) pre[k] = rec[i];
+        if (i < e && NUASM_IN_RANGE(i, a.nrec, dbg::kInterpRec)) pre[k] = rec[i];
     }
     pdl_wait();   // the window comes from the previous kernel; the records are the plan's
     if constexpr (sizeof(V) == 8) {
@@ -818,8 +831,8 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
             const int i = base + k * kInterpThreads;
             if (i < e) {
                 const Rec r = pre[k];
-                if (i + AHEAD < e) pre[k] = rec[i + AHEAD];
-                interp_point<S, WMAX, EXACT>(r, tl, THP, x0, y0, w, kp, v);
+                if (i + AHEAD < e && NUASM_IN_RANGE(i + AHEAD, a.nrec, dbg::kInterpRec)) pre[k] = rec[i + AHEAD];
+                interp_point<S, WMAX, EXACT>(r, tl, THP, x0, y0, w, kp, v, TH * THP, a.m);
             }
         }
     }
@@ -835,6 +848,8 @@ GridArgs grid_args(const nuasm_plan_s* P) {
     a.skew = P->skew;
     a.tskew = P->d.tile_skew;
     a.max_skew = P->d.tile_skew ? kMaxSkew : P->skew;
+    a.m = P->m;
+    a.nrec = P->nrec > 0 ? P->nrec : 4 * P->m;   // unknown on the host (no-allocation path): the capacity
     return a;
 }
 
@@ -1029,6 +1044,7 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
         return NUASM_ERANGE;
     }
     P->nrec = total;
+    a.cap = total;
     if ((e = make_tile_order(P, st)) != cudaSuccess) return fail(e);
     const size_t rsz = P->f64 ? sizeof(RecD) : sizeof(RecF);
     if ((e = xmalloc(&P->d.rec, rsz * size_t(total > 0 ? total : 1))) != cudaSuccess) return fail(e);
@@ -1125,7 +1141,7 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
 cudaError_t bin_points_into(const nuasm_plan_s* P, const double* x, const double* y, int* cnt, void* rec_tmp,
                             cudaStream_t st) {
     const Geometry& g = P->g;
-    const BinArgs a{g.n, g.W, g.T, g.ntx, g.w, g.h, P->p.pitch, P->m};
+    const BinArgs a{g.n, g.W, g.T, g.ntx, g.w, g.h, P->p.pitch, P->m, 4 * P->m};
     const int nt = g.ntiles;
     int* home_cnt = cnt;
     int* dup_cnt = cnt + nt;

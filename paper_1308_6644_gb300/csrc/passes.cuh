@@ -240,16 +240,18 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     pdl_wait();   // A comes from the previous kernel
 
     constexpr int R0 = Cf::MERGE ? Cf::EM : Cf::EF;   // first-pass radix of the forward engines
+    [[maybe_unused]] const int a_n = a.np * Wp;   // extent of A (N' x Wp)
     auto folded = [&](int row, int p, int sgn) -> V {
         const V* x = A + (r0 + row) * Wp;
-        const V u = p < W ? x[p] : zero;
-        const V t = p + NP < W ? x[p + NP] : zero;
+        const V u = p < W && NUASM_IN_RANGE((r0 + row) * Wp + p, a_n, dbg::kRowLoad) ? x[p] : zero;
+        const V t = p + NP < W && NUASM_IN_RANGE((r0 + row) * Wp + p + NP, a_n, dbg::kRowLoad) ? x[p + NP] : zero;
         return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), half_bin<V, -1, LOGNP, R0>(tw, p));
     };
     auto put = [&](int row, int pk, int sgn, V v) {
         const int pb = 2 * pk + sgn;
         const int q = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
-        if (q >= 0) M[row * NP + q] = cmul(v, row_factor<V, ROWS>(q, row, r0, rc0, tx, ty, s, a));
+        if (q >= 0 && NUASM_IN_RANGE(row * NP + q, ROWS * NP, dbg::kRowModes))
+            M[row * NP + q] = cmul(v, row_factor<V, ROWS>(q, row, r0, rc0, tx, ty, s, a));
     };
     if constexpr (Cf::MERGE) {
         block_fft<V, -1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false>(
@@ -265,9 +267,9 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     __syncthreads();
     const int n = a.n;
     block_fft<V, +1, Cf::EF, LOGNP, Cf::LOGROWS, true, Cf::MERGE>(
-        S, tw, [&](int p, int c) { return M[c * NP + p]; },
+        S, tw, [&](int p, int c) { return NUASM_IN_RANGE(c * NP + p, ROWS * NP, dbg::kRowModes) ? M[c * NP + p] : zero; },
         [&](int p, int c, V v) {
-            if (p < n) B[(r0 + c) * n + p] = v;
+            if (p < n && NUASM_IN_RANGE((r0 + c) * n + p, a.np * n, dbg::kRowStore)) B[(r0 + c) * n + p] = v;
         });
 }
 
@@ -315,7 +317,10 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     }
     pdl_wait();   // B comes from the previous kernel
     block_fft<V, -1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
-        S, tw, [&](int p, int c) { return p < n ? B[(r0 + c) * n + p] : zero; },
+        S, tw,
+        [&](int p, int c) {
+            return p < n && NUASM_IN_RANGE((r0 + c) * n + p, a.np * n, dbg::kRowLoad) ? B[(r0 + c) * n + p] : zero;
+        },
         [&](int p, int c, V v) {
             V f;
             const V t = ROWS == 1 ? rc0.ty : __ldg(&ty[r0 + c]);
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
             } else {
                 f = row_factor<V, ROWS>(p, c, r0, rc0, tx, ty, s, a);
             }
-            M[c * NP + p] = cmul(v, f);
+            if (NUASM_IN_RANGE(c * NP + p, ROWS * NP, dbg::kRowModes)) M[c * NP + p] = cmul(v, f);
         },
         [&] {
             if (staged) cp_async_wait_all();
@@ -336,14 +341,14 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     // exp(i pi q / N') with a minus sign for q >= N'/2
     constexpr int R0I = Cf::MERGE ? Cf::EM : Cf::EF;   // first-pass radix of the inverse engines
     auto get = [&](int row, int q, int sgn) -> V {
-        const V y = M[row * NP + q];
+        const V y = NUASM_IN_RANGE(row * NP + q, ROWS * NP, dbg::kRowModes) ? M[row * NP + q] : zero;
         if (sgn == 0) return y;
         const V f = half_bin<V, +1, LOGNP, R0I>(tw, q);
         return cmul(y, q < HALF ? f : CTraits<V>::make(-f.x, -f.y));
     };
     auto put = [&](int row, int k, int sgn, V v) {
         const int u = 2 * k + sgn;
-        if (u < W) A[(r0 + row) * Wp + u] = v;
+        if (u < W && NUASM_IN_RANGE((r0 + row) * Wp + u, a.np * Wp, dbg::kRowStore)) A[(r0 + row) * Wp + u] = v;
     };
     if constexpr (Cf::MERGE) {
         block_fft<V, +1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false, true>(
@@ -380,26 +385,28 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     const RowConst<V> rc0 = row_const<V>(r0, ty, s, a);
     pdl_wait();   // A comes from the previous kernel
     constexpr int R0 = Cf::MERGE ? Cf::EM : Cf::EF;   // first-pass radix of the engines
+    [[maybe_unused]] const int a_n = a.np * Wp;   // extent of A (N' x Wp)
     auto folded = [&](int row, int p, int sgn) -> V {
         const V* x = A + (r0 + row) * Wp;
-        const V u = p < W ? x[p] : zero;
-        const V t = p + NP < W ? x[p + NP] : zero;
+        const V u = p < W && NUASM_IN_RANGE((r0 + row) * Wp + p, a_n, dbg::kRowLoad) ? x[p] : zero;
+        const V t = p + NP < W && NUASM_IN_RANGE((r0 + row) * Wp + p + NP, a_n, dbg::kRowLoad) ? x[p + NP] : zero;
         return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), half_bin<V, -1, LOGNP, R0>(tw, p));
     };
     auto put_mode = [&](int row, int pk, int sgn, V v) {
         const int pb = 2 * pk + sgn;
         const int q = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
-        if (q >= 0) M[row * NP + q] = cmul(v, row_factor<V, ROWS>(q, row, r0, rc0, tx, ty, s, a));
+        if (q >= 0 && NUASM_IN_RANGE(row * NP + q, ROWS * NP, dbg::kRowModes))
+            M[row * NP + q] = cmul(v, row_factor<V, ROWS>(q, row, r0, rc0, tx, ty, s, a));
     };
     auto get_mode = [&](int row, int q, int sgn) -> V {
-        const V y = M[row * NP + q];
+        const V y = NUASM_IN_RANGE(row * NP + q, ROWS * NP, dbg::kRowModes) ? M[row * NP + q] : zero;
         if (sgn == 0) return y;
         const V f = half_bin<V, +1, LOGNP, R0>(tw, q);
         return cmul(y, q < HALF ? f : CTraits<V>::make(-f.x, -f.y));
     };
     auto put_row = [&](int row, int k, int sgn, V v) {
         const int u = 2 * k + sgn;
-        if (u < W) A[(r0 + row) * Wp + u] = v;
+        if (u < W && NUASM_IN_RANGE((r0 + row) * Wp + u, a_n, dbg::kRowStore)) A[(r0 + row) * Wp + u] = v;
     };
     if constexpr (Cf::MERGE) {
         block_fft<V, -1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false>(
@@ -440,6 +447,15 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP, MODE>::P, ColCfg<V, LOGNP, MO
     const int sgn = blockIdx.y;
     const int W = a.W, Wp = a.Wp, n = a.n;
     const V zero = CTraits<V>::zero();
+    // extents of src and dst (elements) for the checks of the debug library
+    [[maybe_unused]] const int src_n = MODE == COL_FWD_FOLD ? W * Wp : MODE == COL_INV ? NP * n
+                                     : MODE == COL_FWD ? n * n : NP * Wp;
+    [[maybe_unused]] const int dst_n = MODE == COL_FWD_FOLD ? NP * Wp : MODE == COL_INV ? n * n
+                                     : MODE == COL_FWD ? NP * n : W * Wp;
+    auto ld = [&](int i) -> V { return NUASM_IN_RANGE(i, src_n, dbg::kColLoad) ? src[i] : zero; };
+    auto st = [&](int i, V v) {
+        if (NUASM_IN_RANGE(i, dst_n, dbg::kColStore)) dst[i] = v;
+    };
     pdl_allow_next();
     pdl_wait();   // src comes from the previous kernel (no-op for the first kernel of a chain)
     if constexpr (MODE == COL_FWD_FOLD) {
@@ -449,28 +465,28 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP, MODE>::P, ColCfg<V, LOGNP, MO
             [&](int p, int c) -> V {
                 const int col = col0 + c;
                 if (col >= W) return zero;
-                const V u = p < W ? src[p * Wp + col] : zero;
-                const V t = p + NP < W ? src[(p + NP) * Wp + col] : zero;
+                const V u = p < W ? ld(p * Wp + col) : zero;
+                const V t = p + NP < W ? ld((p + NP) * Wp + col) : zero;
                 return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), half_bin<V, -1, LOGNP, Cf::E>(tw, p));
             },
             [&](int pk, int c, V v) {
                 const int col = col0 + c;
                 const int pb = 2 * pk + sgn;
                 const int r = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
-                if (r >= 0 && col < W) dst[r * Wp + col] = v;
+                if (r >= 0 && col < W) st(r * Wp + col, v);
             });
     } else if constexpr (MODE == COL_INV) {
         // src: B (N' x N); dst: u2 (N x N)
         block_fft<V, +1, Cf::E, LOGNP, Cf::LOGC, false>(
-            S, tw, [&](int p, int c) { return src[p * n + col0 + c]; },
+            S, tw, [&](int p, int c) { return ld(p * n + col0 + c); },
             [&](int p, int c, V v) {
-                if (p < n) dst[p * n + col0 + c] = v;
+                if (p < n) st(p * n + col0 + c, v);
             });
     } else if constexpr (MODE == COL_FWD) {
         // src: u1 (N x N); dst: B (N' x N)
         block_fft<V, -1, Cf::E, LOGNP, Cf::LOGC, false>(
-            S, tw, [&](int p, int c) { return p < n ? src[p * n + col0 + c] : zero; },
-            [&](int p, int c, V v) { dst[p * n + col0 + c] = v; });
+            S, tw, [&](int p, int c) { return p < n ? ld(p * n + col0 + c) : zero; },
+            [&](int p, int c, V v) { st(p * n + col0 + c, v); });
     } else {
         // src: A (N' x Wp); dst: window (W x Wp)
         block_fft<V, +1, Cf::E, LOGNP, Cf::LOGC, false>(
@@ -478,7 +494,7 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP, MODE>::P, ColCfg<V, LOGNP, MO
             [&](int q, int c) -> V {
                 const int col = col0 + c;
                 if (col >= W) return zero;
-                const V y = src[q * Wp + col];
+                const V y = ld(q * Wp + col);
                 if (sgn == 0) return y;
                 const V f = half_bin<V, +1, LOGNP, Cf::E>(tw, q);
                 return cmul(y, q < HALF ? f : CTraits<V>::make(-f.x, -f.y));
@@ -486,7 +502,7 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP, MODE>::P, ColCfg<V, LOGNP, MO
             [&](int k, int c, V v) {
                 const int col = col0 + c;
                 const int u = 2 * k + sgn;
-                if (u < W && col < W) dst[u * Wp + col] = v;
+                if (u < W && col < W) st(u * Wp + col, v);
             });
     }
 }
@@ -593,6 +609,21 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
     const int tid = threadIdx.x;
     const int W = a.W, Wp = a.Wp, n = a.n;
     const float2 zero = make_float2(0.f, 0.f);
+    // extents for the checks of the debug library: the raw strip, the staging
+    // buffers and dst (elements)
+    [[maybe_unused]] constexpr int RAW_N = Cf::RAW_ROWS * C, O_N = Cf::OWN_STAGE ? NP * C : 0, S_N = spad_size<float2>(NP * Cf::SEQ);
+    [[maybe_unused]] const int dst_n = MODE == COL_FWD_FOLD ? NP * Wp : MODE == COL_INV ? n * n
+                                     : MODE == COL_FWD ? NP * n : W * Wp;
+    auto rd = [&](int i) -> float2 { return NUASM_IN_RANGE(i, RAW_N, dbg::kColRaw) ? raw[i] : zero; };
+    [[maybe_unused]] auto st = [&](int i, float2 v) {
+        if (NUASM_IN_RANGE(i, dst_n, dbg::kColStore)) dst[i] = v;
+    };
+    [[maybe_unused]] auto stage_o = [&](int i, float2 v) {
+        if (NUASM_IN_RANGE(i, O_N, dbg::kColStage)) O[i] = v;
+    };
+    [[maybe_unused]] auto stage_s = [&](int i, float2 v) {
+        if (NUASM_IN_RANGE(i, S_N, dbg::kColStage)) S[i] = v;
+    };
     pdl_allow_next();
     if (tid == 0) tma::mbar_init(bar, 1);
     pdl_wait();   // the strips come from the previous kernel
@@ -634,7 +665,7 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
             // half 0 transforms x(p) + x(p + N'), half 1 (x(p) - x(p + N')) w^p
             auto fold = [&](int p, int c, int sgn) -> float2 {
                 // rows p + N' < W lie within the first BOXR rows past N' (W - N' = 2h <= 16)
-                const float2 u = raw[p * C + c], t = p < BOXR ? raw[(p + NP) * C + c] : zero;
+                const float2 u = rd(p * C + c), t = p < BOXR ? rd((p + NP) * C + c) : zero;
                 const float sg = sgn ? -1.f : 1.f;
                 const float2 v = make_float2(fmaf(sg, t.x, u.x), fmaf(sg, t.y, u.y));
                 return sgn ? cmul(v, half_bin<float2, -1, LOGNP, EE>(tw, p)) : v;
@@ -644,10 +675,10 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
                 const int pb = 2 * pk + sgn;
                 const int r = pb < HALF ? pb : (pb >= 3 * HALF ? pb - NP : -1);
                 if constexpr (Cf::STORE) {
-                    if (r >= 0) O[(r >> 1) * CC + c] = v;   // plane sgn, row r >> 1
+                    if (r >= 0) stage_o((r >> 1) * CC + c, v);   // plane sgn, row r >> 1
                 } else {
                     const int col = col0 + c;
-                    if (r >= 0 && col < W) dst[r * Wp + col] = v;
+                    if (r >= 0 && col < W) st(r * Wp + col, v);
                 }
             };
             if constexpr (Cf::MERGED) {
@@ -671,7 +702,7 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
             // raw: rows [0, N') of A, C columns (zero beyond the window's columns);
             // half 1 is pre-twiddled for the odd outputs
             auto get = [&](int q, int c, int sgn) -> float2 {
-                const float2 y = raw[q * C + c];
+                const float2 y = rd(q * C + c);
                 if (sgn == 0) return y;
                 const float2 f = half_bin<float2, +1, LOGNP, EE>(tw, q);
                 return cmul(y, q < HALF ? f : make_float2(-f.x, -f.y));
@@ -679,11 +710,11 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
             // output row u = 2 k + sgn
             auto put = [&](int k, int c, int sgn, float2 v) {
                 if constexpr (Cf::STORE) {
-                    O[k * CC + c] = v;   // plane sgn, row k
+                    stage_o(k * CC + c, v);   // plane sgn, row k
                 } else {
                     const int col = col0 + c;
                     const int u = 2 * k + sgn;
-                    if (u < W && col < W) dst[u * Wp + col] = v;
+                    if (u < W && col < W) st(u * Wp + col, v);
                 }
             };
             if constexpr (Cf::MERGED) {
@@ -705,19 +736,19 @@ __global__ void __launch_bounds__(TmaColCfg<LOGNP, MODE>::P, TmaColCfg<LOGNP, MO
             }
         } else if constexpr (MODE == COL_INV) {
             block_fft<float2, +1, EE, LOGNP, LOGCC, false>(
-                S, tw, [&](int p, int c) { return raw[p * C + c]; },
+                S, tw, [&](int p, int c) { return rd(p * C + c); },
                 [&](int p, int c, float2 v) {
-                    if constexpr (Cf::STORE) S[p * CC + c] = v;
-                    else if (p < n && col0 + c < n) dst[p * n + col0 + c] = v;
+                    if constexpr (Cf::STORE) stage_s(p * CC + c, v);
+                    else if (p < n && col0 + c < n) st(p * n + col0 + c, v);
                 },
                 prefetch);
             if constexpr (Cf::STORE) flush(S, 0);
         } else {
             block_fft<float2, -1, EE, LOGNP, LOGCC, false>(
-                S, tw, [&](int p, int c) { return p < n ? raw[p * C + c] : zero; },
+                S, tw, [&](int p, int c) { return p < n ? rd(p * C + c) : zero; },
                 [&](int p, int c, float2 v) {
-                    if constexpr (Cf::STORE) S[p * CC + c] = v;
-                    else if (col0 + c < n) dst[p * n + col0 + c] = v;
+                    if constexpr (Cf::STORE) stage_s(p * CC + c, v);
+                    else if (col0 + c < n) st(p * n + col0 + c, v);
                 },
                 prefetch);
             if constexpr (Cf::STORE) flush(S, 0);

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "common.cuh"
+
 namespace nuasm {
 namespace tma {
 
@@ -47,8 +49,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int li
     return false;
 }
 
-// one 2-D box {x, y} of `map` into shared memory at dst (128-byte aligned)
+// one 2-D box {x, y} of `map` into shared memory at dst (128-byte aligned);
+// every map here has 8-byte elements, so x must be even (16-byte rule)
 __device__ __forceinline__ void load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    if (!NUASM_IN_RANGE(x & 1, 1, dbg::kTmaLoad)) return;   // the debug library skips an odd x
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
             smem_u32(dst)),
@@ -66,6 +70,8 @@ __device__ __forceinline__ void store_fence() { asm volatile("fence.proxy.async.
 // one 3-D box {x, y, z} of `map` from shared memory at src (128-byte aligned);
 // elements outside the tensor's extent are not written
 __device__ __forceinline__ void store_3d(const CUtensorMap* map, int x, int y, int z, const void* src) {
+    // the debug library skips an odd x or a negative coordinate
+    if (!NUASM_IN_RANGE(x & 1, 1, dbg::kTmaStore) || !NUASM_IN_RANGE(x | y | z, 1 << 30, dbg::kTmaStore)) return;
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
                  "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
                  : "memory");

@@ -16,7 +16,9 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libnuasm.so")
+# NUASM_LIBRARY selects another build of the same C ABI (the bounds-checking
+# debug library, libnuasm_debug.so); it must exist like the default one.
+LIB_PATH = os.environ.get("NUASM_LIBRARY") or os.path.join(_PKG, "libnuasm.so")
 
 KIND_ASM, KIND_FRESNEL = 0, 1
 PREC_F32_F64PHASE, PREC_F64 = 0, 1
@@ -117,6 +119,9 @@ _SIGS = {
     "nuasm_debug_plan_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "nuasm_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int64]),
     "nuasm_debug_live_resources": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
+    "nuasm_debug_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.c_int32]),
     "nuasm_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(BatchItem),
                                           ctypes.c_int32, ctypes.c_int32]),
     "nuasm_batch_execute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -441,6 +446,18 @@ def nuasm_debug_live_resources() -> int:
     n = ctypes.c_int64()
     _check(lib().nuasm_debug_live_resources(ctypes.byref(n)), "nuasm_debug_live_resources")
     return int(n.value)
+
+
+def nuasm_debug_bounds(reset: bool = True):
+    """(skipped out-of-range accesses, first site, its index, its extent) of
+    the bounds-checking debug library; None from the normal library."""
+    hits, site, index, limit = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    code = lib().nuasm_debug_bounds(ctypes.byref(hits), ctypes.byref(site), ctypes.byref(index), ctypes.byref(limit),
+                                    int(bool(reset)))
+    if code == 6:   # NUASM_EUNSUPPORTED: built without the checks
+        return None
+    _check(code, "nuasm_debug_bounds")
+    return int(hits.value), int(site.value), int(index.value), int(limit.value)
 
 
 # ---------------------------------------------------------------- batches

@@ -220,6 +220,30 @@ def test_allocation_failure_hook_is_host_only_and_arms_and_disarms(P):
     assert lib.nuasm_debug_live_resources(ctypes.byref(n)) == 0 and n.value == before
 
 
+def test_normal_library_has_no_bounds_checks(P):
+    """The bounds records exist only in the debug library; the normal one
+    answers NUASM_EUNSUPPORTED without touching the device."""
+    lib = P.lib()
+    hits = ctypes.c_int64(7)
+    assert lib.nuasm_debug_bounds(None, None, None, None, 0) == 1
+    assert lib.nuasm_debug_bounds(ctypes.byref(hits), None, None, None, 0) == 6 and hits.value == -1
+    assert P.nuasm_debug_bounds() is None
+
+
+def test_debug_library_is_selected_by_environment(tmp_path):
+    """NUASM_LIBRARY names the library the binding loads, and a missing one is
+    an error at load time (no fallback)."""
+    import subprocess
+    import sys
+    code = ("import paper_1308_6644_gb300 as P\n"
+            "print(P.LIB_PATH)\n"
+            "try:\n    P.lib()\nexcept RuntimeError as e:\n    print('missing')\n")
+    env = dict(os.environ, NUASM_LIBRARY=str(tmp_path / "libnuasm_debug.so"))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.split() == [str(tmp_path / "libnuasm_debug.so"), "missing"]
+
+
 _CTYPE_OF = {"int32_t": "c_int32", "int64_t": "c_int64", "uint64_t": "c_uint64", "double": "c_double",
              "float": "c_float"}
 
