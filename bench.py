@@ -162,7 +162,7 @@ def stage_bytes(info: dict, m: int, type_: int = 2, eb: int = 8) -> dict:
     if type_ == 1:
         return {
             "spread": pt * m + eb * W * W,
-            "col_fwd_fold": eb * (2 * W * W + np_ * W),
+            "col_fwd_fold": eb * (W * W + np_ * W),
             "row_t1": eb * (np_ * W + np_ * n),
             "col_inv": eb * (np_ * n + n * n),
         }
@@ -240,10 +240,10 @@ def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
             "col_inv": f"col_tma_kernel<{lognp}, 1>" if tma_wide else f"col_kernel<{v}, {lognp}, 1>"}[stage]
 
 
-STAGE_SOURCES = {"col_fwd": ["passes.cuh", "fft_engine.cuh"], "row_t2": ["passes.cuh", "fft_engine.cuh"],
-                 "col_inv_fold": ["passes.cuh", "fft_engine.cuh", "tma.cuh"], "interp": ["gridding.cu"],
-                 "spread": ["gridding.cu"], "col_fwd_fold": ["passes.cuh", "fft_engine.cuh", "tma.cuh"],
-                 "row_t1": ["passes.cuh", "fft_engine.cuh"], "col_inv": ["passes.cuh", "fft_engine.cuh"]}
+_FFT_SOURCES = ["passes.cuh", "fft_engine.cuh", "tma.cuh"]
+STAGE_SOURCES = {"col_fwd": _FFT_SOURCES, "row_t2": _FFT_SOURCES, "col_inv_fold": _FFT_SOURCES,
+                 "col_fwd_fold": _FFT_SOURCES, "row_t1": _FFT_SOURCES, "col_inv": _FFT_SOURCES,
+                 "interp": ["gridding.cu"], "spread": ["gridding.cu"]}
 
 
 def source_hash(stage: str) -> str:

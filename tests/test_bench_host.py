@@ -25,6 +25,11 @@ def test_stage_bytes_of_the_benchmark_geometry():
         b1 = bench.stage_bytes(dict(C2, phase_table_bytes=tables, points=m), m, 1, 8)
         assert b1["spread"] == 20 * m + 8 * W * W
         assert b1["row_t1"] == 8 * (np_ * W + np_ * n)
+        assert b1["col_fwd_fold"] == 8 * (W * W + np_ * W)   # the window read once for both halves
+        # summed over a solve: the survey's grid traffic 8(2P^2 + 2N'P + 2N'N + N^2) plus 20 B per point
+        grid = 8 * (2 * W * W + 2 * np_ * W + 2 * np_ * n + n * n)
+        assert sum(b1.values()) == grid + 20 * m
+        assert sum(b.values()) == grid + 20 * m
     assert b["row_t2"] == 50_462_720
 
 
