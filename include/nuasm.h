@@ -173,7 +173,8 @@ nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m,
 /*
  * nuasm_plan_lattice -- a plan whose points form a uniform nx x ny lattice,
  *     x = x0 + i * pitch2,  y = y0 + j * pitch2,  point index j * nx + i,
- * generated on the device (no coordinate arrays).  With it, type 2 evaluates
+ * binned on the device without a sort and without coordinate arrays (a
+ * tile's points are a product of one index range per axis).  With it, type 2 evaluates
  * the destination plane at pitch2 and type 1 propagates a source plane
  * sampled at pitch2 onto the uniform plane at p->pitch: the scaled ASM /
  * scaled Fresnel the paper's introduction discusses (different but uniform

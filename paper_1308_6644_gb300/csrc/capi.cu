@@ -307,15 +307,6 @@ nuasm_status exec_type2(nuasm_plan_s* P, const void* u1, void* v, cudaStream_t s
     return NUASM_OK;
 }
 
-__global__ void lattice_kernel(double* __restrict__ x, double* __restrict__ y, int nx, int64_t m, double pitch2,
-                               double x0, double y0) {
-    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < m; t += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t j = t / nx, i = t - j * nx;
-        x[t] = x0 + double(i) * pitch2;
-        y[t] = y0 + double(j) * pitch2;
-    }
-}
-
 nuasm_status exec_type3(nuasm_plan_s* P, nuasm_plan_s* Q, const void* c, void* v, cudaStream_t st) {
     nuasm_status s0 = check_plan_usable(P);
     if (s0 != NUASM_OK) return s0;
@@ -352,13 +343,14 @@ nuasm_status nuasm_plan(nuasm_plan_t* out, const nuasm_params_t* p, int64_t m, c
 }  // extern "C"
 
 nuasm_status nuasm::plan_create(nuasm_plan_s** out, const nuasm_params_t* p, int64_t m, const double* x,
-                                const double* y, const double* w, cudaStream_t st, bool workspace) {
+                                const double* y, const double* w, cudaStream_t st, bool workspace,
+                                const LatticeSpec* lat) {
     *out = nullptr;
     if (!p) return NUASM_EINVAL;
     nuasm_params_t rp;
     nuasm_status s = validate(*p, m, &rp);
     if (s != NUASM_OK) return s;
-    if (m > 0 && (!x || !y)) return NUASM_EINVAL;
+    if (m > 0 && !lat && (!x || !y)) return NUASM_EINVAL;
 
     nuasm_plan_s* P = new (std::nothrow) nuasm_plan_s();
     if (!P) return NUASM_ENOMEM;
@@ -421,6 +413,13 @@ nuasm_status nuasm::plan_create(nuasm_plan_s** out, const nuasm_params_t* p, int
         P->device_bytes += int64_t(sizeof(int));
     }
 
+    if (lat) {
+        s = run_binning_lattice(P, *lat, st);
+        cudaStreamSynchronize(st);
+        if (s != NUASM_OK) return bail(s);
+        *out = P;
+        return NUASM_OK;
+    }
     double *dx = nullptr, *dy = nullptr, *dw = nullptr;
     bool ox = false, oy = false, ow = false;
     auto free_coords = [&]() {
@@ -458,17 +457,8 @@ nuasm_status nuasm_plan_lattice(nuasm_plan_t* out, const nuasm_params_t* p, int3
     const nuasm_status s = validate(*p, m, &rp);
     if (s != NUASM_OK) return s;
     if (m == 0) return nuasm_plan(out, p, 0, nullptr, nullptr, nullptr, stream);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    double* xy = nullptr;
-    cudaError_t e = xmalloc(reinterpret_cast<void**>(&xy), sizeof(double) * 2 * size_t(m));
-    if (e != cudaSuccess) return cuda_status(e);
-    const int blocks = int(std::min<int64_t>((m + 255) / 256, 152 * 8));
-    lattice_kernel<<<blocks, 256, 0, st>>>(xy, xy + m, nx, m, pitch2, x0, y0);
-    e = cudaGetLastError();
-    nuasm_status r = e == cudaSuccess ? nuasm_plan(out, p, m, xy, xy + m, nullptr, stream) : cuda_status(e);
-    cudaStreamSynchronize(st);
-    xfree(xy);
-    return r;
+    const LatticeSpec lat{nx, ny, pitch2, x0, y0};
+    return plan_create(out, p, m, nullptr, nullptr, nullptr, static_cast<cudaStream_t>(stream), true, &lat);
 }
 
 nuasm_status nuasm1_execute(nuasm_plan_t plan, const void* c, void* u2, void* stream) {

@@ -1006,6 +1006,136 @@ cudaError_t make_tile_order(nuasm_plan_s* P, cudaStream_t st) {
     return cudaSuccess;
 }
 
+// --------------------------------------------------------------- lattice plans
+// A lattice x0 + i p2, y0 + j p2 (point j nx + i) bins without a sort: a
+// point's first-tap cell and fraction depend on its column i (x) and row j
+// (y) alone and do not decrease along them, so the points a tile holds, halo
+// duplicates included, are a product of one contiguous index range per axis:
+// for tile k of an axis, [a, b) the indices whose first tap lies in it (home)
+// and [c, a) the preceding ones whose taps reach into it.  Records are
+// written in tile order, home records first, then ordered by bank class like
+// any other plan's.
+__global__ void lattice_axis_kernel(int n, double v0, double p2, BinArgs a, int* __restrict__ l0,
+                                    double* __restrict__ frac, int* __restrict__ err) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = v0 + double(i) * p2;
+        const PointSplit s = split_point(v, v, a);   // the x part of a point at (v, v)
+        if (!s.ok) atomicOr(err, 1);
+        l0[i] = s.l0x;
+        frac[i] = s.fx;
+    }
+}
+
+// one CTA per tile; rx / ry: (c, a, b) of each tile index per axis
+template <typename Rec, typename S>
+__global__ void lattice_records_kernel(const int* __restrict__ l0x, const double* __restrict__ fx,
+                                       const int* __restrict__ l0y, const double* __restrict__ fy,
+                                       const int4* __restrict__ rx, const int4* __restrict__ ry,
+                                       const int* __restrict__ off, int ntx, int nx, long long cap,
+                                       Rec* __restrict__ rec) {
+    const int t = blockIdx.x, ky = t / ntx, kx = t - ky * ntx;
+    const int4 X = rx[kx], Y = ry[ky];
+    const int hw = X.z - X.y, ew = X.y - X.x, aw = X.z - X.x;   // home, extension and all widths in x
+    const int home = hw * (Y.z - Y.y), all = aw * (Y.z - Y.x);
+    const int d1 = ew * (Y.z - Y.x);   // duplicates with i in [c, a), any row of the tile
+    const int b0 = off[t];
+    for (int r = threadIdx.x; r < all; r += blockDim.x) {
+        int i, j;
+        if (r < home) {
+            i = X.y + r % hw;
+            j = Y.y + r / hw;
+        } else if (r - home < d1) {
+            const int q = r - home;
+            i = X.x + q % ew;
+            j = Y.x + q / ew;
+        } else {   // i in [a, b), rows [c, a) of y
+            const int q = r - home - d1;
+            i = X.y + q % hw;
+            j = Y.x + q / hw;
+        }
+        Rec o;
+        o.cell = (uint32_t(l0y[j]) << 16) | uint32_t(l0x[i]);
+        o.fx = S(fx[i]);
+        o.fy = S(fy[j]);
+        o.j = int32_t(j * nx + i);
+        if (NUASM_IN_RANGE(b0 + r, cap, dbg::kBinRec)) rec[b0 + r] = o;
+    }
+}
+
+// Per-plan bank skew (or per-tile skews) and the round-robin record order of
+// every tile (order_tile_kernel), for records already placed in P->d.rec
+// in tile order with the offsets and home counts set.
+cudaError_t order_records(nuasm_plan_s* P, cudaStream_t st) {
+    const Geometry& g = P->g;
+    const int nt = g.ntiles;
+    const int total = int(P->nrec);
+    const size_t rsz = P->f64 ? sizeof(RecD) : sizeof(RecF);
+    cudaError_t e;
+    if (NUASM_TILE_SKEW) {
+        // per-tile bank skew: the candidate that balances the tile's record classes best
+        unsigned long long* hist = nullptr;
+        unsigned long long hh[kNumSkews] = {};
+        if ((e = xmalloc(reinterpret_cast<void**>(&P->d.tile_skew), size_t(nt))) != cudaSuccess) return e;
+        P->device_bytes += nt;
+        if ((e = xmalloc_async(reinterpret_cast<void**>(&hist), sizeof(hh), st)) != cudaSuccess) return e;
+        e = cudaMemsetAsync(hist, 0, sizeof(hh), st);
+        if (e == cudaSuccess) {
+            if (P->f64)
+                tile_skew_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(P->d.rec), P->d.tile_off,
+                                                           P->d.tile_home, g.T, g.ntx, P->d.tile_skew, hist);
+            else
+                tile_skew_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(P->d.rec), P->d.tile_off,
+                                                           P->d.tile_home, g.T, g.ntx, P->d.tile_skew, hist);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        xfree_async(hist, st);
+        if (e != cudaSuccess) return e;
+        int most = 0;
+        for (int k = 1; k < kNumSkews; ++k)
+            if (hh[k] > hh[most]) most = k;
+        P->skew = skew_candidate(most);
+    } else {
+        // one bank skew for every tile: 2 where it balances the record classes at least 5% better
+        unsigned long long* sums = nullptr;
+        unsigned long long hs[2] = {0, 0};
+        if ((e = xmalloc_async(reinterpret_cast<void**>(&sums), sizeof(hs), st)) != cudaSuccess) return e;
+        e = cudaMemsetAsync(sums, 0, sizeof(hs), st);
+        if (e == cudaSuccess) {
+            if (P->f64)
+                class_balance_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(P->d.rec),
+                                                               P->d.tile_off, P->d.tile_home, g.T, g.ntx, sums);
+            else
+                class_balance_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(P->d.rec),
+                                                               P->d.tile_off, P->d.tile_home, g.T, g.ntx, sums);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        xfree_async(sums, st);
+        if (e != cudaSuccess) return e;
+        P->skew = double(hs[1]) < 0.95 * double(hs[0]) ? 2 : 0;
+    }
+    void* tmp = nullptr;
+    if ((e = xmalloc_async(&tmp, rsz * size_t(total), st)) != cudaSuccess) return e;
+    e = cudaMemcpyAsync(tmp, P->d.rec, rsz * size_t(total), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+        if (P->f64)
+            order_tile_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(tmp), static_cast<RecD*>(P->d.rec),
+                                                        P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew,
+                                                P->d.tile_skew);
+        else
+            order_tile_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(tmp), static_cast<RecF*>(P->d.rec),
+                                                        P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew,
+                                                P->d.tile_skew);
+        e = cudaGetLastError();
+    }
+    xfree_async(tmp, st);
+    if (e != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
 nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, const double* w, cudaStream_t st) {
     const Geometry& g = P->g;
     BinArgs a{g.n, g.W, g.T, g.ntx, g.w, g.h, P->p.pitch, P->m};
@@ -1065,71 +1195,106 @@ nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, cons
                                                                     cur_dup, static_cast<RecF*>(P->d.rec));
         if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     }
-    if (P->m > 0 && total > 0) {
-        if (NUASM_TILE_SKEW) {
-            // per-tile bank skew: the candidate that balances the tile's record classes best
-            unsigned long long* hist = nullptr;
-            unsigned long long hh[kNumSkews] = {};
-            if ((e = xmalloc(reinterpret_cast<void**>(&P->d.tile_skew), size_t(nt))) != cudaSuccess) return fail(e);
-            P->device_bytes += nt;
-            if ((e = xmalloc_async(reinterpret_cast<void**>(&hist), sizeof(hh), st)) != cudaSuccess) return fail(e);
-            e = cudaMemsetAsync(hist, 0, sizeof(hh), st);
-            if (e == cudaSuccess) {
-                if (P->f64)
-                    tile_skew_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(P->d.rec), P->d.tile_off,
-                                                               P->d.tile_home, g.T, g.ntx, P->d.tile_skew, hist);
-                else
-                    tile_skew_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(P->d.rec), P->d.tile_off,
-                                                               P->d.tile_home, g.T, g.ntx, P->d.tile_skew, hist);
-                e = cudaGetLastError();
-            }
-            if (e == cudaSuccess) e = cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            xfree_async(hist, st);
-            if (e != cudaSuccess) return fail(e);
-            int most = 0;
-            for (int k = 1; k < kNumSkews; ++k)
-                if (hh[k] > hh[most]) most = k;
-            P->skew = skew_candidate(most);
-        } else {
-            // one bank skew for every tile: 2 where it balances the record classes at least 5% better
-            unsigned long long* sums = nullptr;
-            unsigned long long hs[2] = {0, 0};
-            if ((e = xmalloc_async(reinterpret_cast<void**>(&sums), sizeof(hs), st)) != cudaSuccess) return fail(e);
-            e = cudaMemsetAsync(sums, 0, sizeof(hs), st);
-            if (e == cudaSuccess) {
-                if (P->f64)
-                    class_balance_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(P->d.rec),
-                                                                   P->d.tile_off, P->d.tile_home, g.T, g.ntx, sums);
-                else
-                    class_balance_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(P->d.rec),
-                                                                   P->d.tile_off, P->d.tile_home, g.T, g.ntx, sums);
-                e = cudaGetLastError();
-            }
-            if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            xfree_async(sums, st);
-            if (e != cudaSuccess) return fail(e);
-            P->skew = double(hs[1]) < 0.95 * double(hs[0]) ? 2 : 0;
-        }
-        void* tmp = nullptr;
-        if ((e = xmalloc_async(&tmp, rsz * size_t(total), st)) != cudaSuccess) return fail(e);
-        e = cudaMemcpyAsync(tmp, P->d.rec, rsz * size_t(total), cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess) {
-            if (P->f64)
-                order_tile_kernel<RecD><<<nt, 256, 0, st>>>(static_cast<const RecD*>(tmp), static_cast<RecD*>(P->d.rec),
-                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew,
-                                                    P->d.tile_skew);
-            else
-                order_tile_kernel<RecF><<<nt, 256, 0, st>>>(static_cast<const RecF*>(tmp), static_cast<RecF*>(P->d.rec),
-                                                            P->d.tile_off, P->d.tile_home, g.T, g.ntx, P->skew,
-                                                    P->d.tile_skew);
-            e = cudaGetLastError();
-        }
-        xfree_async(tmp, st);
-        if (e != cudaSuccess) return fail(e);
-    }
+    if (P->m > 0 && total > 0 && (e = order_records(P, st)) != cudaSuccess) return fail(e);
     xfree_async(cnt, st);
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+nuasm_status run_binning_lattice(nuasm_plan_s* P, const LatticeSpec& lat, cudaStream_t st) {
+    const Geometry& g = P->g;
+    const BinArgs a{g.n, g.W, g.T, g.ntx, g.w, g.h, P->p.pitch, P->m};
+    const int nt = g.ntiles, ntx = g.ntx, nx = lat.nx, ny = lat.ny;
+    // scratch: l0x, l0y (int), fx, fy (double), rx, ry (int4)
+    const size_t bi = sizeof(int) * (size_t(nx) + ny), bd = sizeof(double) * (size_t(nx) + ny),
+                 br = sizeof(int4) * 2 * size_t(ntx);
+    char* scratch = nullptr;
+    cudaError_t e = xmalloc_async(reinterpret_cast<void**>(&scratch), bd + br + bi, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    double* dfx = reinterpret_cast<double*>(scratch);
+    double* dfy = dfx + nx;
+    int4* drx = reinterpret_cast<int4*>(scratch + bd);
+    int4* dry = drx + ntx;
+    int* dl0x = reinterpret_cast<int*>(scratch + bd + br);
+    int* dl0y = dl0x + nx;
+    auto fail = [&](cudaError_t err) {
+        cudaStreamSynchronize(st);   // host vectors below may still be read by copies
+        xfree_async(scratch, st);
+        cudaStreamSynchronize(st);
+        return cuda_status(err);
+    };
+    if (P->d.h_err) *P->d.h_err = 0;   // host-mapped: no device work has touched it yet
+    else if ((e = cudaMemsetAsync(P->d.err, 0, sizeof(int), st)) != cudaSuccess) return fail(e);
+    lattice_axis_kernel<<<std::max(1, std::min((nx + 255) / 256, 152 * 4)), 256, 0, st>>>(nx, lat.x0, lat.pitch2, a,
+                                                                                         dl0x, dfx, P->d.err);
+    lattice_axis_kernel<<<std::max(1, std::min((ny + 255) / 256, 152 * 4)), 256, 0, st>>>(ny, lat.y0, lat.pitch2, a,
+                                                                                         dl0y, dfy, P->d.err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    std::vector<int> l0x(nx), l0y(ny);
+    int errw = 0;
+    if ((e = cudaMemcpyAsync(l0x.data(), dl0x, sizeof(int) * size_t(nx), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(l0y.data(), dl0y, sizeof(int) * size_t(ny), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return fail(e);
+    if (!P->d.h_err &&
+        (e = cudaMemcpyAsync(&errw, P->d.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    if (P->d.h_err) errw = *static_cast<volatile int*>(P->d.h_err);
+    if (errw) {
+        fail(cudaSuccess);
+        return NUASM_ERANGE;
+    }
+    // per axis and tile index k: c = first index whose taps reach tile k (l0 >= kT - (w - 1)),
+    // a = first home index (l0 >= kT), b = first index of the next tile (l0 >= (k + 1)T)
+    auto ranges = [&](const std::vector<int>& l0) {
+        std::vector<int4> r(ntx);
+        for (int k = 0; k < ntx; ++k) {
+            auto first = [&](long long v) {
+                return int(std::lower_bound(l0.begin(), l0.end(), v) - l0.begin());
+            };
+            const int ak = first(int64_t(k) * g.T), bk = first(int64_t(k + 1) * g.T);
+            const int ck = k == 0 ? ak : first(int64_t(k) * g.T - (g.w - 1));
+            r[k] = make_int4(ck, ak, bk, 0);
+        }
+        return r;
+    };
+    const std::vector<int4> rx = ranges(l0x), ry = ranges(l0y);
+    std::vector<int> off(size_t(nt) + 1), home(nt);
+    int64_t total = 0;
+    for (int ky = 0; ky < ntx; ++ky)
+        for (int kx = 0; kx < ntx; ++kx) {
+            const int t = ky * ntx + kx;
+            off[t] = int(total);
+            home[t] = (rx[kx].z - rx[kx].y) * (ry[ky].z - ry[ky].y);
+            total += int64_t(rx[kx].z - rx[kx].x) * (ry[ky].z - ry[ky].x);
+            if (total > INT32_MAX) {
+                fail(cudaSuccess);
+                return NUASM_EUNSUPPORTED;
+            }
+        }
+    off[nt] = int(total);
+    if ((e = cudaMemcpyAsync(drx, rx.data(), sizeof(int4) * size_t(ntx), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dry, ry.data(), sizeof(int4) * size_t(ntx), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P->d.tile_off, off.data(), sizeof(int) * (size_t(nt) + 1), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P->d.tile_home, home.data(), sizeof(int) * size_t(nt), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+        return fail(e);
+    P->nrec = total;
+    if ((e = make_tile_order(P, st)) != cudaSuccess) return fail(e);
+    const size_t rsz = P->f64 ? sizeof(RecD) : sizeof(RecF);
+    if ((e = xmalloc(&P->d.rec, rsz * size_t(total > 0 ? total : 1))) != cudaSuccess) return fail(e);
+    P->device_bytes += int64_t(rsz) * (total > 0 ? total : 1);
+    if (total > 0) {
+        if (P->f64)
+            lattice_records_kernel<RecD, double><<<nt, 256, 0, st>>>(dl0x, dfx, dl0y, dfy, drx, dry, P->d.tile_off,
+                                                                    ntx, nx, total, static_cast<RecD*>(P->d.rec));
+        else
+            lattice_records_kernel<RecF, float><<<nt, 256, 0, st>>>(dl0x, dfx, dl0y, dfy, drx, dry, P->d.tile_off,
+                                                                   ntx, nx, total, static_cast<RecF*>(P->d.rec));
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+        if ((e = order_records(P, st)) != cudaSuccess) return fail(e);
+    }
+    xfree_async(scratch, st);
     return cuda_status(cudaStreamSynchronize(st));
 }
 

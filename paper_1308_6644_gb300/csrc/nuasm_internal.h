@@ -175,8 +175,16 @@ int choose_nonsep_mode(const nuasm_params_t& p, double rmax);
 // plan life cycle and device-pointer execute chains (capi.cu).  A plan made
 // without workspace holds tables, twiddles and bins only; it is executed
 // through a view that supplies the workspace (batch.cu, serve.cu).
+// The points of a lattice plan: x0 + i pitch2, y0 + j pitch2, point j nx + i.
+struct LatticeSpec {
+    int nx, ny;
+    double pitch2, x0, y0;
+};
+// x, y, w: the points' coordinates and weights; or, with `lat`, no coordinates
+// (x, y, w null) and the lattice binned without a sort (run_binning_lattice)
 nuasm_status plan_create(nuasm_plan_s** out, const nuasm_params_t* p, int64_t m, const double* x,
-                         const double* y, const double* w, cudaStream_t st, bool workspace);
+                         const double* y, const double* w, cudaStream_t st, bool workspace,
+                         const LatticeSpec* lat = nullptr);
 void plan_release(nuasm_plan_s* P);
 bool same_problem(const nuasm_params_t& a, const nuasm_params_t& b);
 bool device_accessible(const void* p);
@@ -214,6 +222,7 @@ cudaError_t xpool_destroy(cudaMemPool_t pool);
 // time, bit 2 = a bounded device wait gave up)
 nuasm_status run_binning(nuasm_plan_s* P, const double* x, const double* y, const double* w,
                          cudaStream_t s);
+nuasm_status run_binning_lattice(nuasm_plan_s* P, const LatticeSpec& lat, cudaStream_t s);
 cudaError_t bin_points_into(const nuasm_plan_s* P, const double* x, const double* y, int* cnt, void* rec_tmp,
                             cudaStream_t s);
 size_t record_bytes(bool f64);

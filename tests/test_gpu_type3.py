@@ -173,6 +173,48 @@ def test_scaled_type1_source_lattice(P):
     assert O.rel_l2(got, ref) < TOL["f64"]
 
 
+@pytest.mark.parametrize("prec,tile,nx,ny,p2", [("f32", 0, 300, 260, 8e-6), ("f64", 16, 70, 90, 7e-6),
+                                                 ("f32", 32, 1000, 1000, 2.5e-6)])
+def test_lattice_plan_bins_like_the_sorted_path(P, prec, tile, nx, ny, p2):
+    """The lattice plan's no-sort binning gives the records the counting sort
+    of the same points gives: equal record counts, type 2 equal (each output
+    depends on its own record only; bit for bit in FP32, to the last bits of
+    the fractions in FP64, whose lattice coordinates x0 + i p2 are formed on
+    the device with one rounding) and type 1 to rounding (the shared-memory
+    sums run in another order)."""
+    import torch
+    n, pitch = 256, 10e-6
+    x0, y0 = -0.5 * nx * p2 + 0.3e-6, -0.5 * ny * p2 - 1.1e-6
+    params = P.make_params(n, pitch, 633e-9, 0.05, prec=prec, tile=tile)
+    gx = x0 + np.arange(nx) * p2
+    gy = y0 + np.arange(ny) * p2
+    yy, xx = np.meshgrid(gy, gx, indexing="ij")
+    lat = P.nuasm_plan_lattice(params, nx, ny, p2, x0, y0)
+    pts = P.nuasm_plan(params, _dev(xx.ravel()), _dev(yy.ravel()))
+    try:
+        assert P.nuasm_plan_info(lat)["records"] == P.nuasm_plan_info(pts)["records"]
+        rng = np.random.default_rng(44)
+        ct = CDT[prec]
+        tdt = torch.complex64 if prec == "f32" else torch.complex128
+        u1 = _dev((rng.normal(size=n * n) + 1j * rng.normal(size=n * n)).astype(ct))
+        va, vb = (torch.zeros(nx * ny, dtype=tdt, device="cuda") for _ in range(2))
+        P.nuasm2_execute(lat, u1, va)
+        P.nuasm2_execute(pts, u1, vb)
+        c = _dev((rng.normal(size=nx * ny) + 1j * rng.normal(size=nx * ny)).astype(ct))
+        ua, ub = (torch.zeros(n * n, dtype=tdt, device="cuda") for _ in range(2))
+        P.nuasm1_execute(lat, c, ua)
+        P.nuasm1_execute(pts, c, ub)
+        torch.cuda.synchronize()
+        if prec == "f32":
+            assert torch.equal(va, vb)
+        else:
+            assert O.rel_l2(va.cpu().numpy(), vb.cpu().numpy()) < 1e-13
+        assert O.rel_l2(ua.cpu().numpy(), ub.cpu().numpy()) < (1e-6 if prec == "f32" else 1e-13)
+    finally:
+        lat.destroy()
+        pts.destroy()
+
+
 def test_lattice_outside_window_is_rejected(P):
     with pytest.raises(P.NuasmError) as ei:
         P.nuasm_plan_lattice(P.make_params(32, 10e-6, 633e-9, 0.01), 40, 40, 10e-6, -200e-6, -200e-6)
