@@ -29,7 +29,10 @@
  *  - Array arguments of the execute calls may be device memory or host memory
  *    (pinned or pageable); host arrays are staged through plan-owned device
  *    buffers with cudaMemcpyAsync on the given stream.  Pageable host memory
- *    makes the call block the host until its copies are done.
+ *    makes the call block the host until its copies are done.  Device arrays
+ *    need only the alignment of their element type; 16-byte aligned ones let
+ *    the N' >= 4096 column passes read and write them with TMA bulk copies
+ *    (others take the same pass with per-thread loads and stores).
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Execute calls
  *    are asynchronous on it, never allocate device memory and never
  *    synchronise the device; asynchronous CUDA faults surface as NUASM_ECUDA
