@@ -360,6 +360,10 @@ SINGLE = {
     # key: (generator, precision, workload label)
     "nuasm2": (lambda W: W.nuasm2_graded(seed=1002, n=1024, pitch=8e-6), "f32", WORKLOAD),
     "c1": (lambda W: W.nuasm1_small(1001), "f64", "nuasm1_n64_m4864_dense_core_lambda633nm_z5cm"),
+    # the paper's own NU-ASM_1 experiment geometry (context for its CPU timing)
+    "paper1": (lambda W: W.paper_experiment(1006), "f32", "nuasm1_paper_n256_m65536_quadrant_pitch_lambda500nm_z8mm"),
+    "paper1f64": (lambda W: W.paper_experiment(1006), "f64",
+                  "nuasm1_paper_n256_m65536_quadrant_pitch_lambda500nm_z8mm"),
     "c3t1": (lambda W: W.fresnel_clustered(1003, type_=1), "f32", "nufre1_n2048_m4194304_clusters_lambda633nm_z1m"),
     "c3t2": (lambda W: W.fresnel_clustered(1003, type_=2), "f32", "nufre2_n2048_m4194304_clusters_lambda633nm_z1m"),
     "c3t1f64": (lambda W: W.fresnel_clustered(1003, type_=1), "f64",
@@ -431,8 +435,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     x = torch.from_numpy(wl.x).to(dev)
     y = torch.from_numpy(wl.y).to(dev)
+    wts = None if wl.weights is None else torch.from_numpy(np.asarray(wl.weights, np.float64)).to(dev)
     t_plan0 = time.perf_counter()
-    plan = P.nuasm_plan(params, x, y, stream=stream)
+    plan = P.nuasm_plan(params, x, y, wts, stream=stream)
     plan_s = time.perf_counter() - t_plan0
     info = plan.info()
     n_out = wl.n * wl.n if wl.type == 1 else wl.m
@@ -501,7 +506,7 @@ def run_ours(args):
     e2e_flush = e2e_needs_flush(ws_bytes)
     lanes = [(plan, stream, h_in, h_out)]
     for _ in range(E2E_LANES - 1):
-        lanes.append((P.nuasm_plan(params, x, y, stream=stream), torch.cuda.Stream(dev),
+        lanes.append((P.nuasm_plan(params, x, y, wts, stream=stream), torch.cuda.Stream(dev),
                       inp.cpu().pin_memory(), torch.empty(n_out, dtype=tdt).pin_memory()))
     for pl, st, hi, ho in lanes:
         execute(pl, hi, ho, stream=st)

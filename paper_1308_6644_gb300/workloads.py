@@ -164,6 +164,21 @@ def nuasm1_small(seed: int = 1001) -> Workload:
     return Workload("nuasm1_n64_m4864", "asm", 1, n, pitch, 633e-9, 0.05, x=x, y=y, values=c)
 
 
+def paper_experiment(seed: int = 1006) -> Workload:
+    """The paper's NU-ASM_1 experiment geometry: 256 x 256 source samples whose
+    pitch is 0.9/0.8/0.7/1.0 x 5 um in quadrants I-IV (weights: each sample's
+    area relative to 5 um x 5 um), uniform 256 x 256 destination at 5 um,
+    lambda 500 nm, z 8 mm, N' = 512.  Amplitude U[0, 1) and phase
+    U[-pi/2, pi/2) stand in for the paper's two test images."""
+    rng = np.random.default_rng(seed)
+    n, pitch = 256, 5e-6
+    x, y = quadrant_lattice(n, pitch)
+    scale = np.select([(x > 0) & (y > 0), (x < 0) & (y > 0), (x < 0) & (y < 0)], [0.9, 0.8, 0.7], 1.0)
+    c = rng.uniform(0.0, 1.0, n * n) * np.exp(1j * rng.uniform(-0.5 * np.pi, 0.5 * np.pi, n * n))
+    return Workload(f"nuasm1_paper_n{n}_m{n * n}", "asm", 1, n, pitch, 500e-9, 8e-3, x=x, y=y, values=c,
+                    weights=scale ** 2)
+
+
 def nuasm2_graded(seed: int = 1002, n: int = 1024, pitch: float = 8e-6) -> Workload:
     """NU-ASM_2, uniform n x n source at 8 um holding a binary-amplitude
     random-phase pattern; n^2 destination points whose pitch grades 4 -> 16 um
