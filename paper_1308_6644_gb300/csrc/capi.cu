@@ -135,7 +135,8 @@ void nuasm::plan_release(nuasm_plan_s* P) {
         delete X;
     }
     void* ptrs[] = {P->d.tables, P->d.etab, P->d.etab2, P->d.rec, P->d.wpt, P->d.tile_off, P->d.tile_home,
-                    P->d.tile_order, P->d.tile_skew, P->d.interp_items, P->d.win, P->d.bufA, P->d.bufB,
+                    P->d.tile_order, P->d.tile_skew, P->d.interp_items, P->d.spread_items, P->d.win,
+                    P->d.bufA, P->d.bufB,
                     P->d.stage_in, P->d.stage_out};
     for (void* q : ptrs) xfree(q);
     if (P->d.h_err) xfree_host(P->d.h_err);

@@ -361,10 +361,22 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
                                                      const int* __restrict__ order,
                                                      const typename VecOf<S>::type* __restrict__ c,
                                                      typename VecOf<S>::type* __restrict__ win, GridArgs a,
-                                                     const typename PolyOf<S>::type kp) {
+                                                     const typename PolyOf<S>::type kp,
+                                                     const int4* __restrict__ items) {
     using V = typename VecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
-    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
+    int tile, b, e, chunked = 0;
+    if (items) {   // a chunk of a tile's records (several CTAs add into the tile)
+        const int4 it = items[blockIdx.x];
+        tile = it.x;
+        b = it.y;
+        e = it.z;
+        chunked = it.w;
+    } else {       // a whole tile, heaviest tiles first
+        tile = order ? order[blockIdx.x] : blockIdx.x;
+        b = off[tile];
+        e = off[tile + 1];
+    }
     const int T = a.T, w = EXACT ? WMAX : a.w, TS = plane_stride(T, a.skew_of(tile)), TT = T * TS;
     S* sre = reinterpret_cast<S*>(smem_raw);
     S* sim = sre + TT;
@@ -373,7 +385,6 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
     const int x0 = tx * T, y0 = ty * T;
     for (int i = threadIdx.x; i < TT; i += blockDim.x) { sre[i] = S(0); sim[i] = S(0); }
     __syncthreads();
-    const int b = off[tile], e = off[tile + 1];
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
         if (!NUASM_IN_RANGE(i, a.nrec, dbg::kSpreadRec)) continue;
         const auto r = rec[i];
@@ -409,7 +420,13 @@ __global__ void __launch_bounds__(256, sizeof(S) == 4 ? NUASM_SPREAD_MINB : 1) s
             V v;
             v.x = sre[yy * TS + xx];
             v.y = sim[yy * TS + xx];
-            win[size_t(gy) * a.Wp + gx] = v;
+            V* p = &win[size_t(gy) * a.Wp + gx];
+            if (chunked) {   // the window was cleared; the tile's chunks add into it
+                atomicAdd(&p->x, v.x);
+                atomicAdd(&p->y, v.y);
+            } else {
+                *p = v;
+            }
         }
     }
 }
@@ -621,12 +638,24 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
                                                              const int* __restrict__ order,
                                                              const typename VecOf<S>::type* __restrict__ c,
                                                              typename VecOf<S>::type* __restrict__ win, GridArgs a,
-                                                             const typename PolyOf<S>::type kp) {
+                                                             const typename PolyOf<S>::type kp,
+                                                             const int4* __restrict__ items) {
     using V = typename VecOf<S>::type;
     using Rec = typename RecOf<S>::type;
     extern __shared__ unsigned char smem_raw[];
     V* copies = reinterpret_cast<V*>(smem_raw);
-    const int tile = order ? order[blockIdx.x] : blockIdx.x;   // heaviest tiles first
+    int tile, b, e, chunked = 0;
+    if (items) {   // a chunk of a tile's records (several CTAs add into the tile)
+        const int4 it = items[blockIdx.x];
+        tile = it.x;
+        b = it.y;
+        e = it.z;
+        chunked = it.w;
+    } else {       // a whole tile, heaviest tiles first
+        tile = order ? order[blockIdx.x] : blockIdx.x;
+        b = off[tile];
+        e = off[tile + 1];
+    }
     const int T = a.T, w = EXACT ? WMAX : a.w, TS = plane_stride(T, a.skew_of(tile)), TT = T * TS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     V* mine = copies + warp * TT;
@@ -636,7 +665,6 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
     const V zero = CTraits<V>::zero();
     for (int i = threadIdx.x; i < 8 * TT; i += blockDim.x) copies[i] = zero;
     __syncthreads();
-    const int b = off[tile], e = off[tile + 1];
     for (int i0 = b + warp * 32; i0 < e; i0 += 256) {
         const int i = i0 + lane;
         const bool live = i < e && NUASM_IN_RANGE(i, a.nrec, dbg::kSpreadRec) &&
@@ -697,7 +725,13 @@ __global__ void __launch_bounds__(256, 2) spread_private_kernel(const typename R
                 v.x += u.x;
                 v.y += u.y;
             }
-            win[size_t(gy) * a.Wp + gx] = v;
+            V* p = &win[size_t(gy) * a.Wp + gx];
+            if (chunked) {   // the window was cleared; the tile's chunks add into it
+                atomicAdd(&p->x, v.x);
+                atomicAdd(&p->y, v.y);
+            } else {
+                *p = v;
+            }
         }
     }
 }
@@ -838,6 +872,13 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
     }
 }
 
+// whether the plan's spreading runs spread_private_kernel or spread_kernel,
+// which take work items (spread_fixed_kernel keeps one CTA per tile)
+bool spread_by_items(const nuasm_plan_s* P) {
+    if (NUASM_SPREAD_PRIVATE && P->g.T <= (P->f64 ? 16 : 32)) return true;
+    return P->f64 || !NUASM_SPREAD_FIXED;
+}
+
 GridArgs grid_args(const nuasm_plan_s* P) {
     GridArgs a;
     a.W = P->g.W;
@@ -867,13 +908,23 @@ template <typename S, int WMAX, bool EXACT>
 cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     using V = typename VecOf<S>::type;
     GridArgs a = grid_args(P);
+    // chunked tiles add into a cleared window
+    const int4* items = P->d.spread_items;
+    const int grid = items ? P->n_spread_items : P->g.ntiles;
+    auto clear = [&]() -> cudaError_t {
+        return items ? cudaMemsetAsync(P->d.win, 0, ws_win_elems(P->g) * sizeof(V), st) : cudaSuccess;
+    };
+    {
+        cudaError_t e = clear();
+        if (e != cudaSuccess) return e;
+    }
     if (NUASM_SPREAD_PRIVATE && a.T <= (sizeof(S) == 4 ? 32 : 16)) {
         const size_t sm = size_t(8) * a.T * plane_stride(a.T, a.max_skew) * sizeof(V);
         cudaError_t e = set_smem(spread_private_kernel<S, WMAX, EXACT>, sm);
         if (e != cudaSuccess) return e;
-        spread_private_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
+        spread_private_kernel<S, WMAX, EXACT><<<grid, 256, sm, st>>>(
             static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.wpt, P->d.tile_order,
-            static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg<S>(P));
+            static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg<S>(P), items);
         return cudaGetLastError();
     }
     if constexpr (sizeof(S) == 4) {
@@ -891,9 +942,9 @@ cudaError_t spread_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     const size_t sm = size_t(2) * a.T * plane_stride(a.T, a.max_skew) * sizeof(S);
     cudaError_t e = set_smem(spread_kernel<S, WMAX, EXACT>, sm);
     if (e != cudaSuccess) return e;
-    spread_kernel<S, WMAX, EXACT><<<P->g.ntiles, 256, sm, st>>>(
+    spread_kernel<S, WMAX, EXACT><<<grid, 256, sm, st>>>(
         static_cast<const typename RecOf<S>::type*>(P->d.rec), P->d.tile_off, P->d.wpt, P->d.tile_order,
-        static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg<S>(P));
+        static_cast<const V*>(c), static_cast<V*>(P->d.win), a, taps_arg<S>(P), items);
     return cudaGetLastError();
 }
 
@@ -966,6 +1017,14 @@ static nuasm_status cuda_status(cudaError_t e) {
 #ifndef NUASM_INTERP_CHUNK
 #define NUASM_INTERP_CHUNK 0
 #endif
+// smallest spreading chunk (records) of a split tile, by precision
+#ifndef NUASM_SPREAD_CHUNK64
+#define NUASM_SPREAD_CHUNK64 128
+#endif
+#ifndef NUASM_SPREAD_CHUNK32
+#define NUASM_SPREAD_CHUNK32 512
+#endif
+constexpr int64_t kSpreadChunk64 = NUASM_SPREAD_CHUNK64, kSpreadChunk32 = NUASM_SPREAD_CHUNK32;
 cudaError_t make_tile_order(nuasm_plan_s* P, cudaStream_t st) {
     const int nt = P->g.ntiles;
     std::vector<int> off(size_t(nt) + 1), home(nt), order(nt);
@@ -981,6 +1040,40 @@ cudaError_t make_tile_order(nuasm_plan_s* P, cudaStream_t st) {
     P->device_bytes += int64_t(sizeof(int)) * nt;
     e = cudaMemcpyAsync(P->d.tile_order, order.data(), sizeof(int) * size_t(nt), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return e;   // host vectors go out of scope
+    if (spread_by_items(P) && P->nrec > 0) {
+        // Spreading items: a tile whose records would keep one SM busy well past
+        // the rest (more than K, K the larger of a per-precision floor and the
+        // records of an even share over two CTAs per SM) is split into chunks of
+        // at most K records, each its own CTA adding into the window; no split,
+        // no items.
+        const int64_t floor_k = P->f64 ? kSpreadChunk64 : kSpreadChunk32;
+        const int64_t k = std::max<int64_t>(floor_k, (P->nrec + 2 * 152 - 1) / (2 * 152));
+        bool split = false;
+        for (int t = 0; t < nt && !split; ++t) split = off[t + 1] - off[t] > k;
+        if (split) {
+            std::vector<int4> items;
+            items.reserve(size_t(nt) + size_t(P->nrec / k) + 1);
+            for (int t : order) {
+                const int b = off[t], e2 = off[t + 1], n = e2 - b;
+                if (n <= k) {
+                    items.push_back(make_int4(t, b, e2, 0));
+                    continue;
+                }
+                const int pieces = int((n + k - 1) / k), step = (n + pieces - 1) / pieces;
+                for (int s0 = b; s0 < e2; s0 += step) items.push_back(make_int4(t, s0, std::min(e2, s0 + step), 1));
+            }
+            std::stable_sort(items.begin(), items.end(),
+                             [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
+            if ((e = xmalloc(reinterpret_cast<void**>(&P->d.spread_items), sizeof(int4) * items.size())) !=
+                cudaSuccess)
+                return e;
+            P->device_bytes += int64_t(sizeof(int4) * items.size());
+            P->n_spread_items = int(items.size());
+            e = cudaMemcpyAsync(P->d.spread_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
+                                st);
+            if (e != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        }
+    }
     if (NUASM_INTERP_CHUNK > 0) {
         const int ch = NUASM_INTERP_CHUNK > 0 ? NUASM_INTERP_CHUNK : 1;
         std::vector<int4> items;

@@ -71,6 +71,9 @@ struct PlanDevice {
     int8_t* tile_skew = nullptr;    // bank skew of each tile's layouts and record order; null: skew for all
     int4* interp_items = nullptr;   // interpolation work items (tile, first record, end record, 0),
                                     // heaviest first; null = one item per tile in tile_order
+    int4* spread_items = nullptr;   // spreading work items (tile, first record, end record, chunked),
+                                    // heaviest first, where a tile's records are split over CTAs;
+                                    // null = one CTA per tile in tile_order
     void* win = nullptr;        // W x Wp fine-grid window
     void* bufA = nullptr;       // N' x Wp
     void* bufB = nullptr;       // N' x N
@@ -96,6 +99,7 @@ struct nuasm_plan_s {
     int skew = 0;               // bank skew of the gridding tile layouts and record order: the one most
                                 // tiles use when d.tile_skew is set, else the one every tile uses
     int n_interp_items = 0;     // entries of d.interp_items
+    int n_spread_items = 0;     // entries of d.spread_items
     nuasm::KernelPoly poly{};   // kernel taps as polynomials (F32 gridding)
     nuasm::KernelPoly64 poly64{};   // the same in FP64 (F64 gridding)
     int64_t device_bytes = 0;
