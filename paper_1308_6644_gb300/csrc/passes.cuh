@@ -52,22 +52,36 @@ template <typename V> struct Prec;
 #ifndef NUASM_COL_BUDGET
 #define NUASM_COL_BUDGET 8192   // FP32 column passes: complex elements per CTA (columns = budget / N')
 #endif
+// FP64 passes run at the FP64 pipe's pace, so small planes want many CTAs:
+// measured on the N' = 128 plane (C1), 2^9 elements per row-pass CTA and 512
+// per column-pass CTA against 2^11 and 4096: row_t1 57 -> 33 us, the column
+// passes 24 -> 16 and 17 -> 11 us (N' = 512: 440 -> 412 us per solve); the
+// same configuration as before at N' = 4096
+#ifndef NUASM_COL_BUDGET64
+#define NUASM_COL_BUDGET64 512    // FP64 column passes: complex elements per CTA
+#endif
+#ifndef NUASM_ROW_LOGBUDGET64
+#define NUASM_ROW_LOGBUDGET64 9   // FP64 row passes: log2 of the complex elements per CTA
+#endif
 template <> struct Prec<float2> {
     static constexpr bool f64 = false;
     static constexpr int col_e = 16, col_budget = NUASM_COL_BUDGET;   // elements per thread / per CTA
+    static constexpr int row_logbudget = 11;                          // rows per CTA = 2^11 / N'
     static constexpr int regs = 64;
     static constexpr int row_regs = NUASM_ROW_REGS;
 };
 template <> struct Prec<double2> {
     static constexpr bool f64 = true;
-    static constexpr int col_e = 8, col_budget = 4096;
+    static constexpr int col_e = 8, col_budget = NUASM_COL_BUDGET64;
+    static constexpr int row_logbudget = NUASM_ROW_LOGBUDGET64;
     static constexpr int regs = 128;
     static constexpr int row_regs = 128;
 };
 
 template <typename V, int LOGNP> struct RowCfg {
     static constexpr int NP = 1 << LOGNP;
-    static constexpr int LOGROWS = LOGNP >= 11 ? 0 : (11 - LOGNP > LOGNP ? LOGNP : 11 - LOGNP);
+    static constexpr int LB = Prec<V>::row_logbudget;
+    static constexpr int LOGROWS = LOGNP >= LB ? 0 : (LB - LOGNP > LOGNP ? LOGNP : LB - LOGNP);
     static constexpr int ROWS = 1 << LOGROWS;
     // merged even/odd engines (two sequences per row in one pass sequence)
     static constexpr bool MERGE = !Prec<V>::f64 && LOGNP <= 12;
