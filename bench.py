@@ -436,6 +436,11 @@ def run_ours(args):
     x = torch.from_numpy(wl.x).to(dev)
     y = torch.from_numpy(wl.y).to(dev)
     wts = None if wl.weights is None else torch.from_numpy(np.asarray(wl.weights, np.float64)).to(dev)
+    tuned = None
+    if args.autotune:
+        params, tuned_ms = P.nuasm_autotune(params, x, y, wl.type, stream=stream)
+        tuned = {"tile": params.tile, "interp_chunk": params.interp_chunk, "spread_chunk": params.spread_chunk,
+                 "solve_ms": round(tuned_ms, 4)}
     t_plan0 = time.perf_counter()
     plan = P.nuasm_plan(params, x, y, wts, stream=stream)
     plan_s = time.perf_counter() - t_plan0
@@ -596,6 +601,7 @@ def run_ours(args):
                        "kernel_width": info["kernel_width"], "tile": info["tile"],
                        "precision": "complex128" if f64 else "complex64 + FP64-derived phase",
                        "l2": "flushed (256 MB write) before every step", "plan_s": round(plan_s, 3),
+                       "autotuned": tuned,
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h_in.numel() * eb),
@@ -689,7 +695,7 @@ def run_batch(args):
         params = P.make_params(wl.n, wl.pitch, wl.lam, wl.z, kind="asm", prec="f32")
         xd, yd = torch.from_numpy(wl.x).to(dev), torch.from_numpy(wl.y).to(dev)
         if args.autotune:
-            params.tile, _ = P.nuasm_autotune_tile(params, xd, yd, wl.type, stream=stream)
+            params, _ = P.nuasm_autotune(params, xd, yd, wl.type, stream=stream)
         plan = P.nuasm_plan(params, xd, yd, stream=stream)
         t_used = plan.info()["tile"]
         tiles[t_used] = tiles.get(t_used, 0) + 1
@@ -761,7 +767,8 @@ def run_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"mixed{args.planes}_planes_n256-2048_types1+2", "planes": args.planes,
                        "points_per_step": total_m, "lanes": lanes, "graph_kernels": kernels,
-                       "tiles": ("autotuned per plane: " if args.autotune else "library rule: ") +
+                       "tiles": ("autotuned per plane (tile side and split chunks): " if args.autotune
+                                 else "library rule: ") +
                        ", ".join(f"T={k} x{v}" for k, v in sorted(tiles.items())),
                        "plain_points_per_s": plain_value, "batched_over_plain": value / plain_value,
                        "plain": "one execute call per plane, back to back on one stream",
@@ -974,7 +981,8 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=0.0,
                     help="NUFFT tolerance of the single-solve workloads (0: the precision's default)")
     ap.add_argument("--autotune", action="store_true",
-                    help="batch64: time every tile side per plane (nuasm_autotune_tile) instead of the library's rule")
+                    help="pick the tile side and split chunks per plane with nuasm_autotune instead of the "
+                         "library's rule")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -114,6 +114,18 @@ typedef struct {
                            a kernel of w taps).  A side below w - 1 returns
                            NUASM_EUNSUPPORTED.  Results agree to rounding for every
                            choice; nuasm_autotune_tile measures which is fastest. */
+    int32_t interp_chunk;  /* type-2 interpolation: 0 = one CTA per tile; N >= 64 = a tile with
+                              more than N home records is split into chunks of at most N
+                              (rounded up to a multiple of 32), one CTA each.  Results are the
+                              same bit for bit; values 1..63 or < 0 return NUASM_EINVAL. */
+    int32_t spread_chunk;  /* type-1 spreading, for the kernels that can split a tile (FP64, and
+                              FP32 tiles of side <= 32): 0 = the library's rule (a tile with
+                              more records than the larger of 128 (FP64) / 512 (FP32) and an
+                              even share over two CTAs per SM is split into chunks of at most
+                              that many, each adding into the window); -1 = never split;
+                              N >= 32 = split above N records.  Results agree to rounding;
+                              other values return NUASM_EINVAL.  nuasm_autotune measures the
+                              fastest tile side and chunk sizes. */
 } nuasm_params_t;
 
 /* Geometry of a plan (read-only report). */
@@ -263,6 +275,23 @@ nuasm_status nuasm_rs_direct(const nuasm_params_t* p, int64_t m1, const double* 
  */
 nuasm_status nuasm_autotune_tile(const nuasm_params_t* p, int64_t m, const double* x, const double* y, int32_t type,
                                  void* stream, int32_t* tile, double* ms);
+
+/*
+ * nuasm_autotune -- the project's autotuner over the gridding knobs that only
+ * change speed (the paper has no counterpart): for each tile side (16, 32,
+ * 64 that the kernel width allows) and, for type 2, interpolation chunks
+ * (interp_chunk 0, 1024, 2048) or, for type 1, spreading splits
+ * (spread_chunk 0, -1, 256), it builds a plan on the given points, times one
+ * solve of `type` (1 or 2) with CUDA events (after one untimed solve; three
+ * timed) and writes the fastest parameters to *best (a copy of *p with tile,
+ * interp_chunk and spread_chunk set) and their time to *ms (may be NULL).
+ * The spreading width is not searched: it is the smallest that meets p->tol
+ * for p->kernel.  x, y (device, m entries) as for nuasm_plan.  Builds and
+ * destroys temporary plans and zero-filled arrays; synchronises `stream`.
+ * Errors as nuasm_plan; best NULL or type not 1/2: NUASM_EINVAL.
+ */
+nuasm_status nuasm_autotune(const nuasm_params_t* p, int64_t m, const double* x, const double* y, int32_t type,
+                            void* stream, nuasm_params_t* best, double* ms);
 
 /*
  * nuasm_debug_plan_wait -- the same diagnostic aimed at a plan (the paper has

@@ -443,6 +443,93 @@ nuasm_status nuasm::plan_create(nuasm_plan_s** out, const nuasm_params_t* p, int
     return NUASM_OK;
 }
 
+namespace {
+
+// one plan on the points with parameters q and the mean of three timed solves
+// of `type` after an untimed one (CUDA events on st)
+nuasm_status time_solve(const nuasm_params_t& q, int64_t m, const double* x, const double* y, int type,
+                        cudaStream_t st, void* in, void* out, cudaEvent_t t0, cudaEvent_t t1, double* ms) {
+    nuasm_plan_s* P = nullptr;
+    const nuasm_status s = plan_create(&P, &q, m, x, y, nullptr, st, true);
+    if (s != NUASM_OK) return s;
+    cudaError_t e = cudaSuccess;
+    float total = 0.f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // first run untimed
+        e = cudaEventRecord(t0, st);
+        if (e == cudaSuccess) e = type == 1 ? chain_type1(P, in, out, st) : chain_type2(P, in, out, st);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, t0, t1);
+        if (rep > 0) total += t;
+    }
+    plan_release(P);
+    if (e != cudaSuccess) return cuda_status(e);
+    *ms = double(total) / 3.0;
+    return NUASM_OK;
+}
+
+// The autotuner: tile sides (those the kernel width allows) and, with
+// `chunks`, the interpolation chunk (type 2) or spreading split (type 1);
+// the fastest parameters go to *best.
+nuasm_status autotune_search(const nuasm_params_t* p, int64_t m, const double* x, const double* y, int type,
+                             cudaStream_t st, bool chunks, nuasm_params_t* best, double* best_ms) {
+    if (type != 1 && type != 2) return NUASM_EINVAL;
+    nuasm_params_t rp;
+    nuasm_status s = validate(*p, m, &rp);
+    if (s != NUASM_OK) return s;
+    if (m > 0 && (!x || !y || !device_accessible(x) || !device_accessible(y))) return NUASM_EINVAL;
+    const size_t eb = rp.prec == NUASM_PREC_F64 ? 16 : 8;
+    const size_t nn = size_t(rp.n) * rp.n;
+    void* buf = nullptr;
+    cudaError_t e = xmalloc(&buf, eb * (nn + size_t(m > 0 ? m : 1)));
+    if (e != cudaSuccess) return cuda_status(e);
+    char* in = static_cast<char*>(buf);
+    char* out = in + eb * (type == 1 ? size_t(m) : nn);
+    e = cudaMemsetAsync(buf, 0, eb * (nn + size_t(m > 0 ? m : 1)), st);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess) e = xevent_create(&t0, cudaEventDefault);   // timing events
+    if (e == cudaSuccess) e = xevent_create(&t1, cudaEventDefault);
+    bool found = false;
+    double found_ms = 0.0;
+    s = NUASM_OK;
+    const int type2_chunks[] = {0, 1024, 2048}, type1_chunks[] = {0, -1, 256};
+    for (int cand : {16, 32, 64}) {
+        if (e != cudaSuccess || s != NUASM_OK) break;
+        for (int k = 0; k < (chunks ? 3 : 1); ++k) {
+            nuasm_params_t q = *p;
+            q.tile = cand;
+            if (chunks) {
+                if (type == 2) q.interp_chunk = type2_chunks[k];
+                else q.spread_chunk = type1_chunks[k];
+            }
+            double t = 0.0;
+            const nuasm_status r = time_solve(q, m, x, y, type, st, in, out, t0, t1, &t);
+            if (r == NUASM_EUNSUPPORTED) break;   // a side below the kernel's reach: skip it
+            if (r != NUASM_OK) {
+                s = r;
+                break;
+            }
+            if (!found || t < found_ms) {
+                found = true;
+                found_ms = t;
+                *best = q;
+            }
+        }
+    }
+    if (t0) xevent_destroy(t0);
+    if (t1) xevent_destroy(t1);
+    cudaStreamSynchronize(st);
+    xfree(buf);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (s != NUASM_OK) return s;
+    if (!found) return NUASM_EUNSUPPORTED;
+    *best_ms = found_ms;
+    return NUASM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 nuasm_status nuasm_plan_lattice(nuasm_plan_t* out, const nuasm_params_t* p, int32_t nx, int32_t ny,
@@ -496,57 +583,23 @@ nuasm_status nufresnel3_execute(nuasm_plan_t src, nuasm_plan_t dst, const void* 
 
 nuasm_status nuasm_autotune_tile(const nuasm_params_t* p, int64_t m, const double* x, const double* y, int32_t type,
                                  void* stream, int32_t* tile, double* ms) {
-    if (!p || !tile || (type != 1 && type != 2)) return NUASM_EINVAL;
-    nuasm_params_t rp;
-    nuasm_status s = validate(*p, m, &rp);
+    if (!p || !tile) return NUASM_EINVAL;
+    nuasm_params_t best;
+    double t = 0.0;
+    const nuasm_status s = autotune_search(p, m, x, y, type, static_cast<cudaStream_t>(stream), false, &best, &t);
     if (s != NUASM_OK) return s;
-    if (m > 0 && (!x || !y || !device_accessible(x) || !device_accessible(y))) return NUASM_EINVAL;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t eb = rp.prec == NUASM_PREC_F64 ? 16 : 8;
-    const size_t nn = size_t(rp.n) * rp.n;
-    void* buf = nullptr;
-    cudaError_t e = xmalloc(&buf, eb * (nn + size_t(m > 0 ? m : 1)));
-    if (e != cudaSuccess) return cuda_status(e);
-    char* in = static_cast<char*>(buf);
-    char* out = in + eb * (type == 1 ? size_t(m) : nn);
-    e = cudaMemsetAsync(buf, 0, eb * (nn + size_t(m > 0 ? m : 1)), st);
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
-    if (e == cudaSuccess) e = cudaEventCreate(&t0);
-    if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    int best = 0;
-    float best_ms = 0.f;
-    for (int cand : {16, 32, 64}) {
-        if (e != cudaSuccess) break;
-        nuasm_params_t q = rp;
-        q.tile = cand;
-        nuasm_plan_s* P = nullptr;
-        s = plan_create(&P, &q, m, x, y, nullptr, st, true);
-        if (s != NUASM_OK) break;
-        float total = 0.f;
-        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // first run untimed
-            e = cudaEventRecord(t0, st);
-            if (e == cudaSuccess) e = type == 1 ? chain_type1(P, in, out, st) : chain_type2(P, in, out, st);
-            if (e == cudaSuccess) e = cudaEventRecord(t1, st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-            float t = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, t0, t1);
-            if (rep > 0) total += t;
-        }
-        plan_release(P);
-        if (e == cudaSuccess && (best == 0 || total / 3 < best_ms)) {
-            best = cand;
-            best_ms = total / 3;
-        }
-    }
-    if (t0) cudaEventDestroy(t0);
-    if (t1) cudaEventDestroy(t1);
-    cudaStreamSynchronize(st);
-    xfree(buf);
-    if (s != NUASM_OK) return s;
-    if (e != cudaSuccess) return cuda_status(e);
-    *tile = best;
-    if (ms) *ms = best_ms;
+    *tile = best.tile;
+    if (ms) *ms = t;
     return NUASM_OK;
+}
+
+nuasm_status nuasm_autotune(const nuasm_params_t* p, int64_t m, const double* x, const double* y, int32_t type,
+                            void* stream, nuasm_params_t* best, double* ms) {
+    if (!p || !best) return NUASM_EINVAL;
+    double t = 0.0;
+    const nuasm_status s = autotune_search(p, m, x, y, type, static_cast<cudaStream_t>(stream), true, best, &t);
+    if (s == NUASM_OK && ms) *ms = t;
+    return s;
 }
 
 nuasm_status nuasm_destroy(nuasm_plan_t plan) {

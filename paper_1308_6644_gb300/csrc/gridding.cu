@@ -1010,10 +1010,11 @@ static nuasm_status cuda_status(cudaError_t e) {
 // one-CTA-per-tile kernels, so the heaviest tiles start first and the last
 // wave holds the lightest.
 //
-// Interpolation items: a tile with more than NUASM_INTERP_CHUNK home records is
-// split into chunks of at most that many, each its own CTA (which stages the
-// same tile), so that the densest tiles do not hold the last wave; items are
-// launched heaviest first.  0 keeps one item per tile.
+// Interpolation items: a tile with more than the plan's interp_chunk home
+// records (NUASM_INTERP_CHUNK where the plan leaves it 0) is split into
+// chunks of at most that many, each its own CTA (which stages the same tile),
+// so that the densest tiles do not hold the last wave; items are launched
+// heaviest first.  0 keeps one item per tile.
 #ifndef NUASM_INTERP_CHUNK
 #define NUASM_INTERP_CHUNK 0
 #endif
@@ -1040,14 +1041,15 @@ cudaError_t make_tile_order(nuasm_plan_s* P, cudaStream_t st) {
     P->device_bytes += int64_t(sizeof(int)) * nt;
     e = cudaMemcpyAsync(P->d.tile_order, order.data(), sizeof(int) * size_t(nt), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return e;   // host vectors go out of scope
-    if (spread_by_items(P) && P->nrec > 0) {
+    if (spread_by_items(P) && P->nrec > 0 && P->p.spread_chunk >= 0) {
         // Spreading items: a tile whose records would keep one SM busy well past
         // the rest (more than K, K the larger of a per-precision floor and the
         // records of an even share over two CTAs per SM) is split into chunks of
         // at most K records, each its own CTA adding into the window; no split,
         // no items.
         const int64_t floor_k = P->f64 ? kSpreadChunk64 : kSpreadChunk32;
-        const int64_t k = std::max<int64_t>(floor_k, (P->nrec + 2 * 152 - 1) / (2 * 152));
+        const int64_t k = P->p.spread_chunk > 0 ? int64_t(P->p.spread_chunk)
+                                                : std::max<int64_t>(floor_k, (P->nrec + 2 * 152 - 1) / (2 * 152));
         bool split = false;
         for (int t = 0; t < nt && !split; ++t) split = off[t + 1] - off[t] > k;
         if (split) {
@@ -1074,8 +1076,9 @@ cudaError_t make_tile_order(nuasm_plan_s* P, cudaStream_t st) {
             if (e != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
         }
     }
-    if (NUASM_INTERP_CHUNK > 0) {
-        const int ch = NUASM_INTERP_CHUNK > 0 ? NUASM_INTERP_CHUNK : 1;
+    const int ich = P->p.interp_chunk > 0 ? P->p.interp_chunk : NUASM_INTERP_CHUNK;
+    if (ich > 0) {
+        const int ch = ich;
         std::vector<int4> items;
         items.reserve(size_t(nt) + size_t(P->m / ch) + 1);
         for (int t = 0; t < nt; ++t) {

@@ -262,6 +262,8 @@ nuasm_status validate(const nuasm_params_t& p0, int64_t m, nuasm_params_t* out) 
         if (!kernel_shape(p.tol, p.prec, p.kernel, &w, &beta)) return NUASM_EUNSUPPORTED;
     }
     if (p.tile != 0 && p.tile != 16 && p.tile != 32 && p.tile != 64) return NUASM_EINVAL;
+    if (p.interp_chunk != 0 && p.interp_chunk < 64) return NUASM_EINVAL;
+    if (p.spread_chunk < -1 || (p.spread_chunk > 0 && p.spread_chunk < 32)) return NUASM_EINVAL;
     {
         int w;
         double beta;

@@ -214,7 +214,7 @@ void xfree_async(void* p, cudaStream_t s);
 void xfree_host(void* p);
 cudaError_t xstream_create(cudaStream_t* s);
 void xstream_destroy(cudaStream_t s);
-cudaError_t xevent_create(cudaEvent_t* ev);
+cudaError_t xevent_create(cudaEvent_t* ev, unsigned flags = cudaEventDisableTiming);
 void xevent_destroy(cudaEvent_t ev);
 cudaError_t xgraph_instantiate(cudaGraphExec_t* exec, cudaGraph_t graph);
 void xgraph_exec_destroy(cudaGraphExec_t exec);

@@ -95,10 +95,10 @@ void xstream_destroy(cudaStream_t s) {
     live_add(-1);
 }
 
-cudaError_t xevent_create(cudaEvent_t* ev) {
+cudaError_t xevent_create(cudaEvent_t* ev, unsigned flags) {
     *ev = nullptr;
     if (acquire_fails()) return cudaErrorMemoryAllocation;
-    const cudaError_t e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    const cudaError_t e = cudaEventCreateWithFlags(ev, flags);
     if (e == cudaSuccess) live_add(1);
     return e;
 }

@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
                 ("oy", ctypes.c_double), ("band_auto", ctypes.c_int32), ("c_m", ctypes.c_double),
                 ("c_n", ctypes.c_double), ("w_m", ctypes.c_double), ("w_n", ctypes.c_double),
                 ("kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("kernel", ctypes.c_int32), ("tile", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("tile", ctypes.c_int32), ("interp_chunk", ctypes.c_int32),
+                ("spread_chunk", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -115,6 +116,9 @@ _SIGS = {
     "nuasm_autotune_tile": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_double)]),
+    "nuasm_autotune": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(Params),
+                                      ctypes.POINTER(ctypes.c_double)]),
     "nuasm_debug_bounded_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p]),
     "nuasm_debug_plan_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "nuasm_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int64]),
@@ -210,10 +214,11 @@ KERNEL_ES, KERNEL_GAUSSIAN = 0, 1
 
 
 def make_params(n, pitch, lam, z, ox=0.0, oy=0.0, kind="asm", prec="f32", tol=0.0, n_pad=0,
-                band=None, kernel="es", tile=0) -> Params:
+                band=None, kernel="es", tile=0, interp_chunk=0, spread_chunk=0) -> Params:
     """nuasm_params_t from keyword values; band = (c_m, c_n, w_m, w_n) or None
     (auto rule); kernel = "es" (exponential of semicircle) or "gaussian";
-    tile = gridding tile side (0: the library's rule)."""
+    tile = gridding tile side (0: the library's rule); interp_chunk /
+    spread_chunk = records per CTA of split tiles (0: the library's rule)."""
     p = Params()
     p.n, p.n_pad, p.pitch, p.lambda_, p.z, p.ox, p.oy = int(n), int(n_pad), pitch, lam, z, ox, oy
     if band is None:
@@ -226,6 +231,8 @@ def make_params(n, pitch, lam, z, ox=0.0, oy=0.0, kind="asm", prec="f32", tol=0.
     p.tol = float(tol)
     p.kernel = KERNEL_GAUSSIAN if kernel in ("gaussian", KERNEL_GAUSSIAN) else KERNEL_ES
     p.tile = int(tile)
+    p.interp_chunk = int(interp_chunk)
+    p.spread_chunk = int(spread_chunk)
     return p
 
 
@@ -418,6 +425,18 @@ def nuasm_autotune_tile(params: Params, x, y, type_: int, stream=None) -> tuple:
     _check(lib().nuasm_autotune_tile(ctypes.byref(params), m, _ptr(x), _ptr(y), int(type_), _stream(stream),
                                      ctypes.byref(t), ctypes.byref(ms)), "nuasm_autotune_tile")
     return int(t.value), float(ms.value)
+
+
+def nuasm_autotune(params: Params, x, y, type_: int, stream=None) -> tuple:
+    """(the fastest Params over tile sides and split chunks, its solve time in
+    ms) for these device points."""
+    m = _numel(x)
+    _expect(x, m, "float64", "x")
+    _expect(y, m, "float64", "y")
+    best, ms = Params(), ctypes.c_double()
+    _check(lib().nuasm_autotune(ctypes.byref(params), m, _ptr(x), _ptr(y), int(type_), _stream(stream),
+                                ctypes.byref(best), ctypes.byref(ms)), "nuasm_autotune")
+    return best, float(ms.value)
 
 
 def nuasm_debug_bounded_wait(spins: int, stream=None) -> int:

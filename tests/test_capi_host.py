@@ -198,6 +198,16 @@ def test_plan_rejects_unsupported_tiles(P, tile):
     assert ei.value.code == 1
 
 
+@pytest.mark.parametrize("field,value", [("interp_chunk", 32), ("interp_chunk", -1), ("spread_chunk", -2),
+                                         ("spread_chunk", 16)])
+def test_chunk_knobs_are_validated(P, field, value):
+    """interp_chunk is 0 or >= 64 records, spread_chunk -1, 0 or >= 32."""
+    x = np.zeros(2)
+    with pytest.raises(P.NuasmError) as ei:
+        P.nuasm_plan(P.make_params(32, 10e-6, 633e-9, 0.01, **{field: value}), x, x)
+    assert ei.value.code == 1
+
+
 def test_bounded_wait_diagnostic_rejects_bad_counts(P):
     lib = P.lib()
     assert lib.nuasm_debug_bounded_wait(0, None) == 1

@@ -30,11 +30,12 @@ def _t(a, dev="cuda"):
 
 
 def run_gpu(P, kind, type_, prec, n, pitch, lam, z, x, y, values, ox=0.0, oy=0.0, w=None, n_pad=0,
-            band=None, tol=0.0, host=False, kernel="es", tile=0):
+            band=None, tol=0.0, host=False, kernel="es", tile=0, interp_chunk=0, spread_chunk=0):
     """One plan + one execute; returns the output as a numpy array."""
     import torch
     params = P.make_params(n, pitch, lam, z, ox=ox, oy=oy, kind=kind, prec=prec, tol=tol,
-                           n_pad=n_pad, band=band, kernel=kernel, tile=tile)
+                           n_pad=n_pad, band=band, kernel=kernel, tile=tile, interp_chunk=interp_chunk,
+                           spread_chunk=spread_chunk)
     cdt = CDT[prec]
     tdt = torch.complex64 if prec == "f32" else torch.complex128
     if host:
@@ -368,3 +369,49 @@ def test_autotune_tile_picks_a_supported_side(P):
     params = P.make_params(w.n, w.pitch, w.lam, w.z, ox=w.ox)
     tile, ms = P.nuasm_autotune_tile(params, _t(w.x), _t(w.y), 2)
     assert tile in (16, 32, 64) and ms > 0
+
+
+def test_split_work_knobs_keep_results(P):
+    """interp_chunk splits dense tiles' interpolation over CTAs (type 2 equal
+    bit for bit); spread_chunk splits or keeps dense tiles in spreading
+    (type 1 equal to rounding: the chunks add into the window in any order)."""
+    rng = np.random.default_rng(46)
+    n, pitch, m = 64, 10e-6, 30000
+    x = WL.clamp_window(rng.normal(0, 40e-6, m), n, pitch)
+    y = WL.clamp_window(rng.normal(0, 40e-6, m), n, pitch)
+    c = rng.normal(size=m) + 1j * rng.normal(size=m)
+    u1 = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    kw = dict(pitch=pitch, lam=633e-9, z=0.02, x=x, y=y)
+    v0 = run_gpu(P, "asm", 2, "f32", n, values=u1, **kw)
+    v1 = run_gpu(P, "asm", 2, "f32", n, values=u1, **kw, interp_chunk=64)
+    assert np.array_equal(v0, v1)
+    for prec in ("f32", "f64"):
+        tile = 16 if prec == "f64" else 32   # the split-capable spreading kernels
+        a = run_gpu(P, "asm", 1, prec, n, values=c, tile=tile, spread_chunk=-1, **kw)
+        b = run_gpu(P, "asm", 1, prec, n, values=c, tile=tile, spread_chunk=32, **kw)
+        d = run_gpu(P, "asm", 1, prec, n, values=c, tile=tile, **kw)
+        lim = 1e-6 if prec == "f32" else 1e-13
+        assert O.rel_l2(b, a) < lim and O.rel_l2(d, a) < lim
+
+
+def test_autotuner_returns_working_parameters(P):
+    """nuasm_autotune returns the plane's own parameters with a tile side and
+    split chunks from its search space, and a plan made with them gives the
+    default plan's result (to rounding; both are parity-tested elsewhere)."""
+    rng = np.random.default_rng(47)
+    n, pitch, m = 128, 8e-6, 50000
+    h = 0.5 * n * pitch * (1 - 1e-9)
+    x, y = rng.uniform(-h, h, m), rng.uniform(-h, h, m)
+    params = P.make_params(n, pitch, 532e-9, 0.05)
+    for type_ in (1, 2):
+        best, ms = P.nuasm_autotune(params, _t(x), _t(y), type_)
+        assert best.tile in (16, 32, 64) and ms > 0
+        assert best.interp_chunk in (0, 1024, 2048) and best.spread_chunk in (0, -1, 256)
+        assert (best.n, best.pitch, best.z) == (params.n, params.pitch, params.z)
+        kw = dict(pitch=pitch, lam=532e-9, z=0.05, x=x, y=y, tile=best.tile, interp_chunk=best.interp_chunk,
+                  spread_chunk=best.spread_chunk)
+        vals = rng.normal(size=m) + 1j * rng.normal(size=m) if type_ == 1 else \
+            rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+        got = run_gpu(P, "asm", type_, "f32", n, values=vals, **kw)
+        ref2 = run_gpu(P, "asm", type_, "f32", n, values=vals, pitch=pitch, lam=532e-9, z=0.05, x=x, y=y)
+        assert O.rel_l2(got, ref2) < 1e-6
