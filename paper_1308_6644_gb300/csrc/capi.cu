@@ -372,7 +372,10 @@ nuasm_status nuasm::plan_create(nuasm_plan_s** out, const nuasm_params_t* p, int
     build_tables(rp, P->g, &ht);
     P->rc = ht.rc;
     P->poly = ht.poly;
-    if (P->f64) fit_kernel_poly64(P->g, &P->poly64);
+    if (P->f64) {
+        fit_kernel_poly64(P->g, &P->poly64);
+        split_kernel_poly64(P->poly64, &P->poly64df);
+    }
     P->nonsep_mode = choose_nonsep_mode(rp, ht.rmax);
     cudaError_t e = upload_tables(P, ht, st);
     free_tables(&ht);

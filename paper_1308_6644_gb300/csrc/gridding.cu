@@ -872,6 +872,403 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
     }
 }
 
+// ---------------------------------------------------------------- FP64 mode in double-float arithmetic
+// FP64-mode gridding with the ES kernel at its exact widths runs on the FP32
+// pipe, whose rate is 64 times that of the FP64 pipe here: window values and
+// tap weights are unevaluated sums hi + lo of two floats (47 significant
+// bits), products go through FMA-based error-free transforms, and FP64
+// arithmetic is left to once per point or per staged cell.
+#ifndef NUASM_F64_DF
+#define NUASM_F64_DF 1   // 0: FP64 gridding on the FP64 pipe throughout
+#endif
+
+// x 2^-s as hi + lo: hi the leading 24 significant bits of x (truncated), lo
+// the next 23, by integer operations on the bits (no FP64 arithmetic), so the
+// relative error is below 2^-46.  The caller picks s so that the result is
+// below 2 in magnitude.  Zeros, subnormals and values below 2^-100 after the
+// scaling give zero; infinities and NaNs give themselves in hi.
+__device__ __forceinline__ df df_split(double x, int s) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const int ex = int(b >> 52) & 0x7ff;
+    if (ex == 0x7ff) return {__double2float_rn(x), 0.f};
+    const int e = ex - 1023 - s;   // exponent of the scaled value
+    if (ex == 0 || e < -100) return {0.f, 0.f};
+    const unsigned sign = unsigned(b >> 32) & 0x80000000u;
+    const unsigned hb = sign | (unsigned(e + 127) << 23) | unsigned((b >> 29) & 0x7fffffu);
+    // the 29 mantissa bits below hi, r 2^(e - 52), kept as (r >> 6) 2^(e - 46):
+    // the float (2^23 + (r >> 6)) 2^(e - 46) minus 2^(e - 23), an exact subtraction
+    const unsigned r = unsigned(b) & 0x1fffffffu;
+    const unsigned lb = unsigned(e - 23 + 127) << 23;
+    const float lo = __uint_as_float(lb | (r >> 6)) - __uint_as_float(lb);
+    return {__uint_as_float(hb), sign ? -lo : lo};
+}
+
+// exponent k of a double with 2^k <= |x| < 2^(k+1) (-1023 for zeros and
+// subnormals, 1024 for infinities and NaNs)
+__device__ __forceinline__ int dexp(double x) {
+    return (int(static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7ff) - 1023;
+}
+
+// a b + c; the sum is kept as hi + lo without renormalisation (lo collects
+// the rounding errors of the products and of the hi sums exactly or to 2^-24
+// of its own size)
+__device__ __forceinline__ df df_fma(df a, df b, df c) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    const df t = df_two_sum(p, c.hi);
+    return {t.hi, t.lo + (e + c.lo)};
+}
+
+// Tap weights of one axis in double-float: Horner's rule on the FP64
+// polynomials, the degrees from kDfTail up in FP32 (the coefficients' hi
+// parts; for the ES kernel their sum is below 3.1e-7 at w = 11 and 13, so
+// this adds below 2e-14 to a weight) and the rest in double-float.
+constexpr int kDfTail = 9;
+static_assert(kPoly64Deg >= kDfTail, "FP64 tap degree");
+// c: the kPoly64Deg + 1 coefficients of one tap (parameter or shared memory)
+__device__ __forceinline__ df tap_weight_df(const float2* c, df x) {
+    float t = c[kPoly64Deg].x;
+#pragma unroll
+    for (int k = kPoly64Deg - 1; k >= kDfTail; --k) t = fmaf(t, x.hi, c[k].x);
+    df acc = {t, 0.f};
+#pragma unroll
+    for (int k = kDfTail - 1; k >= 0; --k) acc = df_fma(acc, x, df{c[k].x, c[k].y});
+    return df_two_sum(acc.hi, acc.lo);
+}
+constexpr int kDfCoef = kPoly64Deg + 1;
+
+// x weights from the parameter copy of the coefficients (unrolled), y
+// weights one row at a time from the CTA's shared copy cs (rolled row loop)
+template <int WMAX>
+__device__ __forceinline__ void interp_point_df(const RecD& r, const float4* __restrict__ tl, int THP, int x0, int y0,
+                                                const KernelPolyDF& kp, const float2* cs, double scale,
+                                                double2* __restrict__ v, [[maybe_unused]] int tl_n,
+                                                [[maybe_unused]] long long m) {
+    const int lx = int(r.cell & 0xffffu) - x0, ly = int(r.cell >> 16) - y0;
+    df wx[WMAX];
+    const df xv = df_split(fma(2.0, r.fx, -1.0), 0), yv = df_split(fma(2.0, r.fy, -1.0), 0);
+#pragma unroll
+    for (int q = 0; q < WMAX; ++q) wx[q] = tap_weight_df(kp.c[q], xv);
+    df ar = {0.f, 0.f}, ai = {0.f, 0.f};
+#pragma unroll 1
+    for (int qy = 0; qy < WMAX; ++qy) {
+        const df wyq = tap_weight_df(cs + qy * kDfCoef, yv);
+        const float4* row = tl + (ly + qy) * THP + lx;
+        df rr = {0.f, 0.f}, ri = {0.f, 0.f};
+#pragma unroll
+        for (int qx = 0; qx < WMAX; ++qx) {
+            if (!NUASM_IN_RANGE((ly + qy) * THP + lx + qx, tl_n, dbg::kInterpTile)) continue;
+            const float4 g = row[qx];
+            rr = df_fma(df{g.x, g.y}, wx[qx], rr);
+            ri = df_fma(df{g.z, g.w}, wx[qx], ri);
+        }
+        ar = df_fma(df_two_sum(rr.hi, rr.lo), wyq, ar);
+        ai = df_fma(df_two_sum(ri.hi, ri.lo), wyq, ai);
+    }
+    const double2 out = make_double2((double(ar.hi) + double(ar.lo)) * scale, (double(ai.hi) + double(ai.lo)) * scale);
+    if (NUASM_IN_RANGE(r.j, m, dbg::kInterpOut)) v[r.j] = out;
+}
+
+// FP64-mode spreading in double-float arithmetic with exact integer sums,
+// one CTA per whole tile (split tiles keep the FP64 kernels).  Records go in
+// batches of kDfBatch; a batch's values are scaled by 2^-E, S = sum(|re| +
+// |im|) < 2^E over the batch (weights included), so every scaled tap
+// contribution p = v wy wx is at most 1 and a batch adds at most 1 at any
+// cell.  p is split into n_h 2^-30 + n_l 2^-52 + (|error| <= 2^-54) with
+// |n_l| <= 2^21, and n_h, n_l go to two int32 planes per component with
+// shared-memory integer atomics: a batch's sums stay below 2^31 at every
+// cell and are exact.  After each batch the planes become the integer V =
+// n_h 2^22 + n_l (units 2^(E-52)); a tile with one batch writes V 2^(E-52)
+// as FP64, one with several adds V into int64 totals held in its own window
+// cells at the unit 2^(Et-62), Et from the tile's whole sum (a first pass
+// over its records), and converts them to FP64 at the end.  A batch whose
+// sum is not finite makes the tile's cells NaN (so do the FFTs of any
+// window with such a cell).
+constexpr int kDfBatch = 512;
+// a b without renormalisation (the low part is the product's exact error
+// plus the cross terms)
+__device__ __forceinline__ df df_prod(df a, df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return {p, e};
+}
+__device__ __forceinline__ void df_quant_add(df p, int cell, int* ph, int* pl) {
+    const float t = p.hi * 1073741824.f;                 // 2^30: exact
+    const float tl = p.lo * 1073741824.f;
+    const float nf = rintf(t);
+    const float d = (t - nf) + tl;                       // |d| <= 1 unless |t| >= 2^23 (then t - nf = 0, d = tl)
+    const float nf2 = rintf(d);
+    const int nh = __float2int_rn(nf) + __float2int_rn(nf2);
+    const int nl = __float2int_rn(fmaf(d, 4194304.f, -nf2 * 4194304.f));   // (d - nf2) 2^22, |.| <= 2^21
+    atomicAdd(&ph[cell], nh);
+    atomicAdd(&pl[cell], nl);
+}
+// 2^k as a double for k in [-1022, 1023]
+__device__ __forceinline__ double pow2d(int k) { return __longlong_as_double(static_cast<long long>(k + 1023) << 52); }
+// V 2^k for an integer |V| < 2^62 (two exact power-of-two factors when k is below the normal range)
+__device__ __forceinline__ double scaled_int(long long V, int k) {
+    const double v = double(V);
+    return k >= -1022 ? v * pow2d(k) : (v * pow2d(k + 512)) * pow2d(-512);
+}
+
+template <int WMAX>
+__global__ void __launch_bounds__(256, 2) spread_df_kernel(const RecD* __restrict__ rec, const int* __restrict__ off,
+                                                          const double* __restrict__ wpt,
+                                                          const int* __restrict__ order,
+                                                          const double2* __restrict__ c, double2* __restrict__ win,
+                                                          GridArgs a, const KernelPolyDF kp) {
+    constexpr int NT = 256, RPB = kDfBatch / NT;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ float2 cs[WMAX * kDfCoef];
+    __shared__ double red[NT / 32];
+    __shared__ double bsum;
+    const int tile = order ? order[blockIdx.x] : blockIdx.x;
+    const int T = a.T, TS = plane_stride(T, a.skew_of(tile)), TT = T * TS;
+    int* rh = reinterpret_cast<int*>(smem_raw);
+    int* rl = rh + TT;
+    int* ih = rl + TT;
+    int* il = ih + TT;
+    pdl_allow_next();
+    for (int i = threadIdx.x; i < WMAX * kDfCoef; i += NT) cs[i] = kp.c[i / kDfCoef][i % kDfCoef];
+    for (int i = threadIdx.x; i < TT; i += NT) {
+        rh[i] = 0;
+        rl[i] = 0;
+        ih[i] = 0;
+        il[i] = 0;
+    }
+    const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
+    const int x0 = tx * T, y0 = ty * T;
+    const int b = off[tile], e = off[tile + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool multi = e - b > kDfBatch;
+    // block sum of one double per thread
+    auto block_sum = [&](double part) -> double {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < NT / 32; ++k) t += red[k];
+            bsum = t;
+        }
+        __syncthreads();
+        return bsum;
+    };
+    auto value_of = [&](int i) -> double2 {
+        const RecD r = rec[i];
+        const int j = NUASM_IN_RANGE(r.j, a.m, dbg::kSpreadValue) ? r.j : 0;
+        double2 v = c[j];
+        if (wpt) {
+            const double wt = wpt[j];
+            v.x *= wt;
+            v.y *= wt;
+        }
+        return v;
+    };
+    pdl_wait();   // c may come from the previous kernel
+    int Et = 0;   // the tile's unit exponent for int64 totals (several batches)
+    if (multi) {
+        double part = 0.0;
+        for (int i = b + threadIdx.x; i < e; i += NT) {
+            if (!NUASM_IN_RANGE(i, a.nrec, dbg::kSpreadRec)) continue;
+            const double2 v = value_of(i);
+            part += fabs(v.x) + fabs(v.y);
+        }
+        const double St = block_sum(part);
+        Et = dexp(St) + 2;   // St < 2^(Et - 1): the totals stay below 2^61 units
+    }
+    bool started = false, nonfinite = false;
+    for (int i0 = b; i0 < e; i0 += kDfBatch) {
+        RecD r[RPB];
+        double2 val[RPB];
+        double part = 0.0;
+#pragma unroll
+        for (int k = 0; k < RPB; ++k) {
+            const int i = i0 + threadIdx.x + k * NT;
+            val[k] = make_double2(0.0, 0.0);
+            r[k].cell = 0;
+            if (i < e && NUASM_IN_RANGE(i, a.nrec, dbg::kSpreadRec)) {
+                r[k] = rec[i];
+                val[k] = value_of(i);
+                part += fabs(val[k].x) + fabs(val[k].y);
+            }
+        }
+        __syncthreads();   // the previous batch's fold is done before the sum reuses red
+        const double S = block_sum(part);
+        if (S == 0.0) continue;
+        if (!(S <= 1.7976931348623157e308)) {   // infinity or NaN among the values
+            nonfinite = true;
+            break;
+        }
+        const int Eb = dexp(S) + 1;   // S < 2^Eb
+#pragma unroll
+        for (int k = 0; k < RPB; ++k) {
+            const int i = i0 + threadIdx.x + k * NT;
+            if (i >= e) continue;
+            const int lx = int(r[k].cell & 0xffffu) - x0, ly = int(r[k].cell >> 16) - y0;
+            const df vr = df_split(val[k].x, Eb), vi = df_split(val[k].y, Eb);
+            const df xv = df_split(fma(2.0, r[k].fx, -1.0), 0), yv = df_split(fma(2.0, r[k].fy, -1.0), 0);
+            df wx[WMAX];
+#pragma unroll
+            for (int q = 0; q < WMAX; ++q) wx[q] = tap_weight_df(kp.c[q], xv);
+            const int ya = max(0, -ly), yb = min(WMAX, T - ly);
+            const int xa = max(0, -lx), xb = min(WMAX, T - lx);
+#pragma unroll 1
+            for (int qy = ya; qy < yb; ++qy) {
+                const df wyq = tap_weight_df(cs + qy * kDfCoef, yv);
+                const df pr = df_mul(vr, wyq), pi = df_mul(vi, wyq);
+                const int rowi = (ly + qy) * TS + lx;
+#pragma unroll
+                for (int qx = 0; qx < WMAX; ++qx) {
+                    if (qx < xa || qx >= xb) continue;
+                    const int cell = rowi + qx;
+                    if (!NUASM_IN_RANGE(cell, TT, dbg::kSpreadPlane)) continue;
+                    df_quant_add(df_prod(pr, wx[qx]), cell, rh, rl);
+                    df_quant_add(df_prod(pi, wx[qx]), cell, ih, il);
+                }
+            }
+        }
+        __syncthreads();
+        // fold: V = n_h 2^22 + n_l per component, then clear the planes
+        const int sh = Eb - Et + 10;   // units 2^(Eb - 52) to units 2^(Et - 62)
+        for (int i = threadIdx.x; i < T * T; i += NT) {
+            const int yy = i / T, xx = i - yy * T, j = yy * TS + xx;
+            const long long Vr = (static_cast<long long>(rh[j]) << 22) + rl[j];
+            const long long Vi = (static_cast<long long>(ih[j]) << 22) + il[j];
+            rh[j] = 0;
+            rl[j] = 0;
+            ih[j] = 0;
+            il[j] = 0;
+            const int gy = y0 + yy, gx = x0 + xx;
+            if (gy >= a.W || gx >= a.W ||
+                !NUASM_IN_RANGE(gy * (long long)a.Wp + gx, (long long)a.W * a.Wp, dbg::kSpreadWindow))
+                continue;
+            double2* p = &win[size_t(gy) * a.Wp + gx];
+            if (!multi) {
+                *p = make_double2(scaled_int(Vr, Eb - 52), scaled_int(Vi, Eb - 52));
+            } else {
+                long long* q = reinterpret_cast<long long*>(p);
+                auto to_tot = [&](long long V) -> long long {
+                    return sh >= 0 ? V * (1LL << min(sh, 62)) : (V + (1LL << (min(-sh, 62) - 1))) >> min(-sh, 62);
+                };
+                const long long tr = to_tot(Vr), ti = to_tot(Vi);
+                if (started) {
+                    q[0] += tr;
+                    q[1] += ti;
+                } else {
+                    q[0] = tr;
+                    q[1] = ti;
+                }
+            }
+        }
+        started = true;
+    }
+    __syncthreads();
+    // cells the batches did not write: NaN (non-finite values), FP64 from the int64 totals, or zero
+    if (nonfinite || multi || !started) {
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        for (int i = threadIdx.x; i < T * T; i += NT) {
+            const int yy = i / T, xx = i - yy * T;
+            const int gy = y0 + yy, gx = x0 + xx;
+            if (gy >= a.W || gx >= a.W ||
+                !NUASM_IN_RANGE(gy * (long long)a.Wp + gx, (long long)a.W * a.Wp, dbg::kSpreadWindow))
+                continue;
+            double2* p = &win[size_t(gy) * a.Wp + gx];
+            if (nonfinite) {
+                *p = make_double2(nan, nan);
+            } else if (started) {   // several batches
+                const longlong2 t = *reinterpret_cast<const longlong2*>(p);
+                *p = make_double2(scaled_int(t.x, Et - 62), scaled_int(t.y, Et - 62));
+            } else {
+                *p = make_double2(0.0, 0.0);
+            }
+        }
+    }
+}
+
+// FP64-mode interpolation in double-float arithmetic: the interp_kernel
+// schedule (one CTA per tile or chunk, a ring of prefetched records); the
+// tile is staged in FP64, scaled by 2^-s, s the largest exponent among its
+// values (so no value leaves the float range), and split in place into
+// (re.hi, re.lo, im.hi, im.lo) cells of the same 16 bytes.
+template <int WMAX>
+__global__ void __launch_bounds__(kInterpThreads, 2) interp_df_kernel(const RecD* __restrict__ rec,
+                                                                      const int* __restrict__ off,
+                                                                      const int* __restrict__ home,
+                                                                      const int* __restrict__ order,
+                                                                      const int4* __restrict__ items,
+                                                                      const double2* __restrict__ win,
+                                                                      double2* __restrict__ v, GridArgs a,
+                                                                      const KernelPolyDF kp) {
+    extern __shared__ unsigned char smem_raw[];
+    double2* tld = reinterpret_cast<double2*>(smem_raw);
+    float4* tl = reinterpret_cast<float4*>(smem_raw);
+    __shared__ int emax;
+    __shared__ float2 cs[WMAX * kDfCoef];
+    for (int i = threadIdx.x; i < WMAX * kDfCoef; i += kInterpThreads) cs[i] = kp.c[i / kDfCoef][i % kDfCoef];
+    const int T = a.T, TH = T + WMAX - 1;
+    int tile, b, e;
+    if (items) {
+        const int4 it = items[blockIdx.x];
+        tile = it.x;
+        b = it.y;
+        e = it.z;
+    } else {
+        tile = order ? order[blockIdx.x] : blockIdx.x;
+        b = off[tile];
+        e = b + home[tile];
+    }
+    const int THP = halo_pitch(TH, a.skew_of(tile));
+    const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
+    const int x0 = tx * T, y0 = ty * T;
+    pdl_allow_next();
+    RecD pre[kInterpPrefetch];
+#pragma unroll
+    for (int k = 0; k < kInterpPrefetch; ++k) {
+        const int i = b + threadIdx.x + k * kInterpThreads;
+        if (i < e && NUASM_IN_RANGE(i, a.nrec, dbg::kInterpRec)) pre[k] = rec[i];
+    }
+    if (threadIdx.x == 0) emax = -1023;
+    pdl_wait();   // the window comes from the previous kernel
+    __syncthreads();
+    int em = -1023;
+    for (int i = threadIdx.x; i < TH * THP; i += kInterpThreads) {
+        const int yy = i / THP, xx = i - yy * THP;
+        const int gy = y0 + yy, gx = x0 + xx;
+        double2 val = make_double2(0.0, 0.0);
+        if (xx < TH && gy < a.W && gx < a.W) val = win[size_t(gy) * a.Wp + gx];
+        tld[i] = val;
+        em = max(em, max(dexp(val.x), dexp(val.y)));
+    }
+    em = __reduce_max_sync(0xffffffffu, em);
+    if ((threadIdx.x & 31) == 0) atomicMax(&emax, em);
+    __syncthreads();
+    const int sc = min(max(emax, -1022), 1023);
+    for (int i = threadIdx.x; i < TH * THP; i += kInterpThreads) {   // each thread splits the cells it staged
+        const double2 val = tld[i];
+        const df re = df_split(val.x, sc), im = df_split(val.y, sc);
+        tl[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    __syncthreads();
+    const double scale = __longlong_as_double(static_cast<long long>(sc + 1023) << 52);   // 2^sc
+    constexpr int AHEAD = kInterpPrefetch * kInterpThreads;
+    for (int base = b + threadIdx.x; base < e; base += AHEAD) {
+#pragma unroll
+        for (int k = 0; k < kInterpPrefetch; ++k) {
+            const int i = base + k * kInterpThreads;
+            if (i < e) {
+                const RecD r = pre[k];
+                if (i + AHEAD < e && NUASM_IN_RANGE(i + AHEAD, a.nrec, dbg::kInterpRec)) pre[k] = rec[i + AHEAD];
+                interp_point_df<WMAX>(r, tl, THP, x0, y0, kp, cs, scale, v, TH * THP, a.m);
+            }
+        }
+    }
+}
+
 // whether the plan's spreading runs spread_private_kernel or spread_kernel,
 // which take work items (spread_fixed_kernel keeps one CTA per tile)
 bool spread_by_items(const nuasm_plan_s* P) {
@@ -968,6 +1365,35 @@ cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int WMAX> cudaError_t spread_df_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
+    GridArgs a = grid_args(P);
+    const size_t sm = size_t(4) * a.T * plane_stride(a.T, a.max_skew) * sizeof(int);
+    cudaError_t e = set_smem(spread_df_kernel<WMAX>, sm);
+    if (e != cudaSuccess) return e;
+    spread_df_kernel<WMAX><<<P->g.ntiles, 256, sm, st>>>(static_cast<const RecD*>(P->d.rec), P->d.tile_off, P->d.wpt,
+                                                        P->d.tile_order, static_cast<const double2*>(c),
+                                                        static_cast<double2*>(P->d.win), a, P->poly64df);
+    return cudaGetLastError();
+}
+
+template <int WMAX> cudaError_t interp_df_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
+    GridArgs a = grid_args(P);
+    const int TH = a.T + WMAX - 1;
+    int THP = 0;   // the largest staged row pitch over the skews in use
+    for (int k = 0; k <= a.max_skew; k += 2) THP = std::max(THP, halo_pitch(TH, k));
+    if (!a.tskew) THP = halo_pitch(TH, a.skew);
+    const size_t sm = size_t(TH) * THP * sizeof(double2);
+    cudaError_t e = set_smem(interp_df_kernel<WMAX>, sm);
+    if (e != cudaSuccess) return e;
+    const int grid = P->d.interp_items ? P->n_interp_items : P->g.ntiles;
+    e = launch_chained(interp_df_kernel<WMAX>, dim3(grid), dim3(kInterpThreads), sm, st,
+                       static_cast<const RecD*>(P->d.rec), P->d.tile_off, P->d.tile_home, P->d.tile_order,
+                       static_cast<const int4*>(P->d.interp_items), static_cast<const double2*>(P->d.win),
+                       static_cast<double2*>(v), a, P->poly64df);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 template <typename S_, int W_, bool X_> struct GTag {
     using S = S_;
     static constexpr int W = W_;
@@ -982,9 +1408,21 @@ template <bool SPREAD> cudaError_t gridding(const nuasm_plan_s* P, const void* i
         else return interp_impl<typename Tg::S, Tg::W, Tg::X>(P, out, st);
     };
     if (P->f64) {
-        // the FP64 default tolerance (1e-12) gives w = 13: an exact instantiation
+        // double-float gridding for the ES kernel at w = 13 (the FP64 default
+        // tolerance, 1e-12) and w = 11 (1e-10); spreading by whole tiles only
+        if (NUASM_F64_DF && P->g.kernel == NUASM_KERNEL_ES && (P->g.w == 13 || P->g.w == 11)) {
+            if constexpr (SPREAD) {
+                if (!P->d.spread_items)
+                    return P->g.w == 13 ? spread_df_impl<13>(P, in, st) : spread_df_impl<11>(P, in, st);
+            } else {
+                return P->g.w == 13 ? interp_df_impl<13>(P, out, st) : interp_df_impl<11>(P, out, st);
+            }
+        }
+        // the FP64 default tolerance (1e-12) gives w = 13 and a tolerance of
+        // 1e-10 w = 11: exact instantiations
 #if NUASM_F64_EXACT13
         if (P->g.w == 13) return run(GTag<double, 13, true>{});
+        if (P->g.w == 11) return run(GTag<double, 11, true>{});
 #endif
         if (P->g.w <= 8) return run(GTag<double, 8, false>{});
         return P->g.w <= 16 ? run(GTag<double, 16, false>{}) : run(GTag<double, kPolyMaxW, false>{});

@@ -533,6 +533,14 @@ void fit_poly(const Geometry& g, int d, Poly* kp) {
 void fit_kernel_poly(const Geometry& g, KernelPoly* kp) { fit_poly<KernelPoly, float>(g, g.w + 1, kp); }
 void fit_kernel_poly64(const Geometry& g, KernelPoly64* kp) { fit_poly<KernelPoly64, double>(g, kPoly64Deg, kp); }
 
+void split_kernel_poly64(const KernelPoly64& kp, KernelPolyDF* out) {
+    for (int i = 0; i < kPolyMaxW; ++i)
+        for (int k = 0; k < kPolyMaxD; ++k) {
+            const float hi = float(kp.c[i][k]);
+            out->c[i][k] = float2{hi, float(kp.c[i][k] - double(hi))};
+        }
+}
+
 void free_tables(HostTables* t) {
     delete[] t->t1x; delete[] t->t1y; delete[] t->t2x; delete[] t->t2y; delete[] t->t3x; delete[] t->t3y;
     delete[] t->s; delete[] t->tw;

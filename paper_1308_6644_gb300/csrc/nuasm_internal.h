@@ -41,6 +41,12 @@ struct KernelPoly64 {
     double c[kPolyMaxW][kPolyMaxD];
     int deg;
 };
+// The FP64 coefficients as pairs of floats (x: the coefficient rounded to
+// float, y: the rounded remainder), for FP64-mode gridding in double-float
+// arithmetic.
+struct KernelPolyDF {
+    float2 c[kPolyMaxW][kPolyMaxD];
+};
 
 // Host tables in FP64 (complex as re/im pairs), natural N'-bin order.
 struct HostTables {
@@ -102,6 +108,7 @@ struct nuasm_plan_s {
     int n_spread_items = 0;     // entries of d.spread_items
     nuasm::KernelPoly poly{};   // kernel taps as polynomials (F32 gridding)
     nuasm::KernelPoly64 poly64{};   // the same in FP64 (F64 gridding)
+    nuasm::KernelPolyDF poly64df{};   // poly64 as float pairs (F64 gridding in double-float arithmetic)
     int64_t device_bytes = 0;
     nuasm::PlanDevice d;
     // profiling
@@ -131,6 +138,7 @@ void twiddle(int i, int G, double* re, double* im);
 double nonsep_rmax(const nuasm_params_t& p, const Geometry& g);
 void fit_kernel_poly(const Geometry& g, KernelPoly* kp);
 void fit_kernel_poly64(const Geometry& g, KernelPoly64* kp);
+void split_kernel_poly64(const KernelPoly64& kp, KernelPolyDF* out);
 nuasm_status validate(const nuasm_params_t& p, int64_t m, nuasm_params_t* resolved);
 bool kernel_shape(double tol, int prec, int kernel, int* w, double* beta);
 double kernel_value(const Geometry& g, double t);

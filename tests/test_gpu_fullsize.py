@@ -42,11 +42,12 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _solve(P, w, type_, values, weights=None, kind=None, prec="f32", z=None):
+def _solve(P, w, type_, values, weights=None, kind=None, prec="f32", z=None, tol=0.0):
     import torch
     kind = kind or w.kind
     cdt, tdt = (np.complex128, torch.complex128) if prec == "f64" else (np.complex64, torch.complex64)
-    params = P.make_params(w.n, w.pitch, w.lam, w.z if z is None else z, ox=w.ox, oy=w.oy, kind=kind, prec=prec)
+    params = P.make_params(w.n, w.pitch, w.lam, w.z if z is None else z, ox=w.ox, oy=w.oy, kind=kind, prec=prec,
+                           tol=tol)
     plan = P.nuasm_plan(params, _dev(w.x), _dev(w.y), None if weights is None else _dev(weights))
     try:
         src = _dev(np.asarray(values).astype(cdt).reshape(-1))
@@ -126,13 +127,15 @@ def test_nufresnel2_clustered_full_size(P):
     assert_close(got[idx], ref, TOL)
 
 
-def test_nufresnel2_clustered_full_size_fp64(P):
-    """NU-FRE_2 in FP64 mode (complex128 throughout, ES kernel at 1e-12) on
-    the same 4,194,304 clustered points: 2048 sampled points against the
-    oracle at rel-L2 1e-10, and every point against the Gaussian-beam closed
-    form at the accuracy of the sampled Fresnel transform itself."""
+@pytest.mark.parametrize("plan_tol", [0.0, TOL64])
+def test_nufresnel2_clustered_full_size_fp64(P, plan_tol):
+    """NU-FRE_2 in FP64 mode (complex128 throughout; ES kernel at the FP64
+    default 1e-12, 13 taps, and at a plan tolerance of 1e-10, 11 taps) on the
+    same 4,194,304 clustered points: 2048 sampled points against the oracle
+    at rel-L2 1e-10, and every point against the Gaussian-beam closed form at
+    the accuracy of the sampled Fresnel transform itself."""
     w = _fresnel_clustered(2)
-    got = _solve(P, w, 2, w.values, prec="f64")
+    got = _solve(P, w, 2, w.values, prec="f64", tol=plan_tol)
     idx = np.sort(np.random.default_rng(14).choice(w.m, 2048, replace=False))
     ref = O.nudft_type2(_clustered_spectrum(False), w.x[idx] / w.pitch, w.y[idx] / w.pitch, 2 * w.n)
     assert_close(got[idx], ref, TOL64)
@@ -160,18 +163,19 @@ def test_nufresnel1_full_size_warped_lattice_closed_form(P):
     assert_close(got, gaussian_fresnel(gx, gy, lam, z, w0), TOL)
 
 
-@pytest.mark.parametrize("prec,tol", [("f32", TOL), ("f64", TOL64)])
-def test_nufresnel1_clustered_full_size_sparse_sources(P, prec, tol):
+@pytest.mark.parametrize("prec,tol,plan_tol", [("f32", TOL, 0.0), ("f64", TOL64, 0.0), ("f64", TOL64, TOL64)])
+def test_nufresnel1_clustered_full_size_sparse_sources(P, prec, tol, plan_tol):
     """NU-FRE_1 on the 4,194,304 clustered points with 4096 non-zero sources
     (drawn from the point set, so ~3/4 in the clusters): every output pixel
     against the oracle (the full launch configuration with an oracle cost of
-    4096 points), in FP32 and in FP64 mode."""
+    4096 points), in FP32 and in FP64 mode (at the default plan tolerance and
+    at 1e-10)."""
     w = _fresnel_clustered(1)
     rng = np.random.default_rng(13)
     c = np.zeros(w.m, np.complex128)
     nz = np.sort(rng.choice(w.m, 4096, replace=False))
     c[nz] = rng.normal(size=nz.size) + 1j * rng.normal(size=nz.size)
-    got = _solve(P, w, 1, c, prec=prec).reshape(w.n, w.n)
+    got = _solve(P, w, 1, c, prec=prec, tol=plan_tol).reshape(w.n, w.n)
     p = dict(n=w.n, pitch=w.pitch, lam=w.lam, z=w.z, kind="fresnel")
     cin = c[nz].astype(np.complex64) if prec == "f32" else c[nz]
     ref = O.diffraction_type1(w.x[nz], w.y[nz], cin, p, h=_clustered_transfer())

@@ -374,7 +374,11 @@ def test_autotune_tile_picks_a_supported_side(P):
 def test_split_work_knobs_keep_results(P):
     """interp_chunk splits dense tiles' interpolation over CTAs (type 2 equal
     bit for bit); spread_chunk splits or keeps dense tiles in spreading
-    (type 1 equal to rounding: the chunks add into the window in any order)."""
+    (type 1 equal to rounding: the chunks add into the window in any order;
+    in FP64 whole tiles spread in double-float arithmetic with exact integer
+    sums at a quantum of 2^-52 of a 512-record batch's magnitude, split tiles
+    with FP64 atomics, so the two agree to about 1e-13, below the FP64
+    default tolerance 1e-12)."""
     rng = np.random.default_rng(46)
     n, pitch, m = 64, 10e-6, 30000
     x = WL.clamp_window(rng.normal(0, 40e-6, m), n, pitch)
@@ -390,8 +394,50 @@ def test_split_work_knobs_keep_results(P):
         a = run_gpu(P, "asm", 1, prec, n, values=c, tile=tile, spread_chunk=-1, **kw)
         b = run_gpu(P, "asm", 1, prec, n, values=c, tile=tile, spread_chunk=32, **kw)
         d = run_gpu(P, "asm", 1, prec, n, values=c, tile=tile, **kw)
-        lim = 1e-6 if prec == "f32" else 1e-13
+        lim = 1e-6 if prec == "f32" else 1e-12
         assert O.rel_l2(b, a) < lim and O.rel_l2(d, a) < lim
+
+
+@pytest.mark.parametrize("kind", ["asm", "fresnel"])
+@pytest.mark.parametrize("tile,tol", [(16, 0.0), (64, 0.0), (32, 1e-10), (64, 1e-10)])
+def test_fp64_double_float_spreading(P, kind, tile, tol):
+    """FP64-mode spreading on the double-float path (ES kernel at w = 13, the
+    FP64 default, and w = 11, tolerance 1e-10; whole tiles): a cluster and a
+    uniform background give tiles of one record batch and of several, the
+    values span twelve decades and carry point weights.  rel-L2 1e-10 against
+    the oracle, and every pixel within 10 x 1e-10 of the RMS."""
+    rng = np.random.default_rng(61)
+    n, pitch, m = 64, 10e-6, 6000
+    half = 0.5 * n * pitch
+
+    def coord():
+        return WL.clamp_window(np.concatenate([rng.normal(0, 30e-6, m // 2),
+                                               rng.uniform(-half, half, m - m // 2)]), n, pitch)
+    x, y = coord(), coord()
+    c = rng.normal(size=m) + 1j * rng.normal(size=m)
+    c[:10] *= 1e6
+    c[10:40] *= 1e-6
+    wts = rng.uniform(0.5, 1.5, m)
+    kw = dict(pitch=pitch, lam=633e-9, z=0.03, ox=10e-6)
+    got = run_gpu(P, kind, 1, "f64", n, x=x, y=y, values=c, w=wts, tile=tile, tol=tol, spread_chunk=-1, **kw)
+    ref = run_oracle(kind, 1, n, x=x, y=y, values=c, w=wts, prec="f64", **kw)
+    assert O.rel_l2(got, ref) < TOL["f64"]
+    assert np.max(np.abs(got - ref)) <= 10 * TOL["f64"] * np.linalg.norm(ref) / np.sqrt(ref.size)
+
+
+def test_fp64_double_float_spreading_zero_and_non_finite(P):
+    """The double-float FP64 spreading: an all-zero input gives zeros, and an
+    infinity or a NaN among the values reaches the output."""
+    n, pitch, m = 64, 10e-6, 4000
+    x, y, c = random_case(62, n, m, pitch=pitch)
+    kw = dict(pitch=pitch, lam=633e-9, z=0.03, tile=64, spread_chunk=-1)
+    zero = run_gpu(P, "asm", 1, "f64", n, x=x, y=y, values=np.zeros(m), **kw)
+    assert not np.any(zero)
+    for bad in (np.nan, np.inf):
+        cb = c.copy()
+        cb[100] = bad
+        out = run_gpu(P, "asm", 1, "f64", n, x=x, y=y, values=cb, **kw)
+        assert not np.all(np.isfinite(out))
 
 
 def test_autotuner_returns_working_parameters(P):
