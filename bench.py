@@ -193,6 +193,9 @@ def plan_table_bytes(info: dict, type_: int = 2, eb: int = 8) -> dict:
 
 # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64: the part's nominal rate
 ALU_PEAK_TFLOPS = {False: 152 * 128 * 2 * 2.07e9 / 1e12, True: 1.25}
+# FP64 gridding in double-float arithmetic: one double-float multiply-add (2 flops) takes
+# 12 FP32-pipe instructions (product with its FMA error term, two-sum, carries)
+DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12
 
 
 def stage_flops(info: dict, m: int, type_: int = 2, f64: bool = False) -> dict:
@@ -218,13 +221,18 @@ def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
     v, s = ("double2", "double") if f64 else ("float2", "float")
     w = info["kernel_width"]
     if f64:
-        tap = "double, 13, true" if w == 13 else f"double, {8 if w <= 8 else (16 if w <= 16 else 26)}, false"
+        tap = f"double, {w}, true" if w in (11, 13) else f"double, {8 if w <= 8 else (16 if w <= 16 else 26)}, false"
     else:
         tap = f"float, {w}, true" if 4 <= w <= 8 else f"float, {16 if w <= 16 else 26}, false"
     tma = not f64 and 512 <= info["n_pad"] <= 4096          # folded column passes
     tma_wide = not f64 and info["n_pad"] == 4096              # unfolded ones too
     tile = info.get("tile", 64)
-    if f64:
+    interp = f"interp_kernel<{tap}>"
+    if f64 and info.get("double_float"):
+        interp = f"interp_df_kernel<{w}>"
+    if f64 and info.get("double_float") and not info.get("spread_split_ctas"):
+        spread = f"spread_df_kernel<{w}>"
+    elif f64:
         spread = f"spread_private_kernel<{tap}>" if tile <= 16 else f"spread_kernel<{tap}>"
     elif tile <= 32:
         spread = f"spread_private_kernel<{tap}>"
@@ -234,7 +242,7 @@ def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
     return {"col_fwd": f"col_tma_kernel<{lognp}, 2>" if tma_wide else f"col_kernel<{v}, {lognp}, 2>",
             "row_t2": f"row_t2_kernel<{v}, {lognp}>",
             "col_inv_fold": f"col_tma_kernel<{lognp}, 3>" if tma else f"col_kernel<{v}, {lognp}, 3>",
-            "interp": f"interp_kernel<{tap}>", "spread": spread,
+            "interp": interp, "spread": spread,
             "col_fwd_fold": f"col_tma_kernel<{lognp}, 0>" if tma else f"col_kernel<{v}, {lognp}, 0>",
             "row_t1": f"row_t1_kernel<{v}, {lognp}>",
             "col_inv": f"col_tma_kernel<{lognp}, 1>" if tma_wide else f"col_kernel<{v}, {lognp}, 1>"}[stage]
@@ -549,12 +557,18 @@ def run_ours(args):
     tbytes = plan_table_bytes(info, wl.type, eb)
     sflops = stage_flops(info, wl.m, wl.type, f64)
     peak, peak_kind = hbm_peak()
-    alu_peak = ALU_PEAK_TFLOPS[f64]
+    def alu_peak_of(stage):
+        """The arithmetic roof of a stage: FP32, FP64, or double-float for FP64 gridding on the FP32 pipe."""
+        if f64 and "_df_" in kernel_of_stage(stage, info, f64):
+            return DF_PEAK_TFLOPS
+        return ALU_PEAK_TFLOPS[f64]
+
     stages = {}
     for name, b in sbytes.items():
         ms, cnt = prof[name]
         if cnt:
             avg = ms / cnt
+            alu_peak = alu_peak_of(name)
             gbs, tfs = b / (avg * 1e-3) / 1e9, sflops[name] / (avg * 1e-3) / 1e12
             # the binding roof: the one this stage's algorithmic work takes longest on
             bound = "alu" if sflops[name] / (alu_peak * 1e12) > b / (peak * 1e9) else "hbm"
@@ -564,8 +578,11 @@ def run_ours(args):
     dom = max(stages, key=lambda s: stages[s]["ms"])
     d = stages[dom]
     if d["bound"] == "alu":
-        roofline = {"bound": "alu", "achieved": d["tfs"], "peak": alu_peak, "unit": "TFLOP/s", "frac": d["frac"],
-                    "peak_source": ("FP64 nominal rate" if f64 else
+        dom_peak = alu_peak_of(dom)
+        roofline = {"bound": "alu", "achieved": d["tfs"], "peak": dom_peak, "unit": "TFLOP/s", "frac": d["frac"],
+                    "peak_source": ("double-float on the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz / 12 "
+                                    "instructions per 2-flop multiply-add" if dom_peak == DF_PEAK_TFLOPS else
+                                    "FP64 nominal rate" if f64 else
                                     "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz")}
     else:
         roofline = {"bound": "hbm", "achieved": d["gbs"], "peak": peak, "unit": "GB/s", "frac": d["frac"],

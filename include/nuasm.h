@@ -83,7 +83,10 @@ typedef enum {
 typedef enum {
     NUASM_PREC_F32_F64PHASE = 0,  /* complex64 data; phases from FP64 tables and
                                      compensated (double-float) FP32 arithmetic */
-    NUASM_PREC_F64 = 1            /* complex128 data and FP64 arithmetic throughout */
+    NUASM_PREC_F64 = 1            /* complex128 data; FP64 arithmetic, except that gridding with
+                                     the ES kernel at w = 11 or 13 runs in double-float arithmetic
+                                     (pairs of FP32 values, about 47 significant bits; see
+                                     nuasm_plan_info_t.double_float) */
 } nuasm_prec;
 
 /* Problem definition (Eq. 4 / Eq. 5 parameters).  Plain old data. */
@@ -148,6 +151,12 @@ typedef struct {
     int32_t bank_skew;         /* shared-memory bank skew of the gridding tiles (0 or 2; 0 .. 8
                                   in builds with a skew per tile, then the one most tiles
                                   use), chosen from the points' distribution */
+    int32_t spread_split_ctas; /* CTAs of type-1 spreading over split dense tiles (0: one CTA
+                                  per whole tile) */
+    int32_t double_float;      /* 1: FP64 gridding runs in double-float arithmetic (pairs of
+                                  FP32 values, about 47 significant bits) on the FP32 pipe --
+                                  FP64 plans with the ES kernel at w = 11 or 13; spreading
+                                  then takes whole tiles only (split tiles keep FP64) */
 } nuasm_plan_info_t;
 
 /*

@@ -652,6 +652,8 @@ nuasm_status nuasm_plan_info(nuasm_plan_t plan, nuasm_plan_info_t* info) {
         (plan->d.etab ? int64_t(etab_elems(plan->g, &pitch) * (plan->f64 ? 16 : 8)) : 0) +
         (plan->d.etab2 ? int64_t(plan->g.np / 2 + 1) * plan->g.np * 8 : 0);
     info->bank_skew = plan->skew;
+    info->spread_split_ctas = plan->d.spread_items ? plan->n_spread_items : 0;
+    info->double_float = gridding_double_float(plan) ? 1 : 0;
     return NUASM_OK;
 }
 

@@ -873,14 +873,12 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
 }
 
 // ---------------------------------------------------------------- FP64 mode in double-float arithmetic
-// FP64-mode gridding with the ES kernel at its exact widths runs on the FP32
-// pipe, whose rate is 64 times that of the FP64 pipe here: window values and
-// tap weights are unevaluated sums hi + lo of two floats (47 significant
-// bits), products go through FMA-based error-free transforms, and FP64
-// arithmetic is left to once per point or per staged cell.
-#ifndef NUASM_F64_DF
-#define NUASM_F64_DF 1   // 0: FP64 gridding on the FP64 pipe throughout
-#endif
+// FP64-mode gridding with the ES kernel at its exact widths (see
+// gridding_double_float) runs on the FP32 pipe, whose rate is 64 times that
+// of the FP64 pipe here: window values and tap weights are unevaluated sums
+// hi + lo of two floats (47 significant bits), products go through FMA-based
+// error-free transforms, and FP64 arithmetic is left to once per point or
+// per staged cell.
 
 // x 2^-s as hi + lo: hi the leading 24 significant bits of x (truncated), lo
 // the next 23, by integer operations on the bits (no FP64 arithmetic), so the
@@ -986,6 +984,11 @@ __device__ __forceinline__ void interp_point_df(const RecD& r, const float4* __r
 // sum is not finite makes the tile's cells NaN (so do the FFTs of any
 // window with such a cell).
 constexpr int kDfBatch = 512;
+#ifndef NUASM_DF_SPREAD_MINB
+// CTAs per SM the register budget of spread_df_kernel is set for (4M
+// clustered FP64 points: 3.04 ms at 2, 2.85 ms at 3)
+#define NUASM_DF_SPREAD_MINB 3
+#endif
 // a b without renormalisation (the low part is the product's exact error
 // plus the cross terms)
 __device__ __forceinline__ df df_prod(df a, df b) {
@@ -1014,7 +1017,7 @@ __device__ __forceinline__ double scaled_int(long long V, int k) {
 }
 
 template <int WMAX>
-__global__ void __launch_bounds__(256, 2) spread_df_kernel(const RecD* __restrict__ rec, const int* __restrict__ off,
+__global__ void __launch_bounds__(256, NUASM_DF_SPREAD_MINB) spread_df_kernel(const RecD* __restrict__ rec, const int* __restrict__ off,
                                                           const double* __restrict__ wpt,
                                                           const int* __restrict__ order,
                                                           const double2* __restrict__ c, double2* __restrict__ win,
@@ -1410,7 +1413,7 @@ template <bool SPREAD> cudaError_t gridding(const nuasm_plan_s* P, const void* i
     if (P->f64) {
         // double-float gridding for the ES kernel at w = 13 (the FP64 default
         // tolerance, 1e-12) and w = 11 (1e-10); spreading by whole tiles only
-        if (NUASM_F64_DF && P->g.kernel == NUASM_KERNEL_ES && (P->g.w == 13 || P->g.w == 11)) {
+        if (gridding_double_float(P)) {
             if constexpr (SPREAD) {
                 if (!P->d.spread_items)
                     return P->g.w == 13 ? spread_df_impl<13>(P, in, st) : spread_df_impl<11>(P, in, st);

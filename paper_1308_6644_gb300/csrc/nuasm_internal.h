@@ -120,6 +120,16 @@ struct nuasm_plan_s {
 
 namespace nuasm {
 
+// FP64 gridding in double-float arithmetic on the FP32 pipe (gridding.cu):
+// FP64 plans with the ES kernel at its exact FP64 widths (w = 13, the default
+// tolerance 1e-12; w = 11, 1e-10); spreading by whole tiles only.
+#ifndef NUASM_F64_DF
+#define NUASM_F64_DF 1   // 0: FP64 gridding on the FP64 pipe throughout
+#endif
+inline bool gridding_double_float(const nuasm_plan_s* P) {
+    return NUASM_F64_DF && P->f64 && P->g.kernel == NUASM_KERNEL_ES && (P->g.w == 11 || P->g.w == 13);
+}
+
 // Gauss-Legendre quadrature of the kernel on [0, w/2] for its Fourier transform.
 struct KernelQuad {
     static constexpr int kMax = 2 * kPolyMaxW + 48;

@@ -54,7 +54,8 @@ class PlanInfo(ctypes.Structure):
                 ("band_lo_y", ctypes.c_int32), ("band_hi_y", ctypes.c_int32),
                 ("points", ctypes.c_int64), ("records", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("phase_table_bytes", ctypes.c_int64),
-                ("bank_skew", ctypes.c_int32)]
+                ("bank_skew", ctypes.c_int32), ("spread_split_ctas", ctypes.c_int32),
+                ("double_float", ctypes.c_int32)]
 
 
 class BatchItem(ctypes.Structure):

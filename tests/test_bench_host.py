@@ -64,9 +64,21 @@ def test_stage_flops_model():
     (64, False, 13, "spread_fixed_kernel<16, false, 2>"),
     (16, True, 13, "spread_private_kernel<double, 13, true>"),
     (64, True, 13, "spread_kernel<double, 13, true>"),
+    (64, True, 11, "spread_kernel<double, 11, true>"),
 ])
 def test_spreading_kernel_names(tile, f64, w, want):
     assert bench.kernel_of_stage("spread", dict(n_pad=2048, kernel_width=w, tile=tile), f64) == want
+
+
+@pytest.mark.parametrize("split,want", [(0, "spread_df_kernel<13>"), (40, "spread_private_kernel<double, 13, true>")])
+def test_double_float_kernel_names(split, want):
+    """FP64 plans on the double-float path name the double-float kernels, and
+    their gridding stages take the double-float roof (FP32 lane rate / 12
+    instructions per 2-flop multiply-add)."""
+    info = dict(n_pad=2048, kernel_width=13, tile=16, double_float=1, spread_split_ctas=split)
+    assert bench.kernel_of_stage("spread", info, True) == want
+    assert bench.kernel_of_stage("interp", info, True) == "interp_df_kernel<13>"
+    assert bench.DF_PEAK_TFLOPS == pytest.approx(152 * 128 * 2.07e9 / 6 / 1e12)
 
 
 def test_column_kernel_names_follow_the_tma_rule():

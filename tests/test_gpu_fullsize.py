@@ -129,7 +129,7 @@ def test_nufresnel2_clustered_full_size(P):
 
 @pytest.mark.parametrize("plan_tol", [0.0, TOL64])
 def test_nufresnel2_clustered_full_size_fp64(P, plan_tol):
-    """NU-FRE_2 in FP64 mode (complex128 throughout; ES kernel at the FP64
+    """NU-FRE_2 in FP64 mode (complex128 data, double-float gridding; ES kernel at the FP64
     default 1e-12, 13 taps, and at a plan tolerance of 1e-10, 11 taps) on the
     same 4,194,304 clustered points: 2048 sampled points against the oracle
     at rel-L2 1e-10, and every point against the Gaussian-beam closed form at
