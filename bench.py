@@ -230,7 +230,7 @@ def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
     interp = f"interp_kernel<{tap}>"
     if f64 and info.get("double_float"):
         interp = f"interp_df_kernel<{w}>"
-    if f64 and info.get("double_float") and not info.get("spread_split_ctas"):
+    if f64 and info.get("double_float"):
         spread = f"spread_df_kernel<{w}>"
     elif f64:
         spread = f"spread_private_kernel<{tap}>" if tile <= 16 else f"spread_kernel<{tap}>"

@@ -155,8 +155,7 @@ typedef struct {
                                   per whole tile) */
     int32_t double_float;      /* 1: FP64 gridding runs in double-float arithmetic (pairs of
                                   FP32 values, about 47 significant bits) on the FP32 pipe --
-                                  FP64 plans with the ES kernel at w = 11 or 13; spreading
-                                  then takes whole tiles only (split tiles keep FP64) */
+                                  FP64 plans with the ES kernel at w = 11 or 13 */
 } nuasm_plan_info_t;
 
 /*

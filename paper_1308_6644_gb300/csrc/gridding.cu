@@ -969,7 +969,7 @@ __device__ __forceinline__ void interp_point_df(const RecD& r, const float4* __r
 }
 
 // FP64-mode spreading in double-float arithmetic with exact integer sums,
-// one CTA per whole tile (split tiles keep the FP64 kernels).  Records go in
+// one CTA per whole tile or per chunk of a split tile.  Records go in
 // batches of kDfBatch; a batch's values are scaled by 2^-E, S = sum(|re| +
 // |im|) < 2^E over the batch (weights included), so every scaled tap
 // contribution p = v wy wx is at most 1 and a batch adds at most 1 at any
@@ -980,10 +980,14 @@ __device__ __forceinline__ void interp_point_df(const RecD& r, const float4* __r
 // n_h 2^22 + n_l (units 2^(E-52)); a tile with one batch writes V 2^(E-52)
 // as FP64, one with several adds V into int64 totals held in its own window
 // cells at the unit 2^(Et-62), Et from the tile's whole sum (a first pass
-// over its records), and converts them to FP64 at the end.  A batch whose
+// over its records), and converts them to FP64 at the end; a chunk adds each
+// batch's V 2^(E-52) into the cleared window with FP64 atomics.  A batch whose
 // sum is not finite makes the tile's cells NaN (so do the FFTs of any
 // window with such a cell).
 constexpr int kDfBatch = 512;
+#ifndef NUASM_DF_SPLIT
+#define NUASM_DF_SPLIT 1   // 0: split tiles keep the FP64 spreading kernels
+#endif
 #ifndef NUASM_DF_SPREAD_MINB
 // CTAs per SM the register budget of spread_df_kernel is set for (4M
 // clustered FP64 points: 3.04 ms at 2, 2.85 ms at 3)
@@ -1021,13 +1025,26 @@ __global__ void __launch_bounds__(256, NUASM_DF_SPREAD_MINB) spread_df_kernel(co
                                                           const double* __restrict__ wpt,
                                                           const int* __restrict__ order,
                                                           const double2* __restrict__ c, double2* __restrict__ win,
-                                                          GridArgs a, const KernelPolyDF kp) {
+                                                          GridArgs a, const KernelPolyDF kp,
+                                                          const int4* __restrict__ items) {
     constexpr int NT = 256, RPB = kDfBatch / NT;
     extern __shared__ unsigned char smem_raw[];
     __shared__ float2 cs[WMAX * kDfCoef];
     __shared__ double red[NT / 32];
     __shared__ double bsum;
-    const int tile = order ? order[blockIdx.x] : blockIdx.x;
+    int tile, b, e;
+    bool chunked = false;
+    if (items) {   // a chunk of a tile's records: several CTAs add into the tile (window cleared)
+        const int4 it = items[blockIdx.x];
+        tile = it.x;
+        b = it.y;
+        e = it.z;
+        chunked = it.w != 0;
+    } else {       // a whole tile, heaviest tiles first
+        tile = order ? order[blockIdx.x] : blockIdx.x;
+        b = off[tile];
+        e = off[tile + 1];
+    }
     const int T = a.T, TS = plane_stride(T, a.skew_of(tile)), TT = T * TS;
     int* rh = reinterpret_cast<int*>(smem_raw);
     int* rl = rh + TT;
@@ -1043,9 +1060,8 @@ __global__ void __launch_bounds__(256, NUASM_DF_SPREAD_MINB) spread_df_kernel(co
     }
     const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
     const int x0 = tx * T, y0 = ty * T;
-    const int b = off[tile], e = off[tile + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool multi = e - b > kDfBatch;
+    const bool multi = !chunked && e - b > kDfBatch;   // int64 totals in the tile's own cells
     // block sum of one double per thread
     auto block_sum = [&](double part) -> double {
 #pragma unroll
@@ -1151,7 +1167,10 @@ __global__ void __launch_bounds__(256, NUASM_DF_SPREAD_MINB) spread_df_kernel(co
                 !NUASM_IN_RANGE(gy * (long long)a.Wp + gx, (long long)a.W * a.Wp, dbg::kSpreadWindow))
                 continue;
             double2* p = &win[size_t(gy) * a.Wp + gx];
-            if (!multi) {
+            if (chunked) {   // FP64 atomic adds of this batch's exact sums
+                if (Vr) atomicAdd(&p->x, scaled_int(Vr, Eb - 52));
+                if (Vi) atomicAdd(&p->y, scaled_int(Vi, Eb - 52));
+            } else if (!multi) {
                 *p = make_double2(scaled_int(Vr, Eb - 52), scaled_int(Vi, Eb - 52));
             } else {
                 long long* q = reinterpret_cast<long long*>(p);
@@ -1171,8 +1190,9 @@ __global__ void __launch_bounds__(256, NUASM_DF_SPREAD_MINB) spread_df_kernel(co
         started = true;
     }
     __syncthreads();
-    // cells the batches did not write: NaN (non-finite values), FP64 from the int64 totals, or zero
-    if (nonfinite || multi || !started) {
+    // cells the batches did not write: NaN (non-finite values), FP64 from the
+    // int64 totals, or zero (a chunk leaves the cleared window to the others)
+    if (nonfinite || multi || (!started && !chunked)) {
         const double nan = __longlong_as_double(0x7ff8000000000000LL);
         for (int i = threadIdx.x; i < T * T; i += NT) {
             const int yy = i / T, xx = i - yy * T;
@@ -1370,12 +1390,15 @@ cudaError_t interp_impl(const nuasm_plan_s* P, void* v, cudaStream_t st) {
 
 template <int WMAX> cudaError_t spread_df_impl(const nuasm_plan_s* P, const void* c, cudaStream_t st) {
     GridArgs a = grid_args(P);
-    const size_t sm = size_t(4) * a.T * plane_stride(a.T, a.max_skew) * sizeof(int);
-    cudaError_t e = set_smem(spread_df_kernel<WMAX>, sm);
+    const int4* items = P->d.spread_items;   // chunks of split tiles add into a cleared window
+    cudaError_t e = items ? cudaMemsetAsync(P->d.win, 0, ws_win_elems(P->g) * sizeof(double2), st) : cudaSuccess;
     if (e != cudaSuccess) return e;
-    spread_df_kernel<WMAX><<<P->g.ntiles, 256, sm, st>>>(static_cast<const RecD*>(P->d.rec), P->d.tile_off, P->d.wpt,
-                                                        P->d.tile_order, static_cast<const double2*>(c),
-                                                        static_cast<double2*>(P->d.win), a, P->poly64df);
+    const size_t sm = size_t(4) * a.T * plane_stride(a.T, a.max_skew) * sizeof(int);
+    if ((e = set_smem(spread_df_kernel<WMAX>, sm)) != cudaSuccess) return e;
+    const int grid = items ? P->n_spread_items : P->g.ntiles;
+    spread_df_kernel<WMAX><<<grid, 256, sm, st>>>(static_cast<const RecD*>(P->d.rec), P->d.tile_off, P->d.wpt,
+                                                  P->d.tile_order, static_cast<const double2*>(c),
+                                                  static_cast<double2*>(P->d.win), a, P->poly64df, items);
     return cudaGetLastError();
 }
 
@@ -1415,7 +1438,7 @@ template <bool SPREAD> cudaError_t gridding(const nuasm_plan_s* P, const void* i
         // tolerance, 1e-12) and w = 11 (1e-10); spreading by whole tiles only
         if (gridding_double_float(P)) {
             if constexpr (SPREAD) {
-                if (!P->d.spread_items)
+                if (NUASM_DF_SPLIT || !P->d.spread_items)
                     return P->g.w == 13 ? spread_df_impl<13>(P, in, st) : spread_df_impl<11>(P, in, st);
             } else {
                 return P->g.w == 13 ? interp_df_impl<13>(P, out, st) : interp_df_impl<11>(P, out, st);

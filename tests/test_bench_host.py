@@ -70,7 +70,7 @@ def test_spreading_kernel_names(tile, f64, w, want):
     assert bench.kernel_of_stage("spread", dict(n_pad=2048, kernel_width=w, tile=tile), f64) == want
 
 
-@pytest.mark.parametrize("split,want", [(0, "spread_df_kernel<13>"), (40, "spread_private_kernel<double, 13, true>")])
+@pytest.mark.parametrize("split,want", [(0, "spread_df_kernel<13>"), (40, "spread_df_kernel<13>")])
 def test_double_float_kernel_names(split, want):
     """FP64 plans on the double-float path name the double-float kernels, and
     their gridding stages take the double-float roof (FP32 lane rate / 12

@@ -399,10 +399,12 @@ def test_split_work_knobs_keep_results(P):
 
 
 @pytest.mark.parametrize("kind", ["asm", "fresnel"])
-@pytest.mark.parametrize("tile,tol", [(16, 0.0), (64, 0.0), (32, 1e-10), (64, 1e-10)])
-def test_fp64_double_float_spreading(P, kind, tile, tol):
+@pytest.mark.parametrize("tile,tol,chunk", [(16, 0.0, -1), (64, 0.0, -1), (32, 1e-10, -1), (64, 1e-10, -1),
+                                            (16, 0.0, 64), (64, 1e-10, 700)])
+def test_fp64_double_float_spreading(P, kind, tile, tol, chunk):
     """FP64-mode spreading on the double-float path (ES kernel at w = 13, the
-    FP64 default, and w = 11, tolerance 1e-10; whole tiles): a cluster and a
+    FP64 default, and w = 11, tolerance 1e-10), by whole tiles and with dense
+    tiles split into chunks (one batch or several per chunk): a cluster and a
     uniform background give tiles of one record batch and of several, the
     values span twelve decades and carry point weights.  rel-L2 1e-10 against
     the oracle, and every pixel within 10 x 1e-10 of the RMS."""
@@ -419,7 +421,7 @@ def test_fp64_double_float_spreading(P, kind, tile, tol):
     c[10:40] *= 1e-6
     wts = rng.uniform(0.5, 1.5, m)
     kw = dict(pitch=pitch, lam=633e-9, z=0.03, ox=10e-6)
-    got = run_gpu(P, kind, 1, "f64", n, x=x, y=y, values=c, w=wts, tile=tile, tol=tol, spread_chunk=-1, **kw)
+    got = run_gpu(P, kind, 1, "f64", n, x=x, y=y, values=c, w=wts, tile=tile, tol=tol, spread_chunk=chunk, **kw)
     ref = run_oracle(kind, 1, n, x=x, y=y, values=c, w=wts, prec="f64", **kw)
     assert O.rel_l2(got, ref) < TOL["f64"]
     assert np.max(np.abs(got - ref)) <= 10 * TOL["f64"] * np.linalg.norm(ref) / np.sqrt(ref.size)
