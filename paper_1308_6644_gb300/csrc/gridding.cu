@@ -973,8 +973,8 @@ __device__ __forceinline__ void interp_point_df(const RecD& r, const float4* __r
 // batches of kDfBatch; a batch's values are scaled by 2^-E, S = sum(|re| +
 // |im|) < 2^E over the batch (weights included), so every scaled tap
 // contribution p = v wy wx is at most 1 and a batch adds at most 1 at any
-// cell.  p is split into n_h 2^-30 + n_l 2^-52 + (|error| <= 2^-54) with
-// |n_l| <= 2^21, and n_h, n_l go to two int32 planes per component with
+// cell.  p is split into n_h 2^-30 + n_l 2^-52 + (|error| <= 2^-53 + 2^-55)
+// with |n_l| <= 2^21 + 32, and n_h, n_l go to two int32 planes per component with
 // shared-memory integer atomics: a batch's sums stay below 2^31 at every
 // cell and are exact.  After each batch the planes become the integer V =
 // n_h 2^22 + n_l (units 2^(E-52)); a tile with one batch writes V 2^(E-52)
@@ -1001,14 +1001,25 @@ __device__ __forceinline__ df df_prod(df a, df b) {
     e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
     return {p, e};
 }
+// n_h, n_l of p (|p| < 1) by round-to-nearest additions of "magic" constants
+// on the FP32 pipe instead of conversion instructions (whose pipe runs at a
+// quarter of the FP32 rate): t = p.hi 2^30 is rounded to a multiple of 256 by
+// adding 3 2^30 (the sum lies in [2^31, 2^32), whose float spacing is 256),
+// the exact remainder plus p.lo 2^30 (|.| <= 192) to an integer by adding
+// 1.5 2^23 (spacing 1), and what is left (|.| <= 1/2 + 2^-17), times 2^22,
+// likewise; a sum's bits minus the constant's bits are the rounded value in
+// units of the spacing.
 __device__ __forceinline__ void df_quant_add(df p, int cell, int* ph, int* pl) {
-    const float t = p.hi * 1073741824.f;                 // 2^30: exact
-    const float tl = p.lo * 1073741824.f;
-    const float nf = rintf(t);
-    const float d = (t - nf) + tl;                       // |d| <= 1 unless |t| >= 2^23 (then t - nf = 0, d = tl)
-    const float nf2 = rintf(d);
-    const int nh = __float2int_rn(nf) + __float2int_rn(nf2);
-    const int nl = __float2int_rn(fmaf(d, 4194304.f, -nf2 * 4194304.f));   // (d - nf2) 2^22, |.| <= 2^21
+    constexpr float M1 = 3221225472.f, M2 = 12582912.f;   // 3 2^30, 1.5 2^23
+    const float t = p.hi * 1073741824.f;                    // 2^30: exact; |t| < 2^30
+    const float tl = p.lo * 1073741824.f;                   // |tl| < 2^6
+    const float s1 = t + M1;
+    const float r1 = t - (s1 - M1);                         // exact, |r1| <= 128
+    const float s2 = (r1 + tl) + M2;
+    const float d = (r1 - (s2 - M2)) + tl;                  // r1 - (s2 - M2) exact; |d| <= 1/2 + 2^-17
+    const float s3 = fmaf(d, 4194304.f, M2);                // d 2^22 rounded (|d 2^22| <= 2^21 + 32)
+    const int nh = ((__float_as_int(s1) - __float_as_int(M1)) << 8) + (__float_as_int(s2) - __float_as_int(M2));
+    const int nl = __float_as_int(s3) - __float_as_int(M2);
     atomicAdd(&ph[cell], nh);
     atomicAdd(&pl[cell], nl);
 }
