@@ -162,8 +162,12 @@ cudaError_t upload_tables(nuasm_plan_s* P, const HostTables& t, cudaStream_t st)
     const size_t eb = elt_bytes(P);
     const size_t sb = P->f64 ? sizeof(double) : sizeof(float2);
     const size_t bytes = table_bytes(P->g, P->f64, true);
+    const size_t tw_off = 6 * np * eb + np * sb;
+    // F64 plans append the twiddles as float pairs (hi = the value rounded to
+    // float, lo = the remainder rounded) for the double-float row passes
+    const size_t df_bytes = P->f64 ? bytes - tw_off : 0;
     char* base = nullptr;
-    cudaError_t e = dalloc(P, &base, bytes);
+    cudaError_t e = dalloc(P, &base, bytes + df_bytes);
     if (e != cudaSuccess) return e;
     P->d.tables = base;
     P->d.t1x = base;
@@ -173,10 +177,20 @@ cudaError_t upload_tables(nuasm_plan_s* P, const HostTables& t, cudaStream_t st)
     P->d.t3x = base + 4 * np * eb;
     P->d.t3y = base + 5 * np * eb;
     P->d.s = base + 6 * np * eb;
-    P->d.tw = base + 6 * np * eb + np * sb;
-    std::vector<char> host(bytes);
+    P->d.tw = base + tw_off;
+    P->d.tw_df = P->f64 ? base + bytes : nullptr;
+    std::vector<char> host(bytes + df_bytes);
     pack_tables(t, P->g, P->f64, true, host.data());
-    e = cudaMemcpyAsync(base, host.data(), bytes, cudaMemcpyHostToDevice, st);
+    if (P->f64) {
+        const double* tw = reinterpret_cast<const double*>(host.data() + tw_off);
+        float* out = reinterpret_cast<float*>(host.data() + bytes);
+        for (size_t i = 0; i < df_bytes / sizeof(double); ++i) {
+            const float hi = float(tw[i]);
+            out[2 * i] = hi;
+            out[2 * i + 1] = float(tw[i] - double(hi));
+        }
+    }
+    e = cudaMemcpyAsync(base, host.data(), bytes + df_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(st);   // host buffer goes out of scope
 }

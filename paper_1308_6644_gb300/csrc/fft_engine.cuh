@@ -23,6 +23,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "nuasm_internal.h"
 
 namespace nuasm {
@@ -150,7 +151,7 @@ template <int DIR, typename V> __device__ __forceinline__ V cis_pi16(int k) {
 template <typename V, int DIR, int LOGL, int E>
 __device__ __forceinline__ V half_bin(const V* __restrict__ tw, int q) {
     if constexpr (sizeof(V) == 16) {
-        const V t = __ldg(&tw[q]);
+        const V t = ldgv(&tw[q]);
         return DIR < 0 ? t : cconj(t);
     } else {
         // the first pass has radix E, or 2^LOGL when the whole transform is shorter
@@ -158,7 +159,7 @@ __device__ __forceinline__ V half_bin(const V* __restrict__ tw, int q) {
         static_assert(R0 >= 2 && R0 <= 16, "first-pass radix");
         constexpr int LOGLDR = LOGL - Log2<R0>::v;
         const int j = q & ((1 << LOGLDR) - 1), r = q >> LOGLDR;
-        const V t = __ldg(&tw[j]);
+        const V t = ldgv(&tw[j]);
         return cmul(DIR < 0 ? t : cconj(t), cis_pi16<DIR, V>(r * (16 / R0)));
     }
 }
@@ -193,7 +194,7 @@ __device__ __forceinline__ void twiddle_base(const V* __restrict__ tp, int k, Tw
         b.t[1] = CTraits<V>::make(q.z, q.w);
     } else {
 #pragma unroll
-        for (int r = 0; r < N; ++r) b.t[r] = __ldg(&tp[k * N + r]);
+        for (int r = 0; r < N; ++r) b.t[r] = ldgv(&tp[k * N + r]);
     }
 }
 

@@ -65,6 +65,8 @@ struct PlanDevice {
     void* t3x = nullptr; void* t3y = nullptr;
     void* s = nullptr;          // float2 (hi, lo) per bin (F32) or double (F64)
     void* tw = nullptr;         // twiddles, G complex
+    void* tw_df = nullptr;      // F64 plans: the twiddles as float pairs (re.hi, re.lo, im.hi, im.lo), for
+                                // the double-float row passes
     void* etab = nullptr;       // ASM non-separable factor E(|kx|, |ky|): N'/2 + 1 rows of etab_pitch
                                 // entries in the plan precision (null: evaluated per mode)
     void* etab2 = nullptr;      // type 2's T2x(kx) E(|kx|, |ky|): N'/2 + 1 rows of N' entries (FP32 plans

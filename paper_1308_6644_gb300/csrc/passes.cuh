@@ -78,6 +78,10 @@ template <> struct Prec<double2> {
     static constexpr int row_regs = 128;
 };
 
+// double-float row passes of FP64 plans: the FP64 configuration (16-byte
+// elements, as complex128)
+template <> struct Prec<dfc> : Prec<double2> {};
+
 template <typename V, int LOGNP> struct RowCfg {
     static constexpr int NP = 1 << LOGNP;
     static constexpr int LB = Prec<V>::row_logbudget;
@@ -118,6 +122,59 @@ template <typename V, int LOGNP, int MODE = 0> struct ColCfg {
 template <typename V> struct STable;
 template <> struct STable<float2> { using type = float2; };
 template <> struct STable<double2> { using type = double; };
+template <> struct STable<dfc> { using type = double; };
+
+// Global-memory element type of a pass's register type and the conversions
+// between them: the identity, except for double-float registers over FP64
+// arrays (scale s: the arrays hold the values times 2^s, so that a CTA's data
+// stays in the float range).
+template <typename V> struct Mem {
+    using type = V;
+    static constexpr bool scaled = false;
+    __device__ static V ld(V x, int) { return x; }
+    __device__ static V st(V v, int) { return v; }
+};
+template <> struct Mem<dfc> {
+    using type = double2;
+    static constexpr bool scaled = true;
+    __device__ static dfc ld(double2 x, int sc) { return dfc{dfr_split(x.x, sc), dfr_split(x.y, sc)}; }
+    __device__ static double2 st(dfc v, int sc) { return make_double2(dfr_to_double(v.x, sc), dfr_to_double(v.y, sc)); }
+};
+template <typename V> using MemT = typename Mem<V>::type;
+
+__device__ __forceinline__ bool nonzero(float2 v) { return v.x != 0.f || v.y != 0.f; }
+__device__ __forceinline__ bool nonzero(double2 v) { return v.x != 0.0 || v.y != 0.0; }
+__device__ __forceinline__ bool nonzero(dfc v) { return v.x.hi != 0.f || v.y.hi != 0.f; }
+
+// exponent k with 2^k <= |x| < 2^(k+1) (-1023 for zeros and subnormals)
+__device__ __forceinline__ int dexp2(double x) {
+    return (int(static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7ff) - 1023;
+}
+
+// The CTA's scale for double-float registers: the largest exponent among the
+// n elements at stride 1 of the rows r0 .. r0 + rows - 1 of an FP64 array
+// (row pitch `pitch`), clamped to the normal range; 0 for other types.  All
+// threads call it; it synchronises the block.
+template <typename V>
+__device__ __forceinline__ int cta_scale(const MemT<V>* __restrict__ x, int r0, int rows, int n, int pitch) {
+    if constexpr (!Mem<V>::scaled) {
+        return 0;
+    } else {
+        __shared__ int emax;
+        if (threadIdx.x == 0) emax = -1023;
+        __syncthreads();
+        int em = -1023;
+        for (int i = threadIdx.x; i < rows * n; i += blockDim.x) {
+            const int row = i / n, p = i - row * n;
+            const double2 v = x[size_t(r0 + row) * pitch + p];
+            em = max(em, max(dexp2(v.x), dexp2(v.y)));
+        }
+        em = __reduce_max_sync(0xffffffffu, em);
+        if ((threadIdx.x & 31) == 0) atomicMax(&emax, em);
+        __syncthreads();
+        return min(max(emax, -1022), 1023);
+    }
+}
 
 struct RowArgs {
     int n, W, Wp;
@@ -177,31 +234,31 @@ __device__ __forceinline__ double2 nonsep_factor(double sa, double sb, const Row
 template <typename V> struct RowConst {
     V ty;
     typename STable<V>::type s;
-    const V* erow;
+    const MemT<V>* erow;
 };
 
 template <typename V>
-__device__ __forceinline__ RowConst<V> row_const(int r, const V* __restrict__ ty,
+__device__ __forceinline__ RowConst<V> row_const(int r, const MemT<V>* __restrict__ ty,
                                                  const typename STable<V>::type* __restrict__ s, const RowArgs& a) {
-    const V* erow = nullptr;
-    if (a.etab) erow = static_cast<const V*>(a.etab) + size_t(min(r, a.np - r)) * a.ep;
-    return RowConst<V>{__ldg(&ty[r]), __ldg(&s[r]), erow};
+    const MemT<V>* erow = nullptr;
+    if (a.etab) erow = static_cast<const MemT<V>*>(a.etab) + size_t(min(r, a.np - r)) * a.ep;
+    return RowConst<V>{Mem<V>::ld(__ldg(&ty[r]), 0), __ldg(&s[r]), erow};
 }
 
 template <typename V>
-__device__ __forceinline__ V mode_factor(int q, const RowConst<V>& rc, const V* __restrict__ tx,
+__device__ __forceinline__ V mode_factor(int q, const RowConst<V>& rc, const MemT<V>* __restrict__ tx,
                                          const typename STable<V>::type* __restrict__ s, const RowArgs& a) {
-    V f = cmul(__ldg(&tx[q]), rc.ty);
+    V f = cmul(Mem<V>::ld(__ldg(&tx[q]), 0), rc.ty);
     if (rc.erow) {
-        f = cmul(f, __ldg(&rc.erow[min(q, a.np - q)]));   // both loads in flight together
-    } else if (a.nonsep && (f.x != 0 || f.y != 0)) {
-        f = cmul(f, nonsep_factor(__ldg(&s[q]), rc.s, a));
+        f = cmul(f, Mem<V>::ld(__ldg(&rc.erow[min(q, a.np - q)]), 0));   // both loads in flight together
+    } else if (a.nonsep && nonzero(f)) {
+        f = cmul(f, Mem<V>::ld(nonsep_factor(__ldg(&s[q]), rc.s, a), 0));
     }
     return f;
 }
 
 template <typename V>
-__device__ __forceinline__ V mode_factor(int q, int r, const V* __restrict__ tx, const V* __restrict__ ty,
+__device__ __forceinline__ V mode_factor(int q, int r, const MemT<V>* __restrict__ tx, const MemT<V>* __restrict__ ty,
                                          const typename STable<V>::type* __restrict__ s, const RowArgs& a) {
     return mode_factor<V>(q, row_const<V>(r, ty, s, a), tx, s, a);
 }
@@ -213,21 +270,22 @@ __device__ __forceinline__ V mode_factor(int q, int r, const V* __restrict__ tx,
 // same for every thread of the block.
 template <typename V, int ROWS>
 __device__ __forceinline__ bool stage_erows(V* dst, int r0, const RowArgs& a) {
+    using M = MemT<V>;
     if (!a.etab || (reinterpret_cast<uintptr_t>(dst) & 15)) return false;
-    const int chunks = int((size_t(a.ep) * sizeof(V)) / 16);   // ep * sizeof(V) is a multiple of 16
+    const int chunks = int((size_t(a.ep) * sizeof(M)) / 16);   // ep * sizeof(M) is a multiple of 16
     for (int i = threadIdx.x; i < ROWS * chunks; i += blockDim.x) {
         const int c = i / chunks, k = i - c * chunks;
         const int rr = min(r0 + c, a.np - r0 - c);
-        const char* src = static_cast<const char*>(a.etab) + size_t(rr) * a.ep * sizeof(V) + 16 * size_t(k);
-        cp_async16(reinterpret_cast<char*>(dst) + size_t(c) * a.ep * sizeof(V) + 16 * size_t(k), src);
+        const char* src = static_cast<const char*>(a.etab) + size_t(rr) * a.ep * sizeof(M) + 16 * size_t(k);
+        cp_async16(reinterpret_cast<char*>(dst) + size_t(c) * a.ep * sizeof(M) + 16 * size_t(k), src);
     }
     return true;
 }
 
 // the factor of mode q in the CTA's row `row` (ROWS == 1: the constants held in registers)
 template <typename V, int ROWS>
-__device__ __forceinline__ V row_factor(int q, int row, int r0, const RowConst<V>& rc0, const V* __restrict__ tx,
-                                        const V* __restrict__ ty, const typename STable<V>::type* __restrict__ s,
+__device__ __forceinline__ V row_factor(int q, int row, int r0, const RowConst<V>& rc0, const MemT<V>* __restrict__ tx,
+                                        const MemT<V>* __restrict__ ty, const typename STable<V>::type* __restrict__ s,
                                         const RowArgs& a) {
     if constexpr (ROWS == 1) return mode_factor<V>(q, rc0, tx, s, a);
     else return mode_factor<V>(q, r0 + row, tx, ty, s, a);
@@ -239,8 +297,9 @@ __device__ __forceinline__ V row_factor(int q, int row, int r0, const RowConst<V
 // T1x(kx) T1y(ky) E(kx, ky), inverse N'-point FFT, keep the N outputs.
 template <typename V, int LOGNP>
 __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
-    row_t1_kernel(const V* __restrict__ A, V* __restrict__ B, const V* __restrict__ tx, const V* __restrict__ ty,
-                  const typename STable<V>::type* __restrict__ s, const V* __restrict__ tw, RowArgs a) {
+    row_t1_kernel(const MemT<V>* __restrict__ A, MemT<V>* __restrict__ B, const MemT<V>* __restrict__ tx,
+                  const MemT<V>* __restrict__ ty, const typename STable<V>::type* __restrict__ s,
+                  const V* __restrict__ tw, RowArgs a) {
     using Cf = RowCfg<V, LOGNP>;
     constexpr int NP = Cf::NP, ROWS = Cf::ROWS, HALF = NP / 2;
     extern __shared__ unsigned char smem_raw[];
@@ -252,13 +311,15 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     pdl_allow_next();
     const RowConst<V> rc0 = row_const<V>(r0, ty, s, a);
     pdl_wait();   // A comes from the previous kernel
+    const int sc = cta_scale<V>(A, r0, ROWS, W, Wp);
 
     constexpr int R0 = Cf::MERGE ? Cf::EM : Cf::EF;   // first-pass radix of the forward engines
     [[maybe_unused]] const int a_n = a.np * Wp;   // extent of A (N' x Wp)
     auto folded = [&](int row, int p, int sgn) -> V {
-        const V* x = A + (r0 + row) * Wp;
-        const V u = p < W && NUASM_IN_RANGE((r0 + row) * Wp + p, a_n, dbg::kRowLoad) ? x[p] : zero;
-        const V t = p + NP < W && NUASM_IN_RANGE((r0 + row) * Wp + p + NP, a_n, dbg::kRowLoad) ? x[p + NP] : zero;
+        const MemT<V>* x = A + (r0 + row) * Wp;
+        const V u = p < W && NUASM_IN_RANGE((r0 + row) * Wp + p, a_n, dbg::kRowLoad) ? Mem<V>::ld(x[p], sc) : zero;
+        const V t = p + NP < W && NUASM_IN_RANGE((r0 + row) * Wp + p + NP, a_n, dbg::kRowLoad)
+                        ? Mem<V>::ld(x[p + NP], sc) : zero;
         return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), half_bin<V, -1, LOGNP, R0>(tw, p));
     };
     auto put = [&](int row, int pk, int sgn, V v) {
@@ -283,7 +344,8 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     block_fft<V, +1, Cf::EF, LOGNP, Cf::LOGROWS, true, Cf::MERGE>(
         S, tw, [&](int p, int c) { return NUASM_IN_RANGE(c * NP + p, ROWS * NP, dbg::kRowModes) ? M[c * NP + p] : zero; },
         [&](int p, int c, V v) {
-            if (p < n && NUASM_IN_RANGE((r0 + c) * n + p, a.np * n, dbg::kRowStore)) B[(r0 + c) * n + p] = v;
+            if (p < n && NUASM_IN_RANGE((r0 + c) * n + p, a.np * n, dbg::kRowStore))
+                B[(r0 + c) * n + p] = Mem<V>::st(v, sc);
         });
 }
 
@@ -293,8 +355,9 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
 // (even and odd outputs as two N'-point FFTs), keeping the W window entries.
 template <typename V, int LOGNP>
 __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
-    row_t2_kernel(const V* __restrict__ B, V* __restrict__ A, const V* __restrict__ tx, const V* __restrict__ ty,
-                  const typename STable<V>::type* __restrict__ s, const V* __restrict__ tw, RowArgs a) {
+    row_t2_kernel(const MemT<V>* __restrict__ B, MemT<V>* __restrict__ A, const MemT<V>* __restrict__ tx,
+                  const MemT<V>* __restrict__ ty, const typename STable<V>::type* __restrict__ s,
+                  const V* __restrict__ tw, RowArgs a) {
     using Cf = RowCfg<V, LOGNP>;
     constexpr int NP = Cf::NP, ROWS = Cf::ROWS, HALF = NP / 2;
     extern __shared__ unsigned char smem_raw[];
@@ -330,18 +393,21 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
         if (staged) cp_async_commit();
     }
     pdl_wait();   // B comes from the previous kernel
+    const int sc = cta_scale<V>(B, r0, ROWS, n, n);
     block_fft<V, -1, Cf::EF, LOGNP, Cf::LOGROWS, true>(
         S, tw,
         [&](int p, int c) {
-            return p < n && NUASM_IN_RANGE((r0 + c) * n + p, a.np * n, dbg::kRowLoad) ? B[(r0 + c) * n + p] : zero;
+            return p < n && NUASM_IN_RANGE((r0 + c) * n + p, a.np * n, dbg::kRowLoad)
+                       ? Mem<V>::ld(B[(r0 + c) * n + p], sc) : zero;
         },
         [&](int p, int c, V v) {
             V f;
-            const V t = ROWS == 1 ? rc0.ty : __ldg(&ty[r0 + c]);
+            const V t = ROWS == 1 ? rc0.ty : Mem<V>::ld(__ldg(&ty[r0 + c]), 0);
             if (staged == 2) {
                 f = cmul(Es[c * NP + p], t);
             } else if (staged == 1) {
-                f = cmul(cmul(__ldg(&tx[p]), t), Es[c * a.ep + min(p, NP - p)]);
+                const MemT<V>* Em = reinterpret_cast<const MemT<V>*>(Es);
+                f = cmul(cmul(Mem<V>::ld(__ldg(&tx[p]), 0), t), Mem<V>::ld(Em[c * a.ep + min(p, NP - p)], 0));
             } else {
                 f = row_factor<V, ROWS>(p, c, r0, rc0, tx, ty, s, a);
             }
@@ -362,7 +428,8 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     };
     auto put = [&](int row, int k, int sgn, V v) {
         const int u = 2 * k + sgn;
-        if (u < W && NUASM_IN_RANGE((r0 + row) * Wp + u, a.np * Wp, dbg::kRowStore)) A[(r0 + row) * Wp + u] = v;
+        if (u < W && NUASM_IN_RANGE((r0 + row) * Wp + u, a.np * Wp, dbg::kRowStore))
+            A[(r0 + row) * Wp + u] = Mem<V>::st(v, sc);
     };
     if constexpr (Cf::MERGE) {
         block_fft<V, +1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false, true>(
@@ -385,7 +452,7 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
 // reads happen in the first forward pass, before any write).
 template <typename V, int LOGNP>
 __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
-    row_t3_kernel(V* __restrict__ A, const V* __restrict__ tx, const V* __restrict__ ty,
+    row_t3_kernel(MemT<V>* __restrict__ A, const MemT<V>* __restrict__ tx, const MemT<V>* __restrict__ ty,
                   const typename STable<V>::type* __restrict__ s, const V* __restrict__ tw, RowArgs a) {
     using Cf = RowCfg<V, LOGNP>;
     constexpr int NP = Cf::NP, ROWS = Cf::ROWS, HALF = NP / 2;
@@ -398,12 +465,14 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     pdl_allow_next();
     const RowConst<V> rc0 = row_const<V>(r0, ty, s, a);
     pdl_wait();   // A comes from the previous kernel
+    const int sc = cta_scale<V>(A, r0, ROWS, W, Wp);
     constexpr int R0 = Cf::MERGE ? Cf::EM : Cf::EF;   // first-pass radix of the engines
     [[maybe_unused]] const int a_n = a.np * Wp;   // extent of A (N' x Wp)
     auto folded = [&](int row, int p, int sgn) -> V {
-        const V* x = A + (r0 + row) * Wp;
-        const V u = p < W && NUASM_IN_RANGE((r0 + row) * Wp + p, a_n, dbg::kRowLoad) ? x[p] : zero;
-        const V t = p + NP < W && NUASM_IN_RANGE((r0 + row) * Wp + p + NP, a_n, dbg::kRowLoad) ? x[p + NP] : zero;
+        const MemT<V>* x = A + (r0 + row) * Wp;
+        const V u = p < W && NUASM_IN_RANGE((r0 + row) * Wp + p, a_n, dbg::kRowLoad) ? Mem<V>::ld(x[p], sc) : zero;
+        const V t = p + NP < W && NUASM_IN_RANGE((r0 + row) * Wp + p + NP, a_n, dbg::kRowLoad)
+                        ? Mem<V>::ld(x[p + NP], sc) : zero;
         return sgn == 0 ? cadd(u, t) : cmul(csub(u, t), half_bin<V, -1, LOGNP, R0>(tw, p));
     };
     auto put_mode = [&](int row, int pk, int sgn, V v) {
@@ -420,7 +489,8 @@ __global__ void __launch_bounds__(RowCfg<V, LOGNP>::P, RowCfg<V, LOGNP>::MINB)
     };
     auto put_row = [&](int row, int k, int sgn, V v) {
         const int u = 2 * k + sgn;
-        if (u < W && NUASM_IN_RANGE((r0 + row) * Wp + u, a_n, dbg::kRowStore)) A[(r0 + row) * Wp + u] = v;
+        if (u < W && NUASM_IN_RANGE((r0 + row) * Wp + u, a_n, dbg::kRowStore))
+            A[(r0 + row) * Wp + u] = Mem<V>::st(v, sc);
     };
     if constexpr (Cf::MERGE) {
         block_fft<V, -1, Cf::EM, LOGNP, Cf::LOGROWS + 1, false>(
@@ -837,26 +907,29 @@ template <typename V, int LOGNP>
 cudaError_t launch_row(const nuasm_plan_s* P, int type, cudaStream_t st) {
     using Cf = RowCfg<V, LOGNP>;
     using ST = typename STable<V>::type;
+    using M = MemT<V>;
     const RowArgs a = row_args(P);
     const size_t sm = Cf::smem();
-    const V* tw = static_cast<const V*>(P->d.tw);
+    // double-float passes read the plan's twiddles as float pairs
+    const V* tw = static_cast<const V*>(Mem<V>::scaled ? P->d.tw_df : P->d.tw);
+    if (!tw) return cudaErrorInvalidValue;
     const ST* s = static_cast<const ST*>(P->d.s);
     const int blocks = Cf::NP / Cf::ROWS;
     cudaError_t e;
     if (type == 1) {
         if ((e = set_smem(row_t1_kernel<V, LOGNP>, sm)) != cudaSuccess) return e;
         e = launch_chained(row_t1_kernel<V, LOGNP>, dim3(blocks), dim3(Cf::P), sm, st,
-                           static_cast<const V*>(P->d.bufA), static_cast<V*>(P->d.bufB),
-                           static_cast<const V*>(P->d.t1x), static_cast<const V*>(P->d.t1y), s, tw, a);
+                           static_cast<const M*>(P->d.bufA), static_cast<M*>(P->d.bufB),
+                           static_cast<const M*>(P->d.t1x), static_cast<const M*>(P->d.t1y), s, tw, a);
     } else if (type == 3) {
         if ((e = set_smem(row_t3_kernel<V, LOGNP>, sm)) != cudaSuccess) return e;
-        e = launch_chained(row_t3_kernel<V, LOGNP>, dim3(blocks), dim3(Cf::P), sm, st, static_cast<V*>(P->d.bufA),
-                           static_cast<const V*>(P->d.t3x), static_cast<const V*>(P->d.t3y), s, tw, a);
+        e = launch_chained(row_t3_kernel<V, LOGNP>, dim3(blocks), dim3(Cf::P), sm, st, static_cast<M*>(P->d.bufA),
+                           static_cast<const M*>(P->d.t3x), static_cast<const M*>(P->d.t3y), s, tw, a);
     } else {
         if ((e = set_smem(row_t2_kernel<V, LOGNP>, sm)) != cudaSuccess) return e;
         e = launch_chained(row_t2_kernel<V, LOGNP>, dim3(blocks), dim3(Cf::P), sm, st,
-                           static_cast<const V*>(P->d.bufB), static_cast<V*>(P->d.bufA),
-                           static_cast<const V*>(P->d.t2x), static_cast<const V*>(P->d.t2y), s, tw, a);
+                           static_cast<const M*>(P->d.bufB), static_cast<M*>(P->d.bufA),
+                           static_cast<const M*>(P->d.t2x), static_cast<const M*>(P->d.t2y), s, tw, a);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

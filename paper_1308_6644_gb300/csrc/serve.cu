@@ -324,6 +324,7 @@ nuasm_status run_job(Server& S, Slot& sl, const Job& j, PointSet* ps, bool build
     view.d.t3y = part[0] + 5 * np * eb;
     view.d.s = part[0] + 6 * np * eb;
     view.d.tw = B->d.tw;
+    view.d.tw_df = B->d.tw_df;
     view.d.etab = nullptr;   // one solve per table: E is evaluated per mode
     view.d.etab2 = nullptr;
     view.d.win = part[1];

@@ -427,15 +427,17 @@ def test_fp64_double_float_spreading(P, kind, tile, tol, chunk):
     assert np.max(np.abs(got - ref)) <= 10 * TOL["f64"] * np.linalg.norm(ref) / np.sqrt(ref.size)
 
 
+@pytest.mark.parametrize("n,m", [(64, 3000), (256, 1000)])
 @pytest.mark.parametrize("type_", [1, 2])
 @pytest.mark.parametrize("scale", [1e-300, 1e-200, 1e200])
-def test_fp64_double_float_gridding_extreme_magnitudes(P, type_, scale):
+def test_fp64_double_float_gridding_extreme_magnitudes(P, n, m, type_, scale):
     """The double-float FP64 gridding scales each batch (spreading) and each
-    staged tile (interpolation) by a power of two before splitting values
-    into float pairs, so inputs far outside the float range keep FP64-mode
-    accuracy: the scaled input's output is the scaled output (rel-L2 1e-10
-    against the oracle on the scaled input, whose results reach 1e-300)."""
-    n, pitch, m = 64, 10e-6, 3000
+    staged tile (interpolation), and the double-float row passes (N' >= 512)
+    each CTA's rows, by a power of two before splitting values into float
+    pairs, so inputs far outside the float range keep FP64-mode accuracy: the
+    scaled input's output is the scaled output (rel-L2 1e-10 against the
+    oracle on the scaled input, whose results reach 1e-300)."""
+    pitch = 10e-6
     x, y, vals = random_case(63 + type_, n, m, pitch=pitch, type_=type_)
     kw = dict(pitch=pitch, lam=633e-9, z=0.03, ox=10e-6)
     got = run_gpu(P, "fresnel", type_, "f64", n, x=x, y=y, values=vals * scale, tile=64, spread_chunk=-1, **kw)
