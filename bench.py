@@ -219,7 +219,7 @@ def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
     """Name of the kernel a stage launches for this geometry (as ncu lists it)."""
     lognp = int(np.log2(info["n_pad"]))
     v, s = ("double2", "double") if f64 else ("float2", "float")
-    rv = "dfc" if f64 and lognp >= 9 else v   # FP64 row passes from N' = 512 up: double-float
+    rv = "dfc" if f64 and lognp >= 9 else v   # FP64 FFT passes from N' = 512 up: double-float
     w = info["kernel_width"]
     if f64:
         tap = f"double, {w}, true" if w in (11, 13) else f"double, {8 if w <= 8 else (16 if w <= 16 else 26)}, false"
@@ -240,13 +240,13 @@ def kernel_of_stage(stage: str, info: dict, f64: bool) -> str:
     else:
         spread = (f"spread_fixed_kernel<{w}, true, 2>" if 4 <= w <= 8 else
                   f"spread_fixed_kernel<{16 if w <= 16 else 26}, false, 2>")
-    return {"col_fwd": f"col_tma_kernel<{lognp}, 2>" if tma_wide else f"col_kernel<{v}, {lognp}, 2>",
+    return {"col_fwd": f"col_tma_kernel<{lognp}, 2>" if tma_wide else f"col_kernel<{rv}, {lognp}, 2>",
             "row_t2": f"row_t2_kernel<{rv}, {lognp}>",
-            "col_inv_fold": f"col_tma_kernel<{lognp}, 3>" if tma else f"col_kernel<{v}, {lognp}, 3>",
+            "col_inv_fold": f"col_tma_kernel<{lognp}, 3>" if tma else f"col_kernel<{rv}, {lognp}, 3>",
             "interp": interp, "spread": spread,
-            "col_fwd_fold": f"col_tma_kernel<{lognp}, 0>" if tma else f"col_kernel<{v}, {lognp}, 0>",
+            "col_fwd_fold": f"col_tma_kernel<{lognp}, 0>" if tma else f"col_kernel<{rv}, {lognp}, 0>",
             "row_t1": f"row_t1_kernel<{rv}, {lognp}>",
-            "col_inv": f"col_tma_kernel<{lognp}, 1>" if tma_wide else f"col_kernel<{v}, {lognp}, 1>"}[stage]
+            "col_inv": f"col_tma_kernel<{lognp}, 1>" if tma_wide else f"col_kernel<{rv}, {lognp}, 1>"}[stage]
 
 
 _FFT_SOURCES = ["passes.cuh", "fft_engine.cuh", "tma.cuh", "dfloat.cuh"]

@@ -59,28 +59,35 @@ template <> __device__ __forceinline__ dfc ldgv<dfc>(const dfc* p) {
     return dfc{dfr(q.x, q.y), dfr(q.z, q.w)};
 }
 
-// x 2^-s as a double-float by integer operations on the bits (no FP64
-// arithmetic): hi the leading 24 significant bits of x (truncated), lo the
-// next 23, relative error below 2^-46.  The caller picks s so that the result
-// stays within the float range; zeros, subnormals and values below 2^-100
-// after the scaling give zero, infinities and NaNs give themselves in hi.
+// 2^k as a double for k in [-1022, 1023]
+__device__ __forceinline__ double dfr_pow2(int k) {
+    return __longlong_as_double(static_cast<long long>(k + 1023) << 52);
+}
+
+// x 2^-s (s in [-1022, 1023]) as a double-float by integer operations on the
+// bits: hi the leading 24 significant bits of x (truncated), lo the next 23,
+// relative error below 2^-46.  The caller picks s so that the result stays
+// within the float range.  A subnormal x is first scaled by 2^-s in FP64
+// (exact while the product is normal); zeros and values below 2^-100 after
+// the scaling give zero, infinities and NaNs give themselves in hi.
 __device__ __forceinline__ dfr dfr_split(double x, int s) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const int ex = int(b >> 52) & 0x7ff;
+    unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    int ex = int(b >> 52) & 0x7ff;
     if (ex == 0x7ff) return dfr(__double2float_rn(x), 0.f);
+    if (ex == 0) {   // zero or subnormal
+        if ((b << 1) == 0 || s > -923) return dfr(0.f, 0.f);   // zero, or below 2^-100 of 2^s
+        b = static_cast<unsigned long long>(__double_as_longlong(x * dfr_pow2(-s)));
+        ex = int(b >> 52) & 0x7ff;
+        s = 0;
+    }
     const int e = ex - 1023 - s;
-    if (ex == 0 || e < -100) return dfr(0.f, 0.f);
+    if (e < -100) return dfr(0.f, 0.f);
     const unsigned sign = unsigned(b >> 32) & 0x80000000u;
     const unsigned hb = sign | (unsigned(e + 127) << 23) | unsigned((b >> 29) & 0x7fffffu);
     const unsigned r = unsigned(b) & 0x1fffffffu;   // the 29 mantissa bits below hi
     const unsigned lb = unsigned(e - 23 + 127) << 23;
     const float lo = __uint_as_float(lb | (r >> 6)) - __uint_as_float(lb);   // (r >> 6) 2^(e - 46), exact
     return dfr(__uint_as_float(hb), sign ? -lo : lo);
-}
-
-// 2^k as a double for k in [-1022, 1023]
-__device__ __forceinline__ double dfr_pow2(int k) {
-    return __longlong_as_double(static_cast<long long>(k + 1023) << 52);
 }
 
 // (hi + lo) 2^s as a double by integer operations (the 53 leading bits of

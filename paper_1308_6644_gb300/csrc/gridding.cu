@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "nuasm_internal.h"
 
 namespace nuasm {
@@ -880,25 +881,12 @@ __global__ void __launch_bounds__(kInterpThreads, sizeof(S) == 4 ? NUASM_INTERP_
 // error-free transforms, and FP64 arithmetic is left to once per point or
 // per staged cell.
 
-// x 2^-s as hi + lo: hi the leading 24 significant bits of x (truncated), lo
-// the next 23, by integer operations on the bits (no FP64 arithmetic), so the
-// relative error is below 2^-46.  The caller picks s so that the result is
-// below 2 in magnitude.  Zeros, subnormals and values below 2^-100 after the
-// scaling give zero; infinities and NaNs give themselves in hi.
+// x 2^-s as hi + lo (dfr_split: integer operations on the bits, relative
+// error below 2^-46; subnormals rescaled exactly first).  The caller picks s
+// so that the result is below 2 in magnitude.
 __device__ __forceinline__ df df_split(double x, int s) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const int ex = int(b >> 52) & 0x7ff;
-    if (ex == 0x7ff) return {__double2float_rn(x), 0.f};
-    const int e = ex - 1023 - s;   // exponent of the scaled value
-    if (ex == 0 || e < -100) return {0.f, 0.f};
-    const unsigned sign = unsigned(b >> 32) & 0x80000000u;
-    const unsigned hb = sign | (unsigned(e + 127) << 23) | unsigned((b >> 29) & 0x7fffffu);
-    // the 29 mantissa bits below hi, r 2^(e - 52), kept as (r >> 6) 2^(e - 46):
-    // the float (2^23 + (r >> 6)) 2^(e - 46) minus 2^(e - 23), an exact subtraction
-    const unsigned r = unsigned(b) & 0x1fffffffu;
-    const unsigned lb = unsigned(e - 23 + 127) << 23;
-    const float lo = __uint_as_float(lb | (r >> 6)) - __uint_as_float(lb);
-    return {__uint_as_float(hb), sign ? -lo : lo};
+    const dfr r = dfr_split(x, s);
+    return {r.hi, r.lo};
 }
 
 // exponent k of a double with 2^k <= |x| < 2^(k+1) (-1023 for zeros and

@@ -522,7 +522,7 @@ enum ColMode { COL_FWD_FOLD = 0, COL_INV = 1, COL_FWD = 2, COL_INV_FOLD = 3 };
 // half (blockIdx.y: 0 even, 1 odd).
 template <typename V, int LOGNP, int MODE>
 __global__ void __launch_bounds__(ColCfg<V, LOGNP, MODE>::P, ColCfg<V, LOGNP, MODE>::MINB)
-    col_kernel(const V* __restrict__ src, V* __restrict__ dst, const V* __restrict__ tw, ColArgs a) {
+    col_kernel(const MemT<V>* __restrict__ src, MemT<V>* __restrict__ dst, const V* __restrict__ tw, ColArgs a) {
     using Cf = ColCfg<V, LOGNP, MODE>;
     constexpr int NP = Cf::NP, HALF = NP / 2, C = Cf::C;
     extern __shared__ unsigned char smem_raw[];
@@ -536,12 +536,20 @@ __global__ void __launch_bounds__(ColCfg<V, LOGNP, MODE>::P, ColCfg<V, LOGNP, MO
                                      : MODE == COL_FWD ? n * n : NP * Wp;
     [[maybe_unused]] const int dst_n = MODE == COL_FWD_FOLD ? NP * Wp : MODE == COL_INV ? n * n
                                      : MODE == COL_FWD ? NP * n : W * Wp;
-    auto ld = [&](int i) -> V { return NUASM_IN_RANGE(i, src_n, dbg::kColLoad) ? src[i] : zero; };
-    auto st = [&](int i, V v) {
-        if (NUASM_IN_RANGE(i, dst_n, dbg::kColStore)) dst[i] = v;
-    };
     pdl_allow_next();
     pdl_wait();   // src comes from the previous kernel (no-op for the first kernel of a chain)
+    // double-float passes: the CTA's scale over the source rows and columns it reads
+    int sc = 0;
+    if constexpr (Mem<V>::scaled) {
+        const bool win_cols = MODE == COL_FWD_FOLD || MODE == COL_INV_FOLD;   // window-wide arrays
+        const int cols = win_cols ? W : n, pitch = win_cols ? Wp : n;
+        const int rows = MODE == COL_FWD_FOLD ? W : MODE == COL_FWD ? n : NP;
+        sc = cta_scale<V>(src + col0, 0, rows, min(C, cols - col0), pitch);
+    }
+    auto ld = [&](int i) -> V { return NUASM_IN_RANGE(i, src_n, dbg::kColLoad) ? Mem<V>::ld(src[i], sc) : zero; };
+    auto st = [&](int i, V v) {
+        if (NUASM_IN_RANGE(i, dst_n, dbg::kColStore)) dst[i] = Mem<V>::st(v, sc);
+    };
     if constexpr (MODE == COL_FWD_FOLD) {
         // src: window (W x Wp); dst: A (N' x Wp), kept modes in natural N'-bin rows
         block_fft<V, -1, Cf::E, LOGNP, Cf::LOGC, false>(
@@ -943,12 +951,15 @@ cudaError_t launch_col(const nuasm_plan_s* P, const void* src, void* dst, int nc
     cudaError_t e = set_smem(col_kernel<V, LOGNP, MODE>, sm);
     if (e != cudaSuccess) return e;
     dim3 grid((ncols + Cf::C - 1) / Cf::C, halves);
+    using M = MemT<V>;
+    // double-float passes read the plan's twiddles as float pairs
+    const V* tw = static_cast<const V*>(Mem<V>::scaled ? P->d.tw_df : P->d.tw);
+    if (!tw) return cudaErrorInvalidValue;
     if constexpr (MODE == COL_FWD) {   // first kernel of the type-2 chain
-        col_kernel<V, LOGNP, MODE><<<grid, Cf::P, sm, st>>>(static_cast<const V*>(src), static_cast<V*>(dst),
-                                                            static_cast<const V*>(P->d.tw), a);
+        col_kernel<V, LOGNP, MODE><<<grid, Cf::P, sm, st>>>(static_cast<const M*>(src), static_cast<M*>(dst), tw, a);
     } else {
-        e = launch_chained(col_kernel<V, LOGNP, MODE>, grid, dim3(Cf::P), sm, st, static_cast<const V*>(src),
-                           static_cast<V*>(dst), static_cast<const V*>(P->d.tw), a);
+        e = launch_chained(col_kernel<V, LOGNP, MODE>, grid, dim3(Cf::P), sm, st, static_cast<const M*>(src),
+                           static_cast<M*>(dst), tw, a);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();

@@ -82,7 +82,7 @@ def test_double_float_kernel_names(split, want):
 
 
 def test_fp64_row_pass_names_follow_the_size_rule():
-    """FP64 row passes run in double-float from N' = 512 up, in FP64 below."""
+    """FP64 row (and column) passes run in double-float from N' = 512 up, in FP64 below."""
     assert bench.kernel_of_stage("row_t1", dict(n_pad=4096, kernel_width=13), True) == "row_t1_kernel<dfc, 12>"
     assert bench.kernel_of_stage("row_t2", dict(n_pad=512, kernel_width=13), True) == "row_t2_kernel<dfc, 9>"
     assert bench.kernel_of_stage("row_t1", dict(n_pad=128, kernel_width=13), True) == "row_t1_kernel<double2, 7>"
@@ -94,7 +94,9 @@ def test_column_kernel_names_follow_the_tma_rule():
     assert bench.kernel_of_stage("col_fwd", dict(n_pad=2048, kernel_width=7), False) == "col_kernel<float2, 11, 2>"
     assert bench.kernel_of_stage("col_fwd", dict(n_pad=4096, kernel_width=7), False) == "col_tma_kernel<12, 2>"
     assert bench.kernel_of_stage("col_inv_fold", dict(n_pad=2048, kernel_width=13), True) == \
-        "col_kernel<double2, 11, 3>"
+        "col_kernel<dfc, 11, 3>"
+    assert bench.kernel_of_stage("col_fwd_fold", dict(n_pad=128, kernel_width=13), True) == \
+        "col_kernel<double2, 7, 0>"
 
 
 def test_e2e_flush_rule():
