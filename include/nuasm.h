@@ -84,9 +84,10 @@ typedef enum {
     NUASM_PREC_F32_F64PHASE = 0,  /* complex64 data; phases from FP64 tables and
                                      compensated (double-float) FP32 arithmetic */
     NUASM_PREC_F64 = 1            /* complex128 data; FP64 arithmetic, except that gridding with
-                                     the ES kernel at w = 11 or 13 runs in double-float arithmetic
-                                     (pairs of FP32 values, about 47 significant bits; see
-                                     nuasm_plan_info_t.double_float) */
+                                     the ES kernel at w = 11 or 13 and the FFT passes of planes with
+                                     N' >= 512 run in double-float arithmetic (pairs of FP32 values,
+                                     about 47 significant bits; see nuasm_plan_info_t.double_float);
+                                     results within 1e-10 (rel-L2) of exact FP64 evaluation */
 } nuasm_prec;
 
 /* Problem definition (Eq. 4 / Eq. 5 parameters).  Plain old data. */
