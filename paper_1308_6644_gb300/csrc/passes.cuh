@@ -66,21 +66,34 @@ template <typename V> struct Prec;
 template <> struct Prec<float2> {
     static constexpr bool f64 = false;
     static constexpr int col_e = 16, col_budget = NUASM_COL_BUDGET;   // elements per thread / per CTA
+    static constexpr int col_cmax = 16;                               // columns per CTA at most
     static constexpr int row_logbudget = 11;                          // rows per CTA = 2^11 / N'
     static constexpr int regs = 64;
     static constexpr int row_regs = NUASM_ROW_REGS;
 };
 template <> struct Prec<double2> {
     static constexpr bool f64 = true;
-    static constexpr int col_e = 8, col_budget = NUASM_COL_BUDGET64;
+    static constexpr int col_e = 8, col_budget = NUASM_COL_BUDGET64, col_cmax = 16;
     static constexpr int row_logbudget = NUASM_ROW_LOGBUDGET64;
     static constexpr int regs = 128;
     static constexpr int row_regs = 128;
 };
 
-// double-float row passes of FP64 plans: the FP64 configuration (16-byte
-// elements, as complex128)
-template <> struct Prec<dfc> : Prec<double2> {};
+// double-float passes of FP64 plans: the FP64 row configuration (16-byte
+// elements, as complex128); column CTAs of up to NUASM_DF_COL_BUDGET elements
+// and NUASM_DF_COL_CMAX columns, NUASM_DF_COL_E elements per thread
+#ifndef NUASM_DF_COL_E
+#define NUASM_DF_COL_E 8
+#endif
+#ifndef NUASM_DF_COL_BUDGET
+#define NUASM_DF_COL_BUDGET 8192
+#endif
+#ifndef NUASM_DF_COL_CMAX
+#define NUASM_DF_COL_CMAX 4
+#endif
+template <> struct Prec<dfc> : Prec<double2> {
+    static constexpr int col_e = NUASM_DF_COL_E, col_budget = NUASM_DF_COL_BUDGET, col_cmax = NUASM_DF_COL_CMAX;
+};
 
 template <typename V, int LOGNP> struct RowCfg {
     static constexpr int NP = 1 << LOGNP;
@@ -112,7 +125,7 @@ template <typename V, int LOGNP, int MODE = 0> struct ColCfg {
     static constexpr int E = Prec<V>::col_e;
     static constexpr int BUDGET = (MODE == 2 && !Prec<V>::f64) ? NUASM_COL_FWD_BUDGET : Prec<V>::col_budget;
     static constexpr int CRAW = BUDGET / NP;
-    static constexpr int C = CRAW > 16 ? 16 : (CRAW < 1 ? 1 : CRAW);
+    static constexpr int C = CRAW > Prec<V>::col_cmax ? Prec<V>::col_cmax : (CRAW < 1 ? 1 : CRAW);
     static constexpr int LOGC = Log2<C>::v;
     static constexpr int P = (NP * C) / E;
     static constexpr int MINB = (65536 / (P * Prec<V>::regs)) > 0 ? 65536 / (P * Prec<V>::regs) : 1;
