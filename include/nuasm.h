@@ -83,11 +83,12 @@ typedef enum {
 typedef enum {
     NUASM_PREC_F32_F64PHASE = 0,  /* complex64 data; phases from FP64 tables and
                                      compensated (double-float) FP32 arithmetic */
-    NUASM_PREC_F64 = 1            /* complex128 data; FP64 arithmetic, except that gridding with
-                                     the ES kernel at w = 11 or 13 and the FFT passes of planes with
-                                     N' >= 512 run in double-float arithmetic (pairs of FP32 values,
-                                     about 47 significant bits; see nuasm_plan_info_t.double_float);
-                                     results within 1e-10 (rel-L2) of exact FP64 evaluation */
+    NUASM_PREC_F64 = 1            /* complex128 data; FP64 arithmetic, except that gridding at the
+                                     kernel widths of the FP64 tolerances (see
+                                     nuasm_plan_info_t.double_float) and the FFT passes of planes
+                                     with N' >= 512 run in double-float arithmetic (pairs of FP32
+                                     values, about 47 significant bits); results within 1e-10
+                                     (rel-L2) of exact FP64 evaluation */
 } nuasm_prec;
 
 /* Problem definition (Eq. 4 / Eq. 5 parameters).  Plain old data. */
@@ -156,7 +157,8 @@ typedef struct {
                                   per whole tile) */
     int32_t double_float;      /* 1: FP64 gridding runs in double-float arithmetic (pairs of
                                   FP32 values, about 47 significant bits) on the FP32 pipe --
-                                  FP64 plans with the ES kernel at w = 11 or 13 */
+                                  FP64 plans with the ES kernel at w = 11 or 13 or the
+                                  Gaussian at w = 15, 21 or 25 */
 } nuasm_plan_info_t;
 
 /*

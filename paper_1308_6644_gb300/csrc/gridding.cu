@@ -908,8 +908,9 @@ __device__ __forceinline__ df df_fma(df a, df b, df c) {
 
 // Tap weights of one axis in double-float: Horner's rule on the FP64
 // polynomials, the degrees from kDfTail up in FP32 (the coefficients' hi
-// parts; for the ES kernel their sum is below 3.1e-7 at w = 11 and 13, so
-// this adds below 2e-14 to a weight) and the rest in double-float.
+// parts; their sum is below 3.1e-7 for the ES kernel at w = 11 and 13 and
+// 1.1e-7 for the Gaussian at w = 15, 21 and 25, so this adds below 2e-14 to
+// a weight) and the rest in double-float.
 constexpr int kDfTail = 9;
 static_assert(kPoly64Deg >= kDfTail, "FP64 tap degree");
 // c: the kPoly64Deg + 1 coefficients of one tap (parameter or shared memory)
@@ -1020,7 +1021,7 @@ __device__ __forceinline__ double scaled_int(long long V, int k) {
 }
 
 template <int WMAX>
-__global__ void __launch_bounds__(256, NUASM_DF_SPREAD_MINB) spread_df_kernel(const RecD* __restrict__ rec, const int* __restrict__ off,
+__global__ void __launch_bounds__(256, WMAX <= 13 ? NUASM_DF_SPREAD_MINB : 2) spread_df_kernel(const RecD* __restrict__ rec, const int* __restrict__ off,
                                                           const double* __restrict__ wpt,
                                                           const int* __restrict__ order,
                                                           const double2* __restrict__ c, double2* __restrict__ win,
@@ -1436,11 +1437,19 @@ template <bool SPREAD> cudaError_t gridding(const nuasm_plan_s* P, const void* i
         // double-float gridding for the ES kernel at w = 13 (the FP64 default
         // tolerance, 1e-12) and w = 11 (1e-10); spreading by whole tiles only
         if (gridding_double_float(P)) {
-            if constexpr (SPREAD) {
-                if (NUASM_DF_SPLIT || !P->d.spread_items)
-                    return P->g.w == 13 ? spread_df_impl<13>(P, in, st) : spread_df_impl<11>(P, in, st);
-            } else {
-                return P->g.w == 13 ? interp_df_impl<13>(P, out, st) : interp_df_impl<11>(P, out, st);
+            auto df_run = [&](auto wtag) -> cudaError_t {
+                constexpr int WD = decltype(wtag)::value;
+                if constexpr (SPREAD) return spread_df_impl<WD>(P, in, st);
+                else return interp_df_impl<WD>(P, out, st);
+            };
+            if (!SPREAD || NUASM_DF_SPLIT || !P->d.spread_items) {
+                switch (P->g.w) {
+                    case 11: return df_run(std::integral_constant<int, 11>{});
+                    case 13: return df_run(std::integral_constant<int, 13>{});
+                    case 15: return df_run(std::integral_constant<int, 15>{});
+                    case 21: return df_run(std::integral_constant<int, 21>{});
+                    default: return df_run(std::integral_constant<int, 25>{});
+                }
             }
         }
         // the FP64 default tolerance (1e-12) gives w = 13 and a tolerance of

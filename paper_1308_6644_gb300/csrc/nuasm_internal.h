@@ -123,13 +123,15 @@ struct nuasm_plan_s {
 namespace nuasm {
 
 // FP64 gridding in double-float arithmetic on the FP32 pipe (gridding.cu):
-// FP64 plans with the ES kernel at its exact FP64 widths (w = 13, the default
-// tolerance 1e-12; w = 11, 1e-10); spreading by whole tiles only.
+// FP64 plans at the kernel widths of the FP64 tolerances 1e-12 and 1e-10
+// (ES: w = 13 and 11; Gaussian: w = 25 and 21, and 15 for 1e-7).
 #ifndef NUASM_F64_DF
 #define NUASM_F64_DF 1   // 0: FP64 gridding on the FP64 pipe throughout
 #endif
 inline bool gridding_double_float(const nuasm_plan_s* P) {
-    return NUASM_F64_DF && P->f64 && P->g.kernel == NUASM_KERNEL_ES && (P->g.w == 11 || P->g.w == 13);
+    if (!NUASM_F64_DF || !P->f64) return false;
+    if (P->g.kernel == NUASM_KERNEL_ES) return P->g.w == 11 || P->g.w == 13;
+    return P->g.w == 15 || P->g.w == 21 || P->g.w == 25;
 }
 
 // Gauss-Legendre quadrature of the kernel on [0, w/2] for its Fourier transform.
