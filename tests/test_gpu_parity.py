@@ -447,6 +447,20 @@ def test_fp64_double_float_gridding_extreme_magnitudes(P, n, m, type_, scale):
     assert O.rel_l2(got, ref) < TOL["f64"]
 
 
+@pytest.mark.parametrize("n", [512, 1024])
+@pytest.mark.parametrize("type_", [1, 2])
+def test_fp64_double_float_passes_mid_sizes(P, n, type_):
+    """FP64 mode at N' = 1024 and 2048, where the row passes run one row per
+    CTA and the column passes four columns per CTA in double-float: 600
+    points (type 1: sources; type 2: destinations of a random N x N plane)
+    against the oracle at rel-L2 1e-10."""
+    x, y, vals = random_case(70 + n + type_, n, 600, pitch=8e-6, type_=type_)
+    kw = dict(pitch=8e-6, lam=532e-9, z=0.04, ox=20e-6, oy=-8e-6)
+    got = run_gpu(P, "asm", type_, "f64", n, x=x, y=y, values=vals, **kw)
+    ref = run_oracle("asm", type_, n, x=x, y=y, values=vals, prec="f64", **kw)
+    assert O.rel_l2(got, ref) < TOL["f64"]
+
+
 def test_fp64_double_float_spreading_zero_and_non_finite(P):
     """The double-float FP64 spreading: an all-zero input gives zeros, and an
     infinity or a NaN among the values reaches the output."""
