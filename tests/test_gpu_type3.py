@@ -42,8 +42,10 @@ def run3(P, kind, prec, params, x1, y1, c, x2, y2, w=None):
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("kind", ["asm", "fresnel"])
-@pytest.mark.parametrize("n", [16, 64])
+@pytest.mark.parametrize("n", [16, 64, 256])
 def test_type3_random_points(P, prec, kind, n):
+    """Type 3 against the oracle; at N = 256 (N' = 512) the FP64 passes,
+    the type-3 row pass included, run in double-float arithmetic."""
     rng = np.random.default_rng(300 + n)
     pitch = 10e-6
     half = 0.5 * n * pitch
