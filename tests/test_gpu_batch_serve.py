@@ -70,6 +70,7 @@ PLANES = [  # kind, type, prec, n, m, z, lambda
     ("asm", 2, "f32", 128, 5000, 0.20, 532e-9),
     ("asm", 1, "f64", 64, 700, 0.04, 633e-9),
     ("asm", 2, "f32", 256, 20000, 0.35, 450e-9),
+    ("fresnel", 1, "f64", 256, 3000, 0.06, 532e-9),   # FP64 at N' = 512: double-float passes
 ]
 
 
@@ -110,7 +111,7 @@ def test_batch_matches_single_calls_and_the_oracle(P):
         for p in planes:
             got, ref = p["out"].cpu().numpy(), p["ref"].cpu().numpy()
             assert _same(got, ref, p["prec"], p["type"]), (p["kind"], p["type"], p["n"])
-        for p in planes[:4]:
+        for p in planes[:4] + planes[-1:]:   # the last: FP64 at N' = 512
             prm = dict(n=p["n"], pitch=8e-6, lam=p["lam"], z=p["z"], ox=p["ox"], kind=p["kind"])
             vals = p["inp"].cpu().numpy().astype(np.complex128)
             if p["type"] == 1:
@@ -193,7 +194,7 @@ def _requests(P):
     """Requests over three resident point sets (ids 11, 12, 13) and one FP64
     set (id 14), with wavelength, distance, offset, kind and type varying
     between requests on the same set, plus two unkept sets (id 0)."""
-    sets = {11: (64, 800), 12: (32, 300), 13: (128, 3000), 14: (64, 500), 0: (32, 150)}
+    sets = {11: (64, 800), 12: (32, 300), 13: (128, 3000), 14: (256, 500), 0: (32, 150)}
     pts = {k: _points(1000 + k, n, m, 8e-6) for k, (n, m) in sets.items()}
     reqs = []
     rng = np.random.default_rng(77)
