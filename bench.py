@@ -614,11 +614,15 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("df64" if info.get("double_float") or info["n_pad"] >= 512 else "f64") if f64 else prec,
+            "data": "synthetic",
             "config": {"workload": label, "n": wl.n, "n_pad": info["n_pad"], "points": wl.m,
                        "kernel": args.kernel, "tol": params.tol or (1e-12 if f64 else 1e-6),
                        "kernel_width": info["kernel_width"], "tile": info["tile"],
-                       "precision": "complex128" if f64 else "complex64 + FP64-derived phase",
+                       "precision": ("complex128 data; double-float (pairs of FP32) arithmetic in the gridding "
+                                     "and the FFT passes from N' = 512 up, FP64 elsewhere" if f64
+                                     else "complex64 + FP64-derived phase"),
                        "l2": "flushed (256 MB write) before every step", "plan_s": round(plan_s, 3),
                        "autotuned": tuned,
                        "parallelism": f"replicas x{ws}"},
