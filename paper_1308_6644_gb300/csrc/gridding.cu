@@ -1434,8 +1434,8 @@ template <bool SPREAD> cudaError_t gridding(const nuasm_plan_s* P, const void* i
         else return interp_impl<typename Tg::S, Tg::W, Tg::X>(P, out, st);
     };
     if (P->f64) {
-        // double-float gridding for the ES kernel at w = 13 (the FP64 default
-        // tolerance, 1e-12) and w = 11 (1e-10); spreading by whole tiles only
+        // double-float gridding at the kernel widths of the FP64 tolerances
+        // (gridding_double_float); split tiles too unless NUASM_DF_SPLIT is 0
         if (gridding_double_float(P)) {
             auto df_run = [&](auto wtag) -> cudaError_t {
                 constexpr int WD = decltype(wtag)::value;
